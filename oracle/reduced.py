@@ -1,0 +1,251 @@
+"""Reduced-order implicit Euler / quasi-static solve of Eq. 2 (Sec. 3.1) by
+projective Newton with backtracking line search (Supplement, "Tests with
+Projective Newton's method"; line-search cap of 128 and iteration cap of
+1024 from Sec. 5; ||g||_inf < eps exit from the Supplement's convergence
+discussion).
+
+    E(z) = 1/(2 dt^2) ||x(z) - qbar||_M^2 + sum_{e in S} w_e P_e(x(z))   (dynamics)
+    E(z) = sum_{e in S} w_e P_e(x(z)) - sum_v m_v g . x_v(z)             (quasi-static)
+
+The elastic sum runs over a cubature set S with weights w_e (Eq. 11); S = all
+tets with w = 1 is the exact potential.  x(z) = X0 + s f(z) with the
+constrained DOFs overwritten by their prescribed targets and their rows of
+J = dx/dz set to zero (reading: the paper names positional / moving
+constraints but gives no mechanism).  Gravity enters dynamics through the
+inertial guess qbar = q^k + dt v^k + dt^2 g (reading of Eq. 1's "inertial
+guess determined by previous configurations and the external force") and
+quasi-static solves as the potential -sum m_v g . x_v.
+
+Gradient:  g(z) = sum_e w_e J_e^T g_e + J^T M (x - qbar) / dt^2   (Eq. 11 form)
+Hessian:   K(z) = sum_e w_e J_e^T Hproj_e J_e + J^T M J / dt^2   (Gauss-Newton:
+           the term sum_k dE/dx_k d2x_k/dz2 is dropped; reading).
+Newton:    K d = -g by Cholesky; if K is not positive definite, retry with a
+           diagonal shift tau = 1e-12 * max(1, max|diag K|), multiplied by 10
+           per retry, 20 retries at most.
+Armijo:    alpha = 1, halve until E(z + alpha d) <= E(z) + c alpha g.d.
+
+Exit codes (shared meaning with the C ABI's status values):
+    0 converged (||g||_inf < eps), 1 iteration cap, 2 line search exhausted,
+    3 Hessian not positive definite after all shifts.
+
+Pins (tests/test_oracle_reduced.py): reduced gradient equals J^T times the
+assembled full gradient; K equals J^T Hproj_full J + J^T M J / dt^2;
+finite differences of E give g; a linear decoder reproduces an independently
+written linear-subspace Newton solve; a linear decoder with only the
+quadratic inertia term converges in one Newton step to the closed-form
+least-squares solution; rest state with no load has E = 0 and g = 0.
+"""
+from dataclasses import dataclass
+import numpy as np
+
+from . import fem, snh
+from .decoder import Decoder
+
+CONVERGED, MAX_ITERS, LS_FAILED, NOT_SPD = 0, 1, 2, 3
+
+
+class ReducedModel:
+    def __init__(self, X0, tets, decoder, youngs, poisson, rho, gravity,
+                 cub_idx=None, cub_w=None, cnodes=None, chunk=65536):
+        self.X0 = np.asarray(X0, dtype=np.float64)
+        self.tets_all = np.asarray(tets, dtype=np.int64)
+        self.nv = self.X0.shape[0]
+        self.n = 3 * self.nv
+        self.dec = decoder
+        self.mu, self.lam = snh.lame(youngs, poisson)
+        self.gravity = np.asarray(gravity, dtype=np.float64)
+        DmInv, vol = fem.rest_shape(self.X0, self.tets_all)
+        self.mass = fem.lumped_mass(self.nv, self.tets_all, vol, rho)
+        if cub_idx is None:
+            cub_idx = np.arange(self.tets_all.shape[0])
+            cub_w = np.ones(self.tets_all.shape[0])
+        self.cub_idx = np.asarray(cub_idx, dtype=np.int64)
+        self.w = np.asarray(cub_w, dtype=np.float64)
+        self.tets = self.tets_all[self.cub_idx]
+        self.DmInv = DmInv[self.cub_idx]
+        self.vol = vol[self.cub_idx]
+        self.cnodes = (np.zeros(0, dtype=np.int64) if cnodes is None
+                       else np.asarray(cnodes, dtype=np.int64))
+        self.cdofs = (3 * self.cnodes[:, None] + np.arange(3)).ravel()
+        self.targets = self.X0[self.cnodes].copy()
+        self.dt = 0.0
+        self.qbar = None
+        self.chunk = chunk
+
+    # -- problem data ----------------------------------------------------
+    def set_targets(self, targets):
+        self.targets = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
+
+    def set_dynamics(self, dt, qbar):
+        self.dt = float(dt)
+        self.qbar = None if qbar is None else np.asarray(qbar, np.float64).ravel()
+
+    # -- subspace map with constraints ------------------------------------
+    def positions(self, z):
+        x = self.X0.ravel() + self.dec.out(z)
+        x[self.cdofs] = self.targets.ravel()
+        return x
+
+    def positions_jac(self, z):
+        o, J = self.dec.out_jac(z)
+        x = self.X0.ravel() + o
+        x[self.cdofs] = self.targets.ravel()
+        J[self.cdofs, :] = 0.0
+        return x, J
+
+    # -- objective -------------------------------------------------------
+    def _mass_dof(self):
+        return np.repeat(self.mass, 3)
+
+    def energy_x(self, x):
+        Pe = fem.element_energy(x.reshape(-1, 3), self.tets, self.DmInv,
+                                self.vol, self.mu, self.lam)
+        E = float(np.sum(self.w * Pe))
+        m = self._mass_dof()
+        if self.dt > 0.0:
+            d = x - self.qbar
+            E += 0.5 / self.dt ** 2 * float(np.sum(m * d * d))
+        else:
+            E -= float(np.sum(self.mass[:, None] * self.gravity[None, :]
+                              * x.reshape(-1, 3)))
+        return E
+
+    def energy(self, z):
+        return self.energy_x(self.positions(z))
+
+    def full_gradient_x(self, x):
+        """dE/dx as an assembled n-vector (used by pins and the full space)."""
+        ge = fem.element_gradient(x.reshape(-1, 3), self.tets, self.DmInv,
+                                  self.vol, self.mu, self.lam)
+        g = fem.assemble_gradient(ge, self.tets, self.n, self.w)
+        m = self._mass_dof()
+        if self.dt > 0.0:
+            g += m * (x - self.qbar) / self.dt ** 2
+        else:
+            g -= (self.mass[:, None] * self.gravity[None, :]).ravel()
+        return g
+
+    def eval(self, z):
+        """E, reduced gradient g (r), Gauss-Newton reduced Hessian K (r, r)."""
+        x, J = self.positions_jac(z)
+        r = J.shape[1]
+        E = self.energy_x(x)
+        g = np.zeros(r)
+        K = np.zeros((r, r))
+        xv = x.reshape(-1, 3)
+        for s in range(0, self.tets.shape[0], self.chunk):
+            sl = slice(s, s + self.chunk)
+            tets = self.tets[sl]
+            ge = fem.element_gradient(xv, tets, self.DmInv[sl], self.vol[sl],
+                                      self.mu, self.lam)
+            He = fem.element_hessian(xv, tets, self.DmInv[sl], self.vol[sl],
+                                     self.mu, self.lam, project=True)
+            Je = J[fem.element_dofs(tets)]                 # (c, 12, r)
+            w = self.w[sl]
+            g += np.einsum("e,eki,ek->i", w, Je, ge)
+            HJ = He @ Je                                   # H_e J_e
+            WJ = w[:, None, None] * Je
+            K += WJ.reshape(-1, r).T @ HJ.reshape(-1, r)   # sum_e w_e J_e^T H_e J_e
+        m = self._mass_dof()
+        if self.dt > 0.0:
+            g += J.T @ (m * (x - self.qbar)) / self.dt ** 2
+            K += (J.T * m) @ J / self.dt ** 2
+        else:
+            g -= J.T @ (self.mass[:, None] * self.gravity[None, :]).ravel()
+        return E, g, 0.5 * (K + K.T)
+
+
+@dataclass
+class SolveStats:
+    status: int
+    newton_iters: int
+    ls_trials: int
+    grad_inf: float
+    energy: float
+
+
+def cholesky_direction(K, g):
+    """Solve K d = -g by Cholesky with the diagonal-shift retry schedule."""
+    shift = 0.0
+    base = 1e-12 * max(1.0, float(np.max(np.abs(np.diag(K)))))
+    for attempt in range(21):
+        try:
+            L = np.linalg.cholesky(K + shift * np.eye(K.shape[0]))
+            y = np.linalg.solve(L, -g)
+            return np.linalg.solve(L.T, y), True
+        except np.linalg.LinAlgError:
+            shift = base if shift == 0.0 else shift * 10.0
+    return None, False
+
+
+def newton_solve(model, z0, eps, max_newton=1024, max_ls=128, c=1e-4,
+                 trace=None):
+    z = np.asarray(z0, dtype=np.float64).copy()
+    status, ls_total, it = MAX_ITERS, 0, 0
+    E = gi = None
+    for it in range(max_newton + 1):
+        E, g, K = model.eval(z)
+        gi = float(np.max(np.abs(g)))
+        if trace is not None:
+            trace.append((E, gi))
+        if gi < eps:
+            status = CONVERGED
+            break
+        if it == max_newton:
+            break
+        d, ok = cholesky_direction(K, g)
+        if not ok:
+            status = NOT_SPD
+            break
+        gd = float(g @ d)
+        alpha, accepted = 1.0, False
+        for _ in range(max_ls):
+            ls_total += 1
+            if model.energy(z + alpha * d) <= E + c * alpha * gd:
+                accepted = True
+                break
+            alpha *= 0.5
+        if not accepted:
+            status = LS_FAILED
+            break
+        z = z + alpha * d
+    return z, SolveStats(status, it, ls_total, gi, E)
+
+
+class ReducedSimulator:
+    """Implicit Euler stepping (Eq. 2) or a quasi-static solve (dt = 0)."""
+
+    def __init__(self, model, dt, z0=None, eps=1e-5, max_newton=1024,
+                 max_ls=128, c=1e-4):
+        self.m = model
+        self.dt = float(dt)
+        r = model.dec.r
+        self.z = np.zeros(r) if z0 is None else np.asarray(z0, np.float64)
+        self.q = model.positions(self.z)
+        self.v = np.zeros_like(self.q)
+        self.eps, self.max_newton, self.max_ls, self.c = eps, max_newton, max_ls, c
+
+    def step(self, targets):
+        m = self.m
+        m.set_targets(targets)
+        if self.dt > 0.0:
+            g = np.tile(m.gravity, m.nv)
+            m.set_dynamics(self.dt, self.q + self.dt * self.v + self.dt ** 2 * g)
+        else:
+            m.set_dynamics(0.0, None)
+        z, st = newton_solve(m, self.z, self.eps, self.max_newton, self.max_ls,
+                             self.c)
+        self.z = z
+        qn = m.positions(z)
+        if self.dt > 0.0:
+            self.v = (qn - self.q) / self.dt
+        self.q = qn
+        return st
+
+
+def model_from_problem(p, chunk=65536):
+    """Oracle model for a ``workloads.Problem``."""
+    c = p.config
+    dec = Decoder(p.Ws, p.bs, c.out_scale)
+    return ReducedModel(p.X0, p.tets, dec, c.youngs, c.poisson, c.density,
+                        c.gravity, p.cub_idx, p.cub_w, p.cnodes, chunk=chunk)

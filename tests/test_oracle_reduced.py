@@ -1,0 +1,144 @@
+"""Pins of the oracle's reduced objective (Eq. 2), its Eq. 11-form gradient,
+the Gauss-Newton reduced Hessian and the Newton / Armijo solve."""
+import numpy as np
+import pytest
+
+from oracle import fem
+from oracle.decoder import Decoder
+from oracle.fullspace import FullModel
+from oracle.reduced import (ReducedModel, ReducedSimulator, newton_solve,
+                            cholesky_direction, model_from_problem, CONVERGED)
+from workloads import build_problem, make_bar, face_nodes, xavier_decoder
+
+G = (0.0, 0.0, -9.8)
+
+
+def tiny_model(dyn, seed=0, cub=False, gravity=G):
+    mesh = make_bar(6, 3, 3, 0.05)
+    n = 3 * mesh.nv
+    Ws, bs = xavier_decoder([4, 16, 16, n], seed)
+    dec = Decoder(Ws, bs, 1e-2)
+    idx = w = None
+    if cub:
+        rng = np.random.default_rng(7)
+        idx = np.sort(rng.choice(mesh.ne, 20, replace=False))
+        w = rng.uniform(0.5, 3.0, 20)
+    m = ReducedModel(mesh.X0, mesh.tets, dec, 1e5, 0.45, 1000.0, gravity,
+                     idx, w, face_nodes(mesh, 0))
+    if dyn:
+        rng = np.random.default_rng(8)
+        m.set_dynamics(1 / 60, mesh.X0.ravel() + 1e-3 * rng.standard_normal(n))
+    return m
+
+
+@pytest.mark.parametrize("dyn,cub", [(False, False), (True, False), (True, True)])
+def test_reduced_gradient_is_J_transpose_full_gradient(dyn, cub):
+    m = tiny_model(dyn, cub=cub)
+    z = np.random.default_rng(1).standard_normal(4) * 0.5
+    E, g, K = m.eval(z)
+    x, J = m.positions_jac(z)
+    assert np.allclose(g, J.T @ m.full_gradient_x(x), rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("dyn,cub", [(False, False), (True, True)])
+def test_reduced_hessian_is_J_transpose_assembled_J(dyn, cub):
+    m = tiny_model(dyn, cub=cub)
+    z = np.random.default_rng(2).standard_normal(4) * 0.5
+    _, _, K = m.eval(z)
+    x, J = m.positions_jac(z)
+    He = fem.element_hessian(x.reshape(-1, 3), m.tets, m.DmInv, m.vol, m.mu, m.lam)
+    H = fem.assemble_hessian(He, m.tets, m.n, m.w).toarray()
+    if dyn:
+        H += np.diag(np.repeat(m.mass, 3)) / m.dt ** 2
+    assert np.allclose(K, J.T @ H @ J, rtol=1e-10, atol=1e-8)
+
+
+@pytest.mark.parametrize("dyn", [False, True])
+def test_gradient_matches_central_differences_of_energy(dyn):
+    m = tiny_model(dyn)
+    z = np.random.default_rng(3).standard_normal(4) * 0.5
+    _, g, _ = m.eval(z)
+    h = 1e-6
+    for k in range(4):
+        e = np.zeros(4)
+        e[k] = h
+        fd = (m.energy(z + e) - m.energy(z - e)) / (2 * h)
+        assert fd == pytest.approx(g[k], rel=1e-6, abs=1e-8)
+
+
+def test_rest_state_without_load_is_stationary():
+    m = tiny_model(False, gravity=(0.0, 0.0, 0.0))
+    E, g, _ = m.eval(np.zeros(4))
+    assert abs(E) < 1e-10 and np.max(np.abs(g)) < 1e-10
+    z, st = newton_solve(m, np.zeros(4), 1e-10)
+    assert st.status == CONVERGED and st.newton_iters == 0
+
+
+def test_linear_decoder_matches_independent_linear_subspace_newton():
+    """x = X0 + U z: the reduced solve equals a Newton solve written here from
+    the assembled full-space gradient and Hessian projected onto U."""
+    mesh = make_bar(6, 3, 3, 0.05)
+    n = 3 * mesh.nv
+    rng = np.random.default_rng(4)
+    U = 1e-2 * rng.standard_normal((n, 5))
+    cn = face_nodes(mesh, 0)
+    cd = (3 * cn[:, None] + np.arange(3)).ravel()
+    m = ReducedModel(mesh.X0, mesh.tets, Decoder([U], [np.zeros(n)], 1.0),
+                     1e5, 0.45, 1000.0, G, None, None, cn)
+    z_red, st = newton_solve(m, np.zeros(5), 1e-10)
+    assert st.status == CONVERGED
+    fm = FullModel(mesh.X0, mesh.tets, 1e5, 0.45, 1000.0, G, cn)
+    Uc = U.copy()
+    Uc[cd] = 0.0
+    z = np.zeros(5)
+    for _ in range(50):
+        q = mesh.X0.ravel() + Uc @ z
+        g = Uc.T @ fm.gradient(q)
+        if np.max(np.abs(g)) < 1e-10:
+            break
+        K = Uc.T @ (fm.hessian(q) @ Uc)
+        d = -np.linalg.solve(K, g)
+        a = 1.0
+        while fm.energy(mesh.X0.ravel() + Uc @ (z + a * d)) > fm.energy(q) + 1e-4 * a * (g @ d):
+            a *= 0.5
+        z = z + a * d
+    assert np.allclose(z_red, z, rtol=1e-8, atol=1e-10)
+
+
+def test_linear_decoder_with_quadratic_energy_converges_in_one_step():
+    """Only the inertia term (all cubature weights zero): E is quadratic in z,
+    Newton lands on the weighted least-squares solution in one step."""
+    mesh = make_bar(5, 3, 3, 0.05)
+    n = 3 * mesh.nv
+    rng = np.random.default_rng(5)
+    U = rng.standard_normal((n, 6))
+    b = rng.standard_normal(n)
+    m = ReducedModel(mesh.X0, mesh.tets, Decoder([U], [b], 1e-2), 1e5, 0.45,
+                     1000.0, G, np.arange(mesh.ne), np.zeros(mesh.ne), None)
+    qbar = mesh.X0.ravel() + 0.01 * rng.standard_normal(n)
+    m.set_dynamics(0.01, qbar)
+    z, st = newton_solve(m, np.zeros(6), 1e-9)
+    assert st.status == CONVERGED and st.newton_iters == 1
+    W = np.repeat(m.mass, 3)
+    A = 1e-2 * U
+    rhs = qbar - mesh.X0.ravel() - 1e-2 * b
+    z_ls = np.linalg.solve(A.T @ (W[:, None] * A), A.T @ (W * rhs))
+    assert np.allclose(z, z_ls, rtol=1e-9, atol=1e-12)
+
+
+def test_cholesky_shift_gives_descent_direction():
+    K = np.diag([1.0, 2.0, -1e-3])
+    g = np.array([1.0, -1.0, 0.5])
+    d, ok = cholesky_direction(K, g)
+    assert ok and g @ d < 0
+
+
+def test_quasistatic_bar_solve_converges():
+    p = build_problem("tiny_quasistatic")
+    m = model_from_problem(p)
+    sim = ReducedSimulator(m, 0.0, eps=p.config.eps)
+    st = sim.step(p.targets(1))
+    assert st.status == CONVERGED
+    assert np.max(np.abs(m.eval(sim.z)[1])) < p.config.eps
+    # gravity pulls the free end down
+    assert (sim.q.reshape(-1, 3)[:, 2] - p.X0[:, 2]).mean() < 0
