@@ -1,0 +1,175 @@
+/*
+ * lsn.h - C ABI of the GB300 (sm_103a) neural-subspace reduced-order solver.
+ *
+ * The library solves, on one GPU, the reduced implicit-Euler problem of
+ * Eq. 2 (Sec. 3.1):
+ *
+ *   z^{k+1} = argmin_z E(z),
+ *   E(z)    = 1/(2 dt^2) ||x(z) - qbar||_M^2 + sum_{e in S} w_e P_e(x(z))
+ *
+ * (quasi-static when dt = 0: the inertia term is dropped and gravity acts as
+ * the potential -sum_v m_v g . x_v), where x(z) = X0 + s f_theta(z) is an MLP
+ * decoder (the neural subspace map of Sec. 3.1), P_e the Stable Neo-Hookean
+ * energy of tet e (Sec. 5.1) and S a cubature set with weights w_e (Eq. 11;
+ * S = all tets, w = 1 by default).  Each Newton iteration of the projective
+ * Newton solver (Supplement, "Tests with Projective Newton's method") runs
+ * hand-written CUDA kernels: decoder + forward-mode Jacobian J = dx/dz, a
+ * per-tet energy / gradient / PSD-projected Hessian kernel fused with the
+ * J_e^T H_e J_e contraction, an FP64 r x r Cholesky, and an Armijo
+ * backtracking line search whose energy comparison is done in FP64.
+ *
+ * Conventions
+ * -----------
+ *  - Every call returns an int status.  Negative values are errors and leave
+ *    the context unchanged (except that the stream may hold finished work);
+ *    positive values from lsn_step mean the solve ended without meeting the
+ *    tolerance but produced a usable result.  lsn_last_error() describes the
+ *    last error.  No exception crosses the ABI.
+ *  - The library owns the context, its device buffers and the simulation
+ *    state (q, v, z).  The caller owns every array it passes; the library
+ *    copies what it keeps.
+ *  - Pointers marked "host or device" may point to host memory (pageable or
+ *    pinned) or to device memory of the context's GPU; the library detects
+ *    which.  All other pointers are host pointers.
+ *  - All work is issued on the context's CUDA stream (given at creation; NULL
+ *    means the default stream).  Calls that return data synchronise that
+ *    stream before returning.
+ *  - Vertex data is xyz-interleaved: entry 3*v + c.  Matrices are row-major.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef LSN_H
+#define LSN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsn_ctx lsn_ctx; /* opaque, owned by the library */
+
+enum lsn_status {
+  LSN_OK = 0,              /* solve converged: ||g||_inf < tol                */
+  LSN_NOT_CONVERGED = 1,   /* Newton iteration cap reached                     */
+  LSN_LS_FAILED = 2,       /* line search found no Armijo step in max_ls trials */
+  LSN_NOT_SPD = 3,         /* reduced Hessian not positive definite after the
+                              diagonal-shift retries                          */
+  LSN_PRECISION_FLOOR = 4, /* line search stalled at the rounding level of the
+                              chosen precision while ||g||_inf < 100 tol       */
+  LSN_ERR_ARG = -1,        /* invalid argument or size                         */
+  LSN_ERR_CUDA = -2,       /* CUDA runtime error                               */
+  LSN_ERR_NONFINITE = -3,  /* NaN / Inf in inputs or in the reduced system     */
+  LSN_ERR_STATE = -4,      /* call out of order (e.g. step before set_mesh)    */
+  LSN_ERR_OOM = -5         /* device allocation failed                         */
+};
+
+/* Arithmetic of the decoder, Jacobian and J_e^T H_e J_e contraction.  The
+ * r x r Cholesky and the line-search energy comparison are FP64 in every
+ * mode; energies, gradients and partial sums are accumulated in FP64. */
+enum lsn_precision {
+  LSN_PREC_FP64 = 0, /* everything in FP64                                 */
+  LSN_PREC_FP32 = 1, /* plain FP32 on CUDA cores                           */
+  LSN_PREC_TF32 = 2, /* decoder last layer + contraction on tensor cores,
+                        TF32 inputs, FP32 accumulation; rest FP32            */
+  LSN_PREC_BF16 = 3  /* as TF32 with BF16 inputs                           */
+};
+
+typedef struct {
+  int newton_iters; /* Newton updates taken                                */
+  int ls_trials;    /* energy evaluations in the line searches             */
+  int exit;         /* lsn_status of the solve (>= 0)                      */
+  double grad_inf;  /* ||g||_inf at exit                                   */
+  double energy;    /* E(z) at exit                                        */
+  double ms;        /* wall time of the call (host clock)                  */
+} lsn_stats;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = default stream). */
+int lsn_create(lsn_ctx** out, int device, void* cuda_stream);
+void lsn_destroy(lsn_ctx* ctx);
+const char* lsn_last_error(const lsn_ctx* ctx);
+
+/* Tet mesh (Sec. 3.1: the DOF vector q in R^n, n = 3 nv, holds vertex
+ * positions).  X0: nv x 3 rest positions; tets: ne x 4 vertex indices, each
+ * tet with positive rest orientation det[X1-X0, X2-X0, X3-X0] > 0 (rejected
+ * with LSN_ERR_ARG otherwise).  Rest-shape inverses, volumes and the lumped
+ * mass (m_v = sum rho V_e / 4) are computed on the GPU.  Resets cubature to
+ * all tets and clears constraints. */
+int lsn_set_mesh(lsn_ctx* ctx, const double* X0, int nv, const int32_t* tets,
+                 int ne);
+
+/* Stable Neo-Hookean material (Sec. 5.1): Lame parameters from Young's
+ * modulus and Poisson ratio, density rho, gravity vector g (3 doubles).
+ * Must follow lsn_set_mesh (the lumped mass depends on both). */
+int lsn_set_material(lsn_ctx* ctx, double youngs, double poisson,
+                     double density, const double* gravity);
+
+/* Positional constraints (Sec. 5.1 "positional / moving constraints"): the
+ * nc vertices vidx are held at targets (nc x 3, host or device).  Their rows
+ * of x are overwritten by the targets and their rows of J are zero.  Calling
+ * again with the same vidx and new targets is the per-frame update; vidx ==
+ * NULL keeps the current vertex set and only uploads targets. */
+int lsn_set_constraints(lsn_ctx* ctx, const int32_t* vidx, int nc,
+                        const double* targets);
+
+/* Cubature set S with non-negative weights (Eq. 11).  s == 0 selects every
+ * tet with weight 1. */
+int lsn_set_cubature(lsn_ctx* ctx, const int32_t* tet_idx, const double* w,
+                     int s);
+
+/* Ground plane z = height with penalty energy k/2 sum_v min(0, x_v,z - h)^2
+ * (the energy-based contact of Sec. 5.2, as a plane).  stiffness 0 = off. */
+int lsn_set_ground(lsn_ctx* ctx, double height, double stiffness);
+
+/* MLP decoder (Sec. 3.1): widths[0] = r, widths[nlayers] = n; W[l] is
+ * widths[l+1] x widths[l] row-major, b[l] has widths[l+1] entries (host
+ * pointers).  Hidden layers use ELU; the last layer is linear; positions are
+ * x = X0 + out_scale * out.  1 <= r <= 64.  `precision` is an lsn_precision. */
+int lsn_set_decoder(lsn_ctx* ctx, int nlayers, const int* widths,
+                    const float* const* W, const float* const* b,
+                    double out_scale, int precision);
+
+/* Newton controls: exit when ||g||_inf < tol_inf (Supplement, convergence
+ * condition), at most max_newton iterations (Sec. 5: 1024) and max_ls line
+ * search trials per iteration (Sec. 5: 128), Armijo constant armijo_c. */
+int lsn_set_solver(lsn_ctx* ctx, double tol_inf, int max_newton, int max_ls,
+                   double armijo_c);
+
+/* Simulation state.  z (r, host or device) is the subspace coordinate;
+ * q, v (n, host or device) the full-space positions and velocities used by
+ * the inertial guess.  q == NULL sets q = x(z); v == NULL sets v = 0. */
+int lsn_set_state(lsn_ctx* ctx, const double* z, const double* q,
+                  const double* v);
+
+/* One time step: with dt > 0 an implicit-Euler step (Eq. 2) with inertial
+ * guess qbar = q + dt v + dt^2 g; with dt == 0 a quasi-static solve.  Starts
+ * Newton at z_in (r, host or device; NULL = current z), writes the solution
+ * to z_out (r, host or device; may be NULL), then updates q = x(z*),
+ * v = (x(z*) - q_old) / dt.  Returns the exit status (>= 0) or an error. */
+int lsn_step(lsn_ctx* ctx, const double* z_in, double dt, double* z_out,
+             lsn_stats* stats);
+
+/* Copy the current positions q (n doubles) to x_out (host or device). */
+int lsn_get_positions(lsn_ctx* ctx, double* x_out);
+
+/* Parity hook: evaluate at z (r, host or device; becomes the current z) the
+ * reduced energy E, the
+ * reduced gradient g (r) and the Gauss-Newton reduced Hessian K (r x r,
+ * row-major) for the current dynamics setting (dt, qbar from the last
+ * lsn_step or lsn_set_dynamics).  Outputs are host pointers; any may be NULL. */
+int lsn_eval(lsn_ctx* ctx, const double* z, double* E, double* g, double* K);
+
+/* Parity hook for the inertia term: sets dt and qbar (n, host or device)
+ * directly, as lsn_step would. dt == 0 selects the quasi-static objective. */
+int lsn_set_dynamics(lsn_ctx* ctx, double dt, const double* qbar);
+
+/* Parity hook for the decoder (z becomes the current z): x(z) (n doubles) and
+ * J(z) (n x r doubles,
+ * row-major), with constraints applied, copied to host pointers x_out and
+ * J_out (either may be NULL). */
+int lsn_decode(lsn_ctx* ctx, const double* z, double* x_out, double* J_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSN_H */

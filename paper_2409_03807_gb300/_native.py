@@ -1,0 +1,225 @@
+"""ctypes binding of liblsn (include/lsn.h).
+
+Argument marshalling only: every function here converts Python / numpy /
+torch arguments into the plain pointers and sizes of the C ABI and calls the
+function of the same name.  Device tensors are passed by their data pointer;
+numpy arrays by their host pointer.  The library must be built first
+(``paper_2409_03807_gb300.build.build()``); loading fails loudly otherwise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblsn.so")
+
+LSN_OK, LSN_NOT_CONVERGED, LSN_LS_FAILED, LSN_NOT_SPD, LSN_PRECISION_FLOOR = 0, 1, 2, 3, 4
+LSN_ERR_ARG, LSN_ERR_CUDA, LSN_ERR_NONFINITE, LSN_ERR_STATE, LSN_ERR_OOM = -1, -2, -3, -4, -5
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+
+
+class LsnStats(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("ls_trials", ctypes.c_int),
+                ("exit", ctypes.c_int), ("grad_inf", ctypes.c_double),
+                ("energy", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LsnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"liblsn error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+_SIGS = {
+    "lsn_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p],
+    "lsn_destroy": [ctypes.c_void_p],
+    "lsn_last_error": [ctypes.c_void_p],
+    "lsn_set_mesh": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int],
+    "lsn_set_material": [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                         ctypes.c_void_p],
+    "lsn_set_constraints": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "lsn_set_cubature": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
+    "lsn_set_ground": [ctypes.c_void_p, ctypes.c_double, ctypes.c_double],
+    "lsn_set_decoder": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                        ctypes.c_void_p, ctypes.c_double, ctypes.c_int],
+    "lsn_set_solver": [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                       ctypes.c_double],
+    "lsn_set_state": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "lsn_set_dynamics": [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p],
+    "lsn_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                 ctypes.POINTER(LsnStats)],
+    "lsn_get_positions": [ctypes.c_void_p, ctypes.c_void_p],
+    "lsn_eval": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                 ctypes.c_void_p],
+    "lsn_decode": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+}
+
+
+def load(path=None):
+    """Load liblsn.so and declare the C signatures (raises if missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"liblsn.so not built ({path}); run "
+                          "paper_2409_03807_gb300.build.build() on a machine with nvcc")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.lsn_destroy.restype = None
+    lib.lsn_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(a):
+    """Pointer of a numpy array, a torch tensor (host or device) or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _f64(a):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class Context:
+    """One liblsn context; methods are the C ABI calls without the prefix."""
+
+    def __init__(self, device=0, stream=None):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        rc = self.lib.lsn_create(ctypes.byref(h), int(device), st)
+        if rc != 0:
+            raise LsnError(rc, "lsn_create failed")
+        self.h = h
+        self.r = None
+        self.n = None
+
+    def close(self):
+        if self.h:
+            self.lib.lsn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self):
+        return self.lib.lsn_last_error(self.h).decode()
+
+    def _check(self, rc, allow_positive=False):
+        if rc < 0 or (rc > 0 and not allow_positive):
+            raise LsnError(rc, self.last_error())
+        return rc
+
+    def set_mesh(self, X0, tets):
+        X0 = _f64(X0)
+        tets = _i32(tets)
+        self.keep = (X0, tets)
+        self.n = 3 * X0.shape[0]
+        return self._check(self.lib.lsn_set_mesh(self.h, _ptr(X0), X0.shape[0], _ptr(tets),
+                                                 tets.shape[0]))
+
+    def set_material(self, youngs, poisson, density, gravity):
+        g = _f64(gravity)
+        return self._check(self.lib.lsn_set_material(self.h, youngs, poisson, density, _ptr(g)))
+
+    def set_constraints(self, vidx, targets):
+        vidx = _i32(vidx)
+        targets = _f64(targets)
+        nc = 0 if vidx is None else int(vidx.shape[0])
+        if vidx is None:
+            nc = int(targets.shape[0]) if targets is not None else 0
+        return self._check(self.lib.lsn_set_constraints(self.h, _ptr(vidx), nc, _ptr(targets)))
+
+    def set_cubature(self, idx, w):
+        idx = _i32(idx)
+        w = _f64(w)
+        s = 0 if idx is None else int(idx.shape[0])
+        return self._check(self.lib.lsn_set_cubature(self.h, _ptr(idx), _ptr(w), s))
+
+    def set_ground(self, height, stiffness):
+        return self._check(self.lib.lsn_set_ground(self.h, height, stiffness))
+
+    def set_decoder(self, Ws, bs, out_scale, precision="fp32"):
+        Ws = [np.ascontiguousarray(W, dtype=np.float32) for W in Ws]
+        bs = [np.ascontiguousarray(b, dtype=np.float32) for b in bs]
+        widths = [Ws[0].shape[1]] + [W.shape[0] for W in Ws]
+        wa = (ctypes.c_int * len(widths))(*widths)
+        Wp = (ctypes.c_void_p * len(Ws))(*[W.ctypes.data for W in Ws])
+        bp = (ctypes.c_void_p * len(bs))(*[b.ctypes.data for b in bs])
+        self.r = widths[0]
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        return self._check(self.lib.lsn_set_decoder(self.h, len(Ws), wa, Wp, bp,
+                                                    float(out_scale), prec))
+
+    def set_solver(self, tol_inf, max_newton=1024, max_ls=128, armijo_c=1e-4):
+        return self._check(self.lib.lsn_set_solver(self.h, tol_inf, max_newton, max_ls,
+                                                   armijo_c))
+
+    def set_state(self, z=None, q=None, v=None):
+        z, q, v = _f64(z), _f64(q), _f64(v)
+        return self._check(self.lib.lsn_set_state(self.h, _ptr(z), _ptr(q), _ptr(v)))
+
+    def set_dynamics(self, dt, qbar=None):
+        qbar = _f64(qbar)
+        return self._check(self.lib.lsn_set_dynamics(self.h, dt, _ptr(qbar)))
+
+    def step(self, z_in=None, dt=0.0, z_out=None):
+        """Returns (exit status, stats dict, z_out)."""
+        z_in = _f64(z_in)
+        if z_out is None:
+            z_out = np.zeros(self.r)
+        st = LsnStats()
+        rc = self.lib.lsn_step(self.h, _ptr(z_in), float(dt), _ptr(z_out), ctypes.byref(st))
+        self._check(rc, allow_positive=True)
+        return rc, st.as_dict(), z_out
+
+    def get_positions(self, out=None):
+        if out is None:
+            out = np.zeros(self.n)
+        self._check(self.lib.lsn_get_positions(self.h, _ptr(out)))
+        return out
+
+    def eval(self, z):
+        z = _f64(z)
+        E = np.zeros(1)
+        g = np.zeros(self.r)
+        K = np.zeros((self.r, self.r))
+        self._check(self.lib.lsn_eval(self.h, _ptr(z), _ptr(E), _ptr(g), _ptr(K)))
+        return float(E[0]), g, K
+
+    def decode(self, z, want_J=True):
+        z = _f64(z)
+        x = np.zeros(self.n)
+        J = np.zeros((self.n, self.r)) if want_J else None
+        self._check(self.lib.lsn_decode(self.h, _ptr(z), _ptr(x), _ptr(J)))
+        return x, J

@@ -1,0 +1,877 @@
+// C ABI of liblsn (declared in include/lsn.h): context, set-up calls, and the
+// host side of the Newton loop.  Every step of the computation runs in the
+// kernels of mesh.cu, decoder.cu, element.cu and solve.cu; this file only
+// owns buffers, uploads inputs and sequences launches on the context stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/lsn.h"
+#include "lsn_internal.cuh"
+
+using namespace lsn;
+
+namespace {
+
+struct CudaError {
+  cudaError_t e;
+};
+
+inline void ck(cudaError_t e) {
+  if (e != cudaSuccess) throw CudaError{e};
+}
+
+template <typename T>
+T* dalloc(size_t count) {
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw CudaError{e};
+  }
+  return static_cast<T*>(p);
+}
+
+inline void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// copy `bytes` from a host-or-device pointer into device memory
+void upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  ck(cudaMemcpyAsync(dst, src, bytes,
+                     is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+void download(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  ck(cudaMemcpyAsync(dst, src, bytes,
+                     is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+}
+
+struct EngineBase {
+  virtual ~EngineBase() {}
+  virtual void jac_pass() = 0;       // x, J, element, reduce, direction
+  virtual void trial_pass() = 0;     // k trial energies, reduce, Armijo select
+  virtual void finish(double dt) = 0;
+  virtual void decode_to_host(double* x, double* J) = 0;
+  DevSolver* sv = nullptr;
+  double* sys = nullptr;
+};
+
+}  // namespace
+
+struct lsn_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 1;
+  std::string err;
+  // mesh (FP64)
+  int nv = 0, n = 0, ne = 0;
+  double* X0 = nullptr;
+  int4* tets = nullptr;
+  double* dminv = nullptr;
+  double* vol = nullptr;
+  double* mass = nullptr;
+  int* adj_ptr = nullptr;
+  int* adj_tet = nullptr;
+  // material
+  bool have_material = false;
+  double youngs = 0, poisson = 0, rho = 0, grav[3] = {0, 0, 0};
+  // constraints
+  int nc = 0;
+  std::vector<int> cidx;
+  int* cslot = nullptr;   // nv
+  double* cu = nullptr;   // 3 nc target displacements
+  double* ctmp = nullptr; // 3 nc targets (positions) before X0 is subtracted
+  // cubature
+  int S = 0;
+  int* cub_idx = nullptr;
+  double* cub_w = nullptr;
+  // ground
+  double ground_h = 0.0, ground_k = 0.0;
+  // decoder (host copy)
+  bool have_decoder = false;
+  std::vector<int> widths;
+  std::vector<std::vector<float>> W, b;
+  double scale = 1.0;
+  int precision = LSN_PREC_FP32;
+  // solver controls
+  double tol = 1e-5, armijo_c = 1e-4;
+  int max_newton = 1024, max_ls = 128;
+  // state
+  double* q = nullptr;
+  double* v = nullptr;
+  double* ubar = nullptr;
+  double dt = 0.0;
+  bool q_valid = false;
+  std::vector<double> z0;   // host copy of the initial z (set_state)
+  bool z_pending = false;
+  // engine
+  std::unique_ptr<EngineBase> eng;
+  bool dirty = true;
+  int* pinned_status = nullptr;
+  double E_const = 0.0;  // -sum m g . X0 in quasi-static solves
+};
+
+namespace {
+
+// ----------------------------------------------------------------- engine
+template <typename Real>
+struct Engine : EngineBase {
+  lsn_ctx* c;
+  int r, L, n, S, C;
+  std::vector<Real*> dW, db;
+  Real *Z[2] = {nullptr, nullptr}, *Z0 = nullptr, *u = nullptr, *J = nullptr,
+       *ut = nullptr;
+  int4* ctets = nullptr;
+  Real *cdminv = nullptr, *cwv = nullptr;
+  double *part_dec = nullptr, *part_el = nullptr, *part_dec_t = nullptr,
+         *part_el_t = nullptr, *sys_t = nullptr;
+  int grid_dec, grid_el, grid_dec_t, grid_el_t, ns;
+  LastArgs la;
+  ElemArgs ea;
+
+  explicit Engine(lsn_ctx* ctx) : c(ctx) {
+    cudaStream_t s = c->stream;
+    r = c->widths[0];
+    L = (int)c->widths.size() - 1;
+    n = c->n;
+    S = c->S > 0 ? c->S : c->ne;
+    C = r + 1;
+    ns = nslots(r);
+    int hmax = r;
+    for (int w : c->widths) hmax = std::max(hmax, w);
+    for (int l = 0; l < L; ++l) {
+      size_t cnt = (size_t)c->widths[l + 1] * c->widths[l];
+      std::vector<Real> tmp(cnt);
+      for (size_t i = 0; i < cnt; ++i) tmp[i] = (Real)c->W[l][i];
+      dW.push_back(dalloc<Real>(cnt));
+      ck(cudaMemcpyAsync(dW.back(), tmp.data(), cnt * sizeof(Real), cudaMemcpyHostToDevice, s));
+      std::vector<Real> tb(c->widths[l + 1]);
+      for (int i = 0; i < c->widths[l + 1]; ++i) tb[i] = (Real)c->b[l][i];
+      db.push_back(dalloc<Real>(tb.size()));
+      ck(cudaMemcpyAsync(db.back(), tb.data(), tb.size() * sizeof(Real), cudaMemcpyHostToDevice,
+                         s));
+      ck(cudaStreamSynchronize(s));
+    }
+    const int cmax = std::max(C, KTRIAL);
+    Z[0] = dalloc<Real>((size_t)cmax * hmax);
+    Z[1] = dalloc<Real>((size_t)cmax * hmax);
+    Z0 = dalloc<Real>((size_t)cmax * r);
+    u = dalloc<Real>(n);
+    J = dalloc<Real>((size_t)n * r);
+    ut = dalloc<Real>((size_t)KTRIAL * n);
+    ctets = dalloc<int4>(S);
+    cdminv = dalloc<Real>((size_t)9 * S);
+    cwv = dalloc<Real>(S);
+    launch_gather_cubature<Real>(c->tets, c->dminv, c->vol, c->S > 0 ? c->cub_idx : nullptr,
+                                 c->S > 0 ? c->cub_w : nullptr, S, c->ne, ctets, cdminv, cwv,
+                                 s);
+    grid_dec = decoder_last_grid(n, C, c->num_sms);
+    grid_dec_t = decoder_last_grid(n, KTRIAL, c->num_sms);
+    grid_el = element_full_grid(S, c->num_sms);
+    grid_el_t = element_energy_grid(S, c->num_sms);
+    part_dec = dalloc<double>((size_t)grid_dec * ns);
+    part_el = dalloc<double>((size_t)grid_el * ns);
+    part_dec_t = dalloc<double>((size_t)grid_dec_t * 2 * KTRIAL);
+    part_el_t = dalloc<double>((size_t)grid_el_t * 2 * KTRIAL);
+    ck(cudaMemsetAsync(part_dec_t, 0, sizeof(double) * grid_dec_t * 2 * KTRIAL, s));
+    ck(cudaMemsetAsync(part_el_t, 0, sizeof(double) * grid_el_t * 2 * KTRIAL, s));
+    sys = dalloc<double>(ns);
+    sys_t = dalloc<double>(2 * KTRIAL);
+    sv = dalloc<DevSolver>(1);
+    ck(cudaMemsetAsync(sv, 0, sizeof(DevSolver), s));
+    la.n = n;
+    la.r = r;
+    la.scale = c->scale;
+    la.cslot = c->cslot;
+    la.cu = c->cu;
+    la.mass = c->mass;
+    la.ubar = c->ubar;
+    la.inv_dt2 = 0.0;
+    for (int i = 0; i < 3; ++i) la.grav[i] = c->grav[i];
+    la.ground_h = c->ground_h;
+    la.ground_k = c->ground_k;
+    la.X0 = c->X0;
+    ea.S = S;
+    ea.r = r;
+    ea.n = n;
+    ea.tets = ctets;
+    ea.dminv = cdminv;
+    ea.wv = cwv;
+    double mu = c->youngs / (2.0 * (1.0 + c->poisson));
+    double lam = c->youngs * c->poisson / ((1.0 + c->poisson) * (1.0 - 2.0 * c->poisson));
+    ea.mu = mu;
+    ea.lam = lam;
+    ck(cudaStreamSynchronize(s));
+    ck(cudaGetLastError());
+  }
+
+  ~Engine() override {
+    for (auto p : dW) dfree(p);
+    for (auto p : db) dfree(p);
+    dfree(Z[0]);
+    dfree(Z[1]);
+    dfree(Z0);
+    dfree(u);
+    dfree(J);
+    dfree(ut);
+    dfree(ctets);
+    dfree(cdminv);
+    dfree(cwv);
+    dfree(part_dec);
+    dfree(part_el);
+    dfree(part_dec_t);
+    dfree(part_el_t);
+    dfree(sys);
+    dfree(sys_t);
+    dfree(sv);
+  }
+
+  void set_dynamics(double dt) { la.inv_dt2 = dt > 0.0 ? 1.0 / (dt * dt) : 0.0; }
+
+  // Layers 1..L-1 for `cols` columns starting from Z0; returns the buffer
+  // holding the last hidden activations.
+  const Real* hidden(bool jac, int cols) {
+    cudaStream_t s = c->stream;
+    const Real* in = Z0;
+    int cur = 0;
+    for (int l = 0; l < L - 1; ++l) {
+      int M = c->widths[l + 1], K = c->widths[l];
+      launch_decoder_layer<Real>(jac ? Epi::HiddenJac : Epi::HiddenVal, dW[l], db[l], M, K,
+                                 in, cols, Z[cur], M, nullptr, nullptr, nullptr, 0, la, 0, s);
+      in = Z[cur];
+      cur ^= 1;
+    }
+    return in;
+  }
+
+  void jac_pass() override {
+    cudaStream_t s = c->stream;
+    launch_write_jac_columns<Real>(sv, Z0, s);
+    const Real* h = hidden(true, C);
+    launch_decoder_layer<Real>(Epi::LastJac, dW[L - 1], db[L - 1], n, c->widths[L - 1], h, C,
+                               nullptr, 0, u, J, part_dec, ns, la, grid_dec, s);
+    launch_element_full<Real>(ea, u, J, part_el, grid_el, s);
+    launch_reduce_cols(part_dec, grid_dec, part_el, grid_el, ns, sys, s);
+    launch_newton_direction<Real>(sv, sys, Z0, c->max_newton, s);
+  }
+
+  void trial_pass() override {
+    cudaStream_t s = c->stream;
+    const Real* h = hidden(false, KTRIAL);
+    launch_decoder_layer<Real>(Epi::LastVal, dW[L - 1], db[L - 1], n, c->widths[L - 1], h,
+                               KTRIAL, ut, n, nullptr, nullptr, part_dec_t, 2 * KTRIAL, la,
+                               grid_dec_t, s);
+    launch_element_energy<Real>(ea, ut, KTRIAL, part_el_t, grid_el_t, s);
+    launch_reduce_cols(part_dec_t, grid_dec_t, part_el_t, grid_el_t, 2 * KTRIAL, sys_t, s);
+    launch_ls_select<Real>(sv, sys_t, Z0, s);
+  }
+
+  void finish(double dt) override {
+    launch_finish_positions<Real>(c->X0, u, n, dt, c->q, c->v, c->stream);
+  }
+
+  void decode_to_host(double* x, double* Jh) override {
+    cudaStream_t s = c->stream;
+    launch_write_jac_columns<Real>(sv, Z0, s);
+    const Real* h = hidden(true, C);
+    launch_decoder_layer<Real>(Epi::LastJac, dW[L - 1], db[L - 1], n, c->widths[L - 1], h, C,
+                               nullptr, 0, u, J, part_dec, ns, la, grid_dec, s);
+    std::vector<Real> hu(n), hJ;
+    ck(cudaMemcpyAsync(hu.data(), u, n * sizeof(Real), cudaMemcpyDeviceToHost, s));
+    if (Jh) {
+      hJ.resize((size_t)n * r);
+      ck(cudaMemcpyAsync(hJ.data(), J, hJ.size() * sizeof(Real), cudaMemcpyDeviceToHost, s));
+    }
+    std::vector<double> X0h(n);
+    ck(cudaMemcpyAsync(X0h.data(), c->X0, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    if (x)
+      for (int i = 0; i < n; ++i) x[i] = X0h[i] + (double)hu[i];
+    if (Jh)
+      for (size_t i = 0; i < hJ.size(); ++i) Jh[i] = (double)hJ[i];
+  }
+};
+
+int fail(lsn_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(lsn_ctx* c, cudaError_t e) {
+  cudaGetLastError();
+  return fail(c, e == cudaErrorMemoryAllocation ? LSN_ERR_OOM : LSN_ERR_CUDA,
+              std::string("CUDA error: ") + cudaGetErrorString(e));
+}
+
+#define LSN_GUARD_BEGIN try {
+#define LSN_GUARD_END                                                   \
+  }                                                                     \
+  catch (const CudaError& ce) {                                         \
+    return cuda_fail(c, ce.e);                                          \
+  }                                                                     \
+  catch (const std::exception& ex) {                                    \
+    return fail(c, LSN_ERR_STATE, std::string("internal error: ") + ex.what()); \
+  }
+
+int ensure_engine(lsn_ctx* c) {
+  if (c->n == 0) return fail(c, LSN_ERR_STATE, "lsn_set_mesh has not been called");
+  if (!c->have_material) return fail(c, LSN_ERR_STATE, "lsn_set_material has not been called");
+  if (!c->have_decoder) return fail(c, LSN_ERR_STATE, "lsn_set_decoder has not been called");
+  if (!c->dirty && c->eng) return LSN_OK;
+  c->eng.reset();
+  if (c->precision == LSN_PREC_FP64)
+    c->eng.reset(new Engine<double>(c));
+  else
+    c->eng.reset(new Engine<float>(c));
+  c->dirty = false;
+  return LSN_OK;
+}
+
+void set_engine_dynamics(lsn_ctx* c, double dt) {
+  if (c->precision == LSN_PREC_FP64)
+    static_cast<Engine<double>*>(c->eng.get())->set_dynamics(dt);
+  else
+    static_cast<Engine<float>*>(c->eng.get())->set_dynamics(dt);
+}
+
+// device-side solver fields that a new solve or evaluation starts from
+void reset_solver(lsn_ctx* c, int eval_only) {
+  DevSolver h;
+  std::memset(&h, 0, sizeof(h));
+  // z is kept on the device; copy everything except z
+  ck(cudaMemcpyAsync(&h.z[0], &c->eng->sv->z[0], sizeof(h.z), cudaMemcpyDeviceToHost,
+                     c->stream));
+  ck(cudaStreamSynchronize(c->stream));
+  h.tol = c->tol;
+  h.armijo_c = c->armijo_c;
+  h.eta_scale = c->precision == LSN_PREC_FP64 ? 8.0 * 1.1102230246251565e-16
+                                              : 8.0 * 5.960464477539063e-08;
+  h.r = c->widths[0];
+  h.max_ls = c->max_ls;
+  h.status = -1;
+  h.eval_only = eval_only;
+  ck(cudaMemcpyAsync(c->eng->sv, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+  ck(cudaStreamSynchronize(c->stream));
+}
+
+double quasi_static_constant(lsn_ctx* c) {
+  // -sum_v m_v g . X0_v (the part of the gravity potential that does not
+  // depend on z); evaluated once per mesh/material on the host from device
+  // copies of the lumped mass and rest positions.
+  std::vector<double> m(c->nv), X(c->n);
+  ck(cudaMemcpyAsync(m.data(), c->mass, c->nv * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream));
+  ck(cudaMemcpyAsync(X.data(), c->X0, c->n * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream));
+  ck(cudaStreamSynchronize(c->stream));
+  double s = 0.0;
+  for (int v = 0; v < c->nv; ++v)
+    for (int k = 0; k < 3; ++k) s -= m[v] * c->grav[k] * X[3 * v + k];
+  return s;
+}
+
+int read_status(lsn_ctx* c) {
+  ck(cudaMemcpyAsync(c->pinned_status, &c->eng->sv->status, sizeof(int),
+                     cudaMemcpyDeviceToHost, c->stream));
+  ck(cudaStreamSynchronize(c->stream));
+  return *c->pinned_status;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+extern "C" {
+
+int lsn_create(lsn_ctx** out, int device, void* cuda_stream) {
+  if (!out) return LSN_ERR_ARG;
+  *out = nullptr;
+  lsn_ctx* c = new lsn_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->pinned_status, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return LSN_ERR_CUDA;
+  }
+  *out = c;
+  return LSN_OK;
+}
+
+static void free_mesh(lsn_ctx* c) {
+  dfree(c->X0);
+  dfree(c->tets);
+  dfree(c->dminv);
+  dfree(c->vol);
+  dfree(c->mass);
+  dfree(c->adj_ptr);
+  dfree(c->adj_tet);
+  dfree(c->cslot);
+  dfree(c->cu);
+  dfree(c->ctmp);
+  dfree(c->cub_idx);
+  dfree(c->cub_w);
+  dfree(c->q);
+  dfree(c->v);
+  dfree(c->ubar);
+  c->X0 = c->dminv = c->vol = c->mass = c->cu = c->ctmp = c->cub_w = c->q = c->v = c->ubar = nullptr;
+  c->tets = nullptr;
+  c->adj_ptr = c->adj_tet = c->cslot = c->cub_idx = nullptr;
+}
+
+void lsn_destroy(lsn_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  c->eng.reset();
+  free_mesh(c);
+  if (c->pinned_status) cudaFreeHost(c->pinned_status);
+  delete c;
+}
+
+const char* lsn_last_error(const lsn_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int lsn_set_mesh(lsn_ctx* c, const double* X0, int nv, const int32_t* tets, int ne) {
+  if (!c) return LSN_ERR_ARG;
+  if (!X0 || !tets || nv < 4 || ne < 1) return fail(c, LSN_ERR_ARG, "set_mesh: empty mesh");
+  for (long long i = 0; i < 4LL * ne; ++i)
+    if (tets[i] < 0 || tets[i] >= nv)
+      return fail(c, LSN_ERR_ARG, "set_mesh: tet vertex index out of range");
+  for (long long i = 0; i < 3LL * nv; ++i)
+    if (!std::isfinite(X0[i])) return fail(c, LSN_ERR_NONFINITE, "set_mesh: non-finite X0");
+  LSN_GUARD_BEGIN
+  ck(cudaSetDevice(c->device));
+  c->eng.reset();
+  free_mesh(c);
+  cudaStream_t s = c->stream;
+  c->nv = nv;
+  c->n = 3 * nv;
+  c->ne = ne;
+  c->X0 = dalloc<double>(c->n);
+  c->tets = dalloc<int4>(ne);
+  c->dminv = dalloc<double>((size_t)9 * ne);
+  c->vol = dalloc<double>(ne);
+  c->mass = dalloc<double>(nv);
+  c->q = dalloc<double>(c->n);
+  c->v = dalloc<double>(c->n);
+  c->ubar = dalloc<double>(c->n);
+  c->cslot = dalloc<int>(nv);
+  c->cu = dalloc<double>(3);
+  c->ctmp = dalloc<double>(3);
+  ck(cudaMemcpyAsync(c->X0, X0, sizeof(double) * c->n, cudaMemcpyHostToDevice, s));
+  ck(cudaMemcpyAsync(c->tets, tets, sizeof(int4) * ne, cudaMemcpyHostToDevice, s));
+  ck(cudaMemsetAsync(c->cslot, 0xff, sizeof(int) * nv, s));
+  ck(cudaMemcpyAsync(c->q, X0, sizeof(double) * c->n, cudaMemcpyHostToDevice, s));
+  ck(cudaMemsetAsync(c->v, 0, sizeof(double) * c->n, s));
+  ck(cudaMemsetAsync(c->ubar, 0, sizeof(double) * c->n, s));
+  // vertex -> incident tet lists (CSR) for the fixed-order lumped mass
+  std::vector<int> cnt(nv + 1, 0), adj(4LL * ne);
+  for (long long i = 0; i < 4LL * ne; ++i) cnt[tets[i] + 1]++;
+  for (int v = 0; v < nv; ++v) cnt[v + 1] += cnt[v];
+  std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+  for (int e = 0; e < ne; ++e)
+    for (int a = 0; a < 4; ++a) adj[fill[tets[4 * e + a]]++] = e;
+  c->adj_ptr = dalloc<int>(nv + 1);
+  c->adj_tet = dalloc<int>(adj.size());
+  ck(cudaMemcpyAsync(c->adj_ptr, cnt.data(), sizeof(int) * (nv + 1), cudaMemcpyHostToDevice, s));
+  ck(cudaMemcpyAsync(c->adj_tet, adj.data(), sizeof(int) * adj.size(), cudaMemcpyHostToDevice, s));
+  int* bad = dalloc<int>(1);
+  ck(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  launch_rest_shape(c->X0, c->tets, ne, c->dminv, c->vol, bad, s);
+  int hbad = 0;
+  ck(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ck(cudaStreamSynchronize(s));
+  dfree(bad);
+  ck(cudaGetLastError());
+  c->nc = 0;
+  c->cidx.clear();
+  c->S = 0;
+  c->q_valid = false;
+  c->dirty = true;
+  c->have_material = false;
+  if (hbad) {
+    free_mesh(c);
+    c->nv = c->n = c->ne = 0;
+    return fail(c, LSN_ERR_ARG, "set_mesh: a tet has non-positive rest volume");
+  }
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_set_material(lsn_ctx* c, double youngs, double poisson, double density,
+                     const double* gravity) {
+  if (!c) return LSN_ERR_ARG;
+  if (c->n == 0) return fail(c, LSN_ERR_STATE, "set_material: call lsn_set_mesh first");
+  if (!(youngs > 0) || !(poisson > -1.0 && poisson < 0.5) || !(density > 0) || !gravity)
+    return fail(c, LSN_ERR_ARG, "set_material: invalid material parameters");
+  LSN_GUARD_BEGIN
+  c->youngs = youngs;
+  c->poisson = poisson;
+  c->rho = density;
+  for (int k = 0; k < 3; ++k) c->grav[k] = gravity[k];
+  launch_lumped_mass(c->adj_ptr, c->adj_tet, c->vol, c->nv, density, c->mass, c->stream);
+  ck(cudaStreamSynchronize(c->stream));
+  ck(cudaGetLastError());
+  c->E_const = quasi_static_constant(c);
+  c->have_material = true;
+  c->dirty = true;
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_set_constraints(lsn_ctx* c, const int32_t* vidx, int nc, const double* targets) {
+  if (!c) return LSN_ERR_ARG;
+  if (c->n == 0) return fail(c, LSN_ERR_STATE, "set_constraints: call lsn_set_mesh first");
+  LSN_GUARD_BEGIN
+  cudaStream_t s = c->stream;
+  if (vidx) {
+    if (nc < 0 || nc > c->nv) return fail(c, LSN_ERR_ARG, "set_constraints: bad count");
+    std::vector<int> slot(c->nv, -1);
+    for (int i = 0; i < nc; ++i) {
+      if (vidx[i] < 0 || vidx[i] >= c->nv)
+        return fail(c, LSN_ERR_ARG, "set_constraints: vertex index out of range");
+      if (slot[vidx[i]] >= 0) return fail(c, LSN_ERR_ARG, "set_constraints: duplicate vertex");
+      slot[vidx[i]] = i;
+    }
+    if (nc != c->nc) {
+      dfree(c->cu);
+      dfree(c->ctmp);
+      c->cu = dalloc<double>(3 * std::max(nc, 1));
+      c->ctmp = dalloc<double>(3 * std::max(nc, 1));
+      c->dirty = true;  // engine holds the pointer
+    }
+    c->nc = nc;
+    c->cidx.assign(vidx, vidx + nc);
+    ck(cudaMemcpyAsync(c->cslot, slot.data(), sizeof(int) * c->nv, cudaMemcpyHostToDevice, s));
+    ck(cudaStreamSynchronize(s));
+  } else if (nc != c->nc) {
+    return fail(c, LSN_ERR_ARG, "set_constraints: count differs from the current set");
+  }
+  if (c->nc > 0) {
+    if (!targets) return fail(c, LSN_ERR_ARG, "set_constraints: targets missing");
+    upload(c->ctmp, targets, sizeof(double) * 3 * c->nc, s);
+    // displacement targets: target - X0 of each constrained vertex
+    std::vector<double> tg(3 * c->nc), X(3);
+    ck(cudaMemcpyAsync(tg.data(), c->ctmp, sizeof(double) * 3 * c->nc, cudaMemcpyDeviceToHost, s));
+    std::vector<double> X0h(c->n);
+    ck(cudaMemcpyAsync(X0h.data(), c->X0, sizeof(double) * c->n, cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    for (int i = 0; i < c->nc; ++i)
+      for (int k = 0; k < 3; ++k) {
+        if (!std::isfinite(tg[3 * i + k]))
+          return fail(c, LSN_ERR_NONFINITE, "set_constraints: non-finite target");
+        tg[3 * i + k] -= X0h[3 * c->cidx[i] + k];
+      }
+    ck(cudaMemcpyAsync(c->cu, tg.data(), sizeof(double) * 3 * c->nc, cudaMemcpyHostToDevice, s));
+    ck(cudaStreamSynchronize(s));
+  }
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_set_cubature(lsn_ctx* c, const int32_t* tet_idx, const double* w, int s_cnt) {
+  if (!c) return LSN_ERR_ARG;
+  if (c->n == 0) return fail(c, LSN_ERR_STATE, "set_cubature: call lsn_set_mesh first");
+  if (s_cnt < 0 || s_cnt > c->ne) return fail(c, LSN_ERR_ARG, "set_cubature: bad size");
+  LSN_GUARD_BEGIN
+  dfree(c->cub_idx);
+  dfree(c->cub_w);
+  c->cub_idx = nullptr;
+  c->cub_w = nullptr;
+  c->S = s_cnt;
+  if (s_cnt > 0) {
+    if (!tet_idx || !w) return fail(c, LSN_ERR_ARG, "set_cubature: null arrays");
+    for (int i = 0; i < s_cnt; ++i) {
+      if (tet_idx[i] < 0 || tet_idx[i] >= c->ne)
+        return fail(c, LSN_ERR_ARG, "set_cubature: tet index out of range");
+      if (!(w[i] >= 0.0) || !std::isfinite(w[i]))
+        return fail(c, LSN_ERR_ARG, "set_cubature: weights must be finite and >= 0");
+    }
+    c->cub_idx = dalloc<int>(s_cnt);
+    c->cub_w = dalloc<double>(s_cnt);
+    ck(cudaMemcpyAsync(c->cub_idx, tet_idx, sizeof(int) * s_cnt, cudaMemcpyHostToDevice,
+                       c->stream));
+    ck(cudaMemcpyAsync(c->cub_w, w, sizeof(double) * s_cnt, cudaMemcpyHostToDevice, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+  }
+  c->dirty = true;
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_set_ground(lsn_ctx* c, double height, double stiffness) {
+  if (!c) return LSN_ERR_ARG;
+  if (!(stiffness >= 0.0) || !std::isfinite(height))
+    return fail(c, LSN_ERR_ARG, "set_ground: invalid parameters");
+  c->ground_h = height;
+  c->ground_k = stiffness;
+  c->dirty = true;
+  return LSN_OK;
+}
+
+int lsn_set_decoder(lsn_ctx* c, int nlayers, const int* widths, const float* const* W,
+                    const float* const* b, double out_scale, int precision) {
+  if (!c) return LSN_ERR_ARG;
+  if (c->n == 0) return fail(c, LSN_ERR_STATE, "set_decoder: call lsn_set_mesh first");
+  if (nlayers < 1 || !widths || !W || !b) return fail(c, LSN_ERR_ARG, "set_decoder: bad layers");
+  if (widths[0] < 1 || widths[0] > RMAX)
+    return fail(c, LSN_ERR_ARG, "set_decoder: subspace dimension must be in [1, 64]");
+  if (widths[nlayers] != c->n)
+    return fail(c, LSN_ERR_ARG, "set_decoder: last width must equal 3 * nv");
+  if (precision < LSN_PREC_FP64 || precision > LSN_PREC_BF16)
+    return fail(c, LSN_ERR_ARG, "set_decoder: unknown precision");
+  if (!std::isfinite(out_scale)) return fail(c, LSN_ERR_ARG, "set_decoder: bad scale");
+  for (int l = 0; l <= nlayers; ++l)
+    if (widths[l] < 1) return fail(c, LSN_ERR_ARG, "set_decoder: zero width");
+  std::vector<std::vector<float>> Wc, bc;
+  for (int l = 0; l < nlayers; ++l) {
+    size_t cnt = (size_t)widths[l + 1] * widths[l];
+    if (!W[l] || !b[l]) return fail(c, LSN_ERR_ARG, "set_decoder: null layer");
+    Wc.emplace_back(W[l], W[l] + cnt);
+    bc.emplace_back(b[l], b[l] + widths[l + 1]);
+    for (float x : Wc.back())
+      if (!std::isfinite(x)) return fail(c, LSN_ERR_NONFINITE, "set_decoder: non-finite weight");
+    for (float x : bc.back())
+      if (!std::isfinite(x)) return fail(c, LSN_ERR_NONFINITE, "set_decoder: non-finite bias");
+  }
+  c->widths.assign(widths, widths + nlayers + 1);
+  c->W.swap(Wc);
+  c->b.swap(bc);
+  c->scale = out_scale;
+  c->precision = precision;
+  c->have_decoder = true;
+  c->dirty = true;
+  c->z0.assign(widths[0], 0.0);
+  c->z_pending = true;
+  return LSN_OK;
+}
+
+int lsn_set_solver(lsn_ctx* c, double tol_inf, int max_newton, int max_ls, double armijo_c) {
+  if (!c) return LSN_ERR_ARG;
+  if (!(tol_inf > 0) || max_newton < 0 || max_ls < 1 || !(armijo_c > 0 && armijo_c < 1))
+    return fail(c, LSN_ERR_ARG, "set_solver: invalid controls");
+  c->tol = tol_inf;
+  c->max_newton = max_newton;
+  c->max_ls = max_ls;
+  c->armijo_c = armijo_c;
+  return LSN_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// apply a pending z to the device solver state
+int sync_z(lsn_ctx* c) {
+  if (c->z_pending) {
+    ck(cudaMemcpyAsync(&c->eng->sv->z[0], c->z0.data(), sizeof(double) * c->z0.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    c->z_pending = false;
+  }
+  return LSN_OK;
+}
+int prepare(lsn_ctx* c) {
+  bool rebuilt = c->dirty || !c->eng;
+  int rc = ensure_engine(c);
+  if (rc != LSN_OK) return rc;
+  if (rebuilt) c->z_pending = true;  // new engine: z from the host copy
+  return sync_z(c);
+}
+}  // namespace
+
+extern "C" {
+
+int lsn_set_state(lsn_ctx* c, const double* z, const double* q, const double* v) {
+  if (!c) return LSN_ERR_ARG;
+  LSN_GUARD_BEGIN
+  int rc = prepare(c);
+  if (rc != LSN_OK) return rc;
+  const int r = c->widths[0];
+  cudaStream_t s = c->stream;
+  if (z) {
+    upload(&c->eng->sv->z[0], z, sizeof(double) * r, s);
+    ck(cudaMemcpyAsync(c->z0.data(), &c->eng->sv->z[0], sizeof(double) * r,
+                       cudaMemcpyDeviceToHost, s));
+  }
+  if (q) {
+    upload(c->q, q, sizeof(double) * c->n, s);
+  } else {
+    reset_solver(c, 1);
+    set_engine_dynamics(c, 0.0);
+    c->eng->jac_pass();
+    c->eng->finish(0.0);
+  }
+  if (v) upload(c->v, v, sizeof(double) * c->n, s);
+  else ck(cudaMemsetAsync(c->v, 0, sizeof(double) * c->n, s));
+  ck(cudaStreamSynchronize(s));
+  ck(cudaGetLastError());
+  c->q_valid = true;
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_set_dynamics(lsn_ctx* c, double dt, const double* qbar) {
+  if (!c) return LSN_ERR_ARG;
+  if (!(dt >= 0.0)) return fail(c, LSN_ERR_ARG, "set_dynamics: dt must be >= 0");
+  LSN_GUARD_BEGIN
+  int rc = prepare(c);
+  if (rc != LSN_OK) return rc;
+  c->dt = dt;
+  if (dt > 0.0) {
+    if (!qbar) return fail(c, LSN_ERR_ARG, "set_dynamics: qbar missing");
+    // ubar = qbar - X0 on the device (the inertial-guess kernel with dt = 0)
+    upload(c->ubar, qbar, sizeof(double) * c->n, c->stream);
+    launch_inertial_guess(c->X0, c->ubar, c->ubar, c->n, 0.0, c->grav, c->ubar, c->stream);
+  }
+  set_engine_dynamics(c, dt);
+  ck(cudaStreamSynchronize(c->stream));
+  ck(cudaGetLastError());
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_eval(lsn_ctx* c, const double* z, double* E, double* g, double* K) {
+  if (!c) return LSN_ERR_ARG;
+  LSN_GUARD_BEGIN
+  int rc = prepare(c);
+  if (rc != LSN_OK) return rc;
+  const int r = c->widths[0];
+  if (z) {
+    upload(&c->eng->sv->z[0], z, sizeof(double) * r, c->stream);
+    ck(cudaMemcpyAsync(c->z0.data(), &c->eng->sv->z[0], sizeof(double) * r,
+                       cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+  }
+  reset_solver(c, 1);
+  c->eng->jac_pass();
+  std::vector<double> sys(nslots(r));
+  ck(cudaMemcpyAsync(sys.data(), c->eng->sys, sizeof(double) * sys.size(),
+                     cudaMemcpyDeviceToHost, c->stream));
+  ck(cudaStreamSynchronize(c->stream));
+  ck(cudaGetLastError());
+  if (E) *E = sys[0] + (c->dt > 0.0 ? 0.0 : c->E_const);
+  if (g)
+    for (int i = 0; i < r; ++i) g[i] = sys[2 + i];
+  if (K)
+    for (int i = 0; i < r; ++i)
+      for (int j = i; j < r; ++j) {
+        double val = sys[2 + r + i * r - (i * (i - 1)) / 2 + (j - i)];
+        K[i * r + j] = val;
+        K[j * r + i] = val;
+      }
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_decode(lsn_ctx* c, const double* z, double* x_out, double* J_out) {
+  if (!c) return LSN_ERR_ARG;
+  LSN_GUARD_BEGIN
+  int rc = prepare(c);
+  if (rc != LSN_OK) return rc;
+  if (z) {
+    upload(&c->eng->sv->z[0], z, sizeof(double) * c->widths[0], c->stream);
+    ck(cudaMemcpyAsync(c->z0.data(), &c->eng->sv->z[0], sizeof(double) * c->widths[0],
+                       cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+  }
+  c->eng->decode_to_host(x_out, J_out);
+  ck(cudaGetLastError());
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_step(lsn_ctx* c, const double* z_in, double dt, double* z_out, lsn_stats* stats) {
+  if (!c) return LSN_ERR_ARG;
+  if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(c, LSN_ERR_ARG, "step: dt must be >= 0");
+  auto t0 = std::chrono::steady_clock::now();
+  LSN_GUARD_BEGIN
+  int rc = prepare(c);
+  if (rc != LSN_OK) return rc;
+  cudaStream_t s = c->stream;
+  const int r = c->widths[0];
+  if (!c->q_valid) {  // q = x(current z), v = 0
+    rc = lsn_set_state(c, nullptr, nullptr, nullptr);
+    if (rc != LSN_OK) return rc;
+  }
+  if (z_in) upload(&c->eng->sv->z[0], z_in, sizeof(double) * r, s);
+  c->dt = dt;
+  if (dt > 0.0) launch_inertial_guess(c->X0, c->q, c->v, c->n, dt, c->grav, c->ubar, s);
+  set_engine_dynamics(c, dt);
+  reset_solver(c, 0);
+  int status = -1;
+  for (int it = 0; it <= c->max_newton + 1; ++it) {
+    c->eng->jac_pass();
+    status = read_status(c);
+    if (status != -1) break;
+    // line search: batches of KTRIAL step lengths until one is accepted
+    for (int batch = 0; batch < (c->max_ls + KTRIAL - 1) / KTRIAL + 1; ++batch) {
+      c->eng->trial_pass();
+      int acc = 0;
+      ck(cudaMemcpyAsync(c->pinned_status, &c->eng->sv->accepted, sizeof(int),
+                         cudaMemcpyDeviceToHost, s));
+      ck(cudaStreamSynchronize(s));
+      acc = *c->pinned_status;
+      status = read_status(c);
+      if (acc || status != -1) break;
+    }
+    if (status != -1) break;
+  }
+  // the last Jacobian pass evaluated x at the final z
+  c->eng->finish(dt);
+  DevSolver h;
+  ck(cudaMemcpyAsync(&h, c->eng->sv, sizeof(DevSolver), cudaMemcpyDeviceToHost, s));
+  ck(cudaStreamSynchronize(s));
+  ck(cudaGetLastError());
+  if (h.status < -1) {
+    return fail(c, h.status, "step: non-finite values in the reduced system");
+  }
+  if (z_out) {
+    if (is_device_ptr(z_out))
+      ck(cudaMemcpyAsync(z_out, &c->eng->sv->z[0], sizeof(double) * r, cudaMemcpyDeviceToDevice, s));
+    else
+      std::memcpy(z_out, h.z, sizeof(double) * r);
+    ck(cudaStreamSynchronize(s));
+  }
+  std::copy(h.z, h.z + r, c->z0.begin());
+  auto t1 = std::chrono::steady_clock::now();
+  if (stats) {
+    stats->newton_iters = h.iters;
+    stats->ls_trials = h.ls_trials;
+    stats->exit = h.status;
+    stats->grad_inf = h.grad_inf;
+    stats->energy = h.E + (dt > 0.0 ? 0.0 : c->E_const);
+    stats->ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  }
+  return h.status;
+  LSN_GUARD_END
+}
+
+int lsn_get_positions(lsn_ctx* c, double* x_out) {
+  if (!c || !x_out) return LSN_ERR_ARG;
+  if (c->n == 0) return fail(c, LSN_ERR_STATE, "get_positions: no mesh");
+  LSN_GUARD_BEGIN
+  download(x_out, c->q, sizeof(double) * c->n, c->stream);
+  ck(cudaStreamSynchronize(c->stream));
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+}  // extern "C"

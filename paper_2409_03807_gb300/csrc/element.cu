@@ -1,0 +1,485 @@
+// Per-tet Stable Neo-Hookean element kernel fused with the reduced
+// contraction (Sec. 3.1 Eq. 2 and Eq. 11; stable neo-Hookean energy of
+// Sec. 5.1; PSD-projected Hessian of projective Newton, Supplement).
+//
+// For tet e with displacement gradient Hd = F - I = [u1-u0, u2-u0, u3-u0] Dm^-1
+// the kernel evaluates (w_e V_e times) the energy density, its first
+// derivative P and the 9x9 second derivative A = d2Psi/dF2, projects A onto
+// the PSD cone by a cyclic Jacobi eigen-decomposition (clamping negative
+// eigenvalues), and accumulates
+//     g += G_e^T p_e,            p_e = w_e V_e vec(P)
+//     K += C_e^T C_e,            C_e = diag(sqrt(w_e V_e lambda_+)) Q^T G_e
+// where G_e = dvec(F)/dz = B_e J_e (9 x r) is formed from the tet's four
+// vertex rows of J, so that C_e^T C_e = w_e J_e^T Hproj_e J_e.
+//
+// The density is written in terms of Hd (no cancellation near rest):
+//   Psi = mu/2 (Ic-3) - mu/2 log1p((Ic-3)/4) + lam/2 (J-1)(J-1 + 2(1-a))
+//   P   = mu d F + lam (J-1) cof(F) + (3 mu/4)(Hd + Hd^T - tr(Hd) I - cof(Hd))
+// with Ic-3 = 2 tr Hd + |Hd|^2, J-1 = tr Hd + (sum of principal 2x2 minors)
+// + det Hd, d = (Ic-3)/(4 (Ic+1)), a = 1 + 3 mu/(4 lam): algebraically the
+// same function as mu/2 (Ic-3) + lam/2 (J-a)^2 - mu/2 log(Ic+1) - Psi(I).
+//
+// Work split: a CTA takes tiles of 128 tets.  Phase 1 is one thread per tet
+// (element math, eigen-decomposition); phase 2 spreads (tet, column) pairs
+// over the threads to form G_e and C_e in shared memory; phase 3 is the
+// symmetric rank-9T update of the CTA's register-resident K partial, each
+// thread owning a fixed set of upper-triangle entries.  Each CTA writes one
+// partial row (E, sum|E|, g, K upper) that a fixed-order reduction sums.
+#include "lsn_internal.cuh"
+
+#include <algorithm>
+
+namespace lsn {
+namespace {
+
+constexpr int ET = 128;  // threads per CTA = tets per tile
+constexpr int CB = 16;   // tets per contraction batch
+
+template <typename Real>
+struct Consts {
+  static constexpr int sweeps = 8;
+};
+template <>
+struct Consts<double> {
+  static constexpr int sweeps = 12;
+};
+
+template <typename Real>
+__device__ __forceinline__ Real sqrt_r(Real x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float sqrt_r<float>(float x) { return sqrtf(x); }
+template <typename Real>
+__device__ __forceinline__ Real log1p_r(Real x) { return log1p(x); }
+template <>
+__device__ __forceinline__ float log1p_r<float>(float x) { return log1pf(x); }
+
+// Levi-Civita sign of (i, k, 3-i-k) for i != k.
+__host__ __device__ constexpr int eps2(int i, int k) { return (k == (i + 1) % 3) ? 1 : -1; }
+
+template <typename Real>
+struct Invariants {
+  Real Ic3, Jm1, cof[3][3], cofH[3][3], trH;
+};
+
+template <typename Real>
+__device__ __forceinline__ void invariants(const Real (&H)[3][3], Invariants<Real>& iv) {
+  iv.trH = H[0][0] + H[1][1] + H[2][2];
+  Real nrm2 = Real(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) nrm2 += H[i][j] * H[i][j];
+  iv.Ic3 = Real(2) * iv.trH + nrm2;
+  // cofactor of Hd: cofH_ij = Hd_{i+1,j+1} Hd_{i+2,j+2} - Hd_{i+1,j+2} Hd_{i+2,j+1}
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+      iv.cofH[i][j] = H[i1][j1] * H[i2][j2] - H[i1][j2] * H[i2][j1];
+    }
+  const Real m2 = iv.cofH[0][0] + iv.cofH[1][1] + iv.cofH[2][2];
+  const Real detH = H[0][0] * iv.cofH[0][0] + H[0][1] * iv.cofH[0][1] + H[0][2] * iv.cofH[0][2];
+  iv.Jm1 = iv.trH + m2 + detH;
+  // cof(I + Hd) = (1 + tr Hd) I - Hd^T + cof(Hd)
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      iv.cof[i][j] = (i == j ? Real(1) + iv.trH : Real(0)) - H[j][i] + iv.cofH[i][j];
+}
+
+template <typename Real>
+__device__ __forceinline__ Real snh_psi(const Invariants<Real>& iv, Real mu, Real lam,
+                                        Real oma /* 1 - a */) {
+  return Real(0.5) * mu * iv.Ic3 - Real(0.5) * mu * log1p_r<Real>(iv.Ic3 * Real(0.25)) +
+         Real(0.5) * lam * iv.Jm1 * (iv.Jm1 + Real(2) * oma);
+}
+
+// Cyclic Jacobi eigen-decomposition of the symmetric 9x9 matrix A (in place:
+// A becomes diagonal), accumulating the rotations in Q (A_in = Q diag Q^T).
+template <typename Real>
+__device__ __forceinline__ void jacobi9(Real (&A)[9][9], Real (&Q)[9][9]) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+#pragma unroll
+    for (int j = 0; j < 9; ++j) Q[i][j] = (i == j) ? Real(1) : Real(0);
+  const Real tiny = sizeof(Real) == 4 ? Real(1e-30) : Real(1e-300);
+#pragma unroll 1
+  for (int sweep = 0; sweep < Consts<Real>::sweeps; ++sweep) {
+    Real off = Real(0), dia = Real(0);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      dia += A[p][p] * A[p][p];
+#pragma unroll
+      for (int q = p + 1; q < 9; ++q) off += A[p][q] * A[p][q];
+    }
+    const Real rel = sizeof(Real) == 4 ? Real(1e-14) : Real(1e-30);
+    if (off <= rel * dia + tiny) break;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+#pragma unroll
+      for (int q = p + 1; q < 9; ++q) {
+        const Real apq = A[p][q];
+        if (fabs(apq) > tiny) {
+          const Real theta = (A[q][q] - A[p][p]) / (Real(2) * apq);
+          const Real at = fabs(theta);
+          Real t = (at > Real(1e15)) ? Real(0.5) / theta
+                                     : Real(1) / (at + sqrt_r<Real>(theta * theta + Real(1)));
+          if (theta < Real(0) && at <= Real(1e15)) t = -t;
+          const Real c = Real(1) / sqrt_r<Real>(t * t + Real(1));
+          const Real s = t * c;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            const Real akp = A[k][p], akq = A[k][q];
+            A[k][p] = c * akp - s * akq;
+            A[k][q] = s * akp + c * akq;
+          }
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            const Real apk = A[p][k], aqk = A[q][k];
+            A[p][k] = c * apk - s * aqk;
+            A[q][k] = s * apk + c * aqk;
+          }
+          A[p][q] = Real(0);
+          A[q][p] = Real(0);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            const Real qkp = Q[k][p], qkq = Q[k][q];
+            Q[k][p] = c * qkp - s * qkq;
+            Q[k][q] = s * qkp + c * qkq;
+          }
+        }
+      }
+    }
+  }
+}
+
+template <typename Real>
+struct ElemTile {  // shared memory of one tile
+  Real L[ET][81];
+  Real D[ET][12];
+  Real p[ET][9];
+  int4 v[ET];
+};
+
+__device__ __forceinline__ void pair_of(int p, int r, int& i, int& j) {
+  i = 0;
+  while (p >= r - i) {
+    p -= r - i;
+    ++i;
+  }
+  j = i + p;
+}
+
+template <typename Real>
+__device__ __forceinline__ void load_tet(const ElemArgs& ea, int e, int4& tv, Real (&Dmi)[3][3],
+                                         Real& wv) {
+  const Real* dm = static_cast<const Real*>(ea.dminv);
+  tv = ea.tets[e];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) Dmi[a][b] = dm[(3 * a + b) * ea.S + e];
+  wv = static_cast<const Real*>(ea.wv)[e];
+}
+
+template <typename Real>
+__device__ __forceinline__ void disp_grad(const Real* __restrict__ u, const int4& tv,
+                                          const Real (&Dmi)[3][3], Real (&H)[3][3]) {
+  const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
+  Real Du[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const Real u0 = u[3 * vv[0] + i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Du[i][a] = u[3 * vv[a + 1] + i] - u0;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      H[i][j] = Du[i][0] * Dmi[0][j] + Du[i][1] * Dmi[1][j] + Du[i][2] * Dmi[2][j];
+}
+
+template <typename Real, int RT>
+__global__ void __launch_bounds__(ET) element_full_kernel(ElemArgs ea,
+                                                          const Real* __restrict__ u,
+                                                          const Real* __restrict__ J,
+                                                          double* __restrict__ part,
+                                                          int part_stride) {
+  constexpr int PQ = (RT * (RT + 1) / 2 + ET - 1) / ET;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ElemTile<Real>& tl = *reinterpret_cast<ElemTile<Real>*>(smem_raw);
+  Real* Cs = reinterpret_cast<Real*>(smem_raw + sizeof(ElemTile<Real>));  // CB*9 x r
+  Real* Gp = Cs + CB * 9 * ea.r;                                           // CB x r
+  __shared__ double red[2 * ET];
+  const int t = threadIdx.x;
+  const int r = ea.r, np = npairs(r);
+  const Real mu = (Real)ea.mu, lam = (Real)ea.lam;
+  const Real oma = (Real)(-0.75 * ea.mu / ea.lam);  // 1 - a
+  int pi[PQ], pj[PQ];
+  double kacc[PQ];
+#pragma unroll
+  for (int q = 0; q < PQ; ++q) {
+    int p = t + ET * q;
+    if (p < np) pair_of(p, r, pi[q], pj[q]);
+    else pi[q] = pj[q] = -1;
+    kacc[q] = 0.0;
+  }
+  double gacc = 0.0, eacc = 0.0, eabs = 0.0;
+  const int ntiles = (ea.S + ET - 1) / ET;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // ---------------- phase 1: element math, one tet per thread
+    const int e = tile * ET + t;
+    if (e < ea.S) {
+      int4 tv;
+      Real Dmi[3][3], wv, H[3][3];
+      load_tet<Real>(ea, e, tv, Dmi, wv);
+      disp_grad<Real>(u, tv, Dmi, H);
+      Invariants<Real> iv;
+      invariants<Real>(H, iv);
+      const Real psi = snh_psi<Real>(iv, mu, lam, oma);
+      eacc += (double)(wv * psi);
+      eabs += fabs((double)(wv * psi));
+      const Real Ic = iv.Ic3 + Real(3);
+      const Real dl = iv.Ic3 / (Real(4) * (Ic + Real(1)));
+      const Real lJ = lam * iv.Jm1;
+      // first derivative P, stored as p = w V vec(P)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const Real Fij = H[i][j] + (i == j ? Real(1) : Real(0));
+          const Real P = mu * dl * Fij + lJ * iv.cof[i][j] +
+                         Real(0.75) * mu *
+                             (H[i][j] + H[j][i] - (i == j ? iv.trH : Real(0)) - iv.cofH[i][j]);
+          tl.p[t][3 * i + j] = wv * P;
+        }
+      // second derivative A (9x9, row-major vec)
+      Real A[9][9];
+      const Real c1 = mu * Ic / (Ic + Real(1));
+      const Real c2 = Real(2) * mu / ((Ic + Real(1)) * (Ic + Real(1)));
+      const Real c3 = lam * (iv.Jm1 + oma);  // lam (J - a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+              const Real Fij = H[i][j] + (i == j ? Real(1) : Real(0));
+              const Real Fkl = H[k][l] + (k == l ? Real(1) : Real(0));
+              Real val = c2 * Fij * Fkl + lam * iv.cof[i][j] * iv.cof[k][l];
+              if (i == k && j == l) val += c1;
+              if (i != k && j != l) {
+                const int m = 3 - i - k, n = 3 - j - l;
+                const Real Fmn = H[m][n] + (m == n ? Real(1) : Real(0));
+                val += c3 * Real(eps2(i, k) * eps2(j, l)) * Fmn;
+              }
+              A[3 * i + j][3 * k + l] = val;
+            }
+      Real Q[9][9];
+      jacobi9<Real>(A, Q);
+#pragma unroll
+      for (int m = 0; m < 9; ++m) {
+        const Real lp = A[m][m] > Real(0) ? A[m][m] : Real(0);
+        const Real sc = sqrt_r<Real>(wv * lp);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) tl.L[t][9 * m + k] = sc * Q[k][m];
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        tl.D[t][j] = -(Dmi[0][j] + Dmi[1][j] + Dmi[2][j]);
+#pragma unroll
+        for (int a = 1; a < 4; ++a) tl.D[t][3 * a + j] = Dmi[a - 1][j];
+      }
+      tl.v[t] = tv;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 81; ++k) tl.L[t][k] = Real(0);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) tl.D[t][k] = Real(0);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) tl.p[t][k] = Real(0);
+      tl.v[t] = make_int4(0, 0, 0, 0);
+    }
+    __syncthreads();
+    const int tile_tets = min(ET, ea.S - tile * ET);
+    // ---------------- phases 2 + 3 in batches of CB tets
+    for (int b0 = 0; b0 < tile_tets; b0 += CB) {
+      const int nb = min(CB, tile_tets - b0);
+      for (int item = t; item < CB * r; item += ET) {
+        const int lt = item / r, c = item - lt * r;
+        Real Cv[9];
+        Real gp = Real(0);
+        if (lt < nb) {
+          const int q = b0 + lt;
+          const int4 tv = tl.v[q];
+          const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
+          Real jv[4][3];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) jv[a][i] = J[(size_t)(3 * vv[a] + i) * r + c];
+          Real G[9];
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              Real s = Real(0);
+#pragma unroll
+              for (int a = 0; a < 4; ++a) s += tl.D[q][3 * a + j] * jv[a][i];
+              G[3 * i + j] = s;
+            }
+#pragma unroll
+          for (int k = 0; k < 9; ++k) gp += tl.p[q][k] * G[k];
+#pragma unroll
+          for (int m = 0; m < 9; ++m) {
+            Real s = Real(0);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) s += tl.L[q][9 * m + k] * G[k];
+            Cv[m] = s;
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < 9; ++m) Cv[m] = Real(0);
+        }
+#pragma unroll
+        for (int m = 0; m < 9; ++m) Cs[(lt * 9 + m) * r + c] = Cv[m];
+        Gp[lt * r + c] = gp;
+      }
+      __syncthreads();
+      if (t < r) {
+        double s = 0.0;
+        for (int lt = 0; lt < nb; ++lt) s += (double)Gp[lt * r + t];
+        gacc += s;
+      }
+      const int rows = nb * 9;
+#pragma unroll
+      for (int q = 0; q < PQ; ++q) {
+        if (pi[q] >= 0) {
+          Real s = Real(0);
+          for (int row = 0; row < rows; ++row) s += Cs[row * r + pi[q]] * Cs[row * r + pj[q]];
+          kacc[q] += (double)s;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  red[t] = eacc;
+  red[ET + t] = eabs;
+  __syncthreads();
+  for (int s = ET / 2; s > 0; s >>= 1) {
+    if (t < s) {
+      red[t] += red[t + s];
+      red[ET + t] += red[ET + t + s];
+    }
+    __syncthreads();
+  }
+  double* prow = part + (size_t)blockIdx.x * part_stride;
+  if (t == 0) {
+    prow[0] = red[0];
+    prow[1] = red[ET];
+  }
+  if (t < r) prow[2 + t] = gacc;
+#pragma unroll
+  for (int q = 0; q < PQ; ++q)
+    if (pi[q] >= 0) prow[2 + r + t + ET * q] = kacc[q];
+}
+
+// Energy of k trial displacement fields ut[j * n + .] for every cubature tet.
+template <typename Real>
+__global__ void __launch_bounds__(ET) element_energy_kernel(ElemArgs ea,
+                                                            const Real* __restrict__ ut,
+                                                            int k, double* __restrict__ part,
+                                                            int part_stride) {
+  __shared__ double red[2 * KTRIAL][ET];
+  const int t = threadIdx.x;
+  const Real mu = (Real)ea.mu, lam = (Real)ea.lam;
+  const Real oma = (Real)(-0.75 * ea.mu / ea.lam);
+  double ea_[KTRIAL], ab_[KTRIAL];
+#pragma unroll
+  for (int j = 0; j < KTRIAL; ++j) ea_[j] = ab_[j] = 0.0;
+  for (int e = blockIdx.x * ET + t; e < ea.S; e += gridDim.x * ET) {
+    int4 tv;
+    Real Dmi[3][3], wv;
+    load_tet<Real>(ea, e, tv, Dmi, wv);
+#pragma unroll
+    for (int j = 0; j < KTRIAL; ++j) {
+      if (j < k) {
+        Real H[3][3];
+        disp_grad<Real>(ut + (size_t)j * ea.n, tv, Dmi, H);
+        Invariants<Real> iv;
+        invariants<Real>(H, iv);
+        const double pe = (double)(wv * snh_psi<Real>(iv, mu, lam, oma));
+        ea_[j] += pe;
+        ab_[j] += fabs(pe);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < KTRIAL; ++j) {
+    red[2 * j][t] = ea_[j];
+    red[2 * j + 1][t] = ab_[j];
+  }
+  __syncthreads();
+  for (int s = ET / 2; s > 0; s >>= 1) {
+    if (t < s) {
+#pragma unroll
+      for (int j = 0; j < 2 * KTRIAL; ++j) red[j][t] += red[j][t + s];
+    }
+    __syncthreads();
+  }
+  if (t < 2 * k) part[(size_t)blockIdx.x * part_stride + t] = red[t][0];
+}
+
+template <typename Real, int RT>
+void run_full(const ElemArgs& ea, const Real* u, const Real* J, double* part, int grid,
+              cudaStream_t s) {
+  size_t sm = sizeof(ElemTile<Real>) + (size_t)(CB * 9 * ea.r + CB * ea.r) * sizeof(Real);
+  static size_t set = 0;
+  if (sm > set) {
+    cudaFuncSetAttribute(element_full_kernel<Real, RT>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set = sm;
+  }
+  element_full_kernel<Real, RT><<<grid, ET, sm, s>>>(ea, u, J, part, nslots(ea.r));
+}
+
+}  // namespace
+
+int element_full_grid(int S, int num_sms) {
+  int tiles = (S + ET - 1) / ET;
+  return std::max(1, std::min(tiles, num_sms * 2));
+}
+int element_energy_grid(int S, int num_sms) {
+  int blocks = (S + ET - 1) / ET;
+  return std::max(1, std::min(blocks, num_sms * 4));
+}
+
+template <typename Real>
+void launch_element_full(const ElemArgs& ea, const Real* u, const Real* J, double* part,
+                         int grid, cudaStream_t s) {
+  if (ea.r <= 16) run_full<Real, 16>(ea, u, J, part, grid, s);
+  else if (ea.r <= 32) run_full<Real, 32>(ea, u, J, part, grid, s);
+  else run_full<Real, 64>(ea, u, J, part, grid, s);
+}
+
+template <typename Real>
+void launch_element_energy(const ElemArgs& ea, const Real* ut, int k, double* part,
+                           int grid, cudaStream_t s) {
+  element_energy_kernel<Real><<<grid, ET, 0, s>>>(ea, ut, k, part, 2 * KTRIAL);
+}
+
+template void launch_element_full<float>(const ElemArgs&, const float*, const float*,
+                                         double*, int, cudaStream_t);
+template void launch_element_full<double>(const ElemArgs&, const double*, const double*,
+                                          double*, int, cudaStream_t);
+template void launch_element_energy<float>(const ElemArgs&, const float*, int, double*,
+                                           int, cudaStream_t);
+template void launch_element_energy<double>(const ElemArgs&, const double*, int, double*,
+                                            int, cudaStream_t);
+
+}  // namespace lsn

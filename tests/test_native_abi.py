@@ -1,0 +1,40 @@
+"""CPU-side checks of the native library: it builds for sm_103a, loads, and
+exports every entry point that include/lsn.h declares (no GPU calls)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lsn.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(lsn_\w+)\(", src, re.M)))
+
+
+def test_header_declares_the_solver_calls():
+    names = _declared()
+    for n in ["lsn_create", "lsn_destroy", "lsn_last_error", "lsn_set_mesh",
+              "lsn_set_material", "lsn_set_constraints", "lsn_set_cubature",
+              "lsn_set_ground", "lsn_set_decoder", "lsn_set_solver", "lsn_set_state",
+              "lsn_step", "lsn_get_positions", "lsn_eval"]:
+        assert n in names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2409_03807_gb300.build import build
+    build()
+    import paper_2409_03807_gb300 as pkg
+    return pkg.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    import paper_2409_03807_gb300 as pkg
+    assert set(_declared()) <= set(pkg.exported_symbols())
