@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark: reduced-solve implicit-Euler steps per second on one GB300.
+
+Workload (default): bar_twist_dyn_14976 - bar of 40x9x9 nodes (14,976 tets,
+n = 9,720), x = 0 face rotated 2 rad about the long axis over 60 frames,
+implicit Euler dt = 1/60, r = 16, decoder 16-256-256-256-9720 (seeded Xavier
+weights, output scale 1e-2), 256 cubature tets drawn uniformly by seed with
+weights 14976/256, Stable Neo-Hookean E = 1e5 Pa, nu = 0.45, rho = 1000.
+
+A step is one implicit-Euler time step solved by projective Newton to
+||g||_inf < 1e-5 (or its precision-floor / iteration-cap exit): decoder +
+Jacobian, element kernel + contraction, Cholesky, line search, until exit.
+Inputs (constraint targets of every frame, decoder weights, mesh) are
+resident in HBM before the timed region; the L2 is flushed (256 MiB write)
+between timed steps, outside the per-step CUDA events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun) runs N independent replicas, one per GPU (the solve
+does not shard); value = all ranks' steps / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "reduced-solve steps/s on 1 GB300 at stated rel. error vs FP64 oracle; % roofline"
+WORKLOAD = "bar_twist_dyn_14976"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="time budget of the CPU-oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_run(p, frames, budget_s):
+    """Run the FP64 CPU oracle for up to `frames` frames or `budget_s` seconds.
+    Returns (frames done, seconds, positions per frame)."""
+    from oracle.reduced import model_from_problem, ReducedSimulator
+    c = p.config
+    sim = ReducedSimulator(model_from_problem(p), c.dt, eps=c.eps,
+                           max_newton=c.max_newton, max_ls=c.max_ls, c=c.armijo_c)
+    qs = []
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(1, frames + 1):
+        sim.step(p.targets(k))
+        qs.append(sim.q.copy())
+        done = k
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return done, time.perf_counter() - t0, qs
+
+
+# --------------------------------------------------------------- reference
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from workloads import build_problem
+    p = build_problem(args.workload)
+    c = p.config
+    budget = 150.0
+    # timed: frames after the warm-up, continuing the same trajectory
+    from oracle.reduced import model_from_problem, ReducedSimulator
+    sim = ReducedSimulator(model_from_problem(p), c.dt, eps=c.eps, max_newton=c.max_newton,
+                           max_ls=c.max_ls, c=c.armijo_c)
+    for k in range(1, args.warmup + 1):
+        sim.step(p.targets(k))
+    t1 = time.perf_counter()
+    steps = 0
+    for k in range(args.warmup + 1, args.warmup + args.steps + 1):
+        sim.step(p.targets(k))
+        steps += 1
+        if time.perf_counter() - t1 > budget:
+            break
+    el = time.perf_counter() - t1
+    value = steps / el
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
+            "n_gpus": world, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * el / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"frames {args.warmup + 1}..{args.warmup + steps} of "
+                                       f"{args.workload} (FP64 NumPy oracle, implicit Euler)"},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- ours
+def algorithmic_bytes(cls, p, real_bytes):
+    """Bytes one launch of kernel class `cls` must move at minimum."""
+    c = p.config
+    n, r, H = p.n, c.r, p.widths[-2]
+    S = len(p.cub_idx)
+    if cls == "decoder_last":
+        return (n * H + n + (r + 1) * H + n + n * r) * real_bytes + p.nv * (4 + 8) + n * 8
+    if cls == "element":
+        return S * (16 + 10 * real_bytes + 12 * real_bytes + 12 * r * real_bytes)
+    if cls == "decoder_trial":
+        return (n * H + n + 4 * H + 4 * n) * real_bytes + p.nv * (4 + 8) + n * 8
+    if cls == "element_energy":
+        return S * (16 + 10 * real_bytes + 4 * 12 * real_bytes)
+    return None
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the solver has no CPU path)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2409_03807_gb300.build import build
+    if rank == 0:
+        build()
+    if world > 1:
+        torch.distributed.barrier()
+    build()
+    import paper_2409_03807_gb300 as pkg
+    from workloads import build_problem
+
+    p = build_problem(args.workload)
+    c = p.config
+    W, K = args.warmup, args.steps
+    stream = torch.cuda.Stream(dev)
+    ctx = pkg.context_from_problem(p, precision=args.precision, device=local, stream=stream)
+    frames = W + K
+    targets = torch.tensor(np.stack([p.targets(k) for k in range(1, frames + 1)]),
+                           dtype=torch.float64, device=dev)
+    z_dev = torch.zeros(c.r, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def do_step(k, z_out):
+        ctx.set_constraints(None, targets[k - 1])
+        return ctx.step(dt=c.dt, z_out=z_out)
+
+    # warm-up frames 1..W (profile every kernel class to find the dominant one)
+    ctx.set_profiling(pkg._native.KERNEL_CLASSES)
+    warm_q = {}
+    for k in range(1, W + 1):
+        do_step(k, z_dev)
+        warm_q[k] = ctx.get_positions()
+    prof = ctx.get_profile()
+    warm_profile = {k: {"launches": v[0], "ms": v[2]} for k, v in prof.items()}
+    dominant = max(("decoder_last", "element", "decoder_trial", "element_energy"),
+                   key=lambda nm: prof[nm][2])
+    snap = ctx.get_state()
+    # timed frames W+1..W+K, only the dominant class carries events
+    ctx.set_profiling([dominant])
+    ctx.reset_profile()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    iters = trials = 0
+    exits = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for i, k in enumerate(range(W + 1, W + K + 1)):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+            ev0[i].record(stream)
+        rc, st, _ = do_step(k, z_dev)
+        with torch.cuda.stream(stream):
+            ev1[i].record(stream)
+        iters += st["newton_iters"]
+        trials += st["ls_trials"]
+        exits[rc] = exits.get(rc, 0) + 1
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    prof = ctx.get_profile()
+    launches = sum(v[0] for v in prof.values())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / K
+    value = world * K / (total_ms / 1000.0)
+
+    # end to end through the C ABI with host buffers: the same frames again
+    ctx.set_state(*snap)
+    pin_t = torch.empty((frames, p.cnodes.shape[0], 3), dtype=torch.float64).pin_memory()
+    pin_t.copy_(targets.cpu())
+    z_host = torch.zeros(c.r, dtype=torch.float64).pin_memory()
+    q_host = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+    ctx.set_profiling([])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(W + 1, W + K + 1):
+        ctx.set_constraints(None, pin_t[k - 1])
+        ctx.step(dt=c.dt, z_out=z_host)
+        ctx.get_positions(q_host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * K / e2e_s, "unit": "steps/s",
+           "h2d_bytes_per_step": int(p.cnodes.shape[0] * 3 * 8),
+           "d2h_bytes_per_step": int(c.r * 8 + p.n * 8)}
+
+    real_bytes = 8 if args.precision == "fp64" else 4
+    launches_dom, timed_dom, ms_dom = prof[dominant]
+    avg_ms = ms_dom / max(timed_dom, 1)
+    ab = algorithmic_bytes(dominant, p, real_bytes)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback"
+    if os.path.exists(peaks_path):
+        peak = json.load(open(peaks_path))["hbm_gbs"]
+        peak_src = "measured"
+    achieved = ab / (avg_ms / 1000.0) / 1e9 if ab and avg_ms > 0 else None
+    roofline = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "avg_launch_us": avg_ms * 1000.0, "launches": launches_dom,
+                "algorithmic_bytes_per_launch": ab,
+                "share_of_step": ms_dom / total_ms if world == 1 else None}
+
+    cpu = None
+    err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        done, secs, qs = oracle_run(p, max(W, 200), args.cpu_seconds)
+        cpu = {"value": done / secs, "unit": "steps/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"frames 1..{done} of {args.workload} from rest "
+                         f"(FP64 NumPy oracle, {secs:.1f} s)"}
+        f = min(done, W)
+        if f >= 1:
+            uo = qs[f - 1] - p.X0.ravel()
+            ug = warm_q[f] - p.X0.ravel()
+            err = {"frame": f, "rel_displacement_error": float(
+                np.linalg.norm(ug - uo) / max(np.linalg.norm(uo), 1e-300))}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+                "steps": K, "warmup": W, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+                "config": {"workload": args.workload,
+                           "mesh": f"{c.dims[0]}x{c.dims[1]}x{c.dims[2]} nodes, {p.ne} tets, "
+                                   f"n={p.n}",
+                           "r": c.r, "decoder": "-".join(map(str, p.widths)),
+                           "cubature": len(p.cub_idx), "dt": c.dt, "tol_inf": c.eps,
+                           "precision": args.precision + " (FP64 Cholesky + line search)",
+                           "frames": f"{W + 1}..{W + K}",
+                           "l2": "flushed between steps (256 MiB write, outside events)",
+                           "parallelism": "replicas" if world > 1 else "1 GPU"},
+                "newton_iters_per_step": iters / K, "ls_trials_per_step": trials / K,
+                "newton_iters_per_s": iters / (total_ms / 1000.0),
+                "exits": {str(k): v for k, v in sorted(exits.items())},
+                "rel_error_vs_oracle": err,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "warmup_kernel_profile": warm_profile,
+                "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -149,6 +149,11 @@ int lsn_set_state(lsn_ctx* ctx, const double* z, const double* q,
 int lsn_step(lsn_ctx* ctx, const double* z_in, double dt, double* z_out,
              lsn_stats* stats);
 
+/* Copy the current state: z (r), q and v (n each) to host or device pointers
+ * (any may be NULL).  With lsn_set_state this snapshots and restores a
+ * simulation. */
+int lsn_get_state(lsn_ctx* ctx, double* z, double* q, double* v);
+
 /* Copy the current positions q (n doubles) to x_out (host or device). */
 int lsn_get_positions(lsn_ctx* ctx, double* x_out);
 
@@ -168,6 +173,39 @@ int lsn_set_dynamics(lsn_ctx* ctx, double dt, const double* qbar);
  * row-major), with constraints applied, copied to host pointers x_out and
  * J_out (either may be NULL). */
 int lsn_decode(lsn_ctx* ctx, const double* z, double* x_out, double* J_out);
+
+/* History of the last lsn_step: for Newton iteration k < count (at most
+ * `max` and at most 128 entries) the entry k of each non-NULL host array
+ * receives ||g||_inf, E (without the quasi-static constant), the rounding
+ * scale max_i sum |contributions to g_i| and the accepted step length (0 for
+ * the final, exiting evaluation). */
+int lsn_get_trace(lsn_ctx* ctx, int max, double* grad_inf, double* energy,
+                  double* grad_scale, double* alpha, int* count);
+
+/* Kernel classes for profiling. */
+enum lsn_kernel_class {
+  LSN_K_DECODER_HIDDEN = 0, /* hidden layers, Jacobian and trial passes       */
+  LSN_K_DECODER_LAST = 1,   /* output layer + x, J and inertia partials       */
+  LSN_K_ELEMENT = 2,        /* per-tet energy/gradient/projected Hessian with
+                               the J_e^T H_e J_e contraction                   */
+  LSN_K_DECODER_TRIAL = 3,  /* output layer of the line-search trial pass     */
+  LSN_K_ELEMENT_ENERGY = 4, /* per-tet energy of the line-search trials       */
+  LSN_K_SOLVE = 5,          /* partial reductions, Cholesky, Armijo, updates  */
+  LSN_K_COUNT = 6
+};
+
+/* Profiling: launches of every class are always counted.  Classes whose bit
+ * (1 << class) is set in `event_mask` are also timed with CUDA events
+ * recorded on the context stream around each launch (device time; the
+ * events add a few microseconds of host work per launch). */
+int lsn_set_profiling(lsn_ctx* ctx, unsigned event_mask);
+
+/* Accumulated launches and device milliseconds (timed classes only) of
+ * kernel class `cls` since the last lsn_reset_profile.  Synchronises the
+ * stream. */
+int lsn_get_profile(lsn_ctx* ctx, int cls, long long* launches,
+                    long long* timed_launches, double* ms_total);
+int lsn_reset_profile(lsn_ctx* ctx);
 
 #ifdef __cplusplus
 }

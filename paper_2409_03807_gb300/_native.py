@@ -54,10 +54,20 @@ _SIGS = {
     "lsn_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                  ctypes.POINTER(LsnStats)],
     "lsn_get_positions": [ctypes.c_void_p, ctypes.c_void_p],
+    "lsn_get_state": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "lsn_eval": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                  ctypes.c_void_p],
     "lsn_decode": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "lsn_set_profiling": [ctypes.c_void_p, ctypes.c_uint],
+    "lsn_get_trace": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                      ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)],
+    "lsn_get_profile": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                        ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)],
+    "lsn_reset_profile": [ctypes.c_void_p],
 }
+
+KERNEL_CLASSES = ["decoder_hidden", "decoder_last", "element", "decoder_trial",
+                  "element_energy", "solve"]
 
 
 def load(path=None):
@@ -203,6 +213,14 @@ class Context:
         self._check(rc, allow_positive=True)
         return rc, st.as_dict(), z_out
 
+    def get_state(self, z=None, q=None, v=None):
+        """Copy z, q, v into the given arrays / tensors (new numpy arrays if None)."""
+        z = np.zeros(self.r) if z is None else z
+        q = np.zeros(self.n) if q is None else q
+        v = np.zeros(self.n) if v is None else v
+        self._check(self.lib.lsn_get_state(self.h, _ptr(z), _ptr(q), _ptr(v)))
+        return z, q, v
+
     def get_positions(self, out=None):
         if out is None:
             out = np.zeros(self.n)
@@ -216,6 +234,34 @@ class Context:
         K = np.zeros((self.r, self.r))
         self._check(self.lib.lsn_eval(self.h, _ptr(z), _ptr(E), _ptr(g), _ptr(K)))
         return float(E[0]), g, K
+
+    def get_trace(self, max_entries=128):
+        """Per-iteration (grad_inf, energy, grad_scale, alpha) of the last step."""
+        g, e, gs, a = (np.zeros(max_entries) for _ in range(4))
+        cnt = ctypes.c_int()
+        self._check(self.lib.lsn_get_trace(self.h, max_entries, _ptr(g), _ptr(e), _ptr(gs),
+                                           _ptr(a), ctypes.byref(cnt)))
+        k = cnt.value
+        return {"grad_inf": g[:k], "energy": e[:k], "grad_scale": gs[:k], "alpha": a[:k]}
+
+    def set_profiling(self, classes=()):
+        mask = 0
+        for c in classes:
+            mask |= 1 << (KERNEL_CLASSES.index(c) if isinstance(c, str) else int(c))
+        return self._check(self.lib.lsn_set_profiling(self.h, mask))
+
+    def get_profile(self):
+        """{class: (launches, timed_launches, ms_total)}"""
+        out = {}
+        for k, name in enumerate(KERNEL_CLASSES):
+            a, b, ms = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double()
+            self._check(self.lib.lsn_get_profile(self.h, k, ctypes.byref(a), ctypes.byref(b),
+                                                 ctypes.byref(ms)))
+            out[name] = (a.value, b.value, ms.value)
+        return out
+
+    def reset_profile(self):
+        return self._check(self.lib.lsn_reset_profile(self.h))
 
     def decode(self, z, want_J=True):
         z = _f64(z)

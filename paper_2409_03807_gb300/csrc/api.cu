@@ -63,6 +63,75 @@ void download(void* dst, const void* src, size_t bytes, cudaStream_t s) {
                      is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
 }
 
+// CUDA-event timing of kernel classes (see lsn_set_profiling).
+struct Profiler {
+  cudaStream_t stream = nullptr;
+  unsigned mask = 0;
+  long long launches[LSN_K_COUNT] = {0};
+  long long timed[LSN_K_COUNT] = {0};
+  double ms[LSN_K_COUNT] = {0};
+  struct Pending {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  int open_cls = -1;
+  cudaEvent_t open_a = nullptr;
+
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    ck(cudaEventCreate(&e));
+    return e;
+  }
+  void begin(int cls, int count = 1) {
+    launches[cls] += count;
+    if (mask & (1u << cls)) {
+      open_cls = cls;
+      open_a = get();
+      ck(cudaEventRecord(open_a, stream));
+    }
+  }
+  void end(int cls) {
+    if (open_cls == cls && open_a) {
+      cudaEvent_t b = get();
+      ck(cudaEventRecord(b, stream));
+      pending.push_back({cls, open_a, b});
+      open_cls = -1;
+      open_a = nullptr;
+    }
+  }
+  void resolve() {
+    if (pending.empty()) return;
+    ck(cudaStreamSynchronize(stream));
+    for (auto& p : pending) {
+      float t = 0.f;
+      ck(cudaEventElapsedTime(&t, p.a, p.b));
+      ms[p.cls] += t;
+      timed[p.cls] += 1;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  void reset() {
+    resolve();
+    for (int k = 0; k < LSN_K_COUNT; ++k) launches[k] = timed[k] = 0, ms[k] = 0.0;
+  }
+  ~Profiler() {
+    for (auto& p : pending) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct EngineBase {
   virtual ~EngineBase() {}
   virtual void jac_pass() = 0;       // x, J, element, reduce, direction
@@ -126,6 +195,8 @@ struct lsn_ctx {
   bool dirty = true;
   int* pinned_status = nullptr;
   double E_const = 0.0;  // -sum m g . X0 in quasi-static solves
+  int* cidx_dev = nullptr;  // constrained vertex indices
+  Profiler prof;
 };
 
 namespace {
@@ -251,6 +322,7 @@ struct Engine : EngineBase {
     cudaStream_t s = c->stream;
     const Real* in = Z0;
     int cur = 0;
+    c->prof.begin(LSN_K_DECODER_HIDDEN, L - 1);
     for (int l = 0; l < L - 1; ++l) {
       int M = c->widths[l + 1], K = c->widths[l];
       launch_decoder_layer<Real>(jac ? Epi::HiddenJac : Epi::HiddenVal, dW[l], db[l], M, K,
@@ -258,33 +330,52 @@ struct Engine : EngineBase {
       in = Z[cur];
       cur ^= 1;
     }
+    c->prof.end(LSN_K_DECODER_HIDDEN);
     return in;
   }
 
   void jac_pass() override {
     cudaStream_t s = c->stream;
+    Profiler& P = c->prof;
+    P.begin(LSN_K_SOLVE);
     launch_write_jac_columns<Real>(sv, Z0, s);
+    P.end(LSN_K_SOLVE);
     const Real* h = hidden(true, C);
+    P.begin(LSN_K_DECODER_LAST);
     launch_decoder_layer<Real>(Epi::LastJac, dW[L - 1], db[L - 1], n, c->widths[L - 1], h, C,
                                nullptr, 0, u, J, part_dec, ns, la, grid_dec, s);
+    P.end(LSN_K_DECODER_LAST);
+    P.begin(LSN_K_ELEMENT);
     launch_element_full<Real>(ea, u, J, part_el, grid_el, s);
+    P.end(LSN_K_ELEMENT);
+    P.begin(LSN_K_SOLVE, 2);
     launch_reduce_cols(part_dec, grid_dec, part_el, grid_el, ns, sys, s);
     launch_newton_direction<Real>(sv, sys, Z0, c->max_newton, s);
+    P.end(LSN_K_SOLVE);
   }
 
   void trial_pass() override {
     cudaStream_t s = c->stream;
+    Profiler& P = c->prof;
     const Real* h = hidden(false, KTRIAL);
+    P.begin(LSN_K_DECODER_TRIAL);
     launch_decoder_layer<Real>(Epi::LastVal, dW[L - 1], db[L - 1], n, c->widths[L - 1], h,
                                KTRIAL, ut, n, nullptr, nullptr, part_dec_t, 2 * KTRIAL, la,
                                grid_dec_t, s);
+    P.end(LSN_K_DECODER_TRIAL);
+    P.begin(LSN_K_ELEMENT_ENERGY);
     launch_element_energy<Real>(ea, ut, KTRIAL, part_el_t, grid_el_t, s);
+    P.end(LSN_K_ELEMENT_ENERGY);
+    P.begin(LSN_K_SOLVE, 2);
     launch_reduce_cols(part_dec_t, grid_dec_t, part_el_t, grid_el_t, 2 * KTRIAL, sys_t, s);
     launch_ls_select<Real>(sv, sys_t, Z0, s);
+    P.end(LSN_K_SOLVE);
   }
 
   void finish(double dt) override {
+    c->prof.begin(LSN_K_SOLVE);
     launch_finish_positions<Real>(c->X0, u, n, dt, c->q, c->v, c->stream);
+    c->prof.end(LSN_K_SOLVE);
   }
 
   void decode_to_host(double* x, double* Jh) override {
@@ -363,6 +454,9 @@ void reset_solver(lsn_ctx* c, int eval_only) {
   h.armijo_c = c->armijo_c;
   h.eta_scale = c->precision == LSN_PREC_FP64 ? 8.0 * 1.1102230246251565e-16
                                               : 8.0 * 5.960464477539063e-08;
+  h.floor_scale = c->precision == LSN_PREC_FP64 ? 64.0 * 1.1102230246251565e-16
+                                                : 64.0 * 5.960464477539063e-08;
+  h.g_best = 1e300;
   h.r = c->widths[0];
   h.max_ls = c->max_ls;
   h.status = -1;
@@ -407,7 +501,8 @@ int lsn_create(lsn_ctx** out, int device, void* cuda_stream) {
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (e == cudaSuccess) e = cudaMallocHost(&c->pinned_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->pinned_status, 8 * sizeof(int));
+  c->prof.stream = c->stream;
   if (e != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -430,6 +525,8 @@ static void free_mesh(lsn_ctx* c) {
   dfree(c->ctmp);
   dfree(c->cub_idx);
   dfree(c->cub_w);
+  dfree(c->cidx_dev);
+  c->cidx_dev = nullptr;
   dfree(c->q);
   dfree(c->v);
   dfree(c->ubar);
@@ -445,7 +542,7 @@ void lsn_destroy(lsn_ctx* c) {
   c->eng.reset();
   free_mesh(c);
   if (c->pinned_status) cudaFreeHost(c->pinned_status);
-  delete c;
+  delete c;  // the profiler releases its events
 }
 
 const char* lsn_last_error(const lsn_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -561,6 +658,10 @@ int lsn_set_constraints(lsn_ctx* c, const int32_t* vidx, int nc, const double* t
     }
     c->nc = nc;
     c->cidx.assign(vidx, vidx + nc);
+    dfree(c->cidx_dev);
+    c->cidx_dev = dalloc<int>(std::max(nc, 1));
+    if (nc > 0)
+      ck(cudaMemcpyAsync(c->cidx_dev, vidx, sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     ck(cudaMemcpyAsync(c->cslot, slot.data(), sizeof(int) * c->nv, cudaMemcpyHostToDevice, s));
     ck(cudaStreamSynchronize(s));
   } else if (nc != c->nc) {
@@ -569,20 +670,10 @@ int lsn_set_constraints(lsn_ctx* c, const int32_t* vidx, int nc, const double* t
   if (c->nc > 0) {
     if (!targets) return fail(c, LSN_ERR_ARG, "set_constraints: targets missing");
     upload(c->ctmp, targets, sizeof(double) * 3 * c->nc, s);
-    // displacement targets: target - X0 of each constrained vertex
-    std::vector<double> tg(3 * c->nc), X(3);
-    ck(cudaMemcpyAsync(tg.data(), c->ctmp, sizeof(double) * 3 * c->nc, cudaMemcpyDeviceToHost, s));
-    std::vector<double> X0h(c->n);
-    ck(cudaMemcpyAsync(X0h.data(), c->X0, sizeof(double) * c->n, cudaMemcpyDeviceToHost, s));
-    ck(cudaStreamSynchronize(s));
-    for (int i = 0; i < c->nc; ++i)
-      for (int k = 0; k < 3; ++k) {
-        if (!std::isfinite(tg[3 * i + k]))
-          return fail(c, LSN_ERR_NONFINITE, "set_constraints: non-finite target");
-        tg[3 * i + k] -= X0h[3 * c->cidx[i] + k];
-      }
-    ck(cudaMemcpyAsync(c->cu, tg.data(), sizeof(double) * 3 * c->nc, cudaMemcpyHostToDevice, s));
-    ck(cudaStreamSynchronize(s));
+    c->prof.begin(LSN_K_SOLVE);
+    launch_constraint_disp(c->cidx_dev, c->ctmp, c->X0, c->nc, c->cu, s);
+    c->prof.end(LSN_K_SOLVE);
+    ck(cudaGetLastError());
   }
   return LSN_OK;
   LSN_GUARD_END
@@ -769,11 +860,11 @@ int lsn_eval(lsn_ctx* c, const double* z, double* E, double* g, double* K) {
   ck(cudaGetLastError());
   if (E) *E = sys[0] + (c->dt > 0.0 ? 0.0 : c->E_const);
   if (g)
-    for (int i = 0; i < r; ++i) g[i] = sys[2 + i];
+    for (int i = 0; i < r; ++i) g[i] = sys[slot_g(i)];
   if (K)
     for (int i = 0; i < r; ++i)
       for (int j = i; j < r; ++j) {
-        double val = sys[2 + r + i * r - (i * (i - 1)) / 2 + (j - i)];
+        double val = sys[slot_K(r) + i * r - (i * (i - 1)) / 2 + (j - i)];
         K[i * r + j] = val;
         K[j * r + i] = val;
       }
@@ -813,7 +904,11 @@ int lsn_step(lsn_ctx* c, const double* z_in, double dt, double* z_out, lsn_stats
   }
   if (z_in) upload(&c->eng->sv->z[0], z_in, sizeof(double) * r, s);
   c->dt = dt;
-  if (dt > 0.0) launch_inertial_guess(c->X0, c->q, c->v, c->n, dt, c->grav, c->ubar, s);
+  if (dt > 0.0) {
+    c->prof.begin(LSN_K_SOLVE);
+    launch_inertial_guess(c->X0, c->q, c->v, c->n, dt, c->grav, c->ubar, s);
+    c->prof.end(LSN_K_SOLVE);
+  }
   set_engine_dynamics(c, dt);
   reset_solver(c, 0);
   int status = -1;
@@ -824,12 +919,12 @@ int lsn_step(lsn_ctx* c, const double* z_in, double dt, double* z_out, lsn_stats
     // line search: batches of KTRIAL step lengths until one is accepted
     for (int batch = 0; batch < (c->max_ls + KTRIAL - 1) / KTRIAL + 1; ++batch) {
       c->eng->trial_pass();
-      int acc = 0;
-      ck(cudaMemcpyAsync(c->pinned_status, &c->eng->sv->accepted, sizeof(int),
+      // status, iters, ls_trials, ls_iter, accepted are adjacent ints
+      ck(cudaMemcpyAsync(c->pinned_status, &c->eng->sv->status, 5 * sizeof(int),
                          cudaMemcpyDeviceToHost, s));
       ck(cudaStreamSynchronize(s));
-      acc = *c->pinned_status;
-      status = read_status(c);
+      status = c->pinned_status[0];
+      const int acc = c->pinned_status[4];
       if (acc || status != -1) break;
     }
     if (status != -1) break;
@@ -861,6 +956,68 @@ int lsn_step(lsn_ctx* c, const double* z_in, double dt, double* z_out, lsn_stats
     stats->ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
   }
   return h.status;
+  LSN_GUARD_END
+}
+
+int lsn_get_trace(lsn_ctx* c, int max, double* grad_inf, double* energy,
+                  double* grad_scale, double* alpha, int* count) {
+  if (!c || max < 0) return LSN_ERR_ARG;
+  if (!c->eng) return fail(c, LSN_ERR_STATE, "get_trace: no solve yet");
+  LSN_GUARD_BEGIN
+  DevSolver h;
+  ck(cudaMemcpyAsync(&h, c->eng->sv, sizeof(DevSolver), cudaMemcpyDeviceToHost, c->stream));
+  ck(cudaStreamSynchronize(c->stream));
+  int n = std::min(std::min(h.iters + 1, TRACE), max);
+  for (int k = 0; k < n; ++k) {
+    if (grad_inf) grad_inf[k] = h.trace_g[k];
+    if (energy) energy[k] = h.trace_E[k];
+    if (grad_scale) grad_scale[k] = h.trace_gabs[k];
+    if (alpha) alpha[k] = h.trace_alpha[k];
+  }
+  if (count) *count = n;
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_set_profiling(lsn_ctx* c, unsigned event_mask) {
+  if (!c) return LSN_ERR_ARG;
+  LSN_GUARD_BEGIN
+  c->prof.resolve();
+  c->prof.mask = event_mask & ((1u << LSN_K_COUNT) - 1);
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_get_profile(lsn_ctx* c, int cls, long long* launches, long long* timed_launches,
+                    double* ms_total) {
+  if (!c || cls < 0 || cls >= LSN_K_COUNT) return LSN_ERR_ARG;
+  LSN_GUARD_BEGIN
+  c->prof.resolve();
+  if (launches) *launches = c->prof.launches[cls];
+  if (timed_launches) *timed_launches = c->prof.timed[cls];
+  if (ms_total) *ms_total = c->prof.ms[cls];
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_reset_profile(lsn_ctx* c) {
+  if (!c) return LSN_ERR_ARG;
+  LSN_GUARD_BEGIN
+  c->prof.reset();
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_get_state(lsn_ctx* c, double* z, double* q, double* v) {
+  if (!c) return LSN_ERR_ARG;
+  LSN_GUARD_BEGIN
+  int rc = prepare(c);
+  if (rc != LSN_OK) return rc;
+  if (z) download(z, &c->eng->sv->z[0], sizeof(double) * c->widths[0], c->stream);
+  if (q) download(q, c->q, sizeof(double) * c->n, c->stream);
+  if (v) download(v, c->v, sizeof(double) * c->n, c->stream);
+  ck(cudaStreamSynchronize(c->stream));
+  return LSN_OK;
   LSN_GUARD_END
 }
 

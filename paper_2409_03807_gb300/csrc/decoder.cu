@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(NT) last_jac_kernel(const Real* __restrict__ W
     else pi[q] = pj[q] = -1;
     kacc[q] = 0.0;
   }
-  double gacc = 0.0, eacc = 0.0, eabs = 0.0;
+  double gacc = 0.0, gabs = 0.0, eacc = 0.0, eabs = 0.0;
   const int ntiles = (M + BM - 1) / BM;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int m0 = tile * BM;
@@ -239,9 +239,14 @@ __global__ void __launch_bounds__(NT) last_jac_kernel(const Real* __restrict__ W
       J_out[(size_t)(m0 + row) * r + c] = Os[row * OS + 1 + c];
     }
     if (t < r) {
-      double s = 0.0;
-      for (int row = 0; row < rows; ++row) s += gvs[row] * (double)Os[row * OS + 1 + t];
+      double s = 0.0, a = 0.0;
+      for (int row = 0; row < rows; ++row) {
+        const double term = gvs[row] * (double)Os[row * OS + 1 + t];
+        s += term;
+        a += fabs(term);
+      }
       gacc += s;
+      gabs += a;
     }
 #pragma unroll
     for (int q = 0; q < PQ; ++q) {
@@ -271,10 +276,13 @@ __global__ void __launch_bounds__(NT) last_jac_kernel(const Real* __restrict__ W
     prow[0] = red[0];
     prow[1] = red[NT];
   }
-  if (t < r) prow[2 + t] = gacc;
+  if (t < r) {
+    prow[slot_g(t)] = gacc;
+    prow[slot_gabs(r, t)] = gabs;
+  }
 #pragma unroll
   for (int q = 0; q < PQ; ++q)
-    if (pi[q] >= 0) prow[2 + r + t + NT * q] = kacc[q];
+    if (pi[q] >= 0) prow[slot_K(r) + t + NT * q] = kacc[q];
 }
 
 template <typename Real>

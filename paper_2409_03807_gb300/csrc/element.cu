@@ -4,13 +4,27 @@
 //
 // For tet e with displacement gradient Hd = F - I = [u1-u0, u2-u0, u3-u0] Dm^-1
 // the kernel evaluates (w_e V_e times) the energy density, its first
-// derivative P and the 9x9 second derivative A = d2Psi/dF2, projects A onto
-// the PSD cone by a cyclic Jacobi eigen-decomposition (clamping negative
-// eigenvalues), and accumulates
+// derivative P and the eigen-decomposition of the 9x9 second derivative
+// A = d2Psi/dF2, clamps negative eigenvalues (PSD projection), and
+// accumulates
 //     g += G_e^T p_e,            p_e = w_e V_e vec(P)
 //     K += C_e^T C_e,            C_e = diag(sqrt(w_e V_e lambda_+)) Q^T G_e
 // where G_e = dvec(F)/dz = B_e J_e (9 x r) is formed from the tet's four
 // vertex rows of J, so that C_e^T C_e = w_e J_e^T Hproj_e J_e.
+//
+// Eigen-decomposition.  Psi depends on F only through I2 = |F|^2 and
+// I3 = det F, so with the rotation-signed SVD F = U diag(s) V^T the 9
+// eigenvectors of A are U M V^T for
+//   twist  M = (e_j e_k^T - e_k e_j^T)/sqrt2:  lambda = 2 Psi_2 + Psi_3 s_i
+//   flip   M = (e_j e_k^T + e_k e_j^T)/sqrt2:  lambda = 2 Psi_2 - Psi_3 s_i
+// ((i, j, k) a permutation of (0, 1, 2)) and M = diag(a) for the three
+// eigenvectors a of the 3x3 matrix
+//   A_s = 2 Psi_2 I + 4 Psi_22 s s^T + Psi_33 pi pi^T + Psi_3 S,
+// pi_i = s_j s_k, S_jk = s_i (j != k), S_ii = 0, where Psi_2, Psi_3, Psi_22,
+// Psi_33 are the partial derivatives in (I2, I3) (Psi_23 = 0 here).  This
+// follows from d2/dt2 det(diag(s) + t M) and the invariance of Psi; the SVD
+// comes from a Jacobi eigen-decomposition of F^T F.  The coordinates of a
+// perturbation dF along these eigenvectors are read from R = U^T dF V.
 //
 // The density is written in terms of Hd (no cancellation near rest):
 //   Psi = mu/2 (Ic-3) - mu/2 log1p((Ic-3)/4) + lam/2 (J-1)(J-1 + 2(1-a))
@@ -37,11 +51,11 @@ constexpr int CB = 16;   // tets per contraction batch
 
 template <typename Real>
 struct Consts {
-  static constexpr int sweeps = 8;
+  static constexpr int sweeps = 10;
 };
 template <>
 struct Consts<double> {
-  static constexpr int sweeps = 12;
+  static constexpr int sweeps = 16;
 };
 
 template <typename Real>
@@ -52,9 +66,6 @@ template <typename Real>
 __device__ __forceinline__ Real log1p_r(Real x) { return log1p(x); }
 template <>
 __device__ __forceinline__ float log1p_r<float>(float x) { return log1pf(x); }
-
-// Levi-Civita sign of (i, k, 3-i-k) for i != k.
-__host__ __device__ constexpr int eps2(int i, int k) { return (k == (i + 1) % 3) ? 1 : -1; }
 
 template <typename Real>
 struct Invariants {
@@ -96,68 +107,153 @@ __device__ __forceinline__ Real snh_psi(const Invariants<Real>& iv, Real mu, Rea
          Real(0.5) * lam * iv.Jm1 * (iv.Jm1 + Real(2) * oma);
 }
 
-// Cyclic Jacobi eigen-decomposition of the symmetric 9x9 matrix A (in place:
+// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix A (in place:
 // A becomes diagonal), accumulating the rotations in Q (A_in = Q diag Q^T).
 template <typename Real>
-__device__ __forceinline__ void jacobi9(Real (&A)[9][9], Real (&Q)[9][9]) {
+__device__ __forceinline__ void jacobi3(Real (&A)[3][3], Real (&Q)[3][3]) {
 #pragma unroll
-  for (int i = 0; i < 9; ++i)
+  for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 9; ++j) Q[i][j] = (i == j) ? Real(1) : Real(0);
+    for (int j = 0; j < 3; ++j) Q[i][j] = (i == j) ? Real(1) : Real(0);
   const Real tiny = sizeof(Real) == 4 ? Real(1e-30) : Real(1e-300);
+  const Real rel = sizeof(Real) == 4 ? Real(1e-15) : Real(1e-32);
 #pragma unroll 1
   for (int sweep = 0; sweep < Consts<Real>::sweeps; ++sweep) {
-    Real off = Real(0), dia = Real(0);
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-      dia += A[p][p] * A[p][p];
-#pragma unroll
-      for (int q = p + 1; q < 9; ++q) off += A[p][q] * A[p][q];
-    }
-    const Real rel = sizeof(Real) == 4 ? Real(1e-14) : Real(1e-30);
+    const Real off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    const Real dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
     if (off <= rel * dia + tiny) break;
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+      const Real apq = A[p][q];
+      if (fabs(apq) > tiny) {
+        const Real theta = (A[q][q] - A[p][p]) / (Real(2) * apq);
+        const Real at = fabs(theta);
+        Real t = (at > Real(1e15)) ? Real(0.5) / at
+                                   : Real(1) / (at + sqrt_r<Real>(theta * theta + Real(1)));
+        if (theta < Real(0)) t = -t;
+        const Real c = Real(1) / sqrt_r<Real>(t * t + Real(1));
+        const Real s = t * c;
 #pragma unroll
-      for (int q = p + 1; q < 9; ++q) {
-        const Real apq = A[p][q];
-        if (fabs(apq) > tiny) {
-          const Real theta = (A[q][q] - A[p][p]) / (Real(2) * apq);
-          const Real at = fabs(theta);
-          Real t = (at > Real(1e15)) ? Real(0.5) / theta
-                                     : Real(1) / (at + sqrt_r<Real>(theta * theta + Real(1)));
-          if (theta < Real(0) && at <= Real(1e15)) t = -t;
-          const Real c = Real(1) / sqrt_r<Real>(t * t + Real(1));
-          const Real s = t * c;
+        for (int k = 0; k < 3; ++k) {
+          const Real akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
 #pragma unroll
-          for (int k = 0; k < 9; ++k) {
-            const Real akp = A[k][p], akq = A[k][q];
-            A[k][p] = c * akp - s * akq;
-            A[k][q] = s * akp + c * akq;
-          }
+        for (int k = 0; k < 3; ++k) {
+          const Real apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        A[p][q] = Real(0);
+        A[q][p] = Real(0);
 #pragma unroll
-          for (int k = 0; k < 9; ++k) {
-            const Real apk = A[p][k], aqk = A[q][k];
-            A[p][k] = c * apk - s * aqk;
-            A[q][k] = s * apk + c * aqk;
-          }
-          A[p][q] = Real(0);
-          A[q][p] = Real(0);
-#pragma unroll
-          for (int k = 0; k < 9; ++k) {
-            const Real qkp = Q[k][p], qkq = Q[k][q];
-            Q[k][p] = c * qkp - s * qkq;
-            Q[k][q] = s * qkp + c * qkq;
-          }
+        for (int k = 0; k < 3; ++k) {
+          const Real qkp = Q[k][p], qkq = Q[k][q];
+          Q[k][p] = c * qkp - s * qkq;
+          Q[k][q] = s * qkp + c * qkq;
         }
       }
     }
   }
 }
 
+// Rotation-signed SVD F = U diag(sig) V^T with det U = det V = +1 (sig[i]
+// may be negative for an inverted element).
+template <typename Real>
+__device__ __forceinline__ void svd3(const Real (&F)[3][3], Real (&U)[3][3], Real (&sig)[3],
+                                     Real (&V)[3][3]) {
+  Real S[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) S[a][b] = F[0][a] * F[0][b] + F[1][a] * F[1][b] + F[2][a] * F[2][b];
+  jacobi3<Real>(S, V);
+  const Real detV = V[0][0] * (V[1][1] * V[2][2] - V[1][2] * V[2][1]) -
+                    V[0][1] * (V[1][0] * V[2][2] - V[1][2] * V[2][0]) +
+                    V[0][2] * (V[1][0] * V[2][1] - V[1][1] * V[2][0]);
+  if (detV < Real(0)) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) V[k][2] = -V[k][2];
+  }
+  // largest, middle, smallest of the squared singular values
+  const Real d0 = S[0][0], d1 = S[1][1], d2 = S[2][2];
+  int i0 = 0, i1 = 1, i2 = 2;
+  if (d1 > d0) { i0 = 1; i1 = 0; }
+  if (d2 > (i0 == 0 ? d0 : d1)) { i2 = i1; i1 = i0; i0 = 2; }
+  else if (d2 > (i1 == 0 ? d0 : (i1 == 1 ? d1 : d2))) { i2 = i1; i1 = 2; }
+  Real FV[3][3];  // columns F v_i
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) FV[a][i] = F[a][0] * V[0][i] + F[a][1] * V[1][i] + F[a][2] * V[2][i];
+  Real u0[3], u1[3], u2[3];
+  const Real tiny = sizeof(Real) == 4 ? Real(1e-30) : Real(1e-300);
+  Real n0 = Real(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    u0[a] = FV[a][i0];
+    n0 += u0[a] * u0[a];
+  }
+  if (n0 > tiny) {
+    n0 = Real(1) / sqrt_r<Real>(n0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u0[a] *= n0;
+  } else {
+    u0[0] = Real(1); u0[1] = Real(0); u0[2] = Real(0);
+  }
+  Real dp = Real(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dp += u0[a] * FV[a][i1];
+  Real n1 = Real(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    u1[a] = FV[a][i1] - dp * u0[a];
+    n1 += u1[a] * u1[a];
+  }
+  if (n1 > tiny * Real(1e6)) {
+    n1 = Real(1) / sqrt_r<Real>(n1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u1[a] *= n1;
+  } else {  // any unit vector orthogonal to u0
+    const int k = fabs(u0[0]) < Real(0.6) ? 0 : (fabs(u0[1]) < Real(0.6) ? 1 : 2);
+    Real e[3] = {Real(0), Real(0), Real(0)};
+    e[k] = Real(1);
+    const Real ue = u0[k];
+    Real nn = Real(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      u1[a] = e[a] - ue * u0[a];
+      nn += u1[a] * u1[a];
+    }
+    nn = Real(1) / sqrt_r<Real>(nn);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u1[a] *= nn;
+  }
+  // u2 = +-(u0 x u1) so that det[U] = +1 with columns placed at i0, i1, i2
+  const bool even = (i0 == 0 && i1 == 1) || (i0 == 1 && i1 == 2) || (i0 == 2 && i1 == 0);
+  const Real sg = even ? Real(1) : Real(-1);
+  u2[0] = sg * (u0[1] * u1[2] - u0[2] * u1[1]);
+  u2[1] = sg * (u0[2] * u1[0] - u0[0] * u1[2]);
+  u2[2] = sg * (u0[0] * u1[1] - u0[1] * u1[0]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    U[a][i0] = u0[a];
+    U[a][i1] = u1[a];
+    U[a][i2] = u2[a];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    sig[i] = U[0][i] * FV[0][i] + U[1][i] * FV[1][i] + U[2][i] * FV[2][i];
+}
+
 template <typename Real>
 struct ElemTile {  // shared memory of one tile
-  Real L[ET][81];
+  Real U[ET][9];    // U of the signed SVD (row-major)
+  Real V[ET][9];    // V of the signed SVD (row-major)
+  Real As[ET][9];   // row m: sqrt(w V lambda_s,m+) a_m (scaling modes)
+  Real tf[ET][6];   // sqrt(w V lambda+ / 2) of the 3 twist, then 3 flip modes
   Real D[ET][12];
   Real p[ET][9];
   int4 v[ET];
@@ -227,7 +323,7 @@ __global__ void __launch_bounds__(ET) element_full_kernel(ElemArgs ea,
     else pi[q] = pj[q] = -1;
     kacc[q] = 0.0;
   }
-  double gacc = 0.0, eacc = 0.0, eabs = 0.0;
+  double gacc = 0.0, gabs = 0.0, eacc = 0.0, eabs = 0.0;
   const int ntiles = (ea.S + ET - 1) / ET;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     // ---------------- phase 1: element math, one tet per thread
@@ -256,38 +352,41 @@ __global__ void __launch_bounds__(ET) element_full_kernel(ElemArgs ea,
                              (H[i][j] + H[j][i] - (i == j ? iv.trH : Real(0)) - iv.cofH[i][j]);
           tl.p[t][3 * i + j] = wv * P;
         }
-      // second derivative A (9x9, row-major vec)
-      Real A[9][9];
-      const Real c1 = mu * Ic / (Ic + Real(1));
-      const Real c2 = Real(2) * mu / ((Ic + Real(1)) * (Ic + Real(1)));
-      const Real c3 = lam * (iv.Jm1 + oma);  // lam (J - a)
+      // eigen-decomposition of the second derivative (see header)
+      const Real c1 = mu * Ic / (Ic + Real(1));                   // 2 Psi_2
+      const Real c2 = Real(2) * mu / ((Ic + Real(1)) * (Ic + Real(1)));  // 4 Psi_22
+      const Real c3 = lam * (iv.Jm1 + oma);                       // Psi_3 = lam (J - a)
+      Real F[3][3], U[3][3], V[3][3], sg[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) F[i][j] = H[i][j] + (i == j ? Real(1) : Real(0));
+      svd3<Real>(F, U, sg, V);
+      Real As[3][3], Aq[3][3];
+      const Real pi3[3] = {sg[1] * sg[2], sg[0] * sg[2], sg[0] * sg[1]};
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
+          As[i][j] = c2 * sg[i] * sg[j] + lam * pi3[i] * pi3[j] +
+                     (i == j ? c1 : c3 * sg[3 - i - j]);
+      jacobi3<Real>(As, Aq);
 #pragma unroll
-          for (int k = 0; k < 3; ++k)
+      for (int m = 0; m < 3; ++m) {
+        const Real sc = sqrt_r<Real>(wv * (As[m][m] > Real(0) ? As[m][m] : Real(0)));
 #pragma unroll
-            for (int l = 0; l < 3; ++l) {
-              const Real Fij = H[i][j] + (i == j ? Real(1) : Real(0));
-              const Real Fkl = H[k][l] + (k == l ? Real(1) : Real(0));
-              Real val = c2 * Fij * Fkl + lam * iv.cof[i][j] * iv.cof[k][l];
-              if (i == k && j == l) val += c1;
-              if (i != k && j != l) {
-                const int m = 3 - i - k, n = 3 - j - l;
-                const Real Fmn = H[m][n] + (m == n ? Real(1) : Real(0));
-                val += c3 * Real(eps2(i, k) * eps2(j, l)) * Fmn;
-              }
-              A[3 * i + j][3 * k + l] = val;
-            }
-      Real Q[9][9];
-      jacobi9<Real>(A, Q);
+        for (int i = 0; i < 3; ++i) tl.As[t][3 * m + i] = sc * Aq[i][m];
+      }
 #pragma unroll
-      for (int m = 0; m < 9; ++m) {
-        const Real lp = A[m][m] > Real(0) ? A[m][m] : Real(0);
-        const Real sc = sqrt_r<Real>(wv * lp);
+      for (int i = 0; i < 3; ++i) {
+        const Real lt = c1 + c3 * sg[i], lf = c1 - c3 * sg[i];
+        tl.tf[t][i] = sqrt_r<Real>(Real(0.5) * wv * (lt > Real(0) ? lt : Real(0)));
+        tl.tf[t][3 + i] = sqrt_r<Real>(Real(0.5) * wv * (lf > Real(0) ? lf : Real(0)));
+      }
 #pragma unroll
-        for (int k = 0; k < 9; ++k) tl.L[t][9 * m + k] = sc * Q[k][m];
+      for (int k = 0; k < 9; ++k) {
+        tl.U[t][k] = U[k / 3][k % 3];
+        tl.V[t][k] = V[k / 3][k % 3];
       }
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
@@ -298,7 +397,9 @@ __global__ void __launch_bounds__(ET) element_full_kernel(ElemArgs ea,
       tl.v[t] = tv;
     } else {
 #pragma unroll
-      for (int k = 0; k < 81; ++k) tl.L[t][k] = Real(0);
+      for (int k = 0; k < 9; ++k) tl.U[t][k] = tl.V[t][k] = tl.As[t][k] = Real(0);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) tl.tf[t][k] = Real(0);
 #pragma unroll
       for (int k = 0; k < 12; ++k) tl.D[t][k] = Real(0);
 #pragma unroll
@@ -335,12 +436,29 @@ __global__ void __launch_bounds__(ET) element_full_kernel(ElemArgs ea,
             }
 #pragma unroll
           for (int k = 0; k < 9; ++k) gp += tl.p[q][k] * G[k];
+          // R = U^T dF V with dF = G as a 3x3 matrix
+          Real T3[3][3], R[3][3];
 #pragma unroll
-          for (int m = 0; m < 9; ++m) {
-            Real s = Real(0);
+          for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int k = 0; k < 9; ++k) s += tl.L[q][9 * m + k] * G[k];
-            Cv[m] = s;
+            for (int b = 0; b < 3; ++b)
+              T3[i][b] = G[3 * i] * tl.V[q][b] + G[3 * i + 1] * tl.V[q][3 + b] +
+                         G[3 * i + 2] * tl.V[q][6 + b];
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+              R[a][b] = tl.U[q][a] * T3[0][b] + tl.U[q][3 + a] * T3[1][b] +
+                        tl.U[q][6 + a] * T3[2][b];
+#pragma unroll
+          for (int m = 0; m < 3; ++m)
+            Cv[m] = tl.As[q][3 * m] * R[0][0] + tl.As[q][3 * m + 1] * R[1][1] +
+                    tl.As[q][3 * m + 2] * R[2][2];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const int j = (i + 1) % 3, k = (i + 2) % 3;
+            Cv[3 + i] = tl.tf[q][i] * (R[j][k] - R[k][j]);
+            Cv[6 + i] = tl.tf[q][3 + i] * (R[j][k] + R[k][j]);
           }
         } else {
 #pragma unroll
@@ -352,9 +470,13 @@ __global__ void __launch_bounds__(ET) element_full_kernel(ElemArgs ea,
       }
       __syncthreads();
       if (t < r) {
-        double s = 0.0;
-        for (int lt = 0; lt < nb; ++lt) s += (double)Gp[lt * r + t];
+        double s = 0.0, a = 0.0;
+        for (int lt = 0; lt < nb; ++lt) {
+          s += (double)Gp[lt * r + t];
+          a += fabs((double)Gp[lt * r + t]);
+        }
         gacc += s;
+        gabs += a;
       }
       const int rows = nb * 9;
 #pragma unroll
@@ -383,10 +505,13 @@ __global__ void __launch_bounds__(ET) element_full_kernel(ElemArgs ea,
     prow[0] = red[0];
     prow[1] = red[ET];
   }
-  if (t < r) prow[2 + t] = gacc;
+  if (t < r) {
+    prow[slot_g(t)] = gacc;
+    prow[slot_gabs(r, t)] = gabs;
+  }
 #pragma unroll
   for (int q = 0; q < PQ; ++q)
-    if (pi[q] >= 0) prow[2 + r + t + ET * q] = kacc[q];
+    if (pi[q] >= 0) prow[slot_K(r) + t + ET * q] = kacc[q];
 }
 
 // Energy of k trial displacement fields ut[j * n + .] for every cubature tet.

@@ -10,11 +10,17 @@ namespace lsn {
 constexpr int RMAX = 64;           // largest subspace dimension
 constexpr int KTRIAL = 4;          // line-search step lengths evaluated per pass
 constexpr int GEMM_BK = 32;        // k-chunk of the decoder GEMM tiles
+constexpr int TRACE = 128;         // Newton iterations kept in the solve trace
 
 // Number of upper-triangle entries of an r x r symmetric matrix.
 __host__ __device__ inline int npairs(int r) { return r * (r + 1) / 2; }
-// Slots of one reduced-system partial: E, sum |E terms|, g[r], K upper.
-__host__ __device__ inline int nslots(int r) { return 2 + r + npairs(r); }
+// Slots of one reduced-system partial: E, sum |E terms|, g[r], gabs[r]
+// (sum of |contributions| per gradient entry: the rounding scale of g), K
+// upper triangle (row-major, i <= j).
+__host__ __device__ inline int nslots(int r) { return 2 + 2 * r + npairs(r); }
+__host__ __device__ inline int slot_g(int i) { return 2 + i; }
+__host__ __device__ inline int slot_gabs(int r, int i) { return 2 + r + i; }
+__host__ __device__ inline int slot_K(int r) { return 2 + 2 * r; }
 
 // Device-resident Newton / line-search state (one per context).
 struct DevSolver {
@@ -24,15 +30,21 @@ struct DevSolver {
   double E, Eabs;      // energy at z and sum of |terms| (rounding scale)
   double gd;           // g . d
   double grad_inf;     // ||g||_inf at z
+  double gabs_max;     // max_i of the rounding scale of g_i
+  double g_best;       // smallest ||g||_inf of this solve
+  int stall;           // iterations since ||g||_inf last halved
   double alpha_base;   // step length of trial 0 of the current batch
   double alpha_taken;  // accepted step length
   double tol, armijo_c, eta_scale;
+  double floor_scale;  // kappa * unit roundoff of the element precision
   int r, max_ls;
   int status;          // -1 running, else lsn_status of the solve
   int iters, ls_trials;
   int ls_iter;         // trials spent in the current line search
   int accepted;        // line search of this iteration accepted a step
   int eval_only;       // direction kernel only reduces (parity hook)
+  // per-iteration history of the current solve (first TRACE iterations)
+  double trace_g[TRACE], trace_E[TRACE], trace_gabs[TRACE], trace_alpha[TRACE];
 };
 
 // ---------------------------------------------------------------- launchers
@@ -41,6 +53,8 @@ void launch_rest_shape(const double* X0, const int4* tets, int ne,
                        double* dminv, double* vol, int* bad, cudaStream_t s);
 void launch_lumped_mass(const int* adj_ptr, const int* adj_tet, const double* vol,
                         int nv, double rho, double* mass, cudaStream_t s);
+void launch_constraint_disp(const int* cidx, const double* targets, const double* X0, int nc,
+                            double* cu, cudaStream_t s);
 template <typename Real>
 void launch_gather_cubature(const int4* tets, const double* dminv, const double* vol,
                             const int* idx, const double* w, int s_cnt, int ne,

@@ -56,6 +56,17 @@ __global__ void lumped_mass_kernel(const int* __restrict__ adj_ptr,
   mass[v] = m;
 }
 
+// Displacement targets of the constrained vertices: cu = target - X0.
+__global__ void constraint_disp_kernel(const int* __restrict__ cidx,
+                                       const double* __restrict__ targets,
+                                       const double* __restrict__ X0, int nc,
+                                       double* __restrict__ cu) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * nc) return;
+  const int v = cidx[i / 3], k = i % 3;
+  cu[i] = targets[i] - X0[3 * v + k];
+}
+
 template <typename Real>
 __global__ void gather_cubature_kernel(const int4* __restrict__ tets,
                                        const double* __restrict__ dminv,
@@ -93,6 +104,12 @@ void launch_lumped_mass(const int* adj_ptr, const int* adj_tet, const double* vo
   if (nv <= 0) return;
   lumped_mass_kernel<<<(nv + 255) / 256, 256, 0, s>>>(adj_ptr, adj_tet, vol, nv, rho,
                                                        mass);
+}
+
+void launch_constraint_disp(const int* cidx, const double* targets, const double* X0, int nc,
+                            double* cu, cudaStream_t s) {
+  if (nc <= 0) return;
+  constraint_disp_kernel<<<(3 * nc + 255) / 256, 256, 0, s>>>(cidx, targets, X0, nc, cu);
 }
 
 template <typename Real>

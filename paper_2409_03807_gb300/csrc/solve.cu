@@ -49,13 +49,14 @@ __global__ void __launch_bounds__(ST) newton_direction_kernel(DevSolver* sv,
   const int r = sv->r;
   if (sv->status != -1) return;
   // g and the symmetric K (upper triangle in sys) from the reduced partial sums
-  const double* Ku = sys + 2 + r;
-  for (int i = t; i < r; i += ST) g[i] = sys[2 + i];
+  const double* Ku = sys + slot_K(r);
+  for (int i = t; i < r; i += ST) g[i] = sys[slot_g(i)];
   __syncthreads();
-  double gm = 0.0;
+  double gm = 0.0, ga = 0.0;
   bool finite = true;
   for (int i = t; i < r; i += ST) {
     gm = fmax(gm, fabs(g[i]));
+    ga = fmax(ga, sys[slot_gabs(r, i)]);
     finite = finite && isfinite(g[i]);
   }
   for (int e = t; e < npairs(r); e += ST) finite = finite && isfinite(Ku[e]);
@@ -66,14 +67,42 @@ __global__ void __launch_bounds__(ST) newton_direction_kernel(DevSolver* sv,
     __syncthreads();
   }
   const double ginf = red[0];
+  __syncthreads();
+  red[t] = ga;
+  __syncthreads();
+  for (int s = ST / 2; s > 0; s >>= 1) {
+    if (t < s) red[t] = fmax(red[t], red[t + s]);
+    __syncthreads();
+  }
+  const double gabs_max = red[0];
   const double E = sys[0];
   __syncthreads();
+  // progress bookkeeping for the precision-floor exit
+  __shared__ int stall;
   if (t == 0) {
     sv->E = E;
     sv->Eabs = sys[1];
     sv->grad_inf = ginf;
+    sv->gabs_max = gabs_max;
+    if (!sv->eval_only) {
+      if (sv->iters < TRACE) {
+        sv->trace_g[sv->iters] = ginf;
+        sv->trace_E[sv->iters] = E;
+        sv->trace_gabs[sv->iters] = gabs_max;
+        sv->trace_alpha[sv->iters] = 0.0;
+      }
+      if (ginf <= 0.5 * sv->g_best) {
+        sv->g_best = ginf;
+        sv->stall = 0;
+      } else {
+        sv->g_best = fmin(sv->g_best, ginf);
+        sv->stall += 1;
+      }
+    }
+    stall = sv->stall;
   }
   for (int i = t; i < r; i += ST) sv->g[i] = g[i];
+  __syncthreads();
   if (sv->eval_only) return;
   if (ginf < 0.0 || !isfinite(E)) {
     if (t == 0) sv->status = -3;  // LSN_ERR_NONFINITE
@@ -81,6 +110,12 @@ __global__ void __launch_bounds__(ST) newton_direction_kernel(DevSolver* sv,
   }
   if (ginf < sv->tol) {
     if (t == 0) sv->status = 0;  // LSN_OK
+    return;
+  }
+  // ||g|| has stopped decreasing and is within the rounding scale of its own
+  // evaluation: further iterations cannot be resolved at this precision
+  if (stall >= 4 && ginf <= sv->floor_scale * gabs_max) {
+    if (t == 0) sv->status = 4;  // LSN_PRECISION_FLOOR
     return;
   }
   if (sv->iters >= max_newton) {
@@ -190,6 +225,7 @@ __global__ void ls_select_kernel(DevSolver* sv, const double* __restrict__ sys_t
         sv->alpha_base = ldexp(sv->alpha_base, -KTRIAL);
       }
     } else {
+      if (sv->iters < TRACE) sv->trace_alpha[sv->iters] = ldexp(sv->alpha_base, -acc);
       sv->accepted = 1;
       sv->iters += 1;
     }

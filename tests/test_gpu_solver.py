@@ -133,3 +133,34 @@ def test_bar_twist_first_steps_match_oracle(pkg):
         err = rel(ctx.get_positions() - p.X0.ravel(), sim.q - p.X0.ravel())
         assert err < 1e-4, (k, err)
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_large_deformation_projection(pkg, prec):
+    """Large z: strongly stretched / compressed / inverted tets, so the
+    projection clamps many eigenvalues (analytic eigensystem on the GPU vs
+    numeric eigh in the oracle)."""
+    p = build_problem("tiny_dyn")
+    m = model_from_problem(p)
+    ctx = pkg.context_from_problem(p, precision=prec)
+    rng = np.random.default_rng(21)
+    tg = p.targets(p.config.motion_frames)
+    ctx.set_constraints(None, tg)
+    m.set_targets(tg)
+    m.set_dynamics(0.0, None)
+    ctx.set_dynamics(0.0)
+    nclamped = 0
+    for trial in range(3):
+        z = rng.standard_normal(p.config.r) * 40.0
+        x, _ = m.positions_jac(z)
+        from oracle import fem, snh
+        F = fem.deformation_gradient(x.reshape(-1, 3), m.tets, m.DmInv)
+        nclamped += int(np.sum(np.linalg.eigvalsh(snh.d2psi_dF2(F, m.mu, m.lam)) < 0))
+        E, g, K = ctx.eval(z)
+        E_ref, g_ref, K_ref = m.eval(z)
+        t = TOL[prec]
+        assert abs(E - E_ref) <= t["E"] * max(1.0, abs(E_ref))
+        assert rel(g, g_ref) < t["g"]
+        assert rel(K, K_ref) < (t["K"] if prec == "fp64" else 5e-4)
+    assert nclamped > 0
+    ctx.close()
