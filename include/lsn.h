@@ -135,6 +135,14 @@ int lsn_set_decoder(lsn_ctx* ctx, int nlayers, const int* widths,
 int lsn_set_solver(lsn_ctx* ctx, double tol_inf, int max_newton, int max_ls,
                    double armijo_c);
 
+/* Execution of a solve: mode 0 (default) launches the whole Newton loop as
+ * one CUDA graph whose conditional WHILE node repeats an evaluation pass
+ * until the device-side solver stops it; mode 1 drives the same kernels from
+ * the host with one stream synchronisation per pass (used when kernel events
+ * are recorded, see lsn_set_profiling, which also selects mode 1 while an
+ * event mask is set). */
+int lsn_set_execution(lsn_ctx* ctx, int mode);
+
 /* Simulation state.  z (r, host or device) is the subspace coordinate;
  * q, v (n, host or device) the full-space positions and velocities used by
  * the inertial guess.  q == NULL sets q = x(z); v == NULL sets v = 0. */

@@ -187,7 +187,7 @@ def newton_solve(model, z0, eps, max_newton=1024, max_ls=128, c=1e-4,
         E, g, K = model.eval(z)
         gi = float(np.max(np.abs(g)))
         if trace is not None:
-            trace.append((E, gi))
+            trace.append([E, gi, 0.0])
         if gi < eps:
             status = CONVERGED
             break
@@ -208,6 +208,8 @@ def newton_solve(model, z0, eps, max_newton=1024, max_ls=128, c=1e-4,
         if not accepted:
             status = LS_FAILED
             break
+        if trace is not None:
+            trace[-1][2] = alpha
         z = z + alpha * d
     return z, SolveStats(status, it, ls_total, gi, E)
 

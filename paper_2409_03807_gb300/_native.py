@@ -59,6 +59,7 @@ _SIGS = {
                  ctypes.c_void_p],
     "lsn_decode": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "lsn_set_profiling": [ctypes.c_void_p, ctypes.c_uint],
+    "lsn_set_execution": [ctypes.c_void_p, ctypes.c_int],
     "lsn_get_trace": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)],
     "lsn_get_profile": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -243,6 +244,11 @@ class Context:
                                            _ptr(a), ctypes.byref(cnt)))
         k = cnt.value
         return {"grad_inf": g[:k], "energy": e[:k], "grad_scale": gs[:k], "alpha": a[:k]}
+
+    def set_execution(self, mode):
+        """'graph' (0, default) or 'host' (1)."""
+        m = {"graph": 0, "host": 1}.get(mode, mode)
+        return self._check(self.lib.lsn_set_execution(self.h, int(m)))
 
     def set_profiling(self, classes=()):
         mask = 0

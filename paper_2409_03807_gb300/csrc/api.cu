@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -134,12 +135,18 @@ struct Profiler {
 
 struct EngineBase {
   virtual ~EngineBase() {}
-  virtual void jac_pass() = 0;       // x, J, element, reduce, direction
-  virtual void trial_pass() = 0;     // k trial energies, reduce, Armijo select
-  virtual void finish(double dt) = 0;
+  // one evaluation pass (decoder, element, reduction, select_direction)
+  virtual void pass(cudaStream_t s, unsigned long long cond, int use_cond) = 0;
+  virtual void begin(int eval_only) = 0;   // reset the device solve state
+  virtual void finish(double dt) = 0;      // q, v from the positions at z
   virtual void decode_to_host(double* x, double* J) = 0;
+  virtual int kernels_per_pass() const = 0;
   DevSolver* sv = nullptr;
   double* sys = nullptr;
+  // CUDA graph of the whole solve loop (conditional WHILE node)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
 };
 
 }  // namespace
@@ -197,6 +204,8 @@ struct lsn_ctx {
   double E_const = 0.0;  // -sum m g . X0 in quasi-static solves
   int* cidx_dev = nullptr;  // constrained vertex indices
   Profiler prof;
+  bool use_graph = true;
+  long long passes_total = 0;
 };
 
 namespace {
@@ -205,15 +214,14 @@ namespace {
 template <typename Real>
 struct Engine : EngineBase {
   lsn_ctx* c;
-  int r, L, n, S, C;
+  int r, L, n, S, C, nj;
   std::vector<Real*> dW, db;
   Real *Z[2] = {nullptr, nullptr}, *Z0 = nullptr, *u = nullptr, *J = nullptr,
        *ut = nullptr;
   int4* ctets = nullptr;
   Real *cdminv = nullptr, *cwv = nullptr;
-  double *part_dec = nullptr, *part_el = nullptr, *part_dec_t = nullptr,
-         *part_el_t = nullptr, *sys_t = nullptr;
-  int grid_dec, grid_el, grid_dec_t, grid_el_t, ns;
+  double *part_dec = nullptr, *part_el = nullptr;
+  int grid_dec, gfull, genergy, nst;
   LastArgs la;
   ElemArgs ea;
 
@@ -223,8 +231,9 @@ struct Engine : EngineBase {
     L = (int)c->widths.size() - 1;
     n = c->n;
     S = c->S > 0 ? c->S : c->ne;
-    C = r + 1;
-    ns = nslots(r);
+    nj = r + 1;
+    C = nj + KTRIAL;
+    nst = nslots_total(r);
     int hmax = r;
     for (int w : c->widths) hmax = std::max(hmax, w);
     for (int l = 0; l < L; ++l) {
@@ -240,10 +249,12 @@ struct Engine : EngineBase {
                          s));
       ck(cudaStreamSynchronize(s));
     }
-    const int cmax = std::max(C, KTRIAL);
-    Z[0] = dalloc<Real>((size_t)cmax * hmax);
-    Z[1] = dalloc<Real>((size_t)cmax * hmax);
-    Z0 = dalloc<Real>((size_t)cmax * r);
+    const int CPs = zstride(C);
+    Z[0] = dalloc<Real>((size_t)CPs * hmax);
+    Z[1] = dalloc<Real>((size_t)CPs * hmax);
+    Z0 = dalloc<Real>((size_t)CPs * r);
+    ck(cudaMemsetAsync(Z[0], 0, sizeof(Real) * CPs * hmax, s));
+    ck(cudaMemsetAsync(Z[1], 0, sizeof(Real) * CPs * hmax, s));
     u = dalloc<Real>(n);
     J = dalloc<Real>((size_t)n * r);
     ut = dalloc<Real>((size_t)KTRIAL * n);
@@ -254,19 +265,13 @@ struct Engine : EngineBase {
                                  c->S > 0 ? c->cub_w : nullptr, S, c->ne, ctets, cdminv, cwv,
                                  s);
     grid_dec = decoder_last_grid(n, C, c->num_sms);
-    grid_dec_t = decoder_last_grid(n, KTRIAL, c->num_sms);
-    grid_el = element_full_grid(S, c->num_sms);
-    grid_el_t = element_energy_grid(S, c->num_sms);
-    part_dec = dalloc<double>((size_t)grid_dec * ns);
-    part_el = dalloc<double>((size_t)grid_el * ns);
-    part_dec_t = dalloc<double>((size_t)grid_dec_t * 2 * KTRIAL);
-    part_el_t = dalloc<double>((size_t)grid_el_t * 2 * KTRIAL);
-    ck(cudaMemsetAsync(part_dec_t, 0, sizeof(double) * grid_dec_t * 2 * KTRIAL, s));
-    ck(cudaMemsetAsync(part_el_t, 0, sizeof(double) * grid_el_t * 2 * KTRIAL, s));
-    sys = dalloc<double>(ns);
-    sys_t = dalloc<double>(2 * KTRIAL);
+    element_grids(S, r, c->num_sms, gfull, genergy);
+    part_dec = dalloc<double>((size_t)grid_dec * nst);
+    part_el = dalloc<double>((size_t)(gfull + genergy) * nst);
+    sys = dalloc<double>(nst);
     sv = dalloc<DevSolver>(1);
     ck(cudaMemsetAsync(sv, 0, sizeof(DevSolver), s));
+    ck(cudaMemsetAsync(Z0, 0, sizeof(Real) * CPs * r, s));
     la.n = n;
     la.r = r;
     la.scale = c->scale;
@@ -274,7 +279,7 @@ struct Engine : EngineBase {
     la.cu = c->cu;
     la.mass = c->mass;
     la.ubar = c->ubar;
-    la.inv_dt2 = 0.0;
+    la.inv_dt2 = &sv->inv_dt2;
     for (int i = 0; i < 3; ++i) la.grav[i] = c->grav[i];
     la.ground_h = c->ground_h;
     la.ground_k = c->ground_k;
@@ -285,15 +290,33 @@ struct Engine : EngineBase {
     ea.tets = ctets;
     ea.dminv = cdminv;
     ea.wv = cwv;
-    double mu = c->youngs / (2.0 * (1.0 + c->poisson));
-    double lam = c->youngs * c->poisson / ((1.0 + c->poisson) * (1.0 - 2.0 * c->poisson));
-    ea.mu = mu;
-    ea.lam = lam;
+    ea.mu = c->youngs / (2.0 * (1.0 + c->poisson));
+    ea.lam = c->youngs * c->poisson / ((1.0 + c->poisson) * (1.0 - 2.0 * c->poisson));
+    // solver controls
+    DevSolver h;
+    std::memset(&h, 0, sizeof(h));
+    h.tol = c->tol;
+    h.armijo_c = c->armijo_c;
+    const double unit = c->precision == LSN_PREC_FP64 ? 1.1102230246251565e-16
+                                                     : 5.960464477539063e-08;
+    // FP64: the plain Armijo test of the paper's line search.  Lower
+    // precisions accept a step whose energy rise stays within the rounding
+    // scale of the energy evaluation, so the solve can reach their floor.
+    h.eta_scale = c->precision == LSN_PREC_FP64 ? 0.0 : 8.0 * unit;
+    h.floor_scale = 64.0 * unit;
+    h.r = r;
+    h.max_ls = c->max_ls;
+    h.max_newton = c->max_newton;
+    h.status = -1;
+    ck(cudaMemcpyAsync(sv, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     ck(cudaStreamSynchronize(s));
     ck(cudaGetLastError());
   }
 
   ~Engine() override {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto p : dW) dfree(p);
     for (auto p : db) dfree(p);
     dfree(Z[0]);
@@ -307,69 +330,50 @@ struct Engine : EngineBase {
     dfree(cwv);
     dfree(part_dec);
     dfree(part_el);
-    dfree(part_dec_t);
-    dfree(part_el_t);
     dfree(sys);
-    dfree(sys_t);
     dfree(sv);
   }
 
-  void set_dynamics(double dt) { la.inv_dt2 = dt > 0.0 ? 1.0 / (dt * dt) : 0.0; }
+  int kernels_per_pass() const override { return (L - 1) + 4; }
 
-  // Layers 1..L-1 for `cols` columns starting from Z0; returns the buffer
-  // holding the last hidden activations.
-  const Real* hidden(bool jac, int cols) {
-    cudaStream_t s = c->stream;
+  void begin(int eval_only) override {
+    Profiler& P = c->prof;
+    P.begin(LSN_K_SOLVE);
+    launch_solve_begin<Real>(sv, Z0, C, eval_only, c->stream);
+    P.end(LSN_K_SOLVE);
+  }
+
+  // Layers 1..L-1 of the pass; returns the buffer with the last hidden layer.
+  const Real* hidden(cudaStream_t s, bool prof) {
     const Real* in = Z0;
     int cur = 0;
-    c->prof.begin(LSN_K_DECODER_HIDDEN, L - 1);
+    if (prof) c->prof.begin(LSN_K_DECODER_HIDDEN, L - 1);
     for (int l = 0; l < L - 1; ++l) {
-      int M = c->widths[l + 1], K = c->widths[l];
-      launch_decoder_layer<Real>(jac ? Epi::HiddenJac : Epi::HiddenVal, dW[l], db[l], M, K,
-                                 in, cols, Z[cur], M, nullptr, nullptr, nullptr, 0, la, 0, s);
+      const int M = c->widths[l + 1], K = c->widths[l];
+      launch_hidden_layer<Real>(dW[l], db[l], M, K, in, C, nj, Z[cur], s);
       in = Z[cur];
       cur ^= 1;
     }
-    c->prof.end(LSN_K_DECODER_HIDDEN);
+    if (prof) c->prof.end(LSN_K_DECODER_HIDDEN);
     return in;
   }
 
-  void jac_pass() override {
-    cudaStream_t s = c->stream;
+  void pass(cudaStream_t s, unsigned long long cond, int use_cond) override {
+    const bool prof = !use_cond;  // no event timing inside a captured graph
     Profiler& P = c->prof;
-    P.begin(LSN_K_SOLVE);
-    launch_write_jac_columns<Real>(sv, Z0, s);
-    P.end(LSN_K_SOLVE);
-    const Real* h = hidden(true, C);
-    P.begin(LSN_K_DECODER_LAST);
-    launch_decoder_layer<Real>(Epi::LastJac, dW[L - 1], db[L - 1], n, c->widths[L - 1], h, C,
-                               nullptr, 0, u, J, part_dec, ns, la, grid_dec, s);
-    P.end(LSN_K_DECODER_LAST);
-    P.begin(LSN_K_ELEMENT);
-    launch_element_full<Real>(ea, u, J, part_el, grid_el, s);
-    P.end(LSN_K_ELEMENT);
-    P.begin(LSN_K_SOLVE, 2);
-    launch_reduce_cols(part_dec, grid_dec, part_el, grid_el, ns, sys, s);
-    launch_newton_direction<Real>(sv, sys, Z0, c->max_newton, s);
-    P.end(LSN_K_SOLVE);
-  }
-
-  void trial_pass() override {
-    cudaStream_t s = c->stream;
-    Profiler& P = c->prof;
-    const Real* h = hidden(false, KTRIAL);
-    P.begin(LSN_K_DECODER_TRIAL);
-    launch_decoder_layer<Real>(Epi::LastVal, dW[L - 1], db[L - 1], n, c->widths[L - 1], h,
-                               KTRIAL, ut, n, nullptr, nullptr, part_dec_t, 2 * KTRIAL, la,
-                               grid_dec_t, s);
-    P.end(LSN_K_DECODER_TRIAL);
-    P.begin(LSN_K_ELEMENT_ENERGY);
-    launch_element_energy<Real>(ea, ut, KTRIAL, part_el_t, grid_el_t, s);
-    P.end(LSN_K_ELEMENT_ENERGY);
-    P.begin(LSN_K_SOLVE, 2);
-    launch_reduce_cols(part_dec_t, grid_dec_t, part_el_t, grid_el_t, 2 * KTRIAL, sys_t, s);
-    launch_ls_select<Real>(sv, sys_t, Z0, s);
-    P.end(LSN_K_SOLVE);
+    const Real* h = hidden(s, prof);
+    if (prof) P.begin(LSN_K_DECODER_LAST);
+    launch_last_layer<Real>(dW[L - 1], db[L - 1], n, c->widths[L - 1], h, C, nj, u, J, ut,
+                            part_dec, nst, la, grid_dec, s);
+    if (prof) P.end(LSN_K_DECODER_LAST);
+    if (prof) P.begin(LSN_K_ELEMENT);
+    launch_element<Real>(ea, u, J, ut, part_el, gfull, genergy, s);
+    if (prof) P.end(LSN_K_ELEMENT);
+    if (prof) P.begin(LSN_K_SOLVE, 2);
+    launch_reduce_partials(part_dec, grid_dec, part_el, gfull + genergy, gfull, nslots(r), nst,
+                           sys, s);
+    launch_select_direction<Real>(sv, sys, Z0, cond, use_cond, s);
+    if (prof) P.end(LSN_K_SOLVE);
   }
 
   void finish(double dt) override {
@@ -380,10 +384,8 @@ struct Engine : EngineBase {
 
   void decode_to_host(double* x, double* Jh) override {
     cudaStream_t s = c->stream;
-    launch_write_jac_columns<Real>(sv, Z0, s);
-    const Real* h = hidden(true, C);
-    launch_decoder_layer<Real>(Epi::LastJac, dW[L - 1], db[L - 1], n, c->widths[L - 1], h, C,
-                               nullptr, 0, u, J, part_dec, ns, la, grid_dec, s);
+    begin(1);
+    pass(s, 0, 0);
     std::vector<Real> hu(n), hJ;
     ck(cudaMemcpyAsync(hu.data(), u, n * sizeof(Real), cudaMemcpyDeviceToHost, s));
     if (Jh) {
@@ -435,34 +437,59 @@ int ensure_engine(lsn_ctx* c) {
   return LSN_OK;
 }
 
-void set_engine_dynamics(lsn_ctx* c, double dt) {
-  if (c->precision == LSN_PREC_FP64)
-    static_cast<Engine<double>*>(c->eng.get())->set_dynamics(dt);
-  else
-    static_cast<Engine<float>*>(c->eng.get())->set_dynamics(dt);
+// Build (once per engine) the CUDA graph of the solve loop: a conditional
+// WHILE node whose body is one evaluation pass; select_direction sets the
+// loop condition on the device, so a whole solve is one graph launch.
+void ensure_graph(lsn_ctx* c) {
+  EngineBase* e = c->eng.get();
+  if (e->exec) return;
+  if (!e->cap_stream) ck(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
+  ck(cudaGraphCreate(&e->graph, 0));
+  cudaGraphConditionalHandle h;
+  ck(cudaGraphConditionalHandleCreate(&h, e->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  ck(cudaGraphAddNode(&node, e->graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  ck(cudaStreamBeginCaptureToGraph(e->cap_stream, body, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeThreadLocal));
+  e->pass(e->cap_stream, (unsigned long long)h, 1);
+  cudaError_t launch_err = cudaGetLastError();
+  cudaGraph_t captured = nullptr;
+  cudaError_t err = cudaStreamEndCapture(e->cap_stream, &captured);
+  if (err == cudaSuccess) err = launch_err;
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&e->exec, e->graph, 0);
+  if (err != cudaSuccess) {  // leave no half-built graph behind
+    cudaGetLastError();
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    cudaGraphDestroy(e->graph);
+    e->exec = nullptr;
+    e->graph = nullptr;
+    throw CudaError{err};
+  }
 }
 
-// device-side solver fields that a new solve or evaluation starts from
-void reset_solver(lsn_ctx* c, int eval_only) {
-  DevSolver h;
-  std::memset(&h, 0, sizeof(h));
-  // z is kept on the device; copy everything except z
-  ck(cudaMemcpyAsync(&h.z[0], &c->eng->sv->z[0], sizeof(h.z), cudaMemcpyDeviceToHost,
-                     c->stream));
-  ck(cudaStreamSynchronize(c->stream));
-  h.tol = c->tol;
-  h.armijo_c = c->armijo_c;
-  h.eta_scale = c->precision == LSN_PREC_FP64 ? 8.0 * 1.1102230246251565e-16
-                                              : 8.0 * 5.960464477539063e-08;
-  h.floor_scale = c->precision == LSN_PREC_FP64 ? 64.0 * 1.1102230246251565e-16
-                                                : 64.0 * 5.960464477539063e-08;
-  h.g_best = 1e300;
-  h.r = c->widths[0];
-  h.max_ls = c->max_ls;
-  h.status = -1;
-  h.eval_only = eval_only;
-  ck(cudaMemcpyAsync(c->eng->sv, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
-  ck(cudaStreamSynchronize(c->stream));
+// One solve from the current device z: graph launch (default) or host loop
+// (when kernel-event profiling is on).
+void run_solve(lsn_ctx* c, int eval_only) {
+  EngineBase* e = c->eng.get();
+  cudaStream_t s = c->stream;
+  e->begin(eval_only);
+  if (c->prof.mask == 0 && c->use_graph) {
+    ensure_graph(c);
+    ck(cudaGraphLaunch(e->exec, s));
+  } else {
+    for (int guard = 0; guard < 4 * (c->max_newton + 2) * (c->max_ls + 2); ++guard) {
+      e->pass(s, 0, 0);
+      ck(cudaMemcpyAsync(c->pinned_status, &e->sv->running, sizeof(int),
+                         cudaMemcpyDeviceToHost, s));
+      ck(cudaStreamSynchronize(s));
+      if (!c->pinned_status[0]) break;
+    }
+  }
 }
 
 double quasi_static_constant(lsn_ctx* c) {
@@ -479,13 +506,6 @@ double quasi_static_constant(lsn_ctx* c) {
   for (int v = 0; v < c->nv; ++v)
     for (int k = 0; k < 3; ++k) s -= m[v] * c->grav[k] * X[3 * v + k];
   return s;
-}
-
-int read_status(lsn_ctx* c) {
-  ck(cudaMemcpyAsync(c->pinned_status, &c->eng->sv->status, sizeof(int),
-                     cudaMemcpyDeviceToHost, c->stream));
-  ck(cudaStreamSynchronize(c->stream));
-  return *c->pinned_status;
 }
 
 }  // namespace
@@ -764,6 +784,27 @@ int lsn_set_solver(lsn_ctx* c, double tol_inf, int max_newton, int max_ls, doubl
   c->max_newton = max_newton;
   c->max_ls = max_ls;
   c->armijo_c = armijo_c;
+  if (c->eng && !c->dirty) {  // update the controls of the live engine
+    try {
+      DevSolver* sv = c->eng->sv;
+      ck(cudaMemcpyAsync(&sv->tol, &c->tol, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      ck(cudaMemcpyAsync(&sv->armijo_c, &c->armijo_c, sizeof(double), cudaMemcpyHostToDevice,
+                         c->stream));
+      ck(cudaMemcpyAsync(&sv->max_ls, &c->max_ls, sizeof(int), cudaMemcpyHostToDevice,
+                         c->stream));
+      ck(cudaMemcpyAsync(&sv->max_newton, &c->max_newton, sizeof(int), cudaMemcpyHostToDevice,
+                         c->stream));
+      ck(cudaStreamSynchronize(c->stream));
+    } catch (const CudaError& ce) {
+      return cuda_fail(c, ce.e);
+    }
+  }
+  return LSN_OK;
+}
+
+int lsn_set_execution(lsn_ctx* c, int mode) {
+  if (!c || mode < 0 || mode > 1) return LSN_ERR_ARG;
+  c->use_graph = mode == 0;
   return LSN_OK;
 }
 
@@ -804,10 +845,8 @@ int lsn_set_state(lsn_ctx* c, const double* z, const double* q, const double* v)
   }
   if (q) {
     upload(c->q, q, sizeof(double) * c->n, s);
-  } else {
-    reset_solver(c, 1);
-    set_engine_dynamics(c, 0.0);
-    c->eng->jac_pass();
+  } else {  // q = x(z): one evaluation pass at z
+    run_solve(c, 1);
     c->eng->finish(0.0);
   }
   if (v) upload(c->v, v, sizeof(double) * c->n, s);
@@ -828,11 +867,14 @@ int lsn_set_dynamics(lsn_ctx* c, double dt, const double* qbar) {
   c->dt = dt;
   if (dt > 0.0) {
     if (!qbar) return fail(c, LSN_ERR_ARG, "set_dynamics: qbar missing");
-    // ubar = qbar - X0 on the device (the inertial-guess kernel with dt = 0)
+    // ubar = qbar - X0: the inertial-guess kernel with q = qbar, v = 0, g = 0
+    const double zero3[3] = {0.0, 0.0, 0.0};
     upload(c->ubar, qbar, sizeof(double) * c->n, c->stream);
-    launch_inertial_guess(c->X0, c->ubar, c->ubar, c->n, 0.0, c->grav, c->ubar, c->stream);
+    launch_begin_step(c->X0, c->ubar, c->ubar, c->n, 1e-300, zero3, c->ubar, c->eng->sv,
+                      c->stream);
   }
-  set_engine_dynamics(c, dt);
+  launch_begin_step(c->X0, nullptr, nullptr, c->n, dt, c->grav, c->ubar, c->eng->sv,
+                    c->stream);
   ck(cudaStreamSynchronize(c->stream));
   ck(cudaGetLastError());
   return LSN_OK;
@@ -851,8 +893,7 @@ int lsn_eval(lsn_ctx* c, const double* z, double* E, double* g, double* K) {
                        cudaMemcpyDeviceToHost, c->stream));
     ck(cudaStreamSynchronize(c->stream));
   }
-  reset_solver(c, 1);
-  c->eng->jac_pass();
+  run_solve(c, 1);
   std::vector<double> sys(nslots(r));
   ck(cudaMemcpyAsync(sys.data(), c->eng->sys, sizeof(double) * sys.size(),
                      cudaMemcpyDeviceToHost, c->stream));
@@ -904,47 +945,31 @@ int lsn_step(lsn_ctx* c, const double* z_in, double dt, double* z_out, lsn_stats
   }
   if (z_in) upload(&c->eng->sv->z[0], z_in, sizeof(double) * r, s);
   c->dt = dt;
-  if (dt > 0.0) {
-    c->prof.begin(LSN_K_SOLVE);
-    launch_inertial_guess(c->X0, c->q, c->v, c->n, dt, c->grav, c->ubar, s);
-    c->prof.end(LSN_K_SOLVE);
-  }
-  set_engine_dynamics(c, dt);
-  reset_solver(c, 0);
-  int status = -1;
-  for (int it = 0; it <= c->max_newton + 1; ++it) {
-    c->eng->jac_pass();
-    status = read_status(c);
-    if (status != -1) break;
-    // line search: batches of KTRIAL step lengths until one is accepted
-    for (int batch = 0; batch < (c->max_ls + KTRIAL - 1) / KTRIAL + 1; ++batch) {
-      c->eng->trial_pass();
-      // status, iters, ls_trials, ls_iter, accepted are adjacent ints
-      ck(cudaMemcpyAsync(c->pinned_status, &c->eng->sv->status, 5 * sizeof(int),
-                         cudaMemcpyDeviceToHost, s));
-      ck(cudaStreamSynchronize(s));
-      status = c->pinned_status[0];
-      const int acc = c->pinned_status[4];
-      if (acc || status != -1) break;
-    }
-    if (status != -1) break;
-  }
-  // the last Jacobian pass evaluated x at the final z
+  c->prof.begin(LSN_K_SOLVE);
+  launch_begin_step(c->X0, c->q, c->v, c->n, dt, c->grav, c->ubar, c->eng->sv, s);
+  c->prof.end(LSN_K_SOLVE);
+  run_solve(c, 0);
+  // the last pass evaluated the positions at the final z
   c->eng->finish(dt);
-  DevSolver h;
-  ck(cudaMemcpyAsync(&h, c->eng->sv, sizeof(DevSolver), cudaMemcpyDeviceToHost, s));
+  DevSolver h;  // summary: scalars and z (not the trace arrays)
+  const size_t summary = offsetof(DevSolver, z) + sizeof(h.z);
+  ck(cudaMemcpyAsync(&h, c->eng->sv, summary, cudaMemcpyDeviceToHost, s));
+  if (z_out && is_device_ptr(z_out))
+    ck(cudaMemcpyAsync(z_out, &c->eng->sv->z[0], sizeof(double) * r, cudaMemcpyDeviceToDevice,
+                       s));
   ck(cudaStreamSynchronize(s));
   ck(cudaGetLastError());
-  if (h.status < -1) {
-    return fail(c, h.status, "step: non-finite values in the reduced system");
-  }
-  if (z_out) {
-    if (is_device_ptr(z_out))
-      ck(cudaMemcpyAsync(z_out, &c->eng->sv->z[0], sizeof(double) * r, cudaMemcpyDeviceToDevice, s));
-    else
-      std::memcpy(z_out, h.z, sizeof(double) * r);
-    ck(cudaStreamSynchronize(s));
-  }
+  if (c->prof.mask == 0 && c->use_graph)  // launches inside the graph, counted per pass
+    for (int k = 0; k < LSN_K_COUNT; ++k) {
+      const long long per = k == LSN_K_DECODER_HIDDEN ? c->eng->kernels_per_pass() - 4
+                            : k == LSN_K_SOLVE        ? 2
+                            : (k == LSN_K_DECODER_LAST || k == LSN_K_ELEMENT) ? 1
+                                                                              : 0;
+      c->prof.launches[k] += per * h.passes;
+    }
+  c->passes_total += h.passes;
+  if (h.status < -1) return fail(c, h.status, "step: non-finite values in the reduced system");
+  if (z_out && !is_device_ptr(z_out)) std::memcpy(z_out, h.z, sizeof(double) * r);
   std::copy(h.z, h.z + r, c->z0.begin());
   auto t1 = std::chrono::steady_clock::now();
   if (stats) {

@@ -1,22 +1,29 @@
 // Decoder MLP with forward-mode Jacobian (the subspace map f_theta of
-// Sec. 3.1, differentiated as the paper's autodiff does, Sec. 5), FP32/FP64
-// CUDA-core form.
+// Sec. 3.1, differentiated forward as the paper's autodiff does, Sec. 5),
+// FP32/FP64 CUDA-core form.
 //
-// Every layer is one GEMM  out[c][m] = sum_k W[m][k] Z[c][k]  whose columns
-// c carry either the value and the r tangent directions (Jacobian pass,
-// C = r + 1 columns: Z_0 = [z | I_r]) or k independent values (line-search
-// pass, C = k columns: z + alpha_j d).  Column-major activations Z[c][k]
-// (leading dimension = layer width) keep both operands of the k-loop
-// contiguous.  Epilogues:
-//   HiddenJac  a = acc_0 + b,  h = ELU(a),  T_c = ELU'(a) acc_c
-//   HiddenVal  h_c = ELU(acc_c + b)
-//   LastJac    u = s (acc_0 + b), J_c = s acc_c, constrained rows replaced by
-//              target displacement / zero, then the per-row inertia, gravity
-//              and ground terms are folded into per-CTA partials of
-//              (E, sum|E|, g = J^T gv, K = J^T diag(kv) J)  (fixed order)
-//   LastVal    u_j = s (acc_j + b), constraints, per-trial energy partials.
+// Every layer is one skinny GEMM  out[m][c] = sum_k W[m][k] Z[k][c]  over C
+// columns (C <= 2 r + 4).  Columns c < nj carry the Jacobian pass: column 0
+// the value at the point y0 and columns 1..r the tangent directions
+// (Z_0 = [y0 | I_r]); columns c >= nj carry the line-search trial points y_j
+// (values only).  Activations are stored unit-major, Z[k][c] with a padded
+// column stride CPs (zstride(C)), so a layer's input tile is one contiguous
+// block.  Epilogues:
+//   hidden   value columns  h = ELU(acc + b);  tangent columns  ELU'(a0) acc
+//            with a0 = acc_0 + b of the same row
+//   output   u = s (acc_0 + b), J_c = s acc_c (constrained rows replaced by
+//            the target displacement and a zero row), folded into per-CTA
+//            partials of (E, sum|E|, g = J^T gv, sum|J gv|, K = J^T diag(kv) J)
+//            for the terms that act on each DOF alone (inertia, gravity,
+//            ground); trial columns give u_j and per-trial energy partials.
 // Positions are handled as displacements u = x - X0, and the inertia term as
 // u - (qbar - X0), so that FP32 arithmetic works on small numbers.
+//
+// Mapping: a CTA owns BM rows; KP = 8 consecutive lanes share a row and
+// take every eighth k, so a warp reads eight consecutive k of Z (one 16-byte
+// vector per lane, conflict-free for the padded stride) and four rows of W.
+// Tiles are staged with 16-byte cp.async (one load phase for k <= 256), and
+// the eight partial sums of a row are combined with three shuffles.
 #include "lsn_internal.cuh"
 
 #include <algorithm>
@@ -51,112 +58,175 @@ __device__ __forceinline__ void pair_of(int p, int r, int& i, int& j) {
   j = i + p;
 }
 
-constexpr int NT = 256;  // threads per CTA
-
-template <typename Real, int TN, int TM>
-struct Tile {
-  static constexpr int CP = 16 * TN;
-  static constexpr int BM = 16 * TM;
-  static constexpr int BK = GEMM_BK;
-  static constexpr int WS = BK * (BM + 1);
-  static constexpr int ZS = BK * CP;
+template <typename Real>
+struct KChunk {
+  static constexpr int BK = 256;  // k staged per phase
+};
+template <>
+struct KChunk<double> {
+  static constexpr int BK = 128;
 };
 
-// Accumulate the BM x CP tile at rows m0.. for all k.
-template <typename Real, int TN, int TM>
-__device__ __forceinline__ void gemm_tile(const Real* __restrict__ W, int M, int K,
-                                          const Real* __restrict__ Zin, int C, int m0,
-                                          Real* Ws, Real* Zs, Real (&acc)[TM][TN]) {
-  using T = Tile<Real, TN, TM>;
-  const int t = threadIdx.x, cg = t & 15, rg = t >> 4;
+// 16-byte asynchronous copy global -> shared (zero-filled when !valid).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n)
+               : "memory");
+}
+template <typename Real>
+__device__ __forceinline__ void cp_async_elem(Real* dst, const Real* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? (int)sizeof(Real) : 0;
+  if (sizeof(Real) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+constexpr int KP = 8;  // lanes (k-phases) per row
+
+// Shared-memory strides: W rows padded so that 4 rows x 8 k-phases hit 32
+// distinct banks; Z rows have the padded column stride CPs.
+template <typename Real>
+__host__ __device__ constexpr int w_stride() {
+  return KChunk<Real>::BK + (sizeof(Real) == 4 ? 8 : 4);
+}
+
+// acc[c] += sum over this lane's k (k = KP i + q) of W[row][k] Z[k][c] for
+// the CTA's BM rows; returns with the KP phases of a row NOT yet combined.
+template <typename Real, int CQ, int BM>
+__device__ __forceinline__ void skinny_gemm(const Real* __restrict__ W, int M, int K,
+                                            const Real* __restrict__ Zin, int CPs, int m0,
+                                            Real* Ws, Real* Zs, Real (&acc)[4 * CQ]) {
+  constexpr int NT = KP * BM, BK = KChunk<Real>::BK, WSs = w_stride<Real>();
+  constexpr int EV = 16 / sizeof(Real);  // elements per 16-byte chunk
+  const int t = threadIdx.x, q = t % KP, row = t / KP;
 #pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = Real(0);
-  for (int k0 = 0; k0 < K; k0 += T::BK) {
-    for (int e = t; e < T::BM * T::BK; e += NT) {
-      int row = e / T::BK, kk = e % T::BK, gr = m0 + row, gk = k0 + kk;
-      Ws[kk * (T::BM + 1) + row] = (gr < M && gk < K) ? W[(size_t)gr * K + gk] : Real(0);
+  for (int c = 0; c < 4 * CQ; ++c) acc[c] = Real(0);
+  const bool vecW = (K % EV) == 0;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    const int kw = min(BK, K - k0);
+    // W tile: BM rows x kw
+    if (vecW) {
+      const int nch = kw / EV;
+      for (int e = t; e < BM * nch; e += NT) {
+        const int rr = e / nch, ch = e - rr * nch, gr = m0 + rr;
+        const bool ok = gr < M;
+        cp_async16(&Ws[rr * WSs + ch * EV], W + (ok ? (size_t)gr * K + k0 + ch * EV : 0), ok);
+      }
+    } else {
+      for (int e = t; e < BM * kw; e += NT) {
+        const int rr = e / kw, kk = e - rr * kw, gr = m0 + rr;
+        const bool ok = gr < M;
+        cp_async_elem<Real>(&Ws[rr * WSs + kk], W + (ok ? (size_t)gr * K + k0 + kk : 0), ok);
+      }
     }
-    for (int e = t; e < T::CP * T::BK; e += NT) {
-      int c = e / T::BK, kk = e % T::BK, gk = k0 + kk;
-      Zs[kk * T::CP + c] = (c < C && gk < K) ? Zin[(size_t)c * K + gk] : Real(0);
+    // Z tile: kw rows x CPs, contiguous in global memory
+    {
+      const int nel = kw * CPs, nch = nel / EV;
+      const Real* src = Zin + (size_t)k0 * CPs;
+      for (int e = t; e < nch; e += NT) cp_async16(&Zs[e * EV], src + e * EV, true);
     }
+    cp_async_wait_all();
     __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < T::BK; ++kk) {
-      Real wv[TM], zv[TN];
+    const int ksteps = (kw - q + KP - 1) / KP;
+#pragma unroll 2
+    for (int i = 0; i < ksteps; ++i) {
+      const int kk = KP * i + q;
+      const Real w = Ws[row * WSs + kk];
+      const Real* zr = Zs + kk * CPs;
+      if (sizeof(Real) == 4) {
 #pragma unroll
-      for (int i = 0; i < TM; ++i) wv[i] = Ws[kk * (T::BM + 1) + rg + 16 * i];
+        for (int g = 0; g < CQ; ++g) {
+          const float4 z4 = *reinterpret_cast<const float4*>(zr + 4 * g);
+          acc[4 * g + 0] += w * (Real)z4.x;
+          acc[4 * g + 1] += w * (Real)z4.y;
+          acc[4 * g + 2] += w * (Real)z4.z;
+          acc[4 * g + 3] += w * (Real)z4.w;
+        }
+      } else {
 #pragma unroll
-      for (int j = 0; j < TN; ++j) zv[j] = Zs[kk * T::CP + cg + 16 * j];
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] += wv[i] * zv[j];
+        for (int g = 0; g < 2 * CQ; ++g) {
+          const double2 z2 = *reinterpret_cast<const double2*>(zr + 2 * g);
+          acc[2 * g + 0] += w * (Real)z2.x;
+          acc[2 * g + 1] += w * (Real)z2.y;
+        }
+      }
     }
     __syncthreads();
   }
 }
 
+// combine the KP k-phases of a row (KP consecutive lanes); every lane gets
+// the sum
+template <typename Real, int N>
+__device__ __forceinline__ void combine_phases(Real (&acc)[N]) {
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+#pragma unroll
+    for (int o = 1; o < KP; o <<= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+  }
+}
+
+template <typename Real>
+__host__ __device__ constexpr size_t gemm_smem(int BM, int CPs) {
+  return (size_t)(BM * w_stride<Real>() + KChunk<Real>::BK * CPs) * sizeof(Real);
+}
+
 // ------------------------------------------------------------ hidden layers
-template <typename Real, int TN, bool JAC>
-__global__ void __launch_bounds__(NT) hidden_kernel(const Real* __restrict__ W,
-                                                    const Real* __restrict__ b, int M,
-                                                    int K, const Real* __restrict__ Zin,
-                                                    int C, Real* __restrict__ Zout,
-                                                    int ldo) {
-  using T = Tile<Real, TN, 1>;
+constexpr int HBM = 16;  // rows per CTA of a hidden layer
+
+template <typename Real, int CQ>
+__global__ void __launch_bounds__(KP * HBM) hidden_kernel(const Real* __restrict__ W,
+                                                         const Real* __restrict__ b, int M,
+                                                         int K, const Real* __restrict__ Zin,
+                                                         int C, int CPs, int nj,
+                                                         Real* __restrict__ Zout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* Ws = reinterpret_cast<Real*>(smem_raw);
-  Real* Zs = Ws + T::WS;
-  Real* e1s = Zs + T::ZS;
-  const int t = threadIdx.x, cg = t & 15, rg = t >> 4;
-  const int m0 = blockIdx.x * T::BM;
-  Real acc[1][TN];
-  gemm_tile<Real, TN, 1>(W, M, K, Zin, C, m0, Ws, Zs, acc);
-  const int m = m0 + rg;
-  if (JAC) {
-    if (cg == 0 && m < M) {
-      Real a = acc[0][0] + b[m];
-      e1s[rg] = elu_d<Real>(a);
-      Zout[m] = elu_f<Real>(a);
-    }
-    __syncthreads();
-    if (m < M) {
+  Real* Zs = Ws + HBM * w_stride<Real>();
+  const int t = threadIdx.x, q = t % KP, row = t / KP;
+  const int m0 = blockIdx.x * HBM, m = m0 + row;
+  const Real bm = m < M ? b[m] : Real(0);
+  Real acc[4 * CQ];
+  skinny_gemm<Real, CQ, HBM>(W, M, K, Zin, CPs, m0, Ws, Zs, acc);
+  combine_phases<Real, 4 * CQ>(acc);
+  const Real a0 = acc[0] + bm;
+  const Real e1 = elu_d<Real>(a0);
+  if (m < M) {
+    // lane q writes columns q, q + KP, ... of the row
 #pragma unroll
-      for (int j = 0; j < TN; ++j) {
-        int c = cg + 16 * j;
-        if (c >= 1 && c < C) Zout[(size_t)c * ldo + m] = e1s[rg] * acc[0][j];
-      }
-    }
-  } else if (m < M) {
-#pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      int c = cg + 16 * j;
-      if (c < C) Zout[(size_t)c * ldo + m] = elu_f<Real>(acc[0][j] + b[m]);
+    for (int c = 0; c < 4 * CQ; ++c) {
+      if ((c % KP) != q || c >= C) continue;
+      const Real v = (c == 0 || c >= nj) ? elu_f<Real>(acc[c] + bm) : e1 * acc[c];
+      Zout[(size_t)m * CPs + c] = v;
     }
   }
 }
 
 // Per-row energy, force and stiffness scalars of the terms that act on each
 // DOF separately: inertia (dynamics) or gravity (quasi-static), and ground.
-__device__ __forceinline__ void row_terms(const LastArgs& la, int m, double u, double& e,
-                                          double& gv, double& kv) {
-  const int v = m / 3, comp = m - 3 * v;
-  const double mv = la.mass[v];
-  if (la.inv_dt2 > 0.0) {
-    double diff = u - la.ubar[m];
-    e = 0.5 * la.inv_dt2 * mv * diff * diff;
-    gv = la.inv_dt2 * mv * diff;
-    kv = la.inv_dt2 * mv;
+__device__ __forceinline__ void row_terms(const LastArgs& la, double inv_dt2, int comp,
+                                          double mv, double ubar, double x0, double u,
+                                          double& e, double& gv, double& kv) {
+  if (inv_dt2 > 0.0) {
+    const double diff = u - ubar;
+    e = 0.5 * inv_dt2 * mv * diff * diff;
+    gv = inv_dt2 * mv * diff;
+    kv = inv_dt2 * mv;
   } else {
     e = -mv * la.grav[comp] * u;
     gv = -mv * la.grav[comp];
     kv = 0.0;
   }
   if (la.ground_k > 0.0 && comp == 2) {
-    double pen = la.X0[m] + u - la.ground_h;
+    const double pen = x0 + u - la.ground_h;
     if (pen < 0.0) {
       e += 0.5 * la.ground_k * pen * pen;
       gv += la.ground_k * pen;
@@ -166,82 +236,109 @@ __device__ __forceinline__ void row_terms(const LastArgs& la, int m, double u, d
 }
 
 // ------------------------------------------------------------ output layer
-template <typename Real, int TN>
-__global__ void __launch_bounds__(NT) last_jac_kernel(const Real* __restrict__ W,
-                                                      const Real* __restrict__ b, int M,
-                                                      int K, const Real* __restrict__ Zin,
-                                                      int C, Real* __restrict__ u_out,
-                                                      Real* __restrict__ J_out,
-                                                      double* __restrict__ part,
-                                                      int part_stride, LastArgs la) {
-  constexpr int TM = 4;
-  using T = Tile<Real, TN, TM>;
-  constexpr int BM = T::BM, CP = T::CP, OS = CP + 1;
-  constexpr int PQ = (16 * TN * (16 * TN + 1) / 2 + NT - 1) / NT;
+constexpr int LBM = 64;        // rows per tile of the output layer
+constexpr int LNT = KP * LBM;  // threads per CTA
+
+template <typename Real, int CQ>
+__global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
+                                                   const Real* __restrict__ b, int M, int K,
+                                                   const Real* __restrict__ Zin, int C,
+                                                   int CPs, int nj, Real* __restrict__ u_out,
+                                                   Real* __restrict__ J_out,
+                                                   Real* __restrict__ u_trial,
+                                                   double* __restrict__ part, int part_stride,
+                                                   LastArgs la) {
+  constexpr int RQ = 4 * CQ;  // padded columns held per lane
+  constexpr int PQ = (RQ * (RQ + 1) / 2 + LNT - 1) / LNT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* Ws = reinterpret_cast<Real*>(smem_raw);
-  Real* Zs = Ws + T::WS;
-  Real* Os = Zs + T::ZS;                                   // BM x OS
-  double* gvs = reinterpret_cast<double*>(Os + BM * OS + (BM * OS) % 2);
-  double* kvs = gvs + BM;
-  double* red = kvs + BM;                                  // NT * 2
-  const int t = threadIdx.x, cg = t & 15, rg = t >> 4;
-  const int r = la.r;
+  Real* Zs = Ws + LBM * w_stride<Real>();
+  size_t off = gemm_smem<Real>(LBM, CPs);
+  off = (off + 15) & ~size_t(15);
+  const int r = la.r, OS = r + 1;
+  double* gvs = reinterpret_cast<double*>(smem_raw + off);  // LBM (row forces)
+  double* red = gvs + LBM;                                  // (LNT/32 + 1) x 8
+  Real* Js = reinterpret_cast<Real*>(red + (LNT / 32 + 1) * (2 + 2 * KTRIAL));  // LBM x OS
+  Real* kvs = Js + LBM * OS;                                                    // LBM
+  const int t = threadIdx.x, q = t % KP, row = t / KP;
   const int np = npairs(r);
+  const int ntr = C - nj;
+  const double inv_dt2 = *la.inv_dt2;
+  const int tslot = nslots(r);
   int pi[PQ], pj[PQ];
   double kacc[PQ];
 #pragma unroll
-  for (int q = 0; q < PQ; ++q) {
-    int p = t + NT * q;
-    if (p < np) pair_of(p, r, pi[q], pj[q]);
-    else pi[q] = pj[q] = -1;
-    kacc[q] = 0.0;
+  for (int p = 0; p < PQ; ++p) {
+    const int e = t + LNT * p;
+    if (e < np) pair_of(e, r, pi[p], pj[p]);
+    else pi[p] = pj[p] = -1;
+    kacc[p] = 0.0;
   }
   double gacc = 0.0, gabs = 0.0, eacc = 0.0, eabs = 0.0;
-  const int ntiles = (M + BM - 1) / BM;
+  double etr = 0.0, atr = 0.0;  // trial column q - 1 of this lane (q = 1..KTRIAL)
+  const int ntiles = (M + LBM - 1) / LBM;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int m0 = tile * BM;
-    Real acc[TM][TN];
-    gemm_tile<Real, TN, TM>(W, M, K, Zin, C, m0, Ws, Zs, acc);
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-      for (int j = 0; j < TN; ++j) {
-        int row = rg + 16 * i, c = cg + 16 * j, m = m0 + row;
-        Real val = acc[i][j];
-        if (c == 0 && m < M) val += b[m];
-        Os[row * OS + c] = (Real)(la.scale * (double)val);
-      }
-    __syncthreads();
-    if (t < BM) {
-      const int m = m0 + t;
-      double gv = 0.0, kv = 0.0;
-      if (m < M) {
-        const int v = m / 3, comp = m - 3 * v;
-        const int slot = la.cslot[v];
-        if (slot >= 0) {
-          Os[t * OS] = (Real)la.cu[3 * slot + comp];
-          for (int c = 1; c < C; ++c) Os[t * OS + c] = Real(0);
-        }
-        double e;
-        row_terms(la, m, (double)Os[t * OS], e, gv, kv);
+    const int m0 = tile * LBM, m = m0 + row;
+    const bool live = m < M;
+    const int v = m / 3, comp = m - 3 * v;
+    // per-row constants, fetched before the GEMM
+    double mv = 0.0, ub = 0.0, x0 = 0.0, bm = 0.0;
+    int slot = -1;
+    if (live) {
+      mv = la.mass[v];
+      ub = la.ubar[m];
+      x0 = la.X0[m];
+      slot = la.cslot[v];
+      bm = (double)b[m];
+    }
+    Real acc[RQ];
+    skinny_gemm<Real, CQ, LBM>(W, M, K, Zin, CPs, m0, Ws, Zs, acc);
+    combine_phases<Real, RQ>(acc);
+    const double cu = (live && slot >= 0) ? la.cu[3 * slot + comp] : 0.0;
+    // value at y0 and the row terms
+    double u0 = la.scale * ((double)acc[0] + bm);
+    if (slot >= 0) u0 = cu;
+    const Real u0r = (Real)u0;
+    double e = 0.0, gv = 0.0, kv = 0.0;
+    if (live) row_terms(la, inv_dt2, comp, mv, ub, x0, (double)u0r, e, gv, kv);
+    if (q == 0) {
+      if (live) {
+        u_out[m] = u0r;
         eacc += e;
         eabs += fabs(e);
       }
-      gvs[t] = gv;
-      kvs[t] = kv;
+      kvs[row] = live ? (Real)kv : Real(0);
+      gvs[row] = live ? gv : 0.0;
+    }
+    // J row: lane q stores the columns c = q (mod KP) (zero if constrained)
+#pragma unroll
+    for (int c = 1; c < RQ; ++c) {
+      if ((c % KP) != q || c >= nj) continue;
+      const Real jv = (live && slot < 0) ? (Real)(la.scale * (double)acc[c]) : Real(0);
+      if (live) J_out[(size_t)m * r + (c - 1)] = jv;
+      Js[row * OS + (c - 1)] = jv;
+    }
+    // trial columns: lane q = 1..KTRIAL handles trial q - 1
+    if (q >= 1 && q <= ntr && live) {
+      double ut = 0.0;
+#pragma unroll
+      for (int c = 0; c < RQ; ++c)
+        if (c == nj + q - 1) ut = la.scale * ((double)acc[c] + bm);
+      if (slot >= 0) ut = cu;
+      const Real utr = (Real)ut;
+      u_trial[(size_t)(q - 1) * M + m] = utr;
+      double et, g2, k2;
+      row_terms(la, inv_dt2, comp, mv, ub, x0, (double)utr, et, g2, k2);
+      etr += et;
+      atr += fabs(et);
     }
     __syncthreads();
-    const int rows = min(BM, M - m0);
-    for (int e = t; e < rows; e += NT) u_out[m0 + e] = Os[e * OS];
-    for (int e = t; e < rows * r; e += NT) {
-      int row = e / r, c = e - row * r;
-      J_out[(size_t)(m0 + row) * r + c] = Os[row * OS + 1 + c];
-    }
+    const int rows = min(LBM, M - m0);
     if (t < r) {
       double s = 0.0, a = 0.0;
-      for (int row = 0; row < rows; ++row) {
-        const double term = gvs[row] * (double)Os[row * OS + 1 + t];
+#pragma unroll 4
+      for (int rr = 0; rr < rows; ++rr) {
+        const double term = gvs[rr] * (double)Js[rr * OS + t];
         s += term;
         a += fabs(term);
       }
@@ -249,209 +346,149 @@ __global__ void __launch_bounds__(NT) last_jac_kernel(const Real* __restrict__ W
       gabs += a;
     }
 #pragma unroll
-    for (int q = 0; q < PQ; ++q) {
-      if (pi[q] >= 0) {
-        double s = 0.0;
-        const int i = 1 + pi[q], j = 1 + pj[q];
-        for (int row = 0; row < rows; ++row)
-          s += kvs[row] * (double)Os[row * OS + i] * (double)Os[row * OS + j];
-        kacc[q] += s;
+    for (int p = 0; p < PQ; ++p) {
+      if (pi[p] >= 0) {
+        // the Hessian partial of a tile is summed in the element precision
+        Real s0 = Real(0), s1 = Real(0);
+        int rr = 0;
+        for (; rr + 2 <= rows; rr += 2) {
+          s0 += kvs[rr] * Js[rr * OS + pi[p]] * Js[rr * OS + pj[p]];
+          s1 += kvs[rr + 1] * Js[(rr + 1) * OS + pi[p]] * Js[(rr + 1) * OS + pj[p]];
+        }
+        if (rr < rows) s0 += kvs[rr] * Js[rr * OS + pi[p]] * Js[rr * OS + pj[p]];
+        kacc[p] += (double)(s0 + s1);
       }
     }
     __syncthreads();
   }
-  // block reduction of the energy scalars, then one partial row per CTA
-  red[t] = eacc;
-  red[NT + t] = eabs;
-  __syncthreads();
-  for (int s = NT / 2; s > 0; s >>= 1) {
-    if (t < s) {
-      red[t] += red[t + s];
-      red[NT + t] += red[NT + t + s];
+  // block reduction of the energy scalars: warp shuffles, then one value per
+  // warp in shared memory (fixed order), then one partial row per CTA
+  {
+    double vals[2 + 2 * KTRIAL];
+    vals[0] = eacc;
+    vals[1] = eabs;
+#pragma unroll
+    for (int j = 0; j < KTRIAL; ++j) {
+      vals[2 + 2 * j] = (q == j + 1) ? etr : 0.0;
+      vals[3 + 2 * j] = (q == j + 1) ? atr : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 2 + 2 * KTRIAL; ++j) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) vals[j] += __shfl_down_sync(0xffffffffu, vals[j], o);
+    }
+    if ((t & 31) == 0)
+#pragma unroll
+      for (int j = 0; j < 2 + 2 * KTRIAL; ++j) red[(t >> 5) * (2 + 2 * KTRIAL) + j] = vals[j];
+    __syncthreads();
+    if (t < 2 + 2 * KTRIAL) {
+      double sum = 0.0;
+      for (int w = 0; w < LNT / 32; ++w) sum += red[w * (2 + 2 * KTRIAL) + t];
+      red[LNT / 32 * (2 + 2 * KTRIAL) + t] = sum;
     }
     __syncthreads();
   }
+  const double* tot = red + LNT / 32 * (2 + 2 * KTRIAL);
   double* prow = part + (size_t)blockIdx.x * part_stride;
   if (t == 0) {
-    prow[0] = red[0];
-    prow[1] = red[NT];
+    prow[0] = tot[0];
+    prow[1] = tot[1];
   }
+  if (t < 2 * KTRIAL) prow[tslot + t] = (t / 2 < ntr) ? tot[2 + t] : 0.0;
   if (t < r) {
     prow[slot_g(t)] = gacc;
     prow[slot_gabs(r, t)] = gabs;
   }
 #pragma unroll
-  for (int q = 0; q < PQ; ++q)
-    if (pi[q] >= 0) prow[slot_K(r) + t + NT * q] = kacc[q];
+  for (int p = 0; p < PQ; ++p) {
+    const int e = t + LNT * p;
+    if (e < np) prow[slot_K(r) + e] = kacc[p];
+  }
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(NT) last_val_kernel(const Real* __restrict__ W,
-                                                      const Real* __restrict__ b, int M,
-                                                      int K, const Real* __restrict__ Zin,
-                                                      int C, Real* __restrict__ u_trial,
-                                                      double* __restrict__ part,
-                                                      int part_stride, LastArgs la) {
-  constexpr int TM = 4, TN = 1;
-  using T = Tile<Real, TN, TM>;
-  constexpr int BM = T::BM;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* Ws = reinterpret_cast<Real*>(smem_raw);
-  Real* Zs = Ws + T::WS;
-  double* red = reinterpret_cast<double*>(Zs + T::ZS + (T::ZS % 2));  // 2 * NT
-  const int t = threadIdx.x, cg = t & 15, rg = t >> 4;
-  double eacc = 0.0, eabs = 0.0;
-  const int ntiles = (M + BM - 1) / BM;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int m0 = tile * BM;
-    Real acc[TM][TN];
-    gemm_tile<Real, TN, TM>(W, M, K, Zin, C, m0, Ws, Zs, acc);
-#pragma unroll
-    for (int i = 0; i < TM; ++i) {
-      const int m = m0 + rg + 16 * i;
-      if (m < M && cg < C) {
-        const int v = m / 3, comp = m - 3 * v;
-        const int slot = la.cslot[v];
-        double u = slot >= 0 ? la.cu[3 * slot + comp]
-                             : (double)(Real)(la.scale * (double)(acc[i][0] + b[m]));
-        Real ur = (Real)u;
-        u_trial[(size_t)cg * M + m] = ur;
-        double e, gv, kv;
-        row_terms(la, m, (double)ur, e, gv, kv);
-        eacc += e;
-        eabs += fabs(e);
-      }
-    }
-  }
-  red[t] = eacc;
-  red[NT + t] = eabs;
-  __syncthreads();
-  if (t < 16) {  // column t: sum over the 16 row groups
-    double s = 0.0, a = 0.0;
-    for (int g = 0; g < 16; ++g) {
-      s += red[g * 16 + t];
-      a += red[NT + g * 16 + t];
-    }
-    if (t < C) {
-      part[(size_t)blockIdx.x * part_stride + 2 * t] = s;
-      part[(size_t)blockIdx.x * part_stride + 2 * t + 1] = a;
-    }
-  }
+size_t last_smem(int r, int CPs) {
+  size_t off = gemm_smem<Real>(LBM, CPs);
+  off = (off + 15) & ~size_t(15);
+  return off + ((size_t)LBM + (LNT / 32 + 1) * (2 + 2 * KTRIAL)) * sizeof(double) +
+         ((size_t)LBM * (r + 1) + LBM) * sizeof(Real);
 }
 
-template <typename Real, int TN>
-size_t hidden_smem() {
-  using T = Tile<Real, TN, 1>;
-  return (T::WS + T::ZS + T::BM) * sizeof(Real);
-}
-template <typename Real, int TN>
-size_t last_jac_smem() {
-  using T = Tile<Real, TN, 4>;
-  size_t reals = T::WS + T::ZS + T::BM * (T::CP + 1);
-  reals += reals % 2;
-  return reals * sizeof(Real) + (2 * T::BM + 2 * NT) * sizeof(double);
-}
-template <typename Real>
-size_t last_val_smem() {
-  using T = Tile<Real, 1, 4>;
-  size_t reals = T::WS + T::ZS;
-  reals += reals % 2;
-  return reals * sizeof(Real) + 2 * NT * sizeof(double);
+template <typename Real, int CQ>
+void run_hidden(const Real* W, const Real* b, int M, int K, const Real* Zin, int C, int CPs,
+                int nj, Real* Zout, cudaStream_t s) {
+  const size_t sm = gemm_smem<Real>(HBM, CPs);
+  static size_t set = 0;
+  if (sm > set) {
+    cudaFuncSetAttribute(hidden_kernel<Real, CQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+    set = sm;
+  }
+  hidden_kernel<Real, CQ><<<(M + HBM - 1) / HBM, KP * HBM, sm, s>>>(W, b, M, K, Zin, C, CPs,
+                                                                    nj, Zout);
 }
 
-template <typename Real, int TN>
-void run_hidden(bool jac, const Real* W, const Real* b, int M, int K, const Real* Zin,
-                int C, Real* Zout, int ldo, cudaStream_t s) {
-  size_t sm = hidden_smem<Real, TN>();
-  int grid = (M + 15) / 16;
-  if (jac) {
-    static bool set = false;
-    if (!set) {
-      cudaFuncSetAttribute(hidden_kernel<Real, TN, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      set = true;
-    }
-    hidden_kernel<Real, TN, true><<<grid, NT, sm, s>>>(W, b, M, K, Zin, C, Zout, ldo);
-  } else {
-    static bool set = false;
-    if (!set) {
-      cudaFuncSetAttribute(hidden_kernel<Real, TN, false>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      set = true;
-    }
-    hidden_kernel<Real, TN, false><<<grid, NT, sm, s>>>(W, b, M, K, Zin, C, Zout, ldo);
+template <typename Real, int CQ>
+void run_last(const Real* W, const Real* b, int M, int K, const Real* Zin, int C, int CPs,
+              int nj, Real* u_out, Real* J_out, Real* u_trial, double* part, int stride,
+              const LastArgs& la, int grid, cudaStream_t s) {
+  const size_t sm = last_smem<Real>(la.r, CPs);
+  static size_t set = 0;
+  if (sm > set) {
+    cudaFuncSetAttribute(last_kernel<Real, CQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+    set = sm;
   }
-}
-
-template <typename Real, int TN>
-void run_last_jac(const Real* W, const Real* b, int M, int K, const Real* Zin, int C,
-                  Real* u_out, Real* J_out, double* part, int stride, const LastArgs& la,
-                  int grid, cudaStream_t s) {
-  size_t sm = last_jac_smem<Real, TN>();
-  static bool set = false;
-  if (!set) {
-    cudaFuncSetAttribute(last_jac_kernel<Real, TN>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    set = true;
-  }
-  last_jac_kernel<Real, TN><<<grid, NT, sm, s>>>(W, b, M, K, Zin, C, u_out, J_out, part,
-                                                 stride, la);
+  last_kernel<Real, CQ><<<grid, LNT, sm, s>>>(W, b, M, K, Zin, C, CPs, nj, u_out, J_out,
+                                              u_trial, part, stride, la);
 }
 
 }  // namespace
 
-int decoder_cpad(int C) { return 16 * ((C + 15) / 16); }
-
 int decoder_last_grid(int n, int C, int num_sms) {
-  int tiles = (n + 63) / 64;
-  int cap = num_sms * (C > 48 ? 1 : 2);
-  return std::max(1, std::min(tiles, cap));
+  const int tiles = (n + LBM - 1) / LBM;
+  const int per_sm = C > 48 ? 1 : 2;
+  return std::max(1, std::min(tiles, num_sms * per_sm));
+}
+
+#define LSN_CQ_SWITCH(CPs, CALL)                 \
+  switch ((CPs) / 4) {                           \
+    case 1: { constexpr int CQ = 1; CALL; } break; \
+    case 3: { constexpr int CQ = 3; CALL; } break; \
+    case 5: { constexpr int CQ = 5; CALL; } break; \
+    case 7: { constexpr int CQ = 7; CALL; } break; \
+    case 9: { constexpr int CQ = 9; CALL; } break; \
+    case 11: { constexpr int CQ = 11; CALL; } break; \
+    case 13: { constexpr int CQ = 13; CALL; } break; \
+    case 15: { constexpr int CQ = 15; CALL; } break; \
+    case 17: { constexpr int CQ = 17; CALL; } break; \
+    default: break;                              \
+  }
+
+template <typename Real>
+void launch_hidden_layer(const Real* W, const Real* b, int M, int K, const Real* Zin, int C,
+                         int nj, Real* Zout, cudaStream_t s) {
+  const int CPs = zstride(C);
+  LSN_CQ_SWITCH(CPs, (run_hidden<Real, CQ>(W, b, M, K, Zin, C, CPs, nj, Zout, s)))
 }
 
 template <typename Real>
-void launch_decoder_layer(Epi epi, const Real* W, const Real* b, int M, int K,
-                          const Real* Zin, int C, Real* Zout, int ldo, Real* u_out,
-                          Real* J_out, double* part, int part_stride,
-                          const LastArgs& la, int grid, cudaStream_t s) {
-  const int tn = (C + 15) / 16;
-  switch (epi) {
-    case Epi::HiddenJac:
-    case Epi::HiddenVal: {
-      bool jac = epi == Epi::HiddenJac;
-      switch (tn) {
-        case 1: run_hidden<Real, 1>(jac, W, b, M, K, Zin, C, Zout, ldo, s); break;
-        case 2: run_hidden<Real, 2>(jac, W, b, M, K, Zin, C, Zout, ldo, s); break;
-        case 3: run_hidden<Real, 3>(jac, W, b, M, K, Zin, C, Zout, ldo, s); break;
-        case 4: run_hidden<Real, 4>(jac, W, b, M, K, Zin, C, Zout, ldo, s); break;
-        default: run_hidden<Real, 5>(jac, W, b, M, K, Zin, C, Zout, ldo, s); break;
-      }
-      break;
-    }
-    case Epi::LastJac:
-      switch (tn) {
-        case 1: run_last_jac<Real, 1>(W, b, M, K, Zin, C, u_out, J_out, part, part_stride, la, grid, s); break;
-        case 2: run_last_jac<Real, 2>(W, b, M, K, Zin, C, u_out, J_out, part, part_stride, la, grid, s); break;
-        case 3: run_last_jac<Real, 3>(W, b, M, K, Zin, C, u_out, J_out, part, part_stride, la, grid, s); break;
-        case 4: run_last_jac<Real, 4>(W, b, M, K, Zin, C, u_out, J_out, part, part_stride, la, grid, s); break;
-        default: run_last_jac<Real, 5>(W, b, M, K, Zin, C, u_out, J_out, part, part_stride, la, grid, s); break;
-      }
-      break;
-    case Epi::LastVal: {
-      size_t sm = last_val_smem<Real>();
-      last_val_kernel<Real><<<grid, NT, sm, s>>>(W, b, M, K, Zin, C, Zout, part,
-                                                 part_stride, la);
-      break;
-    }
-  }
+void launch_last_layer(const Real* W, const Real* b, int M, int K, const Real* Zin, int C,
+                       int nj, Real* u_out, Real* J_out, Real* u_trial, double* part,
+                       int part_stride, const LastArgs& la, int grid, cudaStream_t s) {
+  const int CPs = zstride(C);
+  LSN_CQ_SWITCH(CPs, (run_last<Real, CQ>(W, b, M, K, Zin, C, CPs, nj, u_out, J_out, u_trial,
+                                          part, part_stride, la, grid, s)))
 }
 
-template void launch_decoder_layer<float>(Epi, const float*, const float*, int, int,
-                                          const float*, int, float*, int, float*, float*,
-                                          double*, int, const LastArgs&, int,
-                                          cudaStream_t);
-template void launch_decoder_layer<double>(Epi, const double*, const double*, int, int,
-                                           const double*, int, double*, int, double*,
-                                           double*, double*, int, const LastArgs&, int,
-                                           cudaStream_t);
+#define LSN_INST(R)                                                                        \
+  template void launch_hidden_layer<R>(const R*, const R*, int, int, const R*, int, int,  \
+                                       R*, cudaStream_t);                                  \
+  template void launch_last_layer<R>(const R*, const R*, int, int, const R*, int, int, R*, \
+                                     R*, R*, double*, int, const LastArgs&, int,           \
+                                     cudaStream_t);
+LSN_INST(float)
+LSN_INST(double)
+#undef LSN_INST
 
 }  // namespace lsn

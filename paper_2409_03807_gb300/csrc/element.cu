@@ -46,8 +46,15 @@
 namespace lsn {
 namespace {
 
-constexpr int ET = 128;  // threads per CTA = tets per tile
-constexpr int CB = 16;   // tets per contraction batch
+// tets per contraction batch (FP64 halves it to fit the shared memory)
+template <typename Real>
+struct Batch {
+  static constexpr int CB = 16;
+};
+template <>
+struct Batch<double> {
+  static constexpr int CB = 8;
+};
 
 template <typename Real>
 struct Consts {
@@ -116,7 +123,8 @@ __device__ __forceinline__ void jacobi3(Real (&A)[3][3], Real (&Q)[3][3]) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) Q[i][j] = (i == j) ? Real(1) : Real(0);
   const Real tiny = sizeof(Real) == 4 ? Real(1e-30) : Real(1e-300);
-  const Real rel = sizeof(Real) == 4 ? Real(1e-15) : Real(1e-32);
+  // off-diagonal mass below (unit roundoff)^2 of the diagonal: converged
+  const Real rel = sizeof(Real) == 4 ? Real(1e-13) : Real(1e-29);
 #pragma unroll 1
   for (int sweep = 0; sweep < Consts<Real>::sweeps; ++sweep) {
     const Real off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
@@ -157,6 +165,27 @@ __device__ __forceinline__ void jacobi3(Real (&A)[3][3], Real (&Q)[3][3]) {
       }
     }
   }
+}
+
+// Asynchronous copies of the tets' J rows into shared memory.
+template <typename Real>
+__device__ __forceinline__ void cp_async_elem(Real* dst, const Real* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (sizeof(Real) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // Rotation-signed SVD F = U diag(sig) V^T with det U = det V = +1 (sig[i]
@@ -248,8 +277,8 @@ __device__ __forceinline__ void svd3(const Real (&F)[3][3], Real (&U)[3][3], Rea
     sig[i] = U[0][i] * FV[0][i] + U[1][i] * FV[1][i] + U[2][i] * FV[2][i];
 }
 
-template <typename Real>
-struct ElemTile {  // shared memory of one tile
+template <typename Real, int ET>
+struct ElemTile {  // shared memory of one tile (ET tets)
   Real U[ET][9];    // U of the signed SVD (row-major)
   Real V[ET][9];    // V of the signed SVD (row-major)
   Real As[ET][9];   // row m: sqrt(w V lambda_s,m+) a_m (scaling modes)
@@ -298,18 +327,70 @@ __device__ __forceinline__ void disp_grad(const Real* __restrict__ u, const int4
       H[i][j] = Du[i][0] * Dmi[0][j] + Du[i][1] * Dmi[1][j] + Du[i][2] * Dmi[2][j];
 }
 
-template <typename Real, int RT>
-__global__ void __launch_bounds__(ET) element_full_kernel(ElemArgs ea,
-                                                          const Real* __restrict__ u,
-                                                          const Real* __restrict__ J,
-                                                          double* __restrict__ part,
-                                                          int part_stride) {
+// Energy of the KTRIAL trial displacement fields ut[j * n + .] for the tets
+// e = first, first + stride, ...; block-reduced into prow[2 j], prow[2 j + 1].
+template <typename Real, int ET>
+__device__ __forceinline__ void element_energy_block(const ElemArgs& ea,
+                                                     const Real* __restrict__ ut, int first,
+                                                     int stride, double* prow,
+                                                     double (*red)[ET]) {
+  const int t = threadIdx.x;
+  const Real mu = (Real)ea.mu, lam = (Real)ea.lam;
+  const Real oma = (Real)(-0.75 * ea.mu / ea.lam);
+  double ea_[KTRIAL], ab_[KTRIAL];
+#pragma unroll
+  for (int j = 0; j < KTRIAL; ++j) ea_[j] = ab_[j] = 0.0;
+  for (int e = first + t; e < ea.S; e += stride) {
+    int4 tv;
+    Real Dmi[3][3], wv;
+    load_tet<Real>(ea, e, tv, Dmi, wv);
+#pragma unroll
+    for (int j = 0; j < KTRIAL; ++j) {
+      Real H[3][3];
+      disp_grad<Real>(ut + (size_t)j * ea.n, tv, Dmi, H);
+      Invariants<Real> iv;
+      invariants<Real>(H, iv);
+      const double pe = (double)(wv * snh_psi<Real>(iv, mu, lam, oma));
+      ea_[j] += pe;
+      ab_[j] += fabs(pe);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < KTRIAL; ++j) {
+    red[2 * j][t] = ea_[j];
+    red[2 * j + 1][t] = ab_[j];
+  }
+  __syncthreads();
+  for (int s = ET / 2; s > 0; s >>= 1) {
+    if (t < s) {
+#pragma unroll
+      for (int j = 0; j < 2 * KTRIAL; ++j) red[j][t] += red[j][t + s];
+    }
+    __syncthreads();
+  }
+  if (t < 2 * KTRIAL) prow[t] = red[t][0];
+}
+
+template <typename Real, int RT, int ET>
+__global__ void __launch_bounds__(ET) element_kernel(ElemArgs ea, const Real* __restrict__ u,
+                                                     const Real* __restrict__ J,
+                                                     const Real* __restrict__ ut,
+                                                     double* __restrict__ part,
+                                                     int part_stride, int gfull) {
+  __shared__ double red[2 * KTRIAL][ET];
+  if ((int)blockIdx.x >= gfull) {
+    const int b = blockIdx.x - gfull, nb = gridDim.x - gfull;
+    element_energy_block<Real, ET>(ea, ut, b * ET, nb * ET,
+                                   part + (size_t)blockIdx.x * part_stride + nslots(ea.r), red);
+    return;
+  }
   constexpr int PQ = (RT * (RT + 1) / 2 + ET - 1) / ET;
+  constexpr int CB = Batch<Real>::CB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ElemTile<Real>& tl = *reinterpret_cast<ElemTile<Real>*>(smem_raw);
-  Real* Cs = reinterpret_cast<Real*>(smem_raw + sizeof(ElemTile<Real>));  // CB*9 x r
-  Real* Gp = Cs + CB * 9 * ea.r;                                           // CB x r
-  __shared__ double red[2 * ET];
+  ElemTile<Real, ET>& tl = *reinterpret_cast<ElemTile<Real, ET>*>(smem_raw);
+  Real* Cs = reinterpret_cast<Real*>(smem_raw + sizeof(ElemTile<Real, ET>));  // CB*9 x r
+  Real* Gp = Cs + CB * 9 * ea.r;                                               // CB x r
+  Real* Jb = Gp + CB * ea.r;  // 2 buffers of CB tets x 12 rows x r (J rows of a batch)
   const int t = threadIdx.x;
   const int r = ea.r, np = npairs(r);
   const Real mu = (Real)ea.mu, lam = (Real)ea.lam;
@@ -325,9 +406,39 @@ __global__ void __launch_bounds__(ET) element_full_kernel(ElemArgs ea,
   }
   double gacc = 0.0, gabs = 0.0, eacc = 0.0, eabs = 0.0;
   const int ntiles = (ea.S + ET - 1) / ET;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    // ---------------- phase 1: element math, one tet per thread
+  const int jbs = CB * 12 * r;  // elements per J buffer
+  // issue the copies of the 12 J rows of tets b0 .. b0 + CB - 1 into buffer buf
+  auto prefetch = [&](int b0, int nb, int buf) {
+    Real* dst = Jb + buf * jbs;
+    if ((r * (int)sizeof(Real)) % 16 == 0) {
+      const int per_row = r * (int)sizeof(Real) / 16, ev = 16 / (int)sizeof(Real);
+      for (int e2 = t; e2 < nb * 12 * per_row; e2 += ET) {
+        const int rowi = e2 / per_row, ch = e2 - rowi * per_row;
+        const int lt = rowi / 12, k = rowi - lt * 12, a = k / 3, i = k - 3 * a;
+        const int4 tv = tl.v[b0 + lt];
+        const int v = a == 0 ? tv.x : (a == 1 ? tv.y : (a == 2 ? tv.z : tv.w));
+        cp_async_16(dst + rowi * r + ch * ev, J + (size_t)(3 * v + i) * r + ch * ev);
+      }
+    } else {
+      for (int e2 = t; e2 < nb * 12 * r; e2 += ET) {
+        const int rowi = e2 / r, c = e2 - rowi * r;
+        const int lt = rowi / 12, k = rowi - lt * 12, a = k / 3, i = k - 3 * a;
+        const int4 tv = tl.v[b0 + lt];
+        const int v = a == 0 ? tv.x : (a == 1 ? tv.y : (a == 2 ? tv.z : tv.w));
+        cp_async_elem<Real>(dst + rowi * r + c, J + (size_t)(3 * v + i) * r + c);
+      }
+    }
+    cp_async_commit();
+  };
+  for (int tile = blockIdx.x; tile < ntiles; tile += gfull) {
     const int e = tile * ET + t;
+    const int tile_tets = min(ET, ea.S - tile * ET);
+    // tet indices first, so that the J rows of the first batch load during
+    // the element math
+    tl.v[t] = e < ea.S ? ea.tets[e] : make_int4(0, 0, 0, 0);
+    __syncthreads();
+    prefetch(0, min(CB, tile_tets), 0);
+    // ---------------- phase 1: element math, one tet per thread
     if (e < ea.S) {
       int4 tv;
       Real Dmi[3][3], wv, H[3][3];
@@ -394,7 +505,6 @@ __global__ void __launch_bounds__(ET) element_full_kernel(ElemArgs ea,
 #pragma unroll
         for (int a = 1; a < 4; ++a) tl.D[t][3 * a + j] = Dmi[a - 1][j];
       }
-      tl.v[t] = tv;
     } else {
 #pragma unroll
       for (int k = 0; k < 9; ++k) tl.U[t][k] = tl.V[t][k] = tl.As[t][k] = Real(0);
@@ -404,26 +514,30 @@ __global__ void __launch_bounds__(ET) element_full_kernel(ElemArgs ea,
       for (int k = 0; k < 12; ++k) tl.D[t][k] = Real(0);
 #pragma unroll
       for (int k = 0; k < 9; ++k) tl.p[t][k] = Real(0);
-      tl.v[t] = make_int4(0, 0, 0, 0);
     }
-    __syncthreads();
-    const int tile_tets = min(ET, ea.S - tile * ET);
     // ---------------- phases 2 + 3 in batches of CB tets
-    for (int b0 = 0; b0 < tile_tets; b0 += CB) {
+    int buf = 0;
+    for (int b0 = 0; b0 < tile_tets; b0 += CB, buf ^= 1) {
       const int nb = min(CB, tile_tets - b0);
+      if (b0 + CB < tile_tets) {
+        prefetch(b0 + CB, min(CB, tile_tets - b0 - CB), buf ^ 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const Real* Jt = Jb + buf * jbs;
       for (int item = t; item < CB * r; item += ET) {
         const int lt = item / r, c = item - lt * r;
         Real Cv[9];
         Real gp = Real(0);
         if (lt < nb) {
           const int q = b0 + lt;
-          const int4 tv = tl.v[q];
-          const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
           Real jv[4][3];
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) jv[a][i] = J[(size_t)(3 * vv[a] + i) * r + c];
+            for (int i = 0; i < 3; ++i) jv[a][i] = Jt[(lt * 12 + 3 * a + i) * r + c];
           Real G[9];
 #pragma unroll
           for (int i = 0; i < 3; ++i)
@@ -482,28 +596,35 @@ __global__ void __launch_bounds__(ET) element_full_kernel(ElemArgs ea,
 #pragma unroll
       for (int q = 0; q < PQ; ++q) {
         if (pi[q] >= 0) {
-          Real s = Real(0);
-          for (int row = 0; row < rows; ++row) s += Cs[row * r + pi[q]] * Cs[row * r + pj[q]];
-          kacc[q] += (double)s;
+          Real s0 = Real(0), s1 = Real(0), s2 = Real(0), s3 = Real(0);
+          int row = 0;
+          for (; row + 4 <= rows; row += 4) {
+            s0 += Cs[row * r + pi[q]] * Cs[row * r + pj[q]];
+            s1 += Cs[(row + 1) * r + pi[q]] * Cs[(row + 1) * r + pj[q]];
+            s2 += Cs[(row + 2) * r + pi[q]] * Cs[(row + 2) * r + pj[q]];
+            s3 += Cs[(row + 3) * r + pi[q]] * Cs[(row + 3) * r + pj[q]];
+          }
+          for (; row < rows; ++row) s0 += Cs[row * r + pi[q]] * Cs[row * r + pj[q]];
+          kacc[q] += (double)((s0 + s1) + (s2 + s3));
         }
       }
       __syncthreads();
     }
   }
-  red[t] = eacc;
-  red[ET + t] = eabs;
+  red[0][t] = eacc;
+  red[1][t] = eabs;
   __syncthreads();
   for (int s = ET / 2; s > 0; s >>= 1) {
     if (t < s) {
-      red[t] += red[t + s];
-      red[ET + t] += red[ET + t + s];
+      red[0][t] += red[0][t + s];
+      red[1][t] += red[1][t + s];
     }
     __syncthreads();
   }
   double* prow = part + (size_t)blockIdx.x * part_stride;
   if (t == 0) {
-    prow[0] = red[0];
-    prow[1] = red[ET];
+    prow[0] = red[0][0];
+    prow[1] = red[1][0];
   }
   if (t < r) {
     prow[slot_g(t)] = gacc;
@@ -514,97 +635,62 @@ __global__ void __launch_bounds__(ET) element_full_kernel(ElemArgs ea,
     if (pi[q] >= 0) prow[slot_K(r) + t + ET * q] = kacc[q];
 }
 
-// Energy of k trial displacement fields ut[j * n + .] for every cubature tet.
-template <typename Real>
-__global__ void __launch_bounds__(ET) element_energy_kernel(ElemArgs ea,
-                                                            const Real* __restrict__ ut,
-                                                            int k, double* __restrict__ part,
-                                                            int part_stride) {
-  __shared__ double red[2 * KTRIAL][ET];
-  const int t = threadIdx.x;
-  const Real mu = (Real)ea.mu, lam = (Real)ea.lam;
-  const Real oma = (Real)(-0.75 * ea.mu / ea.lam);
-  double ea_[KTRIAL], ab_[KTRIAL];
-#pragma unroll
-  for (int j = 0; j < KTRIAL; ++j) ea_[j] = ab_[j] = 0.0;
-  for (int e = blockIdx.x * ET + t; e < ea.S; e += gridDim.x * ET) {
-    int4 tv;
-    Real Dmi[3][3], wv;
-    load_tet<Real>(ea, e, tv, Dmi, wv);
-#pragma unroll
-    for (int j = 0; j < KTRIAL; ++j) {
-      if (j < k) {
-        Real H[3][3];
-        disp_grad<Real>(ut + (size_t)j * ea.n, tv, Dmi, H);
-        Invariants<Real> iv;
-        invariants<Real>(H, iv);
-        const double pe = (double)(wv * snh_psi<Real>(iv, mu, lam, oma));
-        ea_[j] += pe;
-        ab_[j] += fabs(pe);
-      }
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < KTRIAL; ++j) {
-    red[2 * j][t] = ea_[j];
-    red[2 * j + 1][t] = ab_[j];
-  }
-  __syncthreads();
-  for (int s = ET / 2; s > 0; s >>= 1) {
-    if (t < s) {
-#pragma unroll
-      for (int j = 0; j < 2 * KTRIAL; ++j) red[j][t] += red[j][t + s];
-    }
-    __syncthreads();
-  }
-  if (t < 2 * k) part[(size_t)blockIdx.x * part_stride + t] = red[t][0];
-}
-
-template <typename Real, int RT>
-void run_full(const ElemArgs& ea, const Real* u, const Real* J, double* part, int grid,
-              cudaStream_t s) {
-  size_t sm = sizeof(ElemTile<Real>) + (size_t)(CB * 9 * ea.r + CB * ea.r) * sizeof(Real);
+template <typename Real, int RT, int ET>
+void run_element(const ElemArgs& ea, const Real* u, const Real* J, const Real* ut,
+                 double* part, int gfull, int genergy, cudaStream_t s) {
+  constexpr int CB = Batch<Real>::CB;
+  const size_t sm = sizeof(ElemTile<Real, ET>) +
+                    (size_t)(CB * 9 * ea.r + CB * ea.r + 2 * CB * 12 * ea.r) * sizeof(Real);
   static size_t set = 0;
   if (sm > set) {
-    cudaFuncSetAttribute(element_full_kernel<Real, RT>,
+    cudaFuncSetAttribute(element_kernel<Real, RT, ET>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     set = sm;
   }
-  element_full_kernel<Real, RT><<<grid, ET, sm, s>>>(ea, u, J, part, nslots(ea.r));
+  element_kernel<Real, RT, ET><<<gfull + genergy, ET, sm, s>>>(ea, u, J, ut, part,
+                                                               nslots_total(ea.r), gfull);
+}
+
+template <typename Real, int ET>
+void run_element_r(const ElemArgs& ea, const Real* u, const Real* J, const Real* ut,
+                   double* part, int gfull, int genergy, cudaStream_t s) {
+  if (ea.r <= 16) run_element<Real, 16, ET>(ea, u, J, ut, part, gfull, genergy, s);
+  else if (ea.r <= 32) run_element<Real, 32, ET>(ea, u, J, ut, part, gfull, genergy, s);
+  else run_element<Real, 64, ET>(ea, u, J, ut, part, gfull, genergy, s);
 }
 
 }  // namespace
 
-int element_full_grid(int S, int num_sms) {
-  int tiles = (S + ET - 1) / ET;
-  return std::max(1, std::min(tiles, num_sms * 2));
-}
-int element_energy_grid(int S, int num_sms) {
-  int blocks = (S + ET - 1) / ET;
-  return std::max(1, std::min(blocks, num_sms * 4));
+// Small cubature sets use 64-tet tiles so that more CTAs share the work.
+static int element_tile(int S, int num_sms) { return S <= 64 * 2 * num_sms ? 64 : 128; }
+
+void element_grids(int S, int r, int num_sms, int& gfull, int& genergy) {
+  const int et = element_tile(S, num_sms);
+  const int tiles = (S + et - 1) / et;
+  gfull = std::max(1, std::min(tiles, num_sms * 2));
+  genergy = std::max(1, std::min(tiles, num_sms * 2));
+  (void)r;
 }
 
 template <typename Real>
-void launch_element_full(const ElemArgs& ea, const Real* u, const Real* J, double* part,
-                         int grid, cudaStream_t s) {
-  if (ea.r <= 16) run_full<Real, 16>(ea, u, J, part, grid, s);
-  else if (ea.r <= 32) run_full<Real, 32>(ea, u, J, part, grid, s);
-  else run_full<Real, 64>(ea, u, J, part, grid, s);
+void launch_element(const ElemArgs& ea, const Real* u, const Real* J, const Real* ut,
+                    double* part, int gfull, int genergy, cudaStream_t s) {
+  // the tile size must match element_grids
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if (element_tile(ea.S, sms) == 64)
+    run_element_r<Real, 64>(ea, u, J, ut, part, gfull, genergy, s);
+  else
+    run_element_r<Real, 128>(ea, u, J, ut, part, gfull, genergy, s);
 }
 
-template <typename Real>
-void launch_element_energy(const ElemArgs& ea, const Real* ut, int k, double* part,
-                           int grid, cudaStream_t s) {
-  element_energy_kernel<Real><<<grid, ET, 0, s>>>(ea, ut, k, part, 2 * KTRIAL);
-}
-
-template void launch_element_full<float>(const ElemArgs&, const float*, const float*,
-                                         double*, int, cudaStream_t);
-template void launch_element_full<double>(const ElemArgs&, const double*, const double*,
-                                          double*, int, cudaStream_t);
-template void launch_element_energy<float>(const ElemArgs&, const float*, int, double*,
-                                           int, cudaStream_t);
-template void launch_element_energy<double>(const ElemArgs&, const double*, int, double*,
-                                            int, cudaStream_t);
+template void launch_element<float>(const ElemArgs&, const float*, const float*, const float*,
+                                    double*, int, int, cudaStream_t);
+template void launch_element<double>(const ElemArgs&, const double*, const double*,
+                                     const double*, double*, int, int, cudaStream_t);
 
 }  // namespace lsn

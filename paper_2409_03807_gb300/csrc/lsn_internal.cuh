@@ -8,7 +8,7 @@
 namespace lsn {
 
 constexpr int RMAX = 64;           // largest subspace dimension
-constexpr int KTRIAL = 4;          // line-search step lengths evaluated per pass
+constexpr int KTRIAL = 3;          // extra line-search step lengths per pass
 constexpr int GEMM_BK = 32;        // k-chunk of the decoder GEMM tiles
 constexpr int TRACE = 128;         // Newton iterations kept in the solve trace
 
@@ -16,33 +16,51 @@ constexpr int TRACE = 128;         // Newton iterations kept in the solve trace
 __host__ __device__ inline int npairs(int r) { return r * (r + 1) / 2; }
 // Slots of one reduced-system partial: E, sum |E terms|, g[r], gabs[r]
 // (sum of |contributions| per gradient entry: the rounding scale of g), K
-// upper triangle (row-major, i <= j).
+// upper triangle (row-major, i <= j); then (E_j, sum|E_j terms|) of the
+// KTRIAL trial points.
 __host__ __device__ inline int nslots(int r) { return 2 + 2 * r + npairs(r); }
+__host__ __device__ inline int nslots_total(int r) { return nslots(r) + 2 * KTRIAL; }
+// Column stride of the decoder activations Z[k][c]: C rounded up to a
+// multiple of 4 with an odd number of 4-element groups, so that eight
+// consecutive rows of Z fall into distinct shared-memory bank groups.
+__host__ __device__ inline int zstride(int C) {
+  int c = (C + 3) & ~3;
+  return ((c / 4) % 2 == 0) ? c + 4 : c;
+}
 __host__ __device__ inline int slot_g(int i) { return 2 + i; }
 __host__ __device__ inline int slot_gabs(int r, int i) { return 2 + r + i; }
 __host__ __device__ inline int slot_K(int r) { return 2 + 2 * r; }
 
-// Device-resident Newton / line-search state (one per context).
+// Device-resident Newton / line-search state (one per context).  Scalars
+// first so that the host can copy the summary (up to and including z)
+// without the trace arrays.
 struct DevSolver {
-  double z[RMAX];      // current iterate
-  double d[RMAX];      // Newton direction
-  double g[RMAX];      // reduced gradient at z
+  // controls (set by the host)
+  double tol, armijo_c, eta_scale;
+  double floor_scale;  // kappa * unit roundoff of the element precision
+  int r, max_ls, max_newton, eval_only;
+  // dynamics of the current step
+  double inv_dt2;      // 1/dt^2, 0 for quasi-static
+  // progress
   double E, Eabs;      // energy at z and sum of |terms| (rounding scale)
   double gd;           // g . d
   double grad_inf;     // ||g||_inf at z
   double gabs_max;     // max_i of the rounding scale of g_i
-  double g_best;       // smallest ||g||_inf of this solve
-  int stall;           // iterations since ||g||_inf last halved
-  double alpha_base;   // step length of trial 0 of the current batch
-  double alpha_taken;  // accepted step length
-  double tol, armijo_c, eta_scale;
-  double floor_scale;  // kappa * unit roundoff of the element precision
-  int r, max_ls;
+  double g_best;       // reference ||g||_inf for the stall counter
+  double alpha_base;   // step length of candidate 0 of the current pass
+  double alpha_taken;  // last accepted step length
   int status;          // -1 running, else lsn_status of the solve
   int iters, ls_trials;
   int ls_iter;         // trials spent in the current line search
-  int accepted;        // line search of this iteration accepted a step
-  int eval_only;       // direction kernel only reduces (parity hook)
+  int have_dir;        // the current pass evaluated z + alpha d (speculative)
+  int final_pass;      // one more pass at z is queued to refresh positions
+  int running;         // the solve loop continues
+  int stall;           // iterations without a 10 % drop of ||g||_inf
+  int passes;          // evaluation passes of this solve
+  int pad_;
+  double z[RMAX];      // current iterate
+  double d[RMAX];      // Newton direction
+  double g[RMAX];      // reduced gradient at z
   // per-iteration history of the current solve (first TRACE iterations)
   double trace_g[TRACE], trace_E[TRACE], trace_gabs[TRACE], trace_alpha[TRACE];
 };
@@ -63,8 +81,6 @@ template <typename Real>
 void launch_convert(const double* src, Real* dst, long long count, cudaStream_t s);
 
 // decoder.cu
-enum class Epi { HiddenJac = 0, HiddenVal = 1, LastJac = 2, LastVal = 3 };
-
 struct LastArgs {            // data of the output-layer epilogue
   int n, r;
   double scale;
@@ -72,20 +88,21 @@ struct LastArgs {            // data of the output-layer epilogue
   const double* cu;          // constrained displacement targets (3 per slot)
   const double* mass;        // per vertex
   const double* ubar;        // qbar - X0 (n), dynamics only
-  double inv_dt2;            // 1/dt^2, 0 for quasi-static
+  const double* inv_dt2;     // device scalar: 1/dt^2, 0 for quasi-static
   double grav[3];
   double ground_h, ground_k; // ground plane, k = 0 off
   const double* X0;          // rest positions (n)
 };
 
+// Activations are unit-major Z[k][c] with column stride zstride(C).
 template <typename Real>
-void launch_decoder_layer(Epi epi, const Real* W, const Real* b, int M, int K,
-                          const Real* Zin, int C, Real* Zout, int ldo,
-                          Real* u_out, Real* J_out, double* part,
-                          int part_stride, const LastArgs& la, int grid_cap,
-                          cudaStream_t s);
+void launch_hidden_layer(const Real* W, const Real* b, int M, int K, const Real* Zin, int C,
+                         int nj, Real* Zout, cudaStream_t s);
+template <typename Real>
+void launch_last_layer(const Real* W, const Real* b, int M, int K, const Real* Zin, int C,
+                       int nj, Real* u_out, Real* J_out, Real* u_trial, double* part,
+                       int part_stride, const LastArgs& la, int grid, cudaStream_t s);
 int decoder_last_grid(int n, int C, int num_sms);
-int decoder_cpad(int C);
 
 // element.cu
 struct ElemArgs {
@@ -95,30 +112,34 @@ struct ElemArgs {
   const void* wv;      // Real [S]: w_e * V_e
   double mu, lam;
 };
+// grid = gfull + genergy blocks: the first gfull take the fused
+// energy / gradient / projected-Hessian contraction at u, the others the
+// energies of the KTRIAL trial fields ut[j * n + .].  Row b of `part` (stride
+// nslots_total(r)) receives the JAC slots (b < gfull) or the trial slots.
 template <typename Real>
-void launch_element_full(const ElemArgs& ea, const Real* u, const Real* J,
-                         double* part, int grid, cudaStream_t s);
-template <typename Real>
-void launch_element_energy(const ElemArgs& ea, const Real* ut, int k,
-                           double* part, int grid, cudaStream_t s);
-int element_full_grid(int S, int num_sms);
-int element_energy_grid(int S, int num_sms);
+void launch_element(const ElemArgs& ea, const Real* u, const Real* J, const Real* ut,
+                    double* part, int gfull, int genergy, cudaStream_t s);
+void element_grids(int S, int r, int num_sms, int& gfull, int& genergy);
 
 // solve.cu
-void launch_reduce_cols(const double* A, int rowsA, const double* B, int rowsB,
-                        int ncols, double* out, cudaStream_t s);
+// out[c] = sum over rows of A (all rows) and of B: rows [0, splitB) for
+// c < split, rows [splitB, rowsB) for c >= split.  Fixed order.
+void launch_reduce_partials(const double* A, int rowsA, const double* B, int rowsB,
+                            int splitB, int split, int ncols, double* out, cudaStream_t s);
+// Z0 is the first layer's input [r][zstride(C)]: column 0 the point y0,
+// columns 1..r the identity, columns r+1..r+KTRIAL the trial points.
 template <typename Real>
-void launch_newton_direction(DevSolver* sv, const double* sys, Real* Z0, int max_newton,
-                             cudaStream_t s);
+void launch_solve_begin(DevSolver* sv, Real* Z0, int C, int eval_only, cudaStream_t s);
 template <typename Real>
-void launch_ls_select(DevSolver* sv, const double* sys_t, Real* Z0, cudaStream_t s);
-template <typename Real>
-void launch_write_jac_columns(const DevSolver* sv, Real* Z0, cudaStream_t s);
+void launch_select_direction(DevSolver* sv, const double* sys, Real* Z0,
+                             unsigned long long cond, int use_cond, cudaStream_t s);
 template <typename Real>
 void launch_finish_positions(const double* X0, const Real* u, int n, double dt, double* q,
                              double* v, cudaStream_t s);
-void launch_inertial_guess(const double* X0, const double* q, const double* v, int n,
-                           double dt, const double* g /* host, 3 */, double* ubar,
-                           cudaStream_t s);
+// ubar = q + dt v + dt^2 g - X0 (dt > 0, q != NULL) and sv->inv_dt2 = 1/dt^2
+// (0 if dt == 0)
+void launch_begin_step(const double* X0, const double* q, const double* v, int n, double dt,
+                       const double* g /* host, 3 */, double* ubar, DevSolver* sv,
+                       cudaStream_t s);
 
 }  // namespace lsn

@@ -1,9 +1,22 @@
 // Reduced-system kernels of the projective Newton solve (Supplement, "Tests
 // with Projective Newton's method"; exits of Sec. 5): fixed-order reduction
-// of the per-CTA partials, FP64 r x r Cholesky with diagonal-shift retries,
-// Newton direction, and the Armijo acceptance test of the backtracking line
-// search (FP64 comparison).  Single-block kernels; r <= 64.
+// of the per-CTA partials, the Armijo test of the backtracking line search
+// (FP64 comparison), the FP64 r x r Cholesky with diagonal-shift retries and
+// the Newton direction.
+//
+// Evaluation passes.  Every pass evaluates x, J, E, g, K at one point y0 and
+// the energies at KTRIAL more points.  While a line search is open the pass
+// points are z + alpha_base 2^-j d, j = 0..KTRIAL, i.e. the next candidates
+// of the halving sequence 1, 1/2, 1/4, ...; the first that satisfies Armijo
+// is taken, exactly as one-at-a-time backtracking would.  When the full
+// candidate y0 is taken, the pass already holds g and K there and the next
+// direction follows at once (one pass per Newton iteration); when a shorter
+// step is taken, the next pass evaluates at the new z.  select_direction runs
+// after every pass, decides, and writes the points of the next pass.
+// Single-block kernels; r <= 64.
 #include "lsn_internal.cuh"
+
+#include <cstddef>
 
 namespace lsn {
 namespace {
@@ -15,238 +28,310 @@ __device__ __forceinline__ int upper_index(int i, int j, int r) {
   return i * r - (i * (i - 1)) / 2 + (j - i);
 }
 
-__global__ void reduce_cols_kernel(const double* __restrict__ A, int rowsA,
-                                   const double* __restrict__ B, int rowsB, int ncols,
-                                   double* __restrict__ out) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncols) return;
+// One warp per output column; lanes stride over the rows, then a fixed
+// shuffle tree: the summation order does not depend on scheduling.
+__global__ void reduce_partials_kernel(const double* __restrict__ A, int rowsA,
+                                       const double* __restrict__ B, int rowsB, int splitB,
+                                       int split, int ncols, double* __restrict__ out) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= ncols) return;
+  const int c = warp;
   double s = 0.0;
-  for (int b = 0; b < rowsA; ++b) s += A[(size_t)b * ncols + c];
-  for (int b = 0; b < rowsB; ++b) s += B[(size_t)b * ncols + c];
-  out[c] = s;
+  for (int b = lane; b < rowsA; b += 32) s += A[(size_t)b * ncols + c];
+  const int b0 = c < split ? 0 : splitB, b1 = c < split ? splitB : rowsB;
+  for (int b = b0 + lane; b < b1; b += 32) s += B[(size_t)b * ncols + c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) out[c] = s;
 }
 
+// y0 = z + a0 d, trial j: z + a0 2^-j d (Z0[i][col], column stride CPs).
 template <typename Real>
-__device__ void write_trial_columns(DevSolver* sv, Real* Z0) {
-  const int r = sv->r;
-  for (int e = threadIdx.x; e < KTRIAL * r; e += blockDim.x) {
+__device__ void write_pass_points(DevSolver* sv, Real* Z0, double a0, bool with_dir) {
+  const int r = sv->r, CPs = zstride(r + 1 + KTRIAL);
+  for (int e = threadIdx.x; e < (1 + KTRIAL) * r; e += blockDim.x) {
     const int j = e / r, i = e - j * r;
-    const double a = ldexp(sv->alpha_base, -j);
-    Z0[j * r + i] = (Real)(sv->z[i] + a * sv->d[i]);
+    const double a = with_dir ? ldexp(a0, -j) : 0.0;
+    const double v = sv->z[i] + a * sv->d[i];
+    const int col = j == 0 ? 0 : r + j;
+    Z0[i * CPs + col] = (Real)v;
   }
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(ST) newton_direction_kernel(DevSolver* sv,
-                                                              const double* __restrict__ sys,
-                                                              Real* Z0, int max_newton) {
-  __shared__ double L[RMAX][RMAX + 1];
-  __shared__ double g[RMAX], y[RMAX];
-  __shared__ double red[ST];
-  __shared__ int fail;
-  __shared__ double diag_j;
-  const int t = threadIdx.x;
+__global__ void solve_begin_kernel(DevSolver* sv, Real* Z0, int C, int eval_only) {
   const int r = sv->r;
-  if (sv->status != -1) return;
-  // g and the symmetric K (upper triangle in sys) from the reduced partial sums
-  const double* Ku = sys + slot_K(r);
-  for (int i = t; i < r; i += ST) g[i] = sys[slot_g(i)];
-  __syncthreads();
-  double gm = 0.0, ga = 0.0;
-  bool finite = true;
-  for (int i = t; i < r; i += ST) {
-    gm = fmax(gm, fabs(g[i]));
-    ga = fmax(ga, sys[slot_gabs(r, i)]);
-    finite = finite && isfinite(g[i]);
-  }
-  for (int e = t; e < npairs(r); e += ST) finite = finite && isfinite(Ku[e]);
-  red[t] = finite ? gm : -1.0;
-  __syncthreads();
-  for (int s = ST / 2; s > 0; s >>= 1) {
-    if (t < s) red[t] = (red[t] < 0.0 || red[t + s] < 0.0) ? -1.0 : fmax(red[t], red[t + s]);
-    __syncthreads();
-  }
-  const double ginf = red[0];
-  __syncthreads();
-  red[t] = ga;
-  __syncthreads();
-  for (int s = ST / 2; s > 0; s >>= 1) {
-    if (t < s) red[t] = fmax(red[t], red[t + s]);
-    __syncthreads();
-  }
-  const double gabs_max = red[0];
-  const double E = sys[0];
-  __syncthreads();
-  // progress bookkeeping for the precision-floor exit
-  __shared__ int stall;
-  if (t == 0) {
-    sv->E = E;
-    sv->Eabs = sys[1];
-    sv->grad_inf = ginf;
-    sv->gabs_max = gabs_max;
-    if (!sv->eval_only) {
-      if (sv->iters < TRACE) {
-        sv->trace_g[sv->iters] = ginf;
-        sv->trace_E[sv->iters] = E;
-        sv->trace_gabs[sv->iters] = gabs_max;
-        sv->trace_alpha[sv->iters] = 0.0;
-      }
-      if (ginf <= 0.5 * sv->g_best) {
-        sv->g_best = ginf;
-        sv->stall = 0;
-      } else {
-        sv->g_best = fmin(sv->g_best, ginf);
-        sv->stall += 1;
-      }
-    }
-    stall = sv->stall;
-  }
-  for (int i = t; i < r; i += ST) sv->g[i] = g[i];
-  __syncthreads();
-  if (sv->eval_only) return;
-  if (ginf < 0.0 || !isfinite(E)) {
-    if (t == 0) sv->status = -3;  // LSN_ERR_NONFINITE
-    return;
-  }
-  if (ginf < sv->tol) {
-    if (t == 0) sv->status = 0;  // LSN_OK
-    return;
-  }
-  // ||g|| has stopped decreasing and is within the rounding scale of its own
-  // evaluation: further iterations cannot be resolved at this precision
-  if (stall >= 4 && ginf <= sv->floor_scale * gabs_max) {
-    if (t == 0) sv->status = 4;  // LSN_PRECISION_FLOOR
-    return;
-  }
-  if (sv->iters >= max_newton) {
-    if (t == 0) sv->status = 1;  // LSN_NOT_CONVERGED
-    return;
-  }
-  // Cholesky K + shift I = L L^T, shift = 0, then 1e-12 max(1, max|K_ii|) x 10^k
-  double dmax = 0.0;
-  for (int i = 0; i < r; ++i) dmax = fmax(dmax, fabs(Ku[upper_index(i, i, r)]));
-  const double base = 1e-12 * fmax(1.0, dmax);
-  double shift = 0.0;
-  bool ok = false;
-  for (int attempt = 0; attempt < 21 && !ok; ++attempt) {
-    for (int e = t; e < r * r; e += ST) {
-      int i = e / r, j = e - i * r;
-      L[i][j] = (i <= j ? Ku[upper_index(i, j, r)] : Ku[upper_index(j, i, r)]) +
-                (i == j ? shift : 0.0);
-    }
-    if (t == 0) fail = 0;
-    __syncthreads();
-    for (int j = 0; j < r; ++j) {
-      if (t == 0) {
-        double s = L[j][j];
-        for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
-        if (!(s > 0.0)) fail = 1;
-        diag_j = s > 0.0 ? sqrt(s) : 1.0;
-        L[j][j] = diag_j;
-      }
-      __syncthreads();
-      if (fail) break;
-      for (int i = j + 1 + t; i < r; i += ST) {
-        double s = L[i][j];
-        for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-        L[i][j] = s / diag_j;
-      }
-      __syncthreads();
-    }
-    __syncthreads();
-    ok = !fail;
-    if (!ok) shift = shift == 0.0 ? base : shift * 10.0;
-    __syncthreads();
-  }
-  if (!ok) {
-    if (t == 0) sv->status = 3;  // LSN_NOT_SPD
-    return;
-  }
-  // forward L y = -g, backward L^T d = y (column sweeps)
-  for (int i = t; i < r; i += ST) y[i] = -g[i];
-  __syncthreads();
-  for (int i = 0; i < r; ++i) {
-    if (t == 0) y[i] /= L[i][i];
-    __syncthreads();
-    for (int k = i + 1 + t; k < r; k += ST) y[k] -= L[k][i] * y[i];
-    __syncthreads();
-  }
-  for (int i = r - 1; i >= 0; --i) {
-    if (t == 0) y[i] /= L[i][i];
-    __syncthreads();
-    for (int k = t; k < i; k += ST) y[k] -= L[i][k] * y[i];
-    __syncthreads();
-  }
-  for (int i = t; i < r; i += ST) sv->d[i] = y[i];
-  red[t] = 0.0;
-  for (int i = t; i < r; i += ST) red[t] += g[i] * y[i];
-  __syncthreads();
-  for (int s = ST / 2; s > 0; s >>= 1) {
-    if (t < s) red[t] += red[t + s];
-    __syncthreads();
-  }
-  if (t == 0) {
-    sv->gd = red[0];
-    sv->alpha_base = 1.0;
-    sv->accepted = 0;
-    sv->ls_iter = 0;
-  }
-  __syncthreads();
-  write_trial_columns<Real>(sv, Z0);
-}
-
-// Armijo test of the batch of KTRIAL step lengths alpha_base 2^-j, in order;
-// the first that passes is taken (same result as one-at-a-time halving).
-template <typename Real>
-__global__ void ls_select_kernel(DevSolver* sv, const double* __restrict__ sys_t, Real* Z0) {
-  __shared__ int acc, go;
-  if (threadIdx.x == 0) go = (sv->status == -1 && !sv->accepted);
-  __syncthreads();
-  if (!go) return;
   if (threadIdx.x == 0) {
-    acc = -1;
-    for (int j = 0; j < KTRIAL; ++j) {
-      if (sv->ls_iter >= sv->max_ls) break;
-      sv->ls_iter += 1;
-      sv->ls_trials += 1;
-      const double a = ldexp(sv->alpha_base, -j);
-      const double Et = sys_t[2 * j];
-      const double eta = sv->eta_scale * (sys_t[2 * j + 1] + sv->Eabs);
-      if (isfinite(Et) && Et <= sv->E + sv->armijo_c * a * sv->gd + eta) {
-        acc = j;
-        sv->alpha_taken = a;
-        break;
-      }
-    }
-    if (acc < 0) {
-      if (sv->ls_iter >= sv->max_ls) {
-        sv->status = (sv->grad_inf < 100.0 * sv->tol) ? 4 : 2;
-      } else {
-        sv->alpha_base = ldexp(sv->alpha_base, -KTRIAL);
-      }
-    } else {
-      if (sv->iters < TRACE) sv->trace_alpha[sv->iters] = ldexp(sv->alpha_base, -acc);
-      sv->accepted = 1;
-      sv->iters += 1;
-    }
+    sv->status = -1;
+    sv->iters = 0;
+    sv->ls_trials = 0;
+    sv->ls_iter = 0;
+    sv->have_dir = 0;
+    sv->final_pass = 0;
+    sv->running = 1;
+    sv->stall = 0;
+    sv->passes = 0;
+    sv->g_best = 1e300;
+    sv->alpha_base = 1.0;
+    sv->eval_only = eval_only;
   }
-  __syncthreads();
-  if (acc >= 0) {
-    const double a = ldexp(sv->alpha_base, -acc);
-    for (int i = threadIdx.x; i < sv->r; i += blockDim.x) sv->z[i] += a * sv->d[i];
-  } else if (sv->status == -1) {
-    write_trial_columns<Real>(sv, Z0);
+  const int CPs = zstride(C);
+  for (int e = threadIdx.x; e < CPs * r; e += blockDim.x) {
+    const int i = e / CPs, c = e - i * CPs;
+    Z0[e] = c >= C ? Real(0)
+                   : ((c == 0 || c > r) ? (Real)sv->z[i] : (i == c - 1 ? Real(1) : Real(0)));
   }
 }
 
-// Z0 = [z | I_r] (Jacobian pass; column-major, leading dimension r).
+// Warp-wide helpers (the select kernel is a single warp: no block barriers).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// The select kernel works on a shared-memory copy of the solver state: one
+// parallel load at entry and one parallel store at exit, so that the serial
+// decision logic of lane 0 does not wait on global-memory round trips.
+constexpr int SV_SCALAR_WORDS = (int)(offsetof(DevSolver, z) / sizeof(double));
+
 template <typename Real>
-__global__ void write_jac_columns_kernel(const DevSolver* sv, Real* Z0) {
-  const int r = sv->r;
-  for (int e = threadIdx.x; e < (r + 1) * r; e += blockDim.x) {
-    const int c = e / r, i = e - c * r;
-    Z0[e] = c == 0 ? (Real)sv->z[i] : (i == c - 1 ? Real(1) : Real(0));
+__global__ void __launch_bounds__(32) select_direction_kernel(DevSolver* gsv,
+                                                              const double* __restrict__ sys,
+                                                              Real* Z0,
+                                                              unsigned long long cond,
+                                                              int use_cond) {
+  __shared__ double L[RMAX][RMAX + 1];
+  __shared__ double y[RMAX];
+  __shared__ double ssys[4 * RMAX + 2 * KTRIAL + 2];
+  __shared__ __align__(16) DevSolver svs;
+  DevSolver* sv = &svs;
+  const int t = threadIdx.x;
+  // ---- parallel load of the state (scalars, z, d) and of E, g, gabs, trials
+  {
+    const double* src = reinterpret_cast<const double*>(gsv);
+    double* dst = reinterpret_cast<double*>(&svs);
+    for (int e = t; e < SV_SCALAR_WORDS + 2 * RMAX; e += 32) dst[e] = src[e];
   }
+  __syncwarp();
+  const int r = sv->r;
+  const int tslot = nslots(r);
+  const double* Ku = sys + slot_K(r);
+  for (int e = t; e < 2 + 2 * r; e += 32) ssys[e] = sys[e];
+  for (int e = t; e < 2 * KTRIAL; e += 32) ssys[2 + 2 * r + e] = sys[tslot + e];
+  // K into L (needed only when a direction is computed; issued early)
+  for (int e = t; e < r * r; e += 32) {
+    const int i = e / r, j = e - i * r;
+    L[i][j] = i <= j ? Ku[upper_index(i, j, r)] : Ku[upper_index(j, i, r)];
+  }
+  __syncwarp();
+  const double* sE = ssys;                    // E, Eabs at y0
+  const double* sg = ssys + 2;                // g
+  const double* sga = ssys + 2 + r;           // gabs
+  const double* sT = ssys + 2 + 2 * r;        // trial (E_j, Eabs_j)
+  // ------------------------------------------------ line-search decision
+  int at_z = 1, stepped = 0;
+  if (t == 0) {
+    sv->passes += 1;
+    if (sv->final_pass) {
+      sv->final_pass = 0;
+      sv->running = 0;
+      at_z = -2;
+    } else if (sv->have_dir) {
+      int acc = -1;
+      for (int j = 0; j <= KTRIAL; ++j) {
+        if (sv->ls_iter >= sv->max_ls) break;
+        sv->ls_iter += 1;
+        sv->ls_trials += 1;
+        const double a = ldexp(sv->alpha_base, -j);
+        const double Et = j == 0 ? sE[0] : sT[2 * (j - 1)];
+        const double Ea = j == 0 ? sE[1] : sT[2 * (j - 1) + 1];
+        const double eta = sv->eta_scale * (Ea + sv->Eabs);
+        if (isfinite(Et) && Et <= sv->E + sv->armijo_c * a * sv->gd + eta) {
+          acc = j;
+          break;
+        }
+      }
+      if (acc >= 0) {
+        const double a = ldexp(sv->alpha_base, -acc);
+        sv->alpha_taken = a;
+        if (sv->iters < TRACE) gsv->trace_alpha[sv->iters] = a;
+        sv->iters += 1;
+        sv->have_dir = 0;
+        at_z = acc == 0 ? 1 : 0;
+        stepped = 1;
+      } else if (sv->ls_iter >= sv->max_ls) {
+        sv->status = (sv->grad_inf < 100.0 * sv->tol) ? 4 : 2;  // PRECISION_FLOOR : LS_FAILED
+        sv->have_dir = 0;
+        sv->final_pass = 1;  // positions must be re-evaluated at z
+        at_z = -1;
+      } else {
+        sv->alpha_base = ldexp(sv->alpha_base, -(KTRIAL + 1));
+        at_z = -1;  // keep backtracking along d
+      }
+    }
+  }
+  at_z = __shfl_sync(0xffffffffu, at_z, 0);
+  stepped = __shfl_sync(0xffffffffu, stepped, 0);
+  __syncwarp();
+  if (stepped) {  // a step was taken: z += alpha d
+    for (int i = t; i < r; i += 32) sv->z[i] += sv->alpha_taken * sv->d[i];
+    __syncwarp();
+  }
+  int status = -1;
+  bool want_cond = true;
+  int cond_val = 1;
+  if (at_z == -2) {  // the final re-evaluation at z is done
+    cond_val = 0;
+  } else if (at_z == -1) {
+    write_pass_points<Real>(sv, Z0, sv->alpha_base, sv->status == -1);
+    if (t == 0) sv->running = 1;
+  } else if (at_z == 0) {  // a shorter step was taken: evaluate at the new z next
+    write_pass_points<Real>(sv, Z0, 0.0, false);
+  } else {
+    // ------------------------------------------- sys holds E, g, K at z
+    double gm = 0.0, ga = 0.0;
+    bool finite = true;
+    for (int i = t; i < r; i += 32) {
+      const double gi = sg[i];
+      y[i] = -gi;
+      gm = fmax(gm, fabs(gi));
+      ga = fmax(ga, sga[i]);
+      finite = finite && isfinite(gi);
+    }
+    for (int e = t; e < r * r; e += 32) finite = finite && isfinite(L[e / r][e % r]);
+    const double ginf = __all_sync(0xffffffffu, finite) ? warp_max(gm) : -1.0;
+    const double gabs_max = warp_max(ga);
+    const double E = sE[0];
+    int stall = 0;
+    if (t == 0) {
+      sv->E = E;
+      sv->Eabs = sE[1];
+      sv->grad_inf = ginf;
+      sv->gabs_max = gabs_max;
+      if (!sv->eval_only) {
+        if (sv->iters < TRACE) {
+          gsv->trace_g[sv->iters] = ginf;
+          gsv->trace_E[sv->iters] = E;
+          gsv->trace_gabs[sv->iters] = gabs_max;
+          gsv->trace_alpha[sv->iters] = 0.0;
+        }
+        // stall counter: iterations since ||g||_inf last dropped by 10 %
+        if (ginf <= 0.9 * sv->g_best) {
+          sv->g_best = ginf;
+          sv->stall = 0;
+        } else {
+          sv->stall += 1;
+        }
+      }
+      stall = sv->stall;
+    }
+    stall = __shfl_sync(0xffffffffu, stall, 0);
+    if (sv->eval_only) status = 0;
+    else if (ginf < 0.0 || !isfinite(E)) status = -3;              // LSN_ERR_NONFINITE
+    else if (ginf < sv->tol) status = 0;                           // LSN_OK
+    else if (stall >= 4 && ginf <= sv->floor_scale * gabs_max) status = 4;  // PRECISION_FLOOR
+    else if (sv->iters >= sv->max_newton) status = 1;              // LSN_NOT_CONVERGED
+    if (status != -1) {
+      if (t == 0) {
+        if (!sv->eval_only) sv->status = status;
+        sv->running = 0;
+      }
+      cond_val = 0;
+    } else {
+      // Cholesky K + shift I = L L^T, shift = 0, then 1e-12 max(1, max|K_ii|) x 10^k
+      double dm = 0.0;
+      for (int i = t; i < r; i += 32) dm = fmax(dm, fabs(L[i][i]));
+      const double base = 1e-12 * fmax(1.0, warp_max(dm));
+      double shift = 0.0;
+      bool ok = false;
+      for (int attempt = 0; attempt < 21 && !ok; ++attempt) {
+        if (attempt > 0) {
+          __syncwarp();
+          for (int e = t; e < r * r; e += 32) {
+            const int i = e / r, j = e - i * r;
+            L[i][j] = (i <= j ? Ku[upper_index(i, j, r)] : Ku[upper_index(j, i, r)]) +
+                      (i == j ? shift : 0.0);
+          }
+          __syncwarp();
+        }
+        bool fail = false;
+        for (int j = 0; j < r && !fail; ++j) {
+          double s = 0.0;
+          for (int k = t; k < j; k += 32) s += L[j][k] * L[j][k];
+          s = L[j][j] - warp_sum(s);
+          if (!(s > 0.0)) {
+            fail = true;
+            break;
+          }
+          const double djj = sqrt(s);
+          __syncwarp();
+          if (t == 0) L[j][j] = djj;
+          for (int i = j + 1 + t; i < r; i += 32) {
+            double v = L[i][j];
+            for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+            L[i][j] = v / djj;
+          }
+          __syncwarp();
+        }
+        ok = !fail;
+        if (!ok) shift = shift == 0.0 ? base : shift * 10.0;
+      }
+      if (!ok) {
+        if (t == 0) {
+          sv->status = 3;  // LSN_NOT_SPD
+          sv->running = 0;
+        }
+        cond_val = 0;
+      } else {
+        // forward L y = -g, backward L^T d = y (column sweeps within the warp)
+        __syncwarp();
+        for (int i = 0; i < r; ++i) {
+          const double yi = y[i] / L[i][i];
+          __syncwarp();
+          if (t == 0) y[i] = yi;
+          for (int k = i + 1 + t; k < r; k += 32) y[k] -= L[k][i] * yi;
+          __syncwarp();
+        }
+        for (int i = r - 1; i >= 0; --i) {
+          const double yi = y[i] / L[i][i];
+          __syncwarp();
+          if (t == 0) y[i] = yi;
+          for (int k = t; k < i; k += 32) y[k] -= L[i][k] * yi;
+          __syncwarp();
+        }
+        double gd = 0.0;
+        for (int i = t; i < r; i += 32) {
+          sv->d[i] = y[i];
+          gd += sg[i] * y[i];
+        }
+        gd = warp_sum(gd);
+        if (t == 0) {
+          sv->gd = gd;
+          sv->alpha_base = 1.0;
+          sv->ls_iter = 0;
+          sv->have_dir = 1;
+          sv->running = 1;
+        }
+        __syncwarp();
+        write_pass_points<Real>(sv, Z0, 1.0, true);
+      }
+    }
+    for (int i = t; i < r; i += 32) gsv->g[i] = sg[i];
+  }
+  // ---- parallel store of the state
+  __syncwarp();
+  {
+    const double* src = reinterpret_cast<const double*>(&svs);
+    double* dst = reinterpret_cast<double*>(gsv);
+    for (int e = t; e < SV_SCALAR_WORDS + 2 * RMAX; e += 32) dst[e] = src[e];
+  }
+  if (want_cond && use_cond && t == 0) cudaGraphSetConditional(cond, cond_val);
 }
 
 template <typename Real>
@@ -260,13 +345,14 @@ __global__ void finish_positions_kernel(const double* __restrict__ X0,
   q[i] = qn;
 }
 
-__global__ void inertial_guess_kernel(const double* __restrict__ X0,
-                                      const double* __restrict__ q,
-                                      const double* __restrict__ v, int n, double dt,
-                                      double gx, double gy, double gz,
-                                      double* __restrict__ ubar) {
+__global__ void begin_step_kernel(const double* __restrict__ X0,
+                                  const double* __restrict__ q,
+                                  const double* __restrict__ v, int n, double dt,
+                                  double gx, double gy, double gz,
+                                  double* __restrict__ ubar, DevSolver* sv) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i == 0) sv->inv_dt2 = dt > 0.0 ? 1.0 / (dt * dt) : 0.0;
+  if (i >= n || !(dt > 0.0) || q == nullptr) return;
   const int c = i % 3;
   const double g = c == 0 ? gx : (c == 1 ? gy : gz);
   ubar[i] = (q[i] - X0[i]) + dt * v[i] + dt * dt * g;
@@ -274,25 +360,22 @@ __global__ void inertial_guess_kernel(const double* __restrict__ X0,
 
 }  // namespace
 
-void launch_reduce_cols(const double* A, int rowsA, const double* B, int rowsB, int ncols,
-                        double* out, cudaStream_t s) {
-  reduce_cols_kernel<<<(ncols + 127) / 128, 128, 0, s>>>(A, rowsA, B, rowsB, ncols, out);
+void launch_reduce_partials(const double* A, int rowsA, const double* B, int rowsB,
+                            int splitB, int split, int ncols, double* out, cudaStream_t s) {
+  const int threads = 256, warps = threads / 32;
+  reduce_partials_kernel<<<(ncols + warps - 1) / warps, threads, 0, s>>>(
+      A, rowsA, B, rowsB, splitB, split, ncols, out);
 }
 
 template <typename Real>
-void launch_newton_direction(DevSolver* sv, const double* sys, Real* Z0, int max_newton,
-                             cudaStream_t s) {
-  newton_direction_kernel<Real><<<1, ST, 0, s>>>(sv, sys, Z0, max_newton);
+void launch_solve_begin(DevSolver* sv, Real* Z0, int C, int eval_only, cudaStream_t s) {
+  solve_begin_kernel<Real><<<1, 256, 0, s>>>(sv, Z0, C, eval_only);
 }
 
 template <typename Real>
-void launch_ls_select(DevSolver* sv, const double* sys_t, Real* Z0, cudaStream_t s) {
-  ls_select_kernel<Real><<<1, 64, 0, s>>>(sv, sys_t, Z0);
-}
-
-template <typename Real>
-void launch_write_jac_columns(const DevSolver* sv, Real* Z0, cudaStream_t s) {
-  write_jac_columns_kernel<Real><<<1, 256, 0, s>>>(sv, Z0);
+void launch_select_direction(DevSolver* sv, const double* sys, Real* Z0,
+                             unsigned long long cond, int use_cond, cudaStream_t s) {
+  select_direction_kernel<Real><<<1, 32, 0, s>>>(sv, sys, Z0, cond, use_cond);
 }
 
 template <typename Real>
@@ -301,18 +384,17 @@ void launch_finish_positions(const double* X0, const Real* u, int n, double dt, 
   finish_positions_kernel<Real><<<(n + 255) / 256, 256, 0, s>>>(X0, u, n, dt, q, v);
 }
 
-void launch_inertial_guess(const double* X0, const double* q, const double* v, int n,
-                           double dt, const double* g, double* ubar, cudaStream_t s) {
-  inertial_guess_kernel<<<(n + 255) / 256, 256, 0, s>>>(X0, q, v, n, dt, g[0], g[1], g[2],
-                                                        ubar);
+void launch_begin_step(const double* X0, const double* q, const double* v, int n, double dt,
+                       const double* g, double* ubar, DevSolver* sv, cudaStream_t s) {
+  begin_step_kernel<<<(n + 255) / 256, 256, 0, s>>>(X0, q, v, n, dt, g[0], g[1], g[2], ubar,
+                                                    sv);
 }
 
-#define LSN_INST(R)                                                                   \
-  template void launch_newton_direction<R>(DevSolver*, const double*, R*, int,        \
-                                           cudaStream_t);                             \
-  template void launch_ls_select<R>(DevSolver*, const double*, R*, cudaStream_t);     \
-  template void launch_write_jac_columns<R>(const DevSolver*, R*, cudaStream_t);      \
-  template void launch_finish_positions<R>(const double*, const R*, int, double,      \
+#define LSN_INST(R)                                                                      \
+  template void launch_solve_begin<R>(DevSolver*, R*, int, int, cudaStream_t);           \
+  template void launch_select_direction<R>(DevSolver*, const double*, R*,                \
+                                           unsigned long long, int, cudaStream_t);       \
+  template void launch_finish_positions<R>(const double*, const R*, int, double,         \
                                            double*, double*, cudaStream_t);
 LSN_INST(float)
 LSN_INST(double)
