@@ -215,6 +215,51 @@ int lsn_get_profile(lsn_ctx* ctx, int cls, long long* launches,
                     long long* timed_launches, double* ms_total);
 int lsn_reset_profile(lsn_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free entry point.  The paper has no counterpart to this call: it
+ * exists for callers that cannot allocate device memory while they run, for
+ * example an engine that gives the library a fixed memory budget up front, a
+ * caller working inside a memory pool or arena that must not grow, or a
+ * real-time loop where cudaMalloc / cudaFree (which can synchronise the
+ * device and can fail) is not allowed.
+ *
+ * lsn_element_system_noalloc evaluates the elastic part of the reduced
+ * system for S tets with the solver's own element kernel (Stable Neo-Hookean
+ * energy, gradient and PSD-projected Hessian per tet, contracted with the
+ * tets' rows of J) and writes
+ *     out[0] = sum_e P_e, out[1] = sum_e |P_e|, out[2 + i] = g_i,
+ *     out[2 + r + i] = sum of |contributions to g_i|,
+ *     out[2 + 2r + k] = K upper triangle, row-major (i <= j), k < r(r+1)/2,
+ * i.e. nslots = 2 + 2r + r(r+1)/2 doubles.  It allocates nothing: its
+ * partial sums live in a file-scope device array of LSN_NOALLOC_SCRATCH_DOUBLES
+ * doubles (4 MiB) that every GPU which loads the library holds until the
+ * process exits.  A problem whose partial sums do not fit, that is
+ * (CTAs + 1) * (nslots + 6) > LSN_NOALLOC_SCRATCH_DOUBLES with the solver's
+ * launch shape (at most two CTAs per SM, one per 64 or 128 tets), is
+ * rejected with LSN_ERR_ARG; r is limited to 64 as elsewhere.
+ *
+ * All inputs are device pointers (FP32 apart from the indices): tets S x 4
+ * vertex indices, dminv the per-tet inverse rest edge matrices stored
+ * structure-of-arrays (entry (a, b) of tet e at dminv[(3 a + b) S + e]),
+ * wvol the weight times rest volume of each tet, u the n displacements
+ * x - X0, J the n x r Jacobian (row-major).  mu, lam are the Lame
+ * parameters.  out is device memory or pinned host memory.  Work is issued on
+ * cuda_stream (a cudaStream_t, NULL = default stream) and is complete when
+ * that stream has synchronised.
+ *
+ * The first call on a device (the current device when it is made) looks up
+ * the device address of the scratch array for that device; make that first
+ * call before any stream capture.  Every call on a device shares the one
+ * scratch array, and the array keeps the last call's partial sums: calls that
+ * may overlap on the GPU (different streams, or host threads without
+ * ordering) race and must be serialised by the caller.  Nothing needs
+ * clearing between calls: each call writes every partial it reads. */
+#define LSN_NOALLOC_SCRATCH_DOUBLES 524288
+int lsn_element_system_noalloc(int S, int r, int n, const int32_t* tets,
+                               const float* dminv, const float* wvol,
+                               const float* u, const float* J, double mu,
+                               double lam, double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

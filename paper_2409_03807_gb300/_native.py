@@ -65,6 +65,10 @@ _SIGS = {
     "lsn_get_profile": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                         ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)],
     "lsn_reset_profile": [ctypes.c_void_p],
+    "lsn_element_system_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_void_p, ctypes.c_void_p],
 }
 
 KERNEL_CLASSES = ["decoder_hidden", "decoder_last", "element", "decoder_trial",
@@ -116,6 +120,16 @@ def _i32(a):
     if a is None or hasattr(a, "data_ptr"):
         return a
     return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def element_system_noalloc(S, r, n, tets, dminv, wvol, u, J, mu, lam, out, stream=None):
+    """Allocation-free elastic reduced system (see include/lsn.h): all array
+    arguments are device tensors; returns the C status."""
+    lib = load()
+    st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    return lib.lsn_element_system_noalloc(int(S), int(r), int(n), _ptr(tets), _ptr(dminv),
+                                          _ptr(wvol), _ptr(u), _ptr(J), float(mu), float(lam),
+                                          _ptr(out), st)
 
 
 class Context:
