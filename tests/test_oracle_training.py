@@ -1,0 +1,115 @@
+"""Pins of the oracle's training objective (Sec. 4: Eq. 3, 7, 9, 10, 11)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import fem
+from oracle.decoder import Decoder
+from oracle.training import (TrainProblem, lipschitz_loss, lipschitz_estimate,
+                             loss_and_grad, closed_form_hessian)
+from workloads import make_bar, xavier_decoder
+
+
+@pytest.fixture(scope="module")
+def setup():
+    mesh = make_bar(6, 3, 3, 0.05)
+    n = 3 * mesh.nv
+    widths = [3, 8, 8, n]
+    rng = np.random.default_rng(0)
+    cub = np.sort(rng.choice(mesh.ne, 10, replace=False))
+    w = rng.uniform(0.5, 4.0, 10)
+    tp = TrainProblem(mesh.X0, mesh.tets, widths, 0.05, 1e5, 0.45, 1000.0, cub, w)
+    Ws, bs = xavier_decoder(widths, 1)
+    bs = [0.05 * rng.standard_normal(b.shape) for b in bs]
+    Ew = 0.3 * rng.standard_normal((3, n))
+    eb = 0.1 * rng.standard_normal(3)
+    theta = tp.pack(Ew, eb, Ws, bs)
+    Q = mesh.X0.ravel()[None] + 0.02 * rng.standard_normal((4, n))
+    return tp, theta, Q, Ws, bs
+
+
+def test_autodiff_hessian_equals_closed_form(setup):
+    tp, theta, Q, Ws, bs = setup
+    P = tp.unpack(torch.tensor(theta))
+    dec = Decoder([np.asarray(W, np.float64) for W in Ws], [np.asarray(b) for b in bs], tp.scale)
+    for z in np.random.default_rng(1).standard_normal((3, 3)):
+        H = tp.hessian(P, torch.tensor(z)).numpy()
+        Hc = closed_form_hessian(tp, dec, z)
+        assert np.allclose(H, Hc, rtol=1e-9, atol=1e-9 * np.abs(Hc).max())
+        assert np.allclose(H, H.T, atol=1e-12 * np.abs(H).max())
+
+
+def test_hessian_equals_differences_of_reduced_gradient(setup):
+    tp, theta, Q, Ws, bs = setup
+    P = tp.unpack(torch.tensor(theta))
+    dec = Decoder([np.asarray(W, np.float64) for W in Ws], [np.asarray(b) for b in bs], tp.scale)
+    tl = tp.ctets_local.numpy()
+    ones = np.ones(tl.shape[0])
+
+    def grad(z):  # sum_e w_e J_e^T g_e (Eq. 11 over the cubature set)
+        o, J = dec.out_jac(z, tp.rows)
+        xv = (tp.X0.ravel()[tp.rows] + o).reshape(-1, 3)
+        ge = fem.element_gradient(xv, tl, tp.cDmInv.numpy(), ones, tp.mu, tp.lam)
+        return np.einsum("e,eki,ek->i", tp.cw.numpy(), J[fem.element_dofs(tl)], ge)
+
+    z = np.array([0.3, -0.7, 0.4])
+    H = tp.hessian(P, torch.tensor(z)).numpy()
+    h = 1e-6
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        fd = (grad(z + e) - grad(z - e)) / (2 * h)
+        assert np.allclose(fd, H[:, k], rtol=1e-5, atol=1e-6 * np.abs(H).max())
+
+
+def test_lipschitz_loss_brute_force():
+    rng = np.random.default_rng(2)
+    H = torch.tensor(rng.standard_normal((3, 4, 4)))
+    H = H + H.transpose(1, 2)
+    Z = torch.tensor(rng.standard_normal((3, 4)))
+    tot = 0.0
+    for i in range(3):
+        for j in range(3):
+            if i != j:
+                tot += float(((H[i] - H[j]) ** 2).sum() / ((Z[i] - Z[j]) ** 2).sum())
+    assert float(lipschitz_loss(H, Z)) == pytest.approx(tot / 6, rel=1e-14)
+    best = max(float(torch.linalg.norm(H[i] - H[j]) / torch.linalg.norm(Z[i] - Z[j]))
+               for i in range(3) for j in range(3) if i != j)
+    assert lipschitz_estimate(H, Z) == pytest.approx(best, rel=1e-14)
+    # two samples: the mean over the two ordered pairs is the single ratio
+    assert float(lipschitz_loss(H[:2], Z[:2])) == pytest.approx(
+        float(((H[0] - H[1]) ** 2).sum() / ((Z[0] - Z[1]) ** 2).sum()), rel=1e-14)
+
+
+def test_reconstruction_loss_definition(setup):
+    tp, theta, Q, Ws, bs = setup
+    (Lc, Lls, L), g, Z, H = loss_and_grad(tp, theta, Q, 0.0)
+    P = tp.unpack(torch.tensor(theta))
+    dec = Decoder([np.asarray(W, np.float64) for W in Ws], [np.asarray(b) for b in bs], tp.scale)
+    Ew, eb = theta[:3 * tp.n].reshape(3, tp.n), theta[3 * tp.n:3 * tp.n + 3]
+    ref = 0.0
+    for q in Q:
+        z = Ew @ (q - tp.X0.ravel()) + eb
+        x = tp.X0.ravel() + dec.out(z)
+        ref += np.sum(np.repeat(tp.mass, 3) * (x - q) ** 2)
+    assert Lc == pytest.approx(ref / Q.shape[0], rel=1e-12)
+    assert Lls == 0.0 and L == Lc
+
+
+@pytest.mark.parametrize("lam_ls", [0.0, 1e-3])
+def test_parameter_gradient_by_central_differences(setup, lam_ls):
+    tp, theta, Q, Ws, bs = setup
+    (Lc, Lls, L), g, Z, H = loss_and_grad(tp, theta, Q, lam_ls)
+    rng = np.random.default_rng(100)
+    idx = rng.choice(theta.shape[0], 8, replace=False)
+    # include a last-layer weight of a cubature row and a hidden weight
+    for k in idx:
+        h = 1e-6 * max(1.0, abs(theta[k]))
+        tp_, tm_ = theta.copy(), theta.copy()
+        tp_[k] += h
+        tm_[k] -= h
+        # the Lipschitz samples z_i carry no gradient: hold them fixed
+        Lp = loss_and_grad(tp, tp_, Q, lam_ls, Z_samples=Z)[0][2]
+        Lm = loss_and_grad(tp, tm_, Q, lam_ls, Z_samples=Z)[0][2]
+        fd = (Lp - Lm) / (2 * h)
+        assert fd == pytest.approx(g[k], rel=1e-5, abs=1e-8 * max(1.0, abs(L)))
