@@ -190,6 +190,53 @@ int lsn_decode(lsn_ctx* ctx, const double* z, double* x_out, double* J_out);
 int lsn_get_trace(lsn_ctx* ctx, int max, double* grad_inf, double* energy,
                   double* grad_scale, double* alpha, int* count);
 
+/* ---------------------------------------------------------------------------
+ * Decoder training with the Lipschitz loss (Sec. 4), on the GPU, with
+ * hand-written forward and backward kernels (FP32, FP64 loss sums):
+ *   L_C  = 1/B sum_b ||x(g(q_b)) - q_b||_M^2                       (Eq. 3)
+ *   L_LS = 1/(B(B-1)) sum_{i != j} ||Ht_i - Ht_j||_F^2 / ||z_i - z_j||^2  (Eq. 9)
+ *   L    = L_C + lambda_LS L_LS                                     (Eq. 10)
+ * with the linear encoder g(q) = Ew (q - X0) + eb (supervised setting,
+ * Sec. 3.2), z_b = g(q_b) held fixed in L_LS (no gradient through the
+ * samples), and Ht_b the exact Hessian in z of the cubature elastic
+ * potential sum_{e in S} w_e V_e Psi(F_e(x(z))) (Sec. 4.2-4.3: elastic term
+ * only, cubature set S with weights w).  The decoder in training is the one
+ * set by lsn_set_decoder, without constraint override.  r <= 32.
+ *
+ * Parameters are one flat vector, exchanged as FP64 arrays: Ew (r x n
+ * row-major), eb (r), then W_l (out x in row-major), b_l for each decoder
+ * layer.  The trainer computes in FP64 when the decoder precision is
+ * LSN_PREC_FP64 and in FP32 otherwise (FP64 loss sums in both); the Lipschitz
+ * gradient sums large cancelling adjoints, so FP32 gives it to ~1e-2 relative.
+ * --------------------------------------------------------------------------- */
+
+/* Start training: initial encoder (enc_W r x n, enc_b r; host), training
+ * cubature set (tet_idx, non-negative w, s >= 1; host).  Uses the current
+ * mesh, material and decoder weights; Adam state is reset. */
+int lsn_train_init(lsn_ctx* ctx, const float* enc_W, const float* enc_b,
+                   const int32_t* tet_idx, const double* w, int s);
+int lsn_train_num_params(lsn_ctx* ctx, long long* count);
+/* Copy the flat parameter vector out of / into the trainer (host or device). */
+int lsn_train_get_params(lsn_ctx* ctx, double* theta);
+int lsn_train_set_params(lsn_ctx* ctx, const double* theta);
+/* Losses (losses[0..2] = L_C, L_LS, L; host, may be NULL) and the gradient
+ * of L w.r.t. the flat parameters (grad: host or device, may be NULL) for the
+ * snapshot positions q (B x n doubles, host or device), B >= 1.  L_LS needs
+ * B >= 2 and lambda_ls > 0 (otherwise it is 0). */
+int lsn_train_eval(lsn_ctx* ctx, const double* q, int B, double lambda_ls,
+                   double* losses, double* grad);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on the
+ * gradient of L for the batch q; losses as in lsn_train_eval. */
+int lsn_train_step(lsn_ctx* ctx, const double* q, int B, double lambda_ls,
+                   double lr, double* losses);
+/* Cubature Hessians Ht at the B subspace points z (B x r, host) into H
+ * (B x r x r, host), with the trainer's current decoder. */
+int lsn_train_hessians(lsn_ctx* ctx, const double* z, int B, double* H);
+/* Make the trained decoder the solver's decoder (takes effect at the next
+ * solve; the precision set by lsn_set_decoder is kept; weights are rounded
+ * to FP32 as lsn_set_decoder takes them). */
+int lsn_train_apply(lsn_ctx* ctx);
+
 /* Kernel classes for profiling. */
 enum lsn_kernel_class {
   LSN_K_DECODER_HIDDEN = 0, /* hidden layers, Jacobian and trial passes       */

@@ -65,6 +65,17 @@ _SIGS = {
     "lsn_get_profile": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                         ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)],
     "lsn_reset_profile": [ctypes.c_void_p],
+    "lsn_train_init": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                       ctypes.c_void_p, ctypes.c_int],
+    "lsn_train_num_params": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
+    "lsn_train_get_params": [ctypes.c_void_p, ctypes.c_void_p],
+    "lsn_train_set_params": [ctypes.c_void_p, ctypes.c_void_p],
+    "lsn_train_eval": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                       ctypes.c_void_p, ctypes.c_void_p],
+    "lsn_train_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                       ctypes.c_double, ctypes.c_void_p],
+    "lsn_train_hessians": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "lsn_train_apply": [ctypes.c_void_p],
     "lsn_element_system_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
@@ -282,6 +293,58 @@ class Context:
 
     def reset_profile(self):
         return self._check(self.lib.lsn_reset_profile(self.h))
+
+    # -- training (lsn_train_*) -----------------------------------------
+    def train_init(self, enc_W, enc_b, tet_idx, w):
+        enc_W = np.ascontiguousarray(enc_W, dtype=np.float32)
+        enc_b = np.ascontiguousarray(enc_b, dtype=np.float32)
+        tet_idx = _i32(tet_idx)
+        w = _f64(w)
+        self.keep_train = (enc_W, enc_b, tet_idx, w)
+        return self._check(self.lib.lsn_train_init(self.h, _ptr(enc_W), _ptr(enc_b),
+                                                   _ptr(tet_idx), _ptr(w), tet_idx.shape[0]))
+
+    def train_num_params(self):
+        n = ctypes.c_longlong()
+        self._check(self.lib.lsn_train_num_params(self.h, ctypes.byref(n)))
+        return n.value
+
+    def train_get_params(self, out=None):
+        out = np.zeros(self.train_num_params()) if out is None else out
+        self._check(self.lib.lsn_train_get_params(self.h, _ptr(out)))
+        return out
+
+    def train_set_params(self, theta):
+        theta = theta if hasattr(theta, "data_ptr") else np.ascontiguousarray(theta, np.float64)
+        return self._check(self.lib.lsn_train_set_params(self.h, _ptr(theta)))
+
+    def train_eval(self, q, lambda_ls, grad=None, want_grad=True):
+        """(L_C, L_LS, L), gradient (numpy float64 unless `grad` is given)."""
+        q = _f64(q)
+        B = int(q.shape[0])
+        losses = np.zeros(3)
+        if grad is None and want_grad:
+            grad = np.zeros(self.train_num_params())
+        self._check(self.lib.lsn_train_eval(self.h, _ptr(q), B, float(lambda_ls),
+                                            _ptr(losses), _ptr(grad)))
+        return tuple(losses), grad
+
+    def train_step(self, q, lambda_ls, lr):
+        q = _f64(q)
+        losses = np.zeros(3)
+        self._check(self.lib.lsn_train_step(self.h, _ptr(q), int(q.shape[0]), float(lambda_ls),
+                                            float(lr), _ptr(losses)))
+        return tuple(losses)
+
+    def train_hessians(self, Z):
+        Z = np.ascontiguousarray(Z, np.float64)
+        B, r = Z.shape
+        H = np.zeros((B, r, r))
+        self._check(self.lib.lsn_train_hessians(self.h, _ptr(Z), B, _ptr(H)))
+        return H
+
+    def train_apply(self):
+        return self._check(self.lib.lsn_train_apply(self.h))
 
     def decode(self, z, want_J=True):
         z = _f64(z)

@@ -16,6 +16,7 @@
 
 #include "../../include/lsn.h"
 #include "lsn_internal.cuh"
+#include "train_internal.cuh"
 
 using namespace lsn;
 
@@ -206,6 +207,12 @@ struct lsn_ctx {
   Profiler prof;
   bool use_graph = true;
   long long passes_total = 0;
+  // decoder training (lsn_train_*)
+  std::unique_ptr<TrainerBase> trainer;
+  int* tr_cub_idx = nullptr;
+  double* tr_cub_w = nullptr;
+  double* tr_q = nullptr;
+  long long tr_qcap = 0;
 };
 
 namespace {
@@ -560,6 +567,10 @@ void lsn_destroy(lsn_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   c->eng.reset();
+  c->trainer.reset();
+  dfree(c->tr_cub_idx);
+  dfree(c->tr_cub_w);
+  dfree(c->tr_q);
   free_mesh(c);
   if (c->pinned_status) cudaFreeHost(c->pinned_status);
   delete c;  // the profiler releases its events
@@ -1052,6 +1063,264 @@ int lsn_get_positions(lsn_ctx* c, double* x_out) {
   LSN_GUARD_BEGIN
   download(x_out, c->q, sizeof(double) * c->n, c->stream);
   ck(cudaStreamSynchronize(c->stream));
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+}  // extern "C"
+
+// ========================================================== decoder training
+namespace {
+int train_ready(lsn_ctx* c) {
+  if (!c) return LSN_ERR_ARG;
+  if (!c->trainer) return fail(c, LSN_ERR_STATE, "lsn_train_init has not been called");
+  return LSN_OK;
+}
+const double* train_upload_q(lsn_ctx* c, const double* q, int B) {
+  const long long cnt = (long long)B * c->n;
+  if (is_device_ptr(q)) return q;
+  if (cnt > c->tr_qcap) {
+    dfree(c->tr_q);
+    c->tr_q = dalloc<double>(cnt);
+    c->tr_qcap = cnt;
+  }
+  ck(cudaMemcpyAsync(c->tr_q, q, sizeof(double) * cnt, cudaMemcpyHostToDevice, c->stream));
+  return c->tr_q;
+}
+}  // namespace
+
+extern "C" {
+
+int lsn_train_init(lsn_ctx* c, const float* enc_W, const float* enc_b, const int32_t* tet_idx,
+                   const double* w, int s) {
+  if (!c) return LSN_ERR_ARG;
+  if (c->n == 0 || !c->have_material || !c->have_decoder)
+    return fail(c, LSN_ERR_STATE, "train_init: set mesh, material and decoder first");
+  if (!enc_W || !enc_b || !tet_idx || !w || s < 1 || s > c->ne)
+    return fail(c, LSN_ERR_ARG, "train_init: bad arguments");
+  const int r = c->widths[0];
+  if (r > 32) return fail(c, LSN_ERR_ARG, "train_init: training supports r <= 32");
+  for (int i = 0; i < s; ++i) {
+    if (tet_idx[i] < 0 || tet_idx[i] >= c->ne)
+      return fail(c, LSN_ERR_ARG, "train_init: tet index out of range");
+    if (!(w[i] >= 0.0) || !std::isfinite(w[i]))
+      return fail(c, LSN_ERR_ARG, "train_init: weights must be finite and >= 0");
+  }
+  LSN_GUARD_BEGIN
+  cudaStream_t st = c->stream;
+  c->trainer.reset();
+  dfree(c->tr_cub_idx);
+  dfree(c->tr_cub_w);
+  c->tr_cub_idx = dalloc<int>(s);
+  c->tr_cub_w = dalloc<double>(s);
+  ck(cudaMemcpyAsync(c->tr_cub_idx, tet_idx, sizeof(int) * s, cudaMemcpyHostToDevice, st));
+  ck(cudaMemcpyAsync(c->tr_cub_w, w, sizeof(double) * s, cudaMemcpyHostToDevice, st));
+  std::vector<int> all(4 * (size_t)c->ne);
+  ck(cudaMemcpyAsync(all.data(), c->tets, sizeof(int) * all.size(), cudaMemcpyDeviceToHost, st));
+  ck(cudaStreamSynchronize(st));
+  TrainSetup ts;
+  ts.n = c->n;
+  ts.nv = c->nv;
+  ts.widths = c->widths;
+  ts.scale = c->scale;
+  ts.mu = c->youngs / (2.0 * (1.0 + c->poisson));
+  ts.lam = c->youngs * c->poisson / ((1.0 + c->poisson) * (1.0 - 2.0 * c->poisson));
+  ts.alpha = 1.0 + 0.75 * ts.mu / ts.lam;
+  ts.X0 = c->X0;
+  ts.mass = c->mass;
+  ts.S = s;
+  ts.cub_idx = c->tr_cub_idx;
+  ts.cub_w = c->tr_cub_w;
+  ts.tets = c->tets;
+  ts.dminv = c->dminv;
+  ts.vol = c->vol;
+  ts.ne = c->ne;
+  // local numbering of the vertices the cubature tets touch (sorted)
+  std::vector<int> verts;
+  for (int i = 0; i < s; ++i)
+    for (int a = 0; a < 4; ++a) verts.push_back(all[4 * (size_t)tet_idx[i] + a]);
+  std::sort(verts.begin(), verts.end());
+  verts.erase(std::unique(verts.begin(), verts.end()), verts.end());
+  const int nvl = (int)verts.size();
+  ts.RS = 3 * nvl;
+  for (int v : verts)
+    for (int k = 0; k < 3; ++k) ts.rows.push_back(3 * v + k);
+  ts.tets_local.resize(4 * (size_t)s);
+  std::vector<std::vector<int>> lists(nvl);
+  for (int i = 0; i < s; ++i)
+    for (int a = 0; a < 4; ++a) {
+      const int v = all[4 * (size_t)tet_idx[i] + a];
+      const int lv = (int)(std::lower_bound(verts.begin(), verts.end(), v) - verts.begin());
+      ts.tets_local[4 * (size_t)i + a] = lv;
+      lists[lv].push_back((i << 2) | a);
+    }
+  ts.inc_ptr.assign(nvl + 1, 0);
+  for (int v = 0; v < nvl; ++v) {
+    ts.inc_ptr[v + 1] = ts.inc_ptr[v] + (int)lists[v].size();
+    ts.inc.insert(ts.inc.end(), lists[v].begin(), lists[v].end());
+  }
+  // initial parameters: encoder, then the context's decoder
+  std::unique_ptr<TrainerBase> tr(TrainerBase::create(c->precision == LSN_PREC_FP64, ts));
+  std::vector<double> theta(tr->nparams);
+  std::copy(enc_W, enc_W + (size_t)r * c->n, theta.begin() + tr->off[0]);
+  std::copy(enc_b, enc_b + r, theta.begin() + tr->off[1]);
+  for (int l = 0; l + 1 < (int)c->widths.size(); ++l) {
+    std::copy(c->W[l].begin(), c->W[l].end(), theta.begin() + tr->off[2 + 2 * l]);
+    std::copy(c->b[l].begin(), c->b[l].end(), theta.begin() + tr->off[3 + 2 * l]);
+  }
+  try {
+    tr->init_device(theta.data());
+  } catch (...) {
+    cudaGetLastError();
+    return fail(c, LSN_ERR_CUDA, "train_init: CUDA error while setting up the trainer");
+  }
+  c->trainer = std::move(tr);
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_train_num_params(lsn_ctx* c, long long* count) {
+  int rc = train_ready(c);
+  if (rc != LSN_OK) return rc;
+  if (!count) return LSN_ERR_ARG;
+  *count = c->trainer->nparams;
+  return LSN_OK;
+}
+
+// parameters and gradients cross the ABI as FP64 arrays (host or device)
+static void host_to_user(const std::vector<double>& h, double* dst, cudaStream_t s) {
+  download(dst, h.data(), sizeof(double) * h.size(), s);  // direction by dst
+  ck(cudaStreamSynchronize(s));
+}
+
+int lsn_train_get_params(lsn_ctx* c, double* theta) {
+  int rc = train_ready(c);
+  if (rc != LSN_OK) return rc;
+  if (!theta) return LSN_ERR_ARG;
+  LSN_GUARD_BEGIN
+  std::vector<double> h(c->trainer->nparams);
+  try {
+    c->trainer->get_params(h.data());
+  } catch (...) {
+    return fail(c, LSN_ERR_CUDA, "train_get_params: CUDA error");
+  }
+  if (is_device_ptr(theta)) host_to_user(h, theta, c->stream);
+  else std::copy(h.begin(), h.end(), theta);
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_train_set_params(lsn_ctx* c, const double* theta) {
+  int rc = train_ready(c);
+  if (rc != LSN_OK) return rc;
+  if (!theta) return LSN_ERR_ARG;
+  LSN_GUARD_BEGIN
+  std::vector<double> h(c->trainer->nparams);
+  if (is_device_ptr(theta)) {
+    ck(cudaMemcpyAsync(h.data(), theta, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                       c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+  } else {
+    std::copy(theta, theta + h.size(), h.begin());
+  }
+  for (double v : h)
+    if (!std::isfinite(v)) return fail(c, LSN_ERR_NONFINITE, "train_set_params: non-finite");
+  try {
+    c->trainer->set_params(h.data());
+  } catch (...) {
+    return fail(c, LSN_ERR_CUDA, "train_set_params: CUDA error");
+  }
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_train_eval(lsn_ctx* c, const double* q, int B, double lambda_ls, double* losses,
+                   double* grad) {
+  int rc = train_ready(c);
+  if (rc != LSN_OK) return rc;
+  if (!q || B < 1 || !(lambda_ls >= 0.0)) return fail(c, LSN_ERR_ARG, "train_eval: bad arguments");
+  LSN_GUARD_BEGIN
+  double l[3];
+  const double* qd = train_upload_q(c, q, B);
+  try {
+    c->trainer->evaluate(qd, B, lambda_ls, l, c->stream);
+  } catch (...) {
+    return fail(c, LSN_ERR_CUDA, "train_eval: CUDA error in the training kernels");
+  }
+  if (losses) std::copy(l, l + 3, losses);
+  if (grad) {
+    std::vector<double> h(c->trainer->nparams);
+    try {
+      c->trainer->get_grad(h.data());
+    } catch (...) {
+      return fail(c, LSN_ERR_CUDA, "train_eval: CUDA error reading the gradient");
+    }
+    if (is_device_ptr(grad)) host_to_user(h, grad, c->stream);
+    else std::copy(h.begin(), h.end(), grad);
+  }
+  return std::isfinite(l[2]) ? LSN_OK : fail(c, LSN_ERR_NONFINITE, "train_eval: non-finite loss");
+  LSN_GUARD_END
+}
+
+int lsn_train_step(lsn_ctx* c, const double* q, int B, double lambda_ls, double lr,
+                   double* losses) {
+  if (!(lr > 0.0)) return fail(c, LSN_ERR_ARG, "train_step: lr must be > 0");
+  int rc = lsn_train_eval(c, q, B, lambda_ls, losses, nullptr);
+  if (rc != LSN_OK) return rc;
+  LSN_GUARD_BEGIN
+  try {
+    c->trainer->adam(lr, c->stream);
+  } catch (...) {
+    return fail(c, LSN_ERR_CUDA, "train_step: CUDA error in the Adam update");
+  }
+  ck(cudaStreamSynchronize(c->stream));
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_train_hessians(lsn_ctx* c, const double* z, int B, double* H) {
+  int rc = train_ready(c);
+  if (rc != LSN_OK) return rc;
+  if (!z || !H || B < 1) return fail(c, LSN_ERR_ARG, "train_hessians: bad arguments");
+  LSN_GUARD_BEGIN
+  TrainerBase& tr = *c->trainer;
+  const int r = c->widths[0], P = tr.P;
+  std::vector<double> hs((size_t)B * P);
+  try {
+    tr.hessians_host(z, B, hs.data(), c->stream);
+  } catch (...) {
+    return fail(c, LSN_ERR_CUDA, "train_hessians: CUDA error");
+  }
+  for (int b = 0; b < B; ++b) {
+    int p = 0;
+    for (int i = 0; i < r; ++i)
+      for (int j = i; j < r; ++j, ++p) {
+        H[(size_t)b * r * r + i * r + j] = hs[(size_t)b * P + p];
+        H[(size_t)b * r * r + j * r + i] = hs[(size_t)b * P + p];
+      }
+  }
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_train_apply(lsn_ctx* c) {
+  int rc = train_ready(c);
+  if (rc != LSN_OK) return rc;
+  LSN_GUARD_BEGIN
+  TrainerBase& tr = *c->trainer;
+  std::vector<double> theta(tr.nparams);
+  try {
+    tr.get_params(theta.data());
+  } catch (...) {
+    return fail(c, LSN_ERR_CUDA, "train_apply: CUDA error");
+  }
+  for (int l = 0; l + 1 < (int)c->widths.size(); ++l) {
+    const double* W = theta.data() + tr.off[2 + 2 * l];
+    const double* b = theta.data() + tr.off[3 + 2 * l];
+    for (size_t i = 0; i < c->W[l].size(); ++i) c->W[l][i] = (float)W[i];
+    for (size_t i = 0; i < c->b[l].size(); ++i) c->b[l][i] = (float)b[i];
+  }
+  c->dirty = true;
   return LSN_OK;
   LSN_GUARD_END
 }

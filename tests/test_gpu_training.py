@@ -1,0 +1,147 @@
+"""GPU parity of the Lipschitz-loss training kernels (lsn_train_*) against
+the float64 autodiff oracle (oracle/training.py): losses, the cubature
+subspace Hessians, the full parameter gradient, the torch.autograd.Function,
+and that Adam steps lower the loss.
+
+Tolerances.  FP64 trainer: losses, Hessians and every gradient block to
+1e-8 relative.  FP32 trainer: losses and Hessians 1e-4 relative; the
+reconstruction gradient 2e-3; the Lipschitz-loss gradient sums adjoints
+several orders of magnitude above its own size, so FP32 gives it to a few
+percent: its blocks are checked to 0.2 relative and 0.98 cosine."""
+import numpy as np
+import pytest
+
+from oracle.training import TrainProblem, loss_and_grad
+from workloads import make_bar, xavier_decoder
+from tests.gpu_util import rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_03807_gb300.build import build
+    build()
+    import paper_2409_03807_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def make_case(r=3, hidden=(8, 8), dims=(6, 3, 3), S=10, B=4, seed=0):
+    mesh = make_bar(*dims, 0.05)
+    n = 3 * mesh.nv
+    widths = [r, *hidden, n]
+    rng = np.random.default_rng(seed)
+    cub = np.sort(rng.choice(mesh.ne, S, replace=False)).astype(np.int32)
+    w = rng.uniform(0.5, 4.0, S)
+    Ws, bs = xavier_decoder(widths, 1)
+    bs = [(0.05 * rng.standard_normal(b.shape)).astype(np.float32) for b in bs]
+    Ew = (0.3 * rng.standard_normal((r, n))).astype(np.float32)
+    eb = (0.1 * rng.standard_normal(r)).astype(np.float32)
+    Q = mesh.X0.ravel()[None] + 0.02 * rng.standard_normal((B, n))
+    tp = TrainProblem(mesh.X0, mesh.tets, widths, 0.05, 1e5, 0.45, 1000.0, cub, w)
+    theta = tp.pack(Ew, eb, Ws, bs)
+    return mesh, widths, cub, w, Ws, bs, Ew, eb, Q, tp, theta
+
+
+def gpu_ctx(pkg, mesh, Ws, bs, Ew, eb, cub, w, prec="fp32"):
+    ctx = pkg.Context()
+    ctx.set_mesh(mesh.X0, mesh.tets)
+    ctx.set_material(1e5, 0.45, 1000.0, (0.0, 0.0, -9.8))
+    ctx.set_decoder(Ws, bs, 0.05, prec)
+    ctx.train_init(Ew, eb, cub, w)
+    return ctx
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("lam", [0.0, 1e-3])
+def test_losses_and_gradient_match_oracle(pkg, lam, prec):
+    mesh, widths, cub, w, Ws, bs, Ew, eb, Q, tp, theta = make_case()
+    ctx = gpu_ctx(pkg, mesh, Ws, bs, Ew, eb, cub, w, prec)
+    th = ctx.train_get_params()
+    assert np.array_equal(th, theta.astype(np.float32).astype(np.float64))
+    (lc, lls, L), g = ctx.train_eval(Q, lam)
+    (lc0, lls0, L0), g0, Z0, H0 = loss_and_grad(tp, th, Q, lam)
+    tl = 1e-8 if prec == "fp64" else 1e-4
+    assert lc == pytest.approx(lc0, rel=tl)
+    assert lls == pytest.approx(lls0, rel=tl, abs=1e-12)
+    assert L == pytest.approx(L0, rel=tl)
+    # gradient, block by block
+    o = 0
+    for shp in tp.shapes:
+        sz = int(np.prod(shp))
+        gb, g0b = g[o:o + sz], g0[o:o + sz]
+        if np.linalg.norm(g0b) > 1e-8 * np.linalg.norm(g0):
+            if prec == "fp64":
+                assert rel(gb, g0b) < 1e-8, (shp, rel(gb, g0b))
+            elif lam == 0.0:
+                assert rel(gb, g0b) < 2e-3, (shp, rel(gb, g0b))
+            else:
+                cos = gb @ g0b / (np.linalg.norm(gb) * np.linalg.norm(g0b))
+                assert rel(gb, g0b) < 0.2 and cos > 0.98, (shp, rel(gb, g0b), cos)
+        o += sz
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cubature_hessians_match_oracle(pkg, prec):
+    import torch
+    mesh, widths, cub, w, Ws, bs, Ew, eb, Q, tp, theta = make_case(r=4, hidden=(12, 12), S=16)
+    ctx = gpu_ctx(pkg, mesh, Ws, bs, Ew, eb, cub, w, prec)
+    Z = np.random.default_rng(5).standard_normal((5, 4)) * 0.8
+    H = ctx.train_hessians(Z)
+    P = tp.unpack(torch.tensor(theta))
+    for b in range(Z.shape[0]):
+        Hr = tp.hessian(P, torch.tensor(Z[b])).numpy()
+        assert rel(H[b], Hr) < (1e-10 if prec == "fp64" else 1e-4)
+    ctx.close()
+
+
+def test_gradient_by_finite_differences_on_gpu(pkg):
+    """Central differences of the GPU loss itself on 8 random parameters (FP64
+    trainer, relative step 1e-6)."""
+    mesh, widths, cub, w, Ws, bs, Ew, eb, Q, tp, theta = make_case()
+    ctx = gpu_ctx(pkg, mesh, Ws, bs, Ew, eb, cub, w, "fp64")
+    lam = 1e-3
+    (_, _, L), g = ctx.train_eval(Q, lam)
+    th = ctx.train_get_params()
+    rng = np.random.default_rng(100)
+    # the Lipschitz samples z_b are held fixed in training: perturb decoder
+    # parameters only (the encoder enters L_LS only through them)
+    cand = np.arange(tp.sizes[0] + tp.sizes[1], th.shape[0])
+    for k in rng.choice(cand, 8, replace=False):
+        h = 1e-6 * max(1.0, abs(float(th[k])))
+        tp_, tm_ = th.copy(), th.copy()
+        tp_[k] += h
+        tm_[k] -= h
+        ctx.train_set_params(tp_)
+        Lp = ctx.train_eval(Q, lam, want_grad=False)[0][2]
+        ctx.train_set_params(tm_)
+        Lm = ctx.train_eval(Q, lam, want_grad=False)[0][2]
+        fd = (Lp - Lm) / (2 * h)
+        assert fd == pytest.approx(float(g[k]), rel=1e-5, abs=1e-7 * abs(g).max())
+    ctx.close()
+
+
+def test_autograd_function_and_adam_lower_the_loss(pkg):
+    import torch
+    from paper_2409_03807_gb300.autograd import LipschitzTrainingLoss
+    mesh, widths, cub, w, Ws, bs, Ew, eb, Q, tp, theta = make_case(B=6)
+    ctx = gpu_ctx(pkg, mesh, Ws, bs, Ew, eb, cub, w)
+    th = torch.tensor(ctx.train_get_params(), requires_grad=True)
+    q = torch.tensor(Q)
+    L = LipschitzTrainingLoss.apply(th, q, ctx, 1e-3)
+    L.backward()
+    (_, _, L2), g = ctx.train_eval(Q, 1e-3)
+    assert float(L.detach()) == pytest.approx(L2, rel=1e-6)
+    assert np.allclose(th.grad.numpy(), g, rtol=1e-6, atol=0)
+    ctx.train_set_params(th.detach().numpy())
+    l0 = ctx.train_eval(Q, 1e-3, want_grad=False)[0][2]
+    for _ in range(30):
+        ctx.train_step(Q, 1e-3, 1e-3)
+    l1 = ctx.train_eval(Q, 1e-3, want_grad=False)[0][2]
+    assert l1 < 0.5 * l0
+    ctx.close()
