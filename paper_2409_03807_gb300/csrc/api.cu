@@ -16,6 +16,7 @@
 
 #include "../../include/lsn.h"
 #include "lsn_internal.cuh"
+#include "tc_internal.cuh"
 #include "train_internal.cuh"
 
 using namespace lsn;
@@ -142,6 +143,9 @@ struct EngineBase {
   virtual void finish(double dt) = 0;      // q, v from the positions at z
   virtual void decode_to_host(double* x, double* J) = 0;
   virtual int kernels_per_pass() const = 0;
+  // nonzero when a bounded wait inside a tensor-core kernel ran out (reads a
+  // device flag; call after the stream's work is queued)
+  virtual int device_error(cudaStream_t) { return 0; }
   DevSolver* sv = nullptr;
   double* sys = nullptr;
   // CUDA graph of the whole solve loop (conditional WHILE node)
@@ -231,6 +235,8 @@ struct Engine : EngineBase {
   int grid_dec, gfull, genergy, nst;
   LastArgs la;
   ElemArgs ea;
+  TcLast tcl;          // tensor-core output layer (TF32 / BF16 forms)
+  bool use_tc = false;
 
   explicit Engine(lsn_ctx* ctx) : c(ctx) {
     cudaStream_t s = c->stream;
@@ -272,7 +278,18 @@ struct Engine : EngineBase {
                                  c->S > 0 ? c->cub_w : nullptr, S, c->ne, ctets, cdminv, cwv,
                                  s);
     grid_dec = decoder_last_grid(n, C, c->num_sms);
+    use_tc = sizeof(Real) == 4 &&
+             (c->precision == LSN_PREC_TF32 || c->precision == LSN_PREC_BF16);
+    if (use_tc) {
+      ck(tcl.setup(reinterpret_cast<const float*>(dW[L - 1]), n, c->widths[L - 1], C, r,
+                   c->precision == LSN_PREC_BF16, c->num_sms, s));
+      grid_dec = tcl.grid;
+    }
     element_grids(S, r, c->num_sms, gfull, genergy);
+    if (use_tc) {  // one complete partial row per CTA (trial energies included)
+      gfull = element_tc_grid(S, c->num_sms);
+      genergy = 0;
+    }
     part_dec = dalloc<double>((size_t)grid_dec * nst);
     part_el = dalloc<double>((size_t)(gfull + genergy) * nst);
     sys = dalloc<double>(nst);
@@ -304,8 +321,12 @@ struct Engine : EngineBase {
     std::memset(&h, 0, sizeof(h));
     h.tol = c->tol;
     h.armijo_c = c->armijo_c;
-    const double unit = c->precision == LSN_PREC_FP64 ? 1.1102230246251565e-16
-                                                     : 5.960464477539063e-08;
+    // rounding unit of the energy and gradient evaluation: FP64, FP32 (also
+    // the BF16 form, whose activations enter as a two-term split), TF32
+    // (10 stored mantissa bits; the tensor core may truncate)
+    const double unit = c->precision == LSN_PREC_FP64   ? 1.1102230246251565e-16
+                        : c->precision == LSN_PREC_TF32 ? 9.765625e-04
+                                                        : 5.960464477539063e-08;
     // FP64: the plain Armijo test of the paper's line search.  Lower
     // precisions accept a step whose energy rise stays within the rounding
     // scale of the energy evaluation, so the solve can reach their floor.
@@ -370,17 +391,36 @@ struct Engine : EngineBase {
     Profiler& P = c->prof;
     const Real* h = hidden(s, prof);
     if (prof) P.begin(LSN_K_DECODER_LAST);
-    launch_last_layer<Real>(dW[L - 1], db[L - 1], n, c->widths[L - 1], h, C, nj, u, J, ut,
-                            part_dec, nst, la, grid_dec, s);
+    if (use_tc)
+      tcl.launch(reinterpret_cast<const float*>(h), zstride(C),
+                 reinterpret_cast<const float*>(db[L - 1]), nj, reinterpret_cast<float*>(u),
+                 reinterpret_cast<float*>(J), reinterpret_cast<float*>(ut), part_dec, nst, la,
+                 s);
+    else
+      launch_last_layer<Real>(dW[L - 1], db[L - 1], n, c->widths[L - 1], h, C, nj, u, J, ut,
+                              part_dec, nst, la, grid_dec, s);
     if (prof) P.end(LSN_K_DECODER_LAST);
     if (prof) P.begin(LSN_K_ELEMENT);
-    launch_element<Real>(ea, u, J, ut, part_el, gfull, genergy, s);
+    if (use_tc)
+      ck(launch_element_tc(ea, reinterpret_cast<const float*>(u),
+                           reinterpret_cast<const float*>(J), reinterpret_cast<const float*>(ut),
+                           part_el, gfull, c->precision == LSN_PREC_BF16, tcl.err, s));
+    else
+      launch_element<Real>(ea, u, J, ut, part_el, gfull, genergy, s);
     if (prof) P.end(LSN_K_ELEMENT);
     if (prof) P.begin(LSN_K_SOLVE, 2);
-    launch_reduce_partials(part_dec, grid_dec, part_el, gfull + genergy, gfull, nslots(r), nst,
-                           sys, s);
+    launch_reduce_partials(part_dec, grid_dec, part_el, gfull + genergy, use_tc ? -1 : gfull,
+                           nslots(r), nst, sys, s);
     launch_select_direction<Real>(sv, sys, Z0, cond, use_cond, s);
     if (prof) P.end(LSN_K_SOLVE);
+  }
+
+  int device_error(cudaStream_t s) override {
+    if (!use_tc) return 0;
+    int h = 0;
+    ck(cudaMemcpyAsync(&h, tcl.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    return h;
   }
 
   void finish(double dt) override {
@@ -979,6 +1019,8 @@ int lsn_step(lsn_ctx* c, const double* z_in, double dt, double* z_out, lsn_stats
       c->prof.launches[k] += per * h.passes;
     }
   c->passes_total += h.passes;
+  if (c->eng->device_error(s))
+    return fail(c, LSN_ERR_CUDA, "step: a tensor-core pipeline wait timed out");
   if (h.status < -1) return fail(c, h.status, "step: non-finite values in the reduced system");
   if (z_out && !is_device_ptr(z_out)) std::memcpy(z_out, h.z, sizeof(double) * r);
   std::copy(h.z, h.z + r, c->z0.begin());

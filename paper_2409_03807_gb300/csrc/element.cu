@@ -39,7 +39,10 @@
 // symmetric rank-9T update of the CTA's register-resident K partial, each
 // thread owning a fixed set of upper-triangle entries.  Each CTA writes one
 // partial row (E, sum|E|, g, K upper) that a fixed-order reduction sums.
+#include <cuda_bf16.h>
+
 #include "lsn_internal.cuh"
+#include "tc_ptx.cuh"
 
 #include <algorithm>
 
@@ -327,6 +330,135 @@ __device__ __forceinline__ void disp_grad(const Real* __restrict__ u, const int4
       H[i][j] = Du[i][0] * Dmi[0][j] + Du[i][1] * Dmi[1][j] + Du[i][2] * Dmi[2][j];
 }
 
+// Phase 1 of a tile: element math of tet e by thread t (energy, P, the
+// signed SVD and the clamped eigen-decomposition of d2Psi/dF2), stored in the
+// tile's shared memory; a slot past the last tet is zeroed.
+template <typename Real, int ET>
+__device__ __forceinline__ void element_phase1(const ElemArgs& ea, const Real* __restrict__ u,
+                                               int e, int t, ElemTile<Real, ET>& tl, Real mu,
+                                               Real lam, Real oma, double& eacc, double& eabs) {
+  if (e < ea.S) {
+    int4 tv;
+    Real Dmi[3][3], wv, H[3][3];
+    load_tet<Real>(ea, e, tv, Dmi, wv);
+    disp_grad<Real>(u, tv, Dmi, H);
+    Invariants<Real> iv;
+    invariants<Real>(H, iv);
+    const Real psi = snh_psi<Real>(iv, mu, lam, oma);
+    eacc += (double)(wv * psi);
+    eabs += fabs((double)(wv * psi));
+    const Real Ic = iv.Ic3 + Real(3);
+    const Real dl = iv.Ic3 / (Real(4) * (Ic + Real(1)));
+    const Real lJ = lam * iv.Jm1;
+    // first derivative P, stored as p = w V vec(P)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const Real Fij = H[i][j] + (i == j ? Real(1) : Real(0));
+        const Real P = mu * dl * Fij + lJ * iv.cof[i][j] +
+                       Real(0.75) * mu *
+                           (H[i][j] + H[j][i] - (i == j ? iv.trH : Real(0)) - iv.cofH[i][j]);
+        tl.p[t][3 * i + j] = wv * P;
+      }
+    // eigen-decomposition of the second derivative (see header)
+    const Real c1 = mu * Ic / (Ic + Real(1));                   // 2 Psi_2
+    const Real c2 = Real(2) * mu / ((Ic + Real(1)) * (Ic + Real(1)));  // 4 Psi_22
+    const Real c3 = lam * (iv.Jm1 + oma);                       // Psi_3 = lam (J - a)
+    Real F[3][3], U[3][3], V[3][3], sg[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) F[i][j] = H[i][j] + (i == j ? Real(1) : Real(0));
+    svd3<Real>(F, U, sg, V);
+    Real As[3][3], Aq[3][3];
+    const Real pi3[3] = {sg[1] * sg[2], sg[0] * sg[2], sg[0] * sg[1]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        As[i][j] = c2 * sg[i] * sg[j] + lam * pi3[i] * pi3[j] +
+                   (i == j ? c1 : c3 * sg[3 - i - j]);
+    jacobi3<Real>(As, Aq);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const Real sc = sqrt_r<Real>(wv * (As[m][m] > Real(0) ? As[m][m] : Real(0)));
+#pragma unroll
+      for (int i = 0; i < 3; ++i) tl.As[t][3 * m + i] = sc * Aq[i][m];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const Real lt = c1 + c3 * sg[i], lf = c1 - c3 * sg[i];
+      tl.tf[t][i] = sqrt_r<Real>(Real(0.5) * wv * (lt > Real(0) ? lt : Real(0)));
+      tl.tf[t][3 + i] = sqrt_r<Real>(Real(0.5) * wv * (lf > Real(0) ? lf : Real(0)));
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      tl.U[t][k] = U[k / 3][k % 3];
+      tl.V[t][k] = V[k / 3][k % 3];
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      tl.D[t][j] = -(Dmi[0][j] + Dmi[1][j] + Dmi[2][j]);
+#pragma unroll
+      for (int a = 1; a < 4; ++a) tl.D[t][3 * a + j] = Dmi[a - 1][j];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) tl.U[t][k] = tl.V[t][k] = tl.As[t][k] = Real(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) tl.tf[t][k] = Real(0);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) tl.D[t][k] = Real(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) tl.p[t][k] = Real(0);
+  }
+}
+
+// C_e rows (9) and p_e . G for one (tet q, subspace column) pair: G = dvec(F)
+// along the column from the tet's four J rows jv, R = U^T G V, then the
+// projected eigen-coordinates scaled by sqrt(w V lambda+).
+template <typename Real, int ET>
+__device__ __forceinline__ void element_item(const ElemTile<Real, ET>& tl, int q,
+                                             const Real (&jv)[4][3], Real (&Cv)[9], Real& gp) {
+  Real G[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Real s = Real(0);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) s += tl.D[q][3 * a + j] * jv[a][i];
+      G[3 * i + j] = s;
+    }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) gp += tl.p[q][k] * G[k];
+  // R = U^T dF V with dF = G as a 3x3 matrix
+  Real T3[3][3], R[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      T3[i][b] = G[3 * i] * tl.V[q][b] + G[3 * i + 1] * tl.V[q][3 + b] +
+                 G[3 * i + 2] * tl.V[q][6 + b];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      R[a][b] = tl.U[q][a] * T3[0][b] + tl.U[q][3 + a] * T3[1][b] +
+                tl.U[q][6 + a] * T3[2][b];
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+    Cv[m] = tl.As[q][3 * m] * R[0][0] + tl.As[q][3 * m + 1] * R[1][1] +
+            tl.As[q][3 * m + 2] * R[2][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    Cv[3 + i] = tl.tf[q][i] * (R[j][k] - R[k][j]);
+    Cv[6 + i] = tl.tf[q][3 + i] * (R[j][k] + R[k][j]);
+  }
+}
+
 // Energy of the KTRIAL trial displacement fields ut[j * n + .] for the tets
 // e = first, first + stride, ...; block-reduced into prow[2 j], prow[2 j + 1].
 template <typename Real, int ET>
@@ -439,82 +571,7 @@ __global__ void __launch_bounds__(ET) element_kernel(ElemArgs ea, const Real* __
     __syncthreads();
     prefetch(0, min(CB, tile_tets), 0);
     // ---------------- phase 1: element math, one tet per thread
-    if (e < ea.S) {
-      int4 tv;
-      Real Dmi[3][3], wv, H[3][3];
-      load_tet<Real>(ea, e, tv, Dmi, wv);
-      disp_grad<Real>(u, tv, Dmi, H);
-      Invariants<Real> iv;
-      invariants<Real>(H, iv);
-      const Real psi = snh_psi<Real>(iv, mu, lam, oma);
-      eacc += (double)(wv * psi);
-      eabs += fabs((double)(wv * psi));
-      const Real Ic = iv.Ic3 + Real(3);
-      const Real dl = iv.Ic3 / (Real(4) * (Ic + Real(1)));
-      const Real lJ = lam * iv.Jm1;
-      // first derivative P, stored as p = w V vec(P)
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const Real Fij = H[i][j] + (i == j ? Real(1) : Real(0));
-          const Real P = mu * dl * Fij + lJ * iv.cof[i][j] +
-                         Real(0.75) * mu *
-                             (H[i][j] + H[j][i] - (i == j ? iv.trH : Real(0)) - iv.cofH[i][j]);
-          tl.p[t][3 * i + j] = wv * P;
-        }
-      // eigen-decomposition of the second derivative (see header)
-      const Real c1 = mu * Ic / (Ic + Real(1));                   // 2 Psi_2
-      const Real c2 = Real(2) * mu / ((Ic + Real(1)) * (Ic + Real(1)));  // 4 Psi_22
-      const Real c3 = lam * (iv.Jm1 + oma);                       // Psi_3 = lam (J - a)
-      Real F[3][3], U[3][3], V[3][3], sg[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) F[i][j] = H[i][j] + (i == j ? Real(1) : Real(0));
-      svd3<Real>(F, U, sg, V);
-      Real As[3][3], Aq[3][3];
-      const Real pi3[3] = {sg[1] * sg[2], sg[0] * sg[2], sg[0] * sg[1]};
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-          As[i][j] = c2 * sg[i] * sg[j] + lam * pi3[i] * pi3[j] +
-                     (i == j ? c1 : c3 * sg[3 - i - j]);
-      jacobi3<Real>(As, Aq);
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        const Real sc = sqrt_r<Real>(wv * (As[m][m] > Real(0) ? As[m][m] : Real(0)));
-#pragma unroll
-        for (int i = 0; i < 3; ++i) tl.As[t][3 * m + i] = sc * Aq[i][m];
-      }
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const Real lt = c1 + c3 * sg[i], lf = c1 - c3 * sg[i];
-        tl.tf[t][i] = sqrt_r<Real>(Real(0.5) * wv * (lt > Real(0) ? lt : Real(0)));
-        tl.tf[t][3 + i] = sqrt_r<Real>(Real(0.5) * wv * (lf > Real(0) ? lf : Real(0)));
-      }
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        tl.U[t][k] = U[k / 3][k % 3];
-        tl.V[t][k] = V[k / 3][k % 3];
-      }
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        tl.D[t][j] = -(Dmi[0][j] + Dmi[1][j] + Dmi[2][j]);
-#pragma unroll
-        for (int a = 1; a < 4; ++a) tl.D[t][3 * a + j] = Dmi[a - 1][j];
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 9; ++k) tl.U[t][k] = tl.V[t][k] = tl.As[t][k] = Real(0);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) tl.tf[t][k] = Real(0);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) tl.D[t][k] = Real(0);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) tl.p[t][k] = Real(0);
-    }
+    element_phase1<Real, ET>(ea, u, e, t, tl, mu, lam, oma, eacc, eabs);
     // ---------------- phases 2 + 3 in batches of CB tets
     int buf = 0;
     for (int b0 = 0; b0 < tile_tets; b0 += CB, buf ^= 1) {
@@ -538,42 +595,7 @@ __global__ void __launch_bounds__(ET) element_kernel(ElemArgs ea, const Real* __
           for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int i = 0; i < 3; ++i) jv[a][i] = Jt[(lt * 12 + 3 * a + i) * r + c];
-          Real G[9];
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-              Real s = Real(0);
-#pragma unroll
-              for (int a = 0; a < 4; ++a) s += tl.D[q][3 * a + j] * jv[a][i];
-              G[3 * i + j] = s;
-            }
-#pragma unroll
-          for (int k = 0; k < 9; ++k) gp += tl.p[q][k] * G[k];
-          // R = U^T dF V with dF = G as a 3x3 matrix
-          Real T3[3][3], R[3][3];
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-              T3[i][b] = G[3 * i] * tl.V[q][b] + G[3 * i + 1] * tl.V[q][3 + b] +
-                         G[3 * i + 2] * tl.V[q][6 + b];
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-              R[a][b] = tl.U[q][a] * T3[0][b] + tl.U[q][3 + a] * T3[1][b] +
-                        tl.U[q][6 + a] * T3[2][b];
-#pragma unroll
-          for (int m = 0; m < 3; ++m)
-            Cv[m] = tl.As[q][3 * m] * R[0][0] + tl.As[q][3 * m + 1] * R[1][1] +
-                    tl.As[q][3 * m + 2] * R[2][2];
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            const int j = (i + 1) % 3, k = (i + 2) % 3;
-            Cv[3 + i] = tl.tf[q][i] * (R[j][k] - R[k][j]);
-            Cv[6 + i] = tl.tf[q][3 + i] * (R[j][k] + R[k][j]);
-          }
+          element_item<Real, ET>(tl, q, jv, Cv, gp);
         } else {
 #pragma unroll
           for (int m = 0; m < 9; ++m) Cv[m] = Real(0);
@@ -659,6 +681,259 @@ void run_element_r(const ElemArgs& ea, const Real* u, const Real* J, const Real*
   else run_element<Real, 64, ET>(ea, u, J, ut, part, gfull, genergy, s);
 }
 
+
+// ------------------------------------------------------------------------
+// Tensor-core form of the element kernel (TF32 / BF16 forms): the same
+// element math (phase 1, element_item), with the rank-9 updates
+// K += C_e^T C_e of phase 3 replaced by tcgen05 MMAs.  The C_e rows of a
+// chunk of tets are written, rounded to BF16 or TF32, into a K-major
+// 128-byte-swizzled operand whose rows are the subspace columns c and whose
+// K index is (tet, eigen-row); one MMA chain D += Op * Op^T (M = 64, N =
+// r rounded up to 16) accumulates into TMEM across all of the CTA's chunks,
+// while the threads build the next chunk in the other buffer.  The per-tet
+// Hessians and the gradient stay FP32 (FP64 partial sums).  The trial
+// energies of the line search are computed in phase 1 as well, so every CTA
+// writes one complete partial row.
+namespace tcel {
+
+using namespace tc;
+
+constexpr int ET = 128;        // tets per tile
+constexpr int NT = 256;        // threads: phase 1 by the first ET, phase 2 by all
+constexpr int GROWS = 64;      // operand rows (subspace columns, r <= 64)
+constexpr uint32_t KBB = GROWS * 128;  // bytes per 128-byte K block
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+template <bool BF>
+struct Cfg {
+  static constexpr int CH = BF ? 64 : 32;     // tets per chunk
+  static constexpr int EPB = BF ? 64 : 32;    // K values per 128-byte block
+  static constexpr int NKB = 9 * CH / EPB;    // K blocks per chunk (9)
+  static constexpr uint32_t BUF = NKB * KBB;  // operand bytes per chunk
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* err, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (gtimer() - t0 > WAIT_NS) {
+      atomicOr(err, code);
+      return false;
+    }
+  }
+}
+
+template <bool BF>
+__host__ __device__ inline size_t smem_bytes(int r) {
+  return 2 * (size_t)Cfg<BF>::BUF + sizeof(ElemTile<float, ET>) +
+         (size_t)Cfg<BF>::CH * r * sizeof(float) + 1024;
+}
+
+template <bool BF>
+__global__ void __launch_bounds__(NT, 1)
+    element_tc_kernel(ElemArgs ea, const float* __restrict__ u, const float* __restrict__ J,
+                      const float* __restrict__ ut, double* __restrict__ part, int part_stride,
+                      int* __restrict__ err) {
+  using C = Cfg<BF>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t done[2], fin;
+  __shared__ uint32_t tbase_s;
+  __shared__ double red[NT / 32][2 + 2 * KTRIAL];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* sb = smem_raw + (base - raw);
+  ElemTile<float, ET>& tl = *reinterpret_cast<ElemTile<float, ET>*>(sb + 2 * C::BUF);
+  float* Gp = reinterpret_cast<float*>(sb + 2 * C::BUF + sizeof(ElemTile<float, ET>));
+  const int r = ea.r, S = ea.S;
+  const int Ng = (r + 15) / 16 * 16;
+  const uint32_t idesc = BF ? idesc_bf16(GROWS, Ng) : idesc_tf32(GROWS, Ng);
+  const float mu = (float)ea.mu, lam = (float)ea.lam;
+  const float oma = (float)(-0.75 * ea.mu / ea.lam);
+  if (warp == 0) {
+    tmem_alloc(&tbase_s, 64);
+    tmem_relinquish();
+  }
+  if (t == 0) {
+    mbar_init(&done[0], 1);
+    mbar_init(&done[1], 1);
+    mbar_init(&fin, 1);
+    fence_barrier_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tbase_s;
+  double eacc = 0.0, eabs = 0.0, etr[KTRIAL], atr[KTRIAL], gacc = 0.0, gabs = 0.0;
+#pragma unroll
+  for (int j = 0; j < KTRIAL; ++j) etr[j] = atr[j] = 0.0;
+  const int ntiles = (S + ET - 1) / ET;
+  int qc = 0;  // chunks issued by this CTA
+  bool alive = true;
+  for (int tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
+    const int e = tile * ET + t;
+    const int tile_tets = min(ET, S - tile * ET);
+    // ---------------- phase 1 (first ET threads): element math + trial energies
+    if (t < ET) {
+      tl.v[t] = e < S ? ea.tets[e] : make_int4(0, 0, 0, 0);
+      element_phase1<float, ET>(ea, u, e, t, tl, mu, lam, oma, eacc, eabs);
+      if (e < S) {
+        int4 tv;
+        float Dmi[3][3], wv;
+        load_tet<float>(ea, e, tv, Dmi, wv);
+#pragma unroll
+        for (int j = 0; j < KTRIAL; ++j) {
+          float H[3][3];
+          disp_grad<float>(ut + (size_t)j * ea.n, tv, Dmi, H);
+          Invariants<float> iv;
+          invariants<float>(H, iv);
+          const double pe = (double)(wv * snh_psi<float>(iv, mu, lam, oma));
+          etr[j] += pe;
+          atr[j] += fabs(pe);
+        }
+      }
+    }
+    __syncthreads();
+    // ---------------- phases 2 + 3 in chunks of CH tets
+    for (int c0 = 0; c0 < tile_tets; c0 += C::CH, ++qc) {
+      const int nb = min(C::CH, tile_tets - c0);
+      const int buf = qc & 1;
+      // the buffer was last read by the MMAs of chunk qc - 2
+      const bool ok = qc < 2 || wait_bar(&done[buf], ((qc >> 1) & 1) ^ 1, err, 1);
+      if (!__syncthreads_and(ok)) {
+        alive = false;
+        break;
+      }
+      uint8_t* op = sb + buf * C::BUF;
+      for (int item = t; item < C::CH * r; item += NT) {
+        const int lt = item / r, c = item - lt * r;
+        float Cv[9];
+        float gp = 0.f;
+        if (lt < nb) {
+          const int q = c0 + lt;
+          const int4 tv = tl.v[q];
+          const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
+          float jv[4][3];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) jv[a][i] = J[(size_t)(3 * vv[a] + i) * r + c];
+          element_item<float, ET>(tl, q, jv, Cv, gp);
+        } else {
+#pragma unroll
+          for (int m = 0; m < 9; ++m) Cv[m] = 0.f;
+        }
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+          const int k = lt * 9 + m, kb = k / C::EPB, kin = k - kb * C::EPB;
+          if (BF)
+            *reinterpret_cast<__nv_bfloat16*>(op + kb * KBB + sw128_offset(c, kin >> 3) +
+                                              (kin & 7) * 2) = __float2bfloat16_rn(Cv[m]);
+          else
+            *reinterpret_cast<float*>(op + kb * KBB + sw128_offset(c, kin >> 2) +
+                                      (kin & 3) * 4) = Cv[m];
+        }
+        Gp[lt * r + c] = gp;
+      }
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (t == 0) {
+        tc_fence_after();
+        const uint32_t ob = base + buf * C::BUF;
+        for (int kb = 0; kb < C::NKB; ++kb)
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint64_t d = sdesc_sw128(ob + kb * KBB + ks * 32);
+            const uint32_t acc = (qc > 0 || kb > 0 || ks > 0) ? 1u : 0u;
+            if (BF) mma_bf16(tbase, d, d, idesc, acc);
+            else mma_tf32(tbase, d, d, idesc, acc);
+          }
+        mma_commit(&done[buf]);
+      }
+      if (t < r) {  // gradient: FP32 over the chunk, FP64 across chunks
+        float s0 = 0.f, s1 = 0.f, a0 = 0.f, a1 = 0.f;
+        int lt = 0;
+        for (; lt + 2 <= nb; lt += 2) {
+          const float x0 = Gp[lt * r + t], x1 = Gp[(lt + 1) * r + t];
+          s0 += x0;
+          s1 += x1;
+          a0 += fabsf(x0);
+          a1 += fabsf(x1);
+        }
+        if (lt < nb) {
+          s0 += Gp[lt * r + t];
+          a0 += fabsf(Gp[lt * r + t]);
+        }
+        gacc += (double)(s0 + s1);
+        gabs += (double)(a0 + a1);
+      }
+      __syncthreads();
+    }
+  }
+  if (t == 0) mma_commit(&fin);
+  const bool fok = __syncthreads_and(alive && wait_bar(&fin, 0, err, 2));
+  tc_fence_after();
+  // energies: warp shuffles, then the warps in fixed order
+  double vals[2 + 2 * KTRIAL];
+  vals[0] = eacc;
+  vals[1] = eabs;
+#pragma unroll
+  for (int j = 0; j < KTRIAL; ++j) {
+    vals[2 + 2 * j] = etr[j];
+    vals[3 + 2 * j] = atr[j];
+  }
+#pragma unroll
+  for (int j = 0; j < 2 + 2 * KTRIAL; ++j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vals[j] += __shfl_down_sync(0xffffffffu, vals[j], o);
+    if (lane == 0) red[warp][j] = vals[j];
+  }
+  __syncthreads();
+  double* prow = part + (size_t)blockIdx.x * part_stride;
+  if (t < 2 + 2 * KTRIAL) {
+    double sum = 0.0;
+    for (int w = 0; w < NT / 32; ++w) sum += red[w][t];
+    if (t < 2) prow[t] = sum;
+    else prow[nslots(r) + t - 2] = sum;
+  }
+  if (t < r) {
+    prow[slot_g(t)] = gacc;
+    prow[slot_gabs(r, t)] = gabs;
+  }
+  // Gram rows: row c of the M = 64 accumulator is TMEM lane 32 (c / 16) + c % 16
+  if (warp < 4) {
+    const int c = 16 * warp + lane;
+    const uint32_t ta = tbase + ((uint32_t)(32 * warp) << 16);
+    for (int d0 = 0; d0 < Ng; d0 += 16) {
+      uint32_t vv[16];
+      tmem_ld16(ta + d0, vv);
+      tmem_ld_wait();
+      if (lane < 16 && c < r)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int d = d0 + j;
+          if (d >= c && d < r)
+            prow[slot_K(r) + c * r - (c * (c - 1)) / 2 + (d - c)] =
+                fok ? (double)__uint_as_float(vv[j]) : 0.0;
+        }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 64);
+  }
+}
+
+}  // namespace tcel
+
 }  // namespace
 
 // Small cubature sets use 64-tet tiles so that more CTAs share the work.
@@ -686,6 +961,39 @@ void launch_element(const ElemArgs& ea, const Real* u, const Real* J, const Real
     run_element_r<Real, 64>(ea, u, J, ut, part, gfull, genergy, s);
   else
     run_element_r<Real, 128>(ea, u, J, ut, part, gfull, genergy, s);
+}
+
+int element_tc_grid(int S, int num_sms) {
+  return std::max(1, std::min((S + tcel::ET - 1) / tcel::ET, num_sms));
+}
+
+cudaError_t launch_element_tc(const ElemArgs& ea, const float* u, const float* J,
+                              const float* ut, double* part, int grid, bool bf16, int* err,
+                              cudaStream_t s) {
+  if (ea.r > tcel::GROWS) return cudaErrorInvalidValue;
+  static size_t set_bf = 0, set_tf = 0;
+  if (bf16) {
+    const size_t sm = tcel::smem_bytes<true>(ea.r);
+    if (sm > set_bf) {
+      cudaError_t e = cudaFuncSetAttribute(tcel::element_tc_kernel<true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      set_bf = sm;
+    }
+    tcel::element_tc_kernel<true><<<grid, tcel::NT, sm, s>>>(ea, u, J, ut, part,
+                                                             nslots_total(ea.r), err);
+  } else {
+    const size_t sm = tcel::smem_bytes<false>(ea.r);
+    if (sm > set_tf) {
+      cudaError_t e = cudaFuncSetAttribute(tcel::element_tc_kernel<false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      set_tf = sm;
+    }
+    tcel::element_tc_kernel<false><<<grid, tcel::NT, sm, s>>>(ea, u, J, ut, part,
+                                                              nslots_total(ea.r), err);
+  }
+  return cudaGetLastError();
 }
 
 template void launch_element<float>(const ElemArgs&, const float*, const float*, const float*,

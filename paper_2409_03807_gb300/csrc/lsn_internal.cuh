@@ -120,6 +120,13 @@ template <typename Real>
 void launch_element(const ElemArgs& ea, const Real* u, const Real* J, const Real* ut,
                     double* part, int gfull, int genergy, cudaStream_t s);
 void element_grids(int S, int r, int num_sms, int& gfull, int& genergy);
+// Tensor-core element kernel (TF32 / BF16 forms, r <= 64): `grid` CTAs, each
+// writing one complete partial row (elastic slots and trial energies) of
+// nslots_total(r) doubles; err receives a nonzero code if a bounded wait ran out.
+int element_tc_grid(int S, int num_sms);
+cudaError_t launch_element_tc(const ElemArgs& ea, const float* u, const float* J,
+                              const float* ut, double* part, int grid, bool bf16, int* err,
+                              cudaStream_t s);
 
 // solve.cu
 // out[c] = sum over rows of A (all rows) and of B: rows [0, splitB) for

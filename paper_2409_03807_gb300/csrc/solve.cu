@@ -38,7 +38,9 @@ __global__ void reduce_partials_kernel(const double* __restrict__ A, int rowsA,
   const int c = warp;
   double s = 0.0;
   for (int b = lane; b < rowsA; b += 32) s += A[(size_t)b * ncols + c];
-  const int b0 = c < split ? 0 : splitB, b1 = c < split ? splitB : rowsB;
+  // splitB < 0: every B row carries every column
+  const int b0 = (splitB < 0 || c < split) ? 0 : splitB;
+  const int b1 = splitB < 0 ? rowsB : (c < split ? splitB : rowsB);
   for (int b = b0 + lane; b < b1; b += 32) s += B[(size_t)b * ncols + c];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);

@@ -1,0 +1,31 @@
+// Host-side handles of the tensor-core (tcgen05) kernels: the decoder output
+// layer in the BF16 and TF32 forms (tc_decoder.cu).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "lsn_internal.cuh"
+
+namespace lsn {
+
+struct TcLast {
+  CUtensorMap mapW, mapBh, mapBl;  // W_L tiles, packed hidden columns (hi / lo)
+  void* Wlow = nullptr;            // BF16 copy of W_L (BF16 form)
+  void* Bh = nullptr;              // [Cp][H] packed B operand (BF16 hi or FP32)
+  void* Bl = nullptr;              // [Cp][H] BF16 low part (BF16 form)
+  int* err = nullptr;              // device: nonzero when a pipeline wait timed out
+  int M = 0, H = 0, C = 0, Cp = 0, r = 0, grid = 0;
+  size_t smem = 0;
+  bool bf16 = false;
+  // W_fp32: the output layer's FP32 weights (M x H, row-major, device)
+  cudaError_t setup(const float* W_fp32, int M, int H, int C, int r, bool bf16, int num_sms,
+                    cudaStream_t s);
+  void release();
+  // Z: last hidden layer, unit-major [H][CPs] (FP32); same outputs and
+  // partial-row layout as launch_last_layer
+  void launch(const float* Z, int CPs, const float* bias, int nj, float* u, float* J, float* ut,
+              double* part, int part_stride, const LastArgs& la, cudaStream_t s) const;
+  ~TcLast() { release(); }
+};
+
+}  // namespace lsn
