@@ -698,8 +698,9 @@ namespace tcel {
 
 using namespace tc;
 
-constexpr int ET = 128;        // tets per tile
-constexpr int NT = 256;        // threads: phase 1 by the first ET, phase 2 by all
+constexpr int ET = 256;        // tets per tile
+constexpr int NT = 512;        // threads: phase 1 element math by the first ET, the
+                               // trial energies by the others; phase 2 by all
 constexpr int GROWS = 64;      // operand rows (subspace columns, r <= 64)
 constexpr uint32_t KBB = GROWS * 128;  // bytes per 128-byte K block
 constexpr unsigned long long WAIT_NS = 2000000000ull;
@@ -777,16 +778,19 @@ __global__ void __launch_bounds__(NT, 1)
   int qc = 0;  // chunks issued by this CTA
   bool alive = true;
   for (int tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
-    const int e = tile * ET + t;
+    const int e = tile * ET + t;  // (threads < ET)
     const int tile_tets = min(ET, S - tile * ET);
-    // ---------------- phase 1 (first ET threads): element math + trial energies
+    // ---------------- phase 1: element math (threads < ET) and the trial
+    // energies of the line search (threads >= ET), one tet per thread
     if (t < ET) {
       tl.v[t] = e < S ? ea.tets[e] : make_int4(0, 0, 0, 0);
       element_phase1<float, ET>(ea, u, e, t, tl, mu, lam, oma, eacc, eabs);
-      if (e < S) {
+    } else {
+      const int e2 = tile * ET + (t - ET);
+      if (e2 < S) {
         int4 tv;
         float Dmi[3][3], wv;
-        load_tet<float>(ea, e, tv, Dmi, wv);
+        load_tet<float>(ea, e2, tv, Dmi, wv);
 #pragma unroll
         for (int j = 0; j < KTRIAL; ++j) {
           float H[3][3];
@@ -811,8 +815,13 @@ __global__ void __launch_bounds__(NT, 1)
         break;
       }
       uint8_t* op = sb + buf * C::BUF;
-      for (int item = t; item < C::CH * r; item += NT) {
-        const int lt = item / r, c = item - lt * r;
+      // a warp takes 8 consecutive columns of 4 tets: the J reads stay in
+      // 32-byte segments and the operand stores spread over the banks
+      const int nitems = (r + 7) / 8 * 8 * C::CH;
+      for (int item = t; item < nitems; item += NT) {
+        const int w = item >> 5, ln = item & 31;
+        const int lt = (w % (C::CH / 4)) * 4 + (ln >> 3), c = (w / (C::CH / 4)) * 8 + (ln & 7);
+        if (c >= r) continue;
         float Cv[9];
         float gp = 0.f;
         if (lt < nb) {

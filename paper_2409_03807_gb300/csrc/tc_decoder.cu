@@ -247,6 +247,18 @@ __global__ void __launch_bounds__(TNT, 1)
           }
         mma_commit(&jempty[jb]);
       };
+      // the Gram MMA of tile i is issued once its epilogue has written the
+      // operand: polled between the K blocks of tile i + 1, forced at the
+      // end of that tile (the operand buffer is reused two tiles later)
+      int pending = -1;
+      auto poll_gram = [&](bool force) {
+        if (pending < 0) return;
+        const int jb = pending & 1;
+        const uint32_t par = (pending >> 1) & 1;
+        if (!force && !mbar_try_wait(&jfull[jb], par)) return;
+        gram(pending);
+        pending = -1;
+      };
       int kc = 0;
       for (int i = 0; i < my_tiles && alive; ++i) {
         const int ab = i & 1;
@@ -278,12 +290,15 @@ __global__ void __launch_bounds__(TNT, 1)
             }
           }
           mma_commit(&empty[st]);
+          poll_gram(false);
         }
         if (!alive) break;
         mma_commit(&tfull[ab]);
-        if (i >= 1) gram(i - 1);
+        poll_gram(true);
+        if (!alive) break;
+        pending = i;
       }
-      if (alive && my_tiles > 0) gram(my_tiles - 1);
+      if (alive) poll_gram(true);
       mma_commit(&gdone);
     }
     __syncwarp();
@@ -419,11 +434,8 @@ __global__ void __launch_bounds__(TNT, 1)
         gabs += (double)((a0 + a1) + (a2 + a3));
       }
       float* Jdst = J_out + (size_t)m0 * r;
-      const int cnt = rows * r;
-      for (int x = et; x < cnt; x += 128) {
-        const int rr = x / r, c = x - rr * r;
-        Jdst[x] = Js[rr * JS + c];
-      }
+      for (int rr = et >> 5; rr < rows; rr += 4)
+        for (int c = lane; c < r; c += 32) Jdst[(size_t)rr * r + c] = Js[rr * JS + c];
       epi_sync();
       if (!alive) break;
     }

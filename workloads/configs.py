@@ -15,6 +15,8 @@ Seeds: 0 decoder weights, 1 cubature draw, 2 snapshot load parameters,
 * block_twist_960k - block 101x41x41 nodes (960,000 tets, n = 509,343),
   x = 0 face fixed, x = L face twisted 2 rad and pushed in by 0.2 L over 150
   frames, implicit Euler dt = 1/60; r = 64, decoder 64-1024x3-509343, all tets.
+* block_twist_207k - the same block motion on 61x25x25 nodes (207,360 tets,
+  n = 114,375) with the same decoder widths: a mid-size case for profiling.
 * tiny_* - small cases that the oracle finishes in well under a second.
 
 Material for all bars: Young's modulus 1e5 Pa, Poisson ratio 0.45, density
@@ -68,6 +70,11 @@ CONFIGS = {
         1, 1e-5, "pin"),
     "block_twist_960k": Config(
         "block_twist_960k", (101, 41, 41), 0.05, 64, (1024, 1024, 1024), 0,
+        1.0 / 60.0, 300, 1e-5, "twist_compress", motion_frames=150,
+        motion_angle=2.0, motion_shift=-0.2),
+    # the same block at a fifth of the size (profiling and mid-size parity)
+    "block_twist_207k": Config(
+        "block_twist_207k", (61, 25, 25), 0.05, 64, (1024, 1024, 1024), 0,
         1.0 / 60.0, 300, 1e-5, "twist_compress", motion_frames=150,
         motion_angle=2.0, motion_shift=-0.2),
     # small cases for parity tests
