@@ -180,7 +180,7 @@ __host__ __device__ constexpr size_t gemm_smem(int BM, int CPs) {
 }
 
 // ------------------------------------------------------------ hidden layers
-constexpr int HBM = 16;  // rows per CTA of a hidden layer
+constexpr int HBM = 8;  // rows per CTA of a hidden layer (more CTAs: the layers are short)
 
 template <typename Real, int CQ>
 __global__ void __launch_bounds__(KP * HBM) hidden_kernel(const Real* __restrict__ W,

@@ -415,9 +415,71 @@ __device__ __forceinline__ void element_phase1(const ElemArgs& ea, const Real* _
   }
 }
 
-// C_e rows (9) and p_e . G for one (tet q, subspace column) pair: G = dvec(F)
+// Per-tet data of phase 2 held in registers.
+template <typename Real>
+struct TetData {
+  Real D[12], p[9], U[9], V[9], As[9], tf[6];
+};
+
+template <typename Real, int ET>
+__device__ __forceinline__ void load_tet_data(const ElemTile<Real, ET>& tl, int q,
+                                              TetData<Real>& td) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) td.D[k] = tl.D[q][k];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    td.p[k] = tl.p[q][k];
+    td.U[k] = tl.U[q][k];
+    td.V[k] = tl.V[q][k];
+    td.As[k] = tl.As[q][k];
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) td.tf[k] = tl.tf[q][k];
+}
+
+// C_e rows (9) and p_e . G for one (tet, subspace column) pair: G = dvec(F)
 // along the column from the tet's four J rows jv, R = U^T G V, then the
 // projected eigen-coordinates scaled by sqrt(w V lambda+).
+template <typename Real>
+__device__ __forceinline__ void element_item_td(const TetData<Real>& td, const Real (&jv)[4][3],
+                                                Real (&Cv)[9], Real& gp) {
+  Real G[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Real s = Real(0);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) s += td.D[3 * a + j] * jv[a][i];
+      G[3 * i + j] = s;
+    }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) gp += td.p[k] * G[k];
+  // R = U^T dF V with dF = G as a 3x3 matrix
+  Real T3[3][3], R[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      T3[i][b] = G[3 * i] * td.V[b] + G[3 * i + 1] * td.V[3 + b] + G[3 * i + 2] * td.V[6 + b];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      R[a][b] = td.U[a] * T3[0][b] + td.U[3 + a] * T3[1][b] + td.U[6 + a] * T3[2][b];
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+    Cv[m] = td.As[3 * m] * R[0][0] + td.As[3 * m + 1] * R[1][1] + td.As[3 * m + 2] * R[2][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    Cv[3 + i] = td.tf[i] * (R[j][k] - R[k][j]);
+    Cv[6 + i] = td.tf[3 + i] * (R[j][k] + R[k][j]);
+  }
+}
+
+// The same as element_item_td, reading the tet's data from shared memory as
+// it goes (fewer live registers in the CUDA-core kernel).
 template <typename Real, int ET>
 __device__ __forceinline__ void element_item(const ElemTile<Real, ET>& tl, int q,
                                              const Real (&jv)[4][3], Real (&Cv)[9], Real& gp) {
@@ -433,7 +495,6 @@ __device__ __forceinline__ void element_item(const ElemTile<Real, ET>& tl, int q
     }
 #pragma unroll
   for (int k = 0; k < 9; ++k) gp += tl.p[q][k] * G[k];
-  // R = U^T dF V with dF = G as a 3x3 matrix
   Real T3[3][3], R[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -445,8 +506,7 @@ __device__ __forceinline__ void element_item(const ElemTile<Real, ET>& tl, int q
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b)
-      R[a][b] = tl.U[q][a] * T3[0][b] + tl.U[q][3 + a] * T3[1][b] +
-                tl.U[q][6 + a] * T3[2][b];
+      R[a][b] = tl.U[q][a] * T3[0][b] + tl.U[q][3 + a] * T3[1][b] + tl.U[q][6 + a] * T3[2][b];
 #pragma unroll
   for (int m = 0; m < 3; ++m)
     Cv[m] = tl.As[q][3 * m] * R[0][0] + tl.As[q][3 * m + 1] * R[1][1] +
@@ -816,39 +876,53 @@ __global__ void __launch_bounds__(NT, 1)
       }
       uint8_t* op = sb + buf * C::BUF;
       // a warp takes 8 consecutive columns of 4 tets: the J reads stay in
-      // 32-byte segments and the operand stores spread over the banks
-      const int nitems = (r + 7) / 8 * 8 * C::CH;
-      for (int item = t; item < nitems; item += NT) {
-        const int w = item >> 5, ln = item & 31;
-        const int lt = (w % (C::CH / 4)) * 4 + (ln >> 3), c = (w / (C::CH / 4)) * 8 + (ln & 7);
-        if (c >= r) continue;
-        float Cv[9];
-        float gp = 0.f;
-        if (lt < nb) {
-          const int q = c0 + lt;
-          const int4 tv = tl.v[q];
-          const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
-          float jv[4][3];
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int i = 0; i < 3; ++i) jv[a][i] = J[(size_t)(3 * vv[a] + i) * r + c];
-          element_item<float, ET>(tl, q, jv, Cv, gp);
-        } else {
-#pragma unroll
-          for (int m = 0; m < 9; ++m) Cv[m] = 0.f;
+      // 32-byte segments and the operand stores spread over the banks.  A
+      // thread keeps one tet (lt) for all of its column blocks, so the tet's
+      // data is read from shared memory once per chunk.
+      {
+        static_assert((NT / 8) % C::CH == 0, "column groups must tile the chunk");
+        constexpr int CBSTEP = (NT / 8) / C::CH;        // column blocks in parallel per tet
+        const int slot = t >> 3, c8 = t & 7;
+        const int lt = slot % C::CH, cb0 = slot / C::CH;
+        const bool live_t = lt < nb;
+        TetData<float> td;
+        int vv[4] = {0, 0, 0, 0};
+        if (live_t) {
+          load_tet_data<float, ET>(tl, c0 + lt, td);
+          const int4 tv = tl.v[c0 + lt];
+          vv[0] = tv.x;
+          vv[1] = tv.y;
+          vv[2] = tv.z;
+          vv[3] = tv.w;
         }
+        for (int cb = cb0; cb * 8 < r; cb += CBSTEP) {
+          const int c = cb * 8 + c8;
+          if (c >= r) continue;
+          float Cv[9];
+          float gp = 0.f;
+          if (live_t) {
+            float jv[4][3];
 #pragma unroll
-        for (int m = 0; m < 9; ++m) {
-          const int k = lt * 9 + m, kb = k / C::EPB, kin = k - kb * C::EPB;
-          if (BF)
-            *reinterpret_cast<__nv_bfloat16*>(op + kb * KBB + sw128_offset(c, kin >> 3) +
-                                              (kin & 7) * 2) = __float2bfloat16_rn(Cv[m]);
-          else
-            *reinterpret_cast<float*>(op + kb * KBB + sw128_offset(c, kin >> 2) +
-                                      (kin & 3) * 4) = Cv[m];
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int i = 0; i < 3; ++i) jv[a][i] = J[(size_t)(3 * vv[a] + i) * r + c];
+            element_item_td<float>(td, jv, Cv, gp);
+          } else {
+#pragma unroll
+            for (int m = 0; m < 9; ++m) Cv[m] = 0.f;
+          }
+#pragma unroll
+          for (int m = 0; m < 9; ++m) {
+            const int k = lt * 9 + m, kb = k / C::EPB, kin = k - kb * C::EPB;
+            if (BF)
+              *reinterpret_cast<__nv_bfloat16*>(op + kb * KBB + sw128_offset(c, kin >> 3) +
+                                                (kin & 7) * 2) = __float2bfloat16_rn(Cv[m]);
+            else
+              *reinterpret_cast<float*>(op + kb * KBB + sw128_offset(c, kin >> 2) +
+                                        (kin & 3) * 4) = Cv[m];
+          }
+          Gp[lt * r + c] = gp;
         }
-        Gp[lt * r + c] = gp;
       }
       fence_proxy_async_smem();
       __syncthreads();

@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(32) select_direction_kernel(DevSolver* gsv,
                                                               int use_cond) {
   __shared__ double L[RMAX][RMAX + 1];
   __shared__ double y[RMAX];
+  __shared__ double invd[RMAX];  // reciprocals of the Cholesky diagonal
   __shared__ double ssys[4 * RMAX + 2 * KTRIAL + 2];
   __shared__ __align__(16) DevSolver svs;
   DevSolver* sv = &svs;
@@ -262,25 +263,30 @@ __global__ void __launch_bounds__(32) select_direction_kernel(DevSolver* gsv,
           }
           __syncwarp();
         }
+        // right-looking: per column one square root and one reciprocal, then
+        // independent FMAs over the trailing lower triangle (lanes take the
+        // columns k of each row), so the FP64 pipe is fed without dependent
+        // chains or divisions per element
         bool fail = false;
-        for (int j = 0; j < r && !fail; ++j) {
-          double s = 0.0;
-          for (int k = t; k < j; k += 32) s += L[j][k] * L[j][k];
-          s = L[j][j] - warp_sum(s);
+        for (int j = 0; j < r; ++j) {
+          const double s = L[j][j];
           if (!(s > 0.0)) {
             fail = true;
             break;
           }
-          const double djj = sqrt(s);
+          const double djj = sqrt(s), inv = 1.0 / djj;
           __syncwarp();
           if (t == 0) L[j][j] = djj;
-          for (int i = j + 1 + t; i < r; i += 32) {
-            double v = L[i][j];
-            for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
-            L[i][j] = v / djj;
+          for (int i = j + 1 + t; i < r; i += 32) L[i][j] *= inv;
+          if (t == 0) invd[j] = inv;
+          __syncwarp();
+          for (int i = j + 1; i < r; ++i) {
+            const double lij = L[i][j];
+            for (int k = j + 1 + t; k <= i; k += 32) L[i][k] -= lij * L[k][j];
           }
           __syncwarp();
         }
+        fail = __any_sync(0xffffffffu, fail);
         ok = !fail;
         if (!ok) shift = shift == 0.0 ? base : shift * 10.0;
       }
@@ -294,14 +300,14 @@ __global__ void __launch_bounds__(32) select_direction_kernel(DevSolver* gsv,
         // forward L y = -g, backward L^T d = y (column sweeps within the warp)
         __syncwarp();
         for (int i = 0; i < r; ++i) {
-          const double yi = y[i] / L[i][i];
+          const double yi = y[i] * invd[i];
           __syncwarp();
           if (t == 0) y[i] = yi;
           for (int k = i + 1 + t; k < r; k += 32) y[k] -= L[k][i] * yi;
           __syncwarp();
         }
         for (int i = r - 1; i >= 0; --i) {
-          const double yi = y[i] / L[i][i];
+          const double yi = y[i] * invd[i];
           __syncwarp();
           if (t == 0) y[i] = yi;
           for (int k = t; k < i; k += 32) y[k] -= L[i][k] * yi;
