@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp64", "fp32", "tf32", "bf16"],
+                    help="bf16 (default): BF16 weights and tensor-core contractions, FP32 "
+                         "element math, FP64 Cholesky and energy comparison")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="time budget of the CPU-oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -172,19 +174,24 @@ def run_reference(args, world, rank):
 
 
 # --------------------------------------------------------------------- ours
-def algorithmic_bytes(cls, p, real_bytes):
-    """Bytes one launch of kernel class `cls` must move at minimum."""
+def algorithmic_bytes(cls, p, precision):
+    """Bytes one launch of kernel class `cls` must move at minimum (each datum
+    once): weights and inputs read, outputs written."""
     c = p.config
     n, r, H = p.n, c.r, p.widths[-2]
-    S = len(p.cub_idx)
+    b = 8 if precision == "fp64" else 4
+    w = 2 if precision == "bf16" else b          # stored bytes of W_L
+    C = r + 4                                    # value, r tangents, 3 trial columns
+    cub = p.tets[p.cub_idx] if len(p.cub_idx) else p.tets
+    S = cub.shape[0]
+    rows = 3 * np.unique(cub).shape[0]           # decoder rows the element kernel reads
     if cls == "decoder_last":
-        return (n * H + n + (r + 1) * H + n + n * r) * real_bytes + p.nv * (4 + 8) + n * 8
+        act = C * H * (4 if precision == "bf16" else b)  # packed columns (BF16 hi + lo)
+        per_row = n * (b + 8 + 8) + p.nv * (8 + 4)        # bias, ubar, X0; mass, slot
+        out = (n + n * r + 3 * n) * b                      # u, J, trial u
+        return n * H * w + act + per_row + out
     if cls == "element":
-        return S * (16 + 10 * real_bytes + 12 * real_bytes + 12 * r * real_bytes)
-    if cls == "decoder_trial":
-        return (n * H + n + 4 * H + 4 * n) * real_bytes + p.nv * (4 + 8) + n * 8
-    if cls == "element_energy":
-        return S * (16 + 10 * real_bytes + 4 * 12 * real_bytes)
+        return S * (16 + 10 * b) + rows * (r + 4) * b
     return None
 
 
@@ -302,7 +309,7 @@ def run_ours(args, world, rank, local):
     launches_dom, timed_dom, ms_dom = prof[dominant]
     avg_ms = ms_dom / max(timed_dom, 1)
     replay_ms = sum(v[2] for v in prof.values())
-    ab = algorithmic_bytes(dominant, p, real_bytes)
+    ab = algorithmic_bytes(dominant, p, args.precision)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak, peak_src = 6800.0, "fallback"
     if os.path.exists(peaks_path):
@@ -337,7 +344,7 @@ def run_ours(args, world, rank, local):
         line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
                 "steps": K, "warmup": W, "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+                "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.precision], "data": "synthetic",
                 "config": {"workload": args.workload,
                            "mesh": f"{c.dims[0]}x{c.dims[1]}x{c.dims[2]} nodes, {p.ne} tets, "
                                    f"n={p.n}",

@@ -800,7 +800,7 @@ template <bool BF>
 __global__ void __launch_bounds__(NT, 1)
     element_tc_kernel(ElemArgs ea, const float* __restrict__ u, const float* __restrict__ J,
                       const float* __restrict__ ut, double* __restrict__ part, int part_stride,
-                      int* __restrict__ err) {
+                      int TT, int* __restrict__ err) {
   using C = Cfg<BF>;
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t done[2], fin;
@@ -834,20 +834,21 @@ __global__ void __launch_bounds__(NT, 1)
   double eacc = 0.0, eabs = 0.0, etr[KTRIAL], atr[KTRIAL], gacc = 0.0, gabs = 0.0;
 #pragma unroll
   for (int j = 0; j < KTRIAL; ++j) etr[j] = atr[j] = 0.0;
-  const int ntiles = (S + ET - 1) / ET;
+  // TT <= ET tets per tile (small cubature sets use small tiles, more CTAs)
+  const int ntiles = (S + TT - 1) / TT;
   int qc = 0;  // chunks issued by this CTA
   bool alive = true;
   for (int tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
-    const int e = tile * ET + t;  // (threads < ET)
-    const int tile_tets = min(ET, S - tile * ET);
+    const int e = t < TT ? tile * TT + t : S;  // (threads < ET)
+    const int tile_tets = min(TT, S - tile * TT);
     // ---------------- phase 1: element math (threads < ET) and the trial
     // energies of the line search (threads >= ET), one tet per thread
     if (t < ET) {
       tl.v[t] = e < S ? ea.tets[e] : make_int4(0, 0, 0, 0);
       element_phase1<float, ET>(ea, u, e, t, tl, mu, lam, oma, eacc, eabs);
     } else {
-      const int e2 = tile * ET + (t - ET);
-      if (e2 < S) {
+      const int e2 = tile * TT + (t - ET);
+      if (t - ET < TT && e2 < S) {
         int4 tv;
         float Dmi[3][3], wv;
         load_tet<float>(ea, e2, tv, Dmi, wv);
@@ -1046,8 +1047,26 @@ void launch_element(const ElemArgs& ea, const Real* u, const Real* J, const Real
     run_element_r<Real, 128>(ea, u, J, ut, part, gfull, genergy, s);
 }
 
+static int num_sms_cached() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return sms;
+}
+
+// tets per tile: 256, or fewer (down to 16) when that leaves SMs idle
+int element_tc_tile(int S, int num_sms) {
+  int tt = tcel::ET;
+  while (tt > 16 && (long long)(tt / 2) * num_sms >= S) tt /= 2;
+  return tt;
+}
+
 int element_tc_grid(int S, int num_sms) {
-  return std::max(1, std::min((S + tcel::ET - 1) / tcel::ET, num_sms));
+  const int tt = element_tc_tile(S, num_sms);
+  return std::max(1, std::min((S + tt - 1) / tt, num_sms));
 }
 
 cudaError_t launch_element_tc(const ElemArgs& ea, const float* u, const float* J,
@@ -1063,8 +1082,8 @@ cudaError_t launch_element_tc(const ElemArgs& ea, const float* u, const float* J
       if (e != cudaSuccess) return e;
       set_bf = sm;
     }
-    tcel::element_tc_kernel<true><<<grid, tcel::NT, sm, s>>>(ea, u, J, ut, part,
-                                                             nslots_total(ea.r), err);
+    tcel::element_tc_kernel<true><<<grid, tcel::NT, sm, s>>>(
+        ea, u, J, ut, part, nslots_total(ea.r), element_tc_tile(ea.S, num_sms_cached()), err);
   } else {
     const size_t sm = tcel::smem_bytes<false>(ea.r);
     if (sm > set_tf) {
@@ -1073,8 +1092,8 @@ cudaError_t launch_element_tc(const ElemArgs& ea, const float* u, const float* J
       if (e != cudaSuccess) return e;
       set_tf = sm;
     }
-    tcel::element_tc_kernel<false><<<grid, tcel::NT, sm, s>>>(ea, u, J, ut, part,
-                                                              nslots_total(ea.r), err);
+    tcel::element_tc_kernel<false><<<grid, tcel::NT, sm, s>>>(
+        ea, u, J, ut, part, nslots_total(ea.r), element_tc_tile(ea.S, num_sms_cached()), err);
   }
   return cudaGetLastError();
 }
