@@ -378,7 +378,11 @@ struct Engine : EngineBase {
     if (prof) c->prof.begin(LSN_K_DECODER_HIDDEN, L - 1);
     for (int l = 0; l < L - 1; ++l) {
       const int M = c->widths[l + 1], K = c->widths[l];
-      launch_hidden_layer<Real>(dW[l], db[l], M, K, in, C, nj, Z[cur], s);
+      // the last hidden layer also writes the tensor-core output layer's operand
+      const bool pack = use_tc && l == L - 2;
+      launch_hidden_layer<Real>(dW[l], db[l], M, K, in, C, nj, Z[cur], s,
+                                pack ? tcl.Bh : nullptr, pack ? tcl.Bl : nullptr,
+                                pack ? tcl.bkind() : 0);
       in = Z[cur];
       cur ^= 1;
     }
@@ -395,7 +399,7 @@ struct Engine : EngineBase {
       tcl.launch(reinterpret_cast<const float*>(h), zstride(C),
                  reinterpret_cast<const float*>(db[L - 1]), nj, reinterpret_cast<float*>(u),
                  reinterpret_cast<float*>(J), reinterpret_cast<float*>(ut), part_dec, nst, la,
-                 s);
+                 s, /*packed=*/L >= 2);
     else
       launch_last_layer<Real>(dW[L - 1], db[L - 1], n, c->widths[L - 1], h, C, nj, u, J, ut,
                               part_dec, nst, la, grid_dec, s);

@@ -24,6 +24,8 @@
 // vector per lane, conflict-free for the padded stride) and four rows of W.
 // Tiles are staged with 16-byte cp.async (one load phase for k <= 256), and
 // the eight partial sums of a row are combined with three shuffles.
+#include <cuda_bf16.h>
+
 #include "lsn_internal.cuh"
 
 #include <algorithm>
@@ -182,12 +184,16 @@ __host__ __device__ constexpr size_t gemm_smem(int BM, int CPs) {
 // ------------------------------------------------------------ hidden layers
 constexpr int HBM = 8;  // rows per CTA of a hidden layer (more CTAs: the layers are short)
 
+// When the next layer is the tensor-core output layer, the layer's columns
+// are also written as its K-major B operand: bkind 1 = BF16 two-term split
+// (Bh = bf16(v), Bl = bf16(v - Bh)), 2 = FP32 (B[c][m], c < C).
 template <typename Real, int CQ>
 __global__ void __launch_bounds__(KP * HBM) hidden_kernel(const Real* __restrict__ W,
                                                          const Real* __restrict__ b, int M,
                                                          int K, const Real* __restrict__ Zin,
                                                          int C, int CPs, int nj,
-                                                         Real* __restrict__ Zout) {
+                                                         Real* __restrict__ Zout, void* Bh,
+                                                         void* Bl, int bkind) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* Ws = reinterpret_cast<Real*>(smem_raw);
   Real* Zs = Ws + HBM * w_stride<Real>();
@@ -206,6 +212,14 @@ __global__ void __launch_bounds__(KP * HBM) hidden_kernel(const Real* __restrict
       if ((c % KP) != q || c >= C) continue;
       const Real v = (c == 0 || c >= nj) ? elu_f<Real>(acc[c] + bm) : e1 * acc[c];
       Zout[(size_t)m * CPs + c] = v;
+      if (bkind == 1) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
+        static_cast<__nv_bfloat16*>(Bh)[(size_t)c * M + m] = hi;
+        static_cast<__nv_bfloat16*>(Bl)[(size_t)c * M + m] =
+            __float2bfloat16_rn((float)v - __bfloat162float(hi));
+      } else if (bkind == 2) {
+        static_cast<float*>(Bh)[(size_t)c * M + m] = (float)v;
+      }
     }
   }
 }
@@ -416,7 +430,7 @@ size_t last_smem(int r, int CPs) {
 
 template <typename Real, int CQ>
 void run_hidden(const Real* W, const Real* b, int M, int K, const Real* Zin, int C, int CPs,
-                int nj, Real* Zout, cudaStream_t s) {
+                int nj, Real* Zout, void* Bh, void* Bl, int bkind, cudaStream_t s) {
   const size_t sm = gemm_smem<Real>(HBM, CPs);
   static size_t set = 0;
   if (sm > set) {
@@ -425,7 +439,7 @@ void run_hidden(const Real* W, const Real* b, int M, int K, const Real* Zin, int
     set = sm;
   }
   hidden_kernel<Real, CQ><<<(M + HBM - 1) / HBM, KP * HBM, sm, s>>>(W, b, M, K, Zin, C, CPs,
-                                                                    nj, Zout);
+                                                                    nj, Zout, Bh, Bl, bkind);
 }
 
 template <typename Real, int CQ>
@@ -467,9 +481,10 @@ int decoder_last_grid(int n, int C, int num_sms) {
 
 template <typename Real>
 void launch_hidden_layer(const Real* W, const Real* b, int M, int K, const Real* Zin, int C,
-                         int nj, Real* Zout, cudaStream_t s) {
+                         int nj, Real* Zout, cudaStream_t s, void* Bh, void* Bl, int bkind) {
   const int CPs = zstride(C);
-  LSN_CQ_SWITCH(CPs, (run_hidden<Real, CQ>(W, b, M, K, Zin, C, CPs, nj, Zout, s)))
+  LSN_CQ_SWITCH(CPs,
+                (run_hidden<Real, CQ>(W, b, M, K, Zin, C, CPs, nj, Zout, Bh, Bl, bkind, s)))
 }
 
 template <typename Real>
@@ -483,7 +498,7 @@ void launch_last_layer(const Real* W, const Real* b, int M, int K, const Real* Z
 
 #define LSN_INST(R)                                                                        \
   template void launch_hidden_layer<R>(const R*, const R*, int, int, const R*, int, int,  \
-                                       R*, cudaStream_t);                                  \
+                                       R*, cudaStream_t, void*, void*, int);               \
   template void launch_last_layer<R>(const R*, const R*, int, int, const R*, int, int, R*, \
                                      R*, R*, double*, int, const LastArgs&, int,           \
                                      cudaStream_t);

@@ -336,7 +336,7 @@ __device__ __forceinline__ void disp_grad(const Real* __restrict__ u, const int4
 template <typename Real, int ET>
 __device__ __forceinline__ void element_phase1(const ElemArgs& ea, const Real* __restrict__ u,
                                                int e, int t, ElemTile<Real, ET>& tl, Real mu,
-                                               Real lam, Real oma, double& eacc, double& eabs) {
+                                               Real lam, Real oma, Real& pe_out) {
   if (e < ea.S) {
     int4 tv;
     Real Dmi[3][3], wv, H[3][3];
@@ -345,8 +345,7 @@ __device__ __forceinline__ void element_phase1(const ElemArgs& ea, const Real* _
     Invariants<Real> iv;
     invariants<Real>(H, iv);
     const Real psi = snh_psi<Real>(iv, mu, lam, oma);
-    eacc += (double)(wv * psi);
-    eabs += fabs((double)(wv * psi));
+    pe_out = wv * psi;
     const Real Ic = iv.Ic3 + Real(3);
     const Real dl = iv.Ic3 / (Real(4) * (Ic + Real(1)));
     const Real lJ = lam * iv.Jm1;
@@ -404,6 +403,7 @@ __device__ __forceinline__ void element_phase1(const ElemArgs& ea, const Real* _
       for (int a = 1; a < 4; ++a) tl.D[t][3 * a + j] = Dmi[a - 1][j];
     }
   } else {
+    pe_out = Real(0);
 #pragma unroll
     for (int k = 0; k < 9; ++k) tl.U[t][k] = tl.V[t][k] = tl.As[t][k] = Real(0);
 #pragma unroll
@@ -631,7 +631,12 @@ __global__ void __launch_bounds__(ET) element_kernel(ElemArgs ea, const Real* __
     __syncthreads();
     prefetch(0, min(CB, tile_tets), 0);
     // ---------------- phase 1: element math, one tet per thread
-    element_phase1<Real, ET>(ea, u, e, t, tl, mu, lam, oma, eacc, eabs);
+    {
+      Real pe;
+      element_phase1<Real, ET>(ea, u, e, t, tl, mu, lam, oma, pe);
+      eacc += (double)pe;
+      eabs += fabs((double)pe);
+    }
     // ---------------- phases 2 + 3 in batches of CB tets
     int buf = 0;
     for (int b0 = 0; b0 < tile_tets; b0 += CB, buf ^= 1) {
@@ -805,7 +810,7 @@ __global__ void __launch_bounds__(NT, 1)
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t done[2], fin;
   __shared__ uint32_t tbase_s;
-  __shared__ double red[NT / 32][2 + 2 * KTRIAL];
+  __shared__ FAcc red[NT / 32][2 + 2 * KTRIAL];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -831,9 +836,8 @@ __global__ void __launch_bounds__(NT, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tbase_s;
-  double eacc = 0.0, eabs = 0.0, etr[KTRIAL], atr[KTRIAL], gacc = 0.0, gabs = 0.0;
-#pragma unroll
-  for (int j = 0; j < KTRIAL; ++j) etr[j] = atr[j] = 0.0;
+  // energies and gradient partials in double-float (FP32 TwoSum) accumulators
+  FAcc eacc, eabs, etr[KTRIAL], atr[KTRIAL], gacc, gabs;
   // TT <= ET tets per tile (small cubature sets use small tiles, more CTAs)
   const int ntiles = (S + TT - 1) / TT;
   int qc = 0;  // chunks issued by this CTA
@@ -845,7 +849,10 @@ __global__ void __launch_bounds__(NT, 1)
     // energies of the line search (threads >= ET), one tet per thread
     if (t < ET) {
       tl.v[t] = e < S ? ea.tets[e] : make_int4(0, 0, 0, 0);
-      element_phase1<float, ET>(ea, u, e, t, tl, mu, lam, oma, eacc, eabs);
+      float pe;
+      element_phase1<float, ET>(ea, u, e, t, tl, mu, lam, oma, pe);
+      facc_add(eacc, pe);
+      facc_add(eabs, fabsf(pe));
     } else {
       const int e2 = tile * TT + (t - ET);
       if (t - ET < TT && e2 < S) {
@@ -858,9 +865,9 @@ __global__ void __launch_bounds__(NT, 1)
           disp_grad<float>(ut + (size_t)j * ea.n, tv, Dmi, H);
           Invariants<float> iv;
           invariants<float>(H, iv);
-          const double pe = (double)(wv * snh_psi<float>(iv, mu, lam, oma));
-          etr[j] += pe;
-          atr[j] += fabs(pe);
+          const float pe = wv * snh_psi<float>(iv, mu, lam, oma);
+          facc_add(etr[j], pe);
+          facc_add(atr[j], fabsf(pe));
         }
       }
     }
@@ -954,8 +961,8 @@ __global__ void __launch_bounds__(NT, 1)
           s0 += Gp[lt * r + t];
           a0 += fabsf(Gp[lt * r + t]);
         }
-        gacc += (double)(s0 + s1);
-        gabs += (double)(a0 + a1);
+        facc_add(gacc, s0 + s1);
+        facc_add(gabs, a0 + a1);
       }
       __syncthreads();
     }
@@ -963,8 +970,8 @@ __global__ void __launch_bounds__(NT, 1)
   if (t == 0) mma_commit(&fin);
   const bool fok = __syncthreads_and(alive && wait_bar(&fin, 0, err, 2));
   tc_fence_after();
-  // energies: warp shuffles, then the warps in fixed order
-  double vals[2 + 2 * KTRIAL];
+  // energies: warp shuffles, then the warps in fixed order (double-float)
+  FAcc vals[2 + 2 * KTRIAL];
   vals[0] = eacc;
   vals[1] = eabs;
 #pragma unroll
@@ -975,20 +982,20 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
   for (int j = 0; j < 2 + 2 * KTRIAL; ++j) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) vals[j] += __shfl_down_sync(0xffffffffu, vals[j], o);
+    for (int o = 16; o > 0; o >>= 1) facc_merge(vals[j], facc_shfl_down(vals[j], o));
     if (lane == 0) red[warp][j] = vals[j];
   }
   __syncthreads();
   double* prow = part + (size_t)blockIdx.x * part_stride;
   if (t < 2 + 2 * KTRIAL) {
-    double sum = 0.0;
-    for (int w = 0; w < NT / 32; ++w) sum += red[w][t];
-    if (t < 2) prow[t] = sum;
-    else prow[nslots(r) + t - 2] = sum;
+    FAcc sum;
+    for (int w = 0; w < NT / 32; ++w) facc_merge(sum, red[w][t]);
+    if (t < 2) prow[t] = facc_value(sum);
+    else prow[nslots(r) + t - 2] = facc_value(sum);
   }
   if (t < r) {
-    prow[slot_g(t)] = gacc;
-    prow[slot_gabs(r, t)] = gabs;
+    prow[slot_g(t)] = facc_value(gacc);
+    prow[slot_gabs(r, t)] = facc_value(gabs);
   }
   // Gram rows: row c of the M = 64 accumulator is TMEM lane 32 (c / 16) + c % 16
   if (warp < 4) {

@@ -97,7 +97,8 @@ struct LastArgs {            // data of the output-layer epilogue
 // Activations are unit-major Z[k][c] with column stride zstride(C).
 template <typename Real>
 void launch_hidden_layer(const Real* W, const Real* b, int M, int K, const Real* Zin, int C,
-                         int nj, Real* Zout, cudaStream_t s);
+                         int nj, Real* Zout, cudaStream_t s, void* Bh = nullptr,
+                         void* Bl = nullptr, int bkind = 0);
 template <typename Real>
 void launch_last_layer(const Real* W, const Real* b, int M, int K, const Real* Zin, int C,
                        int nj, Real* u_out, Real* J_out, Real* u_trial, double* part,

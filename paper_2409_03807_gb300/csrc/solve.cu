@@ -51,7 +51,7 @@ __global__ void reduce_partials_kernel(const double* __restrict__ A, int rowsA,
 template <typename Real>
 __device__ void write_pass_points(DevSolver* sv, Real* Z0, double a0, bool with_dir) {
   const int r = sv->r, CPs = zstride(r + 1 + KTRIAL);
-  for (int e = threadIdx.x; e < (1 + KTRIAL) * r; e += blockDim.x) {
+  for (int e = threadIdx.x & 31; e < (1 + KTRIAL) * r; e += 32) {  // warp 0
     const int j = e / r, i = e - j * r;
     const double a = with_dir ? ldexp(a0, -j) : 0.0;
     const double v = sv->z[i] + a * sv->d[i];
@@ -102,194 +102,247 @@ __device__ __forceinline__ double warp_max(double v) {
 // decision logic of lane 0 does not wait on global-memory round trips.
 constexpr int SV_SCALAR_WORDS = (int)(offsetof(DevSolver, z) / sizeof(double));
 
+constexpr int SEL_THREADS = 128;  // warp 0: solver state logic; all four warps: Cholesky
+
+// FP64 square root and its reciprocal: an FP32 reciprocal-square-root
+// estimate refined by two Newton steps y <- y (3 - s y^2) / 2, which converge
+// quadratically (about 2^-22 -> 2^-44 -> FP64 rounding).  Few FP64
+// instructions on the serial path of the factorisation (GB300 issues a
+// warp-wide FP64 instruction in about 64 cycles per sub-partition).
+__device__ __forceinline__ void sqrt_and_inverse(double s, double& root, double& inv) {
+  if (s > 1e-30 && s < 1e30) {
+    double yv = (double)rsqrtf((float)s);
+    yv = yv * (1.5 - 0.5 * s * yv * yv);
+    yv = yv * (1.5 - 0.5 * s * yv * yv);
+    inv = yv;
+    root = s * yv;
+  } else {
+    root = sqrt(s);
+    inv = 1.0 / root;
+  }
+}
+
+// Right-looking Cholesky L L^T of the symmetric matrix held in L (lower
+// triangle used), all SEL_THREADS threads: per column one square root and
+// one reciprocal (thread 0), the column scaled, then independent FMAs over
+// the trailing lower triangle spread over the four warps.  Returns false
+// (uniformly) when a pivot is not positive.
+__device__ bool block_cholesky(double (*L)[RMAX + 1], double* invd, int r, int* s_fail) {
+  const int t = threadIdx.x;
+  for (int j = 0; j < r; ++j) {
+    if (t == 0) {
+      const double sjj = L[j][j];
+      if (!(sjj > 0.0)) {
+        *s_fail = 1;
+      } else {
+        double root, inv;
+        sqrt_and_inverse(sjj, root, inv);
+        L[j][j] = root;
+        invd[j] = inv;
+        *s_fail = 0;
+      }
+    }
+    __syncthreads();
+    if (*s_fail) return false;
+    const double inv = invd[j];
+    for (int i = j + 1 + t; i < r; i += SEL_THREADS) L[i][j] *= inv;
+    __syncthreads();
+    const int m = r - 1 - j;
+    for (int e = t; e < m * m; e += SEL_THREADS) {
+      const int ii = e / m, kk = e - ii * m;
+      if (kk <= ii) {
+        const int i = j + 1 + ii, k = j + 1 + kk;
+        L[i][k] -= L[i][j] * L[k][j];
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Warp-0 state logic around a block-wide FP64 Cholesky (SEL_THREADS threads,
+// one CTA): the line-search decision on the trial energies of the pass, the
+// exit tests, and (when a new direction is due) d = -K^-1 g with diagonal
+// shifts on failure, then the points of the next pass.
 template <typename Real>
-__global__ void __launch_bounds__(32) select_direction_kernel(DevSolver* gsv,
-                                                              const double* __restrict__ sys,
-                                                              Real* Z0,
-                                                              unsigned long long cond,
-                                                              int use_cond) {
+__global__ void __launch_bounds__(SEL_THREADS) select_direction_kernel(
+    DevSolver* gsv, const double* __restrict__ sys, Real* Z0, unsigned long long cond,
+    int use_cond) {
   __shared__ double L[RMAX][RMAX + 1];
   __shared__ double y[RMAX];
   __shared__ double invd[RMAX];  // reciprocals of the Cholesky diagonal
   __shared__ double ssys[4 * RMAX + 2 * KTRIAL + 2];
   __shared__ __align__(16) DevSolver svs;
+  __shared__ int s_need, s_fail;
+  __shared__ double s_base;
   DevSolver* sv = &svs;
   const int t = threadIdx.x;
   // ---- parallel load of the state (scalars, z, d) and of E, g, gabs, trials
   {
     const double* src = reinterpret_cast<const double*>(gsv);
     double* dst = reinterpret_cast<double*>(&svs);
-    for (int e = t; e < SV_SCALAR_WORDS + 2 * RMAX; e += 32) dst[e] = src[e];
+    for (int e = t; e < SV_SCALAR_WORDS + 2 * RMAX; e += SEL_THREADS) dst[e] = src[e];
   }
-  __syncwarp();
+  if (t == 0) s_need = 0;
+  __syncthreads();
   const int r = sv->r;
   const int tslot = nslots(r);
   const double* Ku = sys + slot_K(r);
-  for (int e = t; e < 2 + 2 * r; e += 32) ssys[e] = sys[e];
-  for (int e = t; e < 2 * KTRIAL; e += 32) ssys[2 + 2 * r + e] = sys[tslot + e];
+  for (int e = t; e < 2 + 2 * r; e += SEL_THREADS) ssys[e] = sys[e];
+  for (int e = t; e < 2 * KTRIAL; e += SEL_THREADS) ssys[2 + 2 * r + e] = sys[tslot + e];
   // K into L (needed only when a direction is computed; issued early)
-  for (int e = t; e < r * r; e += 32) {
+  for (int e = t; e < r * r; e += SEL_THREADS) {
     const int i = e / r, j = e - i * r;
     L[i][j] = i <= j ? Ku[upper_index(i, j, r)] : Ku[upper_index(j, i, r)];
   }
-  __syncwarp();
-  const double* sE = ssys;                    // E, Eabs at y0
-  const double* sg = ssys + 2;                // g
-  const double* sga = ssys + 2 + r;           // gabs
-  const double* sT = ssys + 2 + 2 * r;        // trial (E_j, Eabs_j)
-  // ------------------------------------------------ line-search decision
-  int at_z = 1, stepped = 0;
-  if (t == 0) {
-    sv->passes += 1;
-    if (sv->final_pass) {
-      sv->final_pass = 0;
-      sv->running = 0;
-      at_z = -2;
-    } else if (sv->have_dir) {
-      int acc = -1;
-      for (int j = 0; j <= KTRIAL; ++j) {
-        if (sv->ls_iter >= sv->max_ls) break;
-        sv->ls_iter += 1;
-        sv->ls_trials += 1;
-        const double a = ldexp(sv->alpha_base, -j);
-        const double Et = j == 0 ? sE[0] : sT[2 * (j - 1)];
-        const double Ea = j == 0 ? sE[1] : sT[2 * (j - 1) + 1];
-        const double eta = sv->eta_scale * (Ea + sv->Eabs);
-        if (isfinite(Et) && Et <= sv->E + sv->armijo_c * a * sv->gd + eta) {
-          acc = j;
-          break;
-        }
-      }
-      if (acc >= 0) {
-        const double a = ldexp(sv->alpha_base, -acc);
-        sv->alpha_taken = a;
-        if (sv->iters < TRACE) gsv->trace_alpha[sv->iters] = a;
-        sv->iters += 1;
-        sv->have_dir = 0;
-        at_z = acc == 0 ? 1 : 0;
-        stepped = 1;
-      } else if (sv->ls_iter >= sv->max_ls) {
-        sv->status = (sv->grad_inf < 100.0 * sv->tol) ? 4 : 2;  // PRECISION_FLOOR : LS_FAILED
-        sv->have_dir = 0;
-        sv->final_pass = 1;  // positions must be re-evaluated at z
-        at_z = -1;
-      } else {
-        sv->alpha_base = ldexp(sv->alpha_base, -(KTRIAL + 1));
-        at_z = -1;  // keep backtracking along d
-      }
-    }
-  }
-  at_z = __shfl_sync(0xffffffffu, at_z, 0);
-  stepped = __shfl_sync(0xffffffffu, stepped, 0);
-  __syncwarp();
-  if (stepped) {  // a step was taken: z += alpha d
-    for (int i = t; i < r; i += 32) sv->z[i] += sv->alpha_taken * sv->d[i];
-    __syncwarp();
-  }
+  __syncthreads();
   int status = -1;
   bool want_cond = true;
   int cond_val = 1;
-  if (at_z == -2) {  // the final re-evaluation at z is done
-    cond_val = 0;
-  } else if (at_z == -1) {
-    write_pass_points<Real>(sv, Z0, sv->alpha_base, sv->status == -1);
-    if (t == 0) sv->running = 1;
-  } else if (at_z == 0) {  // a shorter step was taken: evaluate at the new z next
-    write_pass_points<Real>(sv, Z0, 0.0, false);
-  } else {
-    // ------------------------------------------- sys holds E, g, K at z
-    double gm = 0.0, ga = 0.0;
-    bool finite = true;
-    for (int i = t; i < r; i += 32) {
-      const double gi = sg[i];
-      y[i] = -gi;
-      gm = fmax(gm, fabs(gi));
-      ga = fmax(ga, sga[i]);
-      finite = finite && isfinite(gi);
-    }
-    for (int e = t; e < r * r; e += 32) finite = finite && isfinite(L[e / r][e % r]);
-    const double ginf = __all_sync(0xffffffffu, finite) ? warp_max(gm) : -1.0;
-    const double gabs_max = warp_max(ga);
-    const double E = sE[0];
-    int stall = 0;
+  if (t < 32) {
+    const double* sE = ssys;                    // E, Eabs at y0
+    const double* sg = ssys + 2;                // g
+    const double* sga = ssys + 2 + r;           // gabs
+    const double* sT = ssys + 2 + 2 * r;        // trial (E_j, Eabs_j)
+    // ------------------------------------------------ line-search decision
+    int at_z = 1, stepped = 0;
     if (t == 0) {
-      sv->E = E;
-      sv->Eabs = sE[1];
-      sv->grad_inf = ginf;
-      sv->gabs_max = gabs_max;
-      if (!sv->eval_only) {
-        if (sv->iters < TRACE) {
-          gsv->trace_g[sv->iters] = ginf;
-          gsv->trace_E[sv->iters] = E;
-          gsv->trace_gabs[sv->iters] = gabs_max;
-          gsv->trace_alpha[sv->iters] = 0.0;
-        }
-        // stall counter: iterations since ||g||_inf last dropped by 10 %
-        if (ginf <= 0.9 * sv->g_best) {
-          sv->g_best = ginf;
-          sv->stall = 0;
-        } else {
-          sv->stall += 1;
-        }
-      }
-      stall = sv->stall;
-    }
-    stall = __shfl_sync(0xffffffffu, stall, 0);
-    if (sv->eval_only) status = 0;
-    else if (ginf < 0.0 || !isfinite(E)) status = -3;              // LSN_ERR_NONFINITE
-    else if (ginf < sv->tol) status = 0;                           // LSN_OK
-    else if (stall >= 4 && ginf <= sv->floor_scale * gabs_max) status = 4;  // PRECISION_FLOOR
-    else if (sv->iters >= sv->max_newton) status = 1;              // LSN_NOT_CONVERGED
-    if (status != -1) {
-      if (t == 0) {
-        if (!sv->eval_only) sv->status = status;
+      sv->passes += 1;
+      if (sv->final_pass) {
+        sv->final_pass = 0;
         sv->running = 0;
-      }
-      cond_val = 0;
-    } else {
-      // Cholesky K + shift I = L L^T, shift = 0, then 1e-12 max(1, max|K_ii|) x 10^k
-      double dm = 0.0;
-      for (int i = t; i < r; i += 32) dm = fmax(dm, fabs(L[i][i]));
-      const double base = 1e-12 * fmax(1.0, warp_max(dm));
-      double shift = 0.0;
-      bool ok = false;
-      for (int attempt = 0; attempt < 21 && !ok; ++attempt) {
-        if (attempt > 0) {
-          __syncwarp();
-          for (int e = t; e < r * r; e += 32) {
-            const int i = e / r, j = e - i * r;
-            L[i][j] = (i <= j ? Ku[upper_index(i, j, r)] : Ku[upper_index(j, i, r)]) +
-                      (i == j ? shift : 0.0);
-          }
-          __syncwarp();
-        }
-        // right-looking: per column one square root and one reciprocal, then
-        // independent FMAs over the trailing lower triangle (lanes take the
-        // columns k of each row), so the FP64 pipe is fed without dependent
-        // chains or divisions per element
-        bool fail = false;
-        for (int j = 0; j < r; ++j) {
-          const double s = L[j][j];
-          if (!(s > 0.0)) {
-            fail = true;
+        at_z = -2;
+      } else if (sv->have_dir) {
+        int acc = -1;
+        for (int j = 0; j <= KTRIAL; ++j) {
+          if (sv->ls_iter >= sv->max_ls) break;
+          sv->ls_iter += 1;
+          sv->ls_trials += 1;
+          const double a = ldexp(sv->alpha_base, -j);
+          const double Et = j == 0 ? sE[0] : sT[2 * (j - 1)];
+          const double Ea = j == 0 ? sE[1] : sT[2 * (j - 1) + 1];
+          const double eta = sv->eta_scale * (Ea + sv->Eabs);
+          if (isfinite(Et) && Et <= sv->E + sv->armijo_c * a * sv->gd + eta) {
+            acc = j;
             break;
           }
-          const double djj = sqrt(s), inv = 1.0 / djj;
-          __syncwarp();
-          if (t == 0) L[j][j] = djj;
-          for (int i = j + 1 + t; i < r; i += 32) L[i][j] *= inv;
-          if (t == 0) invd[j] = inv;
-          __syncwarp();
-          for (int i = j + 1; i < r; ++i) {
-            const double lij = L[i][j];
-            for (int k = j + 1 + t; k <= i; k += 32) L[i][k] -= lij * L[k][j];
-          }
-          __syncwarp();
         }
-        fail = __any_sync(0xffffffffu, fail);
-        ok = !fail;
-        if (!ok) shift = shift == 0.0 ? base : shift * 10.0;
+        if (acc >= 0) {
+          const double a = ldexp(sv->alpha_base, -acc);
+          sv->alpha_taken = a;
+          if (sv->iters < TRACE) gsv->trace_alpha[sv->iters] = a;
+          sv->iters += 1;
+          sv->have_dir = 0;
+          at_z = acc == 0 ? 1 : 0;
+          stepped = 1;
+        } else if (sv->ls_iter >= sv->max_ls) {
+          sv->status = (sv->grad_inf < 100.0 * sv->tol) ? 4 : 2;  // PRECISION_FLOOR : LS_FAILED
+          sv->have_dir = 0;
+          sv->final_pass = 1;  // positions must be re-evaluated at z
+          at_z = -1;
+        } else {
+          sv->alpha_base = ldexp(sv->alpha_base, -(KTRIAL + 1));
+          at_z = -1;  // keep backtracking along d
+        }
       }
+    }
+    at_z = __shfl_sync(0xffffffffu, at_z, 0);
+    stepped = __shfl_sync(0xffffffffu, stepped, 0);
+    __syncwarp();
+    if (stepped) {  // a step was taken: z += alpha d
+      for (int i = t; i < r; i += 32) sv->z[i] += sv->alpha_taken * sv->d[i];
+      __syncwarp();
+    }
+    if (at_z == -2) {  // the final re-evaluation at z is done
+      cond_val = 0;
+    } else if (at_z == -1) {
+      write_pass_points<Real>(sv, Z0, sv->alpha_base, sv->status == -1);
+      if (t == 0) sv->running = 1;
+    } else if (at_z == 0) {  // a shorter step was taken: evaluate at the new z next
+      write_pass_points<Real>(sv, Z0, 0.0, false);
+    } else {
+      // ------------------------------------------- sys holds E, g, K at z
+      double gm = 0.0, ga = 0.0;
+      bool finite = true;
+      for (int i = t; i < r; i += 32) {
+        const double gi = sg[i];
+        y[i] = -gi;
+        gm = fmax(gm, fabs(gi));
+        ga = fmax(ga, sga[i]);
+        finite = finite && isfinite(gi);
+      }
+      for (int e = t; e < r * r; e += 32) finite = finite && isfinite(L[e / r][e % r]);
+      const double ginf = __all_sync(0xffffffffu, finite) ? warp_max(gm) : -1.0;
+      const double gabs_max = warp_max(ga);
+      const double E = sE[0];
+      int stall = 0;
+      if (t == 0) {
+        sv->E = E;
+        sv->Eabs = sE[1];
+        sv->grad_inf = ginf;
+        sv->gabs_max = gabs_max;
+        if (!sv->eval_only) {
+          if (sv->iters < TRACE) {
+            gsv->trace_g[sv->iters] = ginf;
+            gsv->trace_E[sv->iters] = E;
+            gsv->trace_gabs[sv->iters] = gabs_max;
+            gsv->trace_alpha[sv->iters] = 0.0;
+          }
+          // stall counter: iterations since ||g||_inf last dropped by 10 %
+          if (ginf <= 0.9 * sv->g_best) {
+            sv->g_best = ginf;
+            sv->stall = 0;
+          } else {
+            sv->stall += 1;
+          }
+        }
+        stall = sv->stall;
+      }
+      stall = __shfl_sync(0xffffffffu, stall, 0);
+      if (sv->eval_only) status = 0;
+      else if (ginf < 0.0 || !isfinite(E)) status = -3;              // LSN_ERR_NONFINITE
+      else if (ginf < sv->tol) status = 0;                           // LSN_OK
+      else if (stall >= 4 && ginf <= sv->floor_scale * gabs_max) status = 4;  // PRECISION_FLOOR
+      else if (sv->iters >= sv->max_newton) status = 1;              // LSN_NOT_CONVERGED
+      if (status != -1) {
+        if (t == 0) {
+          if (!sv->eval_only) sv->status = status;
+          sv->running = 0;
+        }
+        cond_val = 0;
+      } else {
+        // a new direction is due: factorised below by all four warps
+        double dm = 0.0;
+        for (int i = t; i < r; i += 32) dm = fmax(dm, fabs(L[i][i]));
+        const double base = 1e-12 * fmax(1.0, warp_max(dm));
+        if (t == 0) {
+          s_base = base;
+          s_need = 1;
+        }
+      }
+    }
+    for (int i = t; i < r; i += 32) gsv->g[i] = sg[i];
+  }
+  __syncthreads();
+  if (s_need) {
+    // Cholesky K + shift I = L L^T, shift = 0, then 1e-12 max(1, max|K_ii|) x 10^k
+    double shift = 0.0;
+    bool ok = false;
+    for (int attempt = 0; attempt < 21 && !ok; ++attempt) {
+      if (attempt > 0) {
+        for (int e = t; e < r * r; e += SEL_THREADS) {
+          const int i = e / r, j = e - i * r;
+          L[i][j] = (i <= j ? Ku[upper_index(i, j, r)] : Ku[upper_index(j, i, r)]) +
+                    (i == j ? shift : 0.0);
+        }
+        __syncthreads();
+      }
+      ok = block_cholesky(L, invd, r, &s_fail);
+      if (!ok) shift = shift == 0.0 ? s_base : shift * 10.0;
+      __syncthreads();
+    }
+    if (t < 32) {
+      const double* sg = ssys + 2;
       if (!ok) {
         if (t == 0) {
           sv->status = 3;  // LSN_NOT_SPD
@@ -297,8 +350,7 @@ __global__ void __launch_bounds__(32) select_direction_kernel(DevSolver* gsv,
         }
         cond_val = 0;
       } else {
-        // forward L y = -g, backward L^T d = y (column sweeps within the warp)
-        __syncwarp();
+        // forward L y = -g, backward L^T d = y (column sweeps within warp 0)
         for (int i = 0; i < r; ++i) {
           const double yi = y[i] * invd[i];
           __syncwarp();
@@ -330,14 +382,13 @@ __global__ void __launch_bounds__(32) select_direction_kernel(DevSolver* gsv,
         write_pass_points<Real>(sv, Z0, 1.0, true);
       }
     }
-    for (int i = t; i < r; i += 32) gsv->g[i] = sg[i];
   }
   // ---- parallel store of the state
-  __syncwarp();
+  __syncthreads();
   {
     const double* src = reinterpret_cast<const double*>(&svs);
     double* dst = reinterpret_cast<double*>(gsv);
-    for (int e = t; e < SV_SCALAR_WORDS + 2 * RMAX; e += 32) dst[e] = src[e];
+    for (int e = t; e < SV_SCALAR_WORDS + 2 * RMAX; e += SEL_THREADS) dst[e] = src[e];
   }
   if (want_cond && use_cond && t == 0) cudaGraphSetConditional(cond, cond_val);
 }
@@ -383,7 +434,7 @@ void launch_solve_begin(DevSolver* sv, Real* Z0, int C, int eval_only, cudaStrea
 template <typename Real>
 void launch_select_direction(DevSolver* sv, const double* sys, Real* Z0,
                              unsigned long long cond, int use_cond, cudaStream_t s) {
-  select_direction_kernel<Real><<<1, 32, 0, s>>>(sv, sys, Z0, cond, use_cond);
+  select_direction_kernel<Real><<<1, SEL_THREADS, 0, s>>>(sv, sys, Z0, cond, use_cond);
 }
 
 template <typename Real>

@@ -309,15 +309,13 @@ __global__ void __launch_bounds__(TNT, 1)
     const int row = 32 * q + lane;   // row of the tile
     float* Js = reinterpret_cast<float*>(sb + SL.js_off);
     float* gvs = reinterpret_cast<float*>(sb + SL.gv_off);
-    double* red = reinterpret_cast<double*>(sb + SL.red_off);
     const int JS = r + 4;
     const float inv_dt2 = (float)*la.inv_dt2;
     const float scale = (float)la.scale;
     const int ntr = C - nj;
-    double eacc = 0.0, eabs = 0.0, etr[KTRIAL], atr[KTRIAL];
-#pragma unroll
-    for (int j = 0; j < KTRIAL; ++j) etr[j] = atr[j] = 0.0;
-    double gacc = 0.0, gabs = 0.0;  // column et of g (et < r)
+    // double-float (FP32 TwoSum) accumulators: no FP64 instructions per row
+    FAcc eacc, eabs, etr[KTRIAL], atr[KTRIAL];
+    FAcc gacc, gabs;  // column et of g (et < r)
     bool alive = true;
     for (int i = 0; i < my_tiles; ++i) {
       const int m0 = (blockIdx.x + i * gridDim.x) * TBM, m = m0 + row;
@@ -361,8 +359,8 @@ __global__ void __launch_bounds__(TNT, 1)
             if (live) {
               row_terms_tc(la, inv_dt2, comp, mv, ub, x0, u0r, e, gv, kv);
               u_out[m] = u0r;
-              eacc += (double)e;
-              eabs += (double)fabsf(e);
+              facc_add(eacc, e);
+              facc_add(eabs, fabsf(e));
             }
             wk = sqrtf(kv);
           } else if (c <= r) {
@@ -393,8 +391,8 @@ __global__ void __launch_bounds__(TNT, 1)
 #pragma unroll
             for (int x = 0; x < KTRIAL; ++x)
               if (x == tj) {
-                etr[x] += (double)et2;
-                atr[x] += (double)fabsf(et2);
+                facc_add(etr[x], et2);
+                facc_add(atr[x], fabsf(et2));
               }
           }
         }
@@ -430,8 +428,8 @@ __global__ void __launch_bounds__(TNT, 1)
           s0 += t0;
           a0 += fabsf(t0);
         }
-        gacc += (double)((s0 + s1) + (s2 + s3));
-        gabs += (double)((a0 + a1) + (a2 + a3));
+        facc_add(gacc, (s0 + s1) + (s2 + s3));
+        facc_add(gabs, (a0 + a1) + (a2 + a3));
       }
       float* Jdst = J_out + (size_t)m0 * r;
       for (int rr = et >> 5; rr < rows; rr += 4)
@@ -440,7 +438,7 @@ __global__ void __launch_bounds__(TNT, 1)
       if (!alive) break;
     }
     // energy sums: warp shuffles, then the 4 warps in fixed order
-    double vals[2 + 2 * KTRIAL];
+    FAcc vals[2 + 2 * KTRIAL];
     vals[0] = eacc;
     vals[1] = eabs;
 #pragma unroll
@@ -451,22 +449,24 @@ __global__ void __launch_bounds__(TNT, 1)
 #pragma unroll
     for (int j = 0; j < 2 + 2 * KTRIAL; ++j)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) vals[j] += __shfl_down_sync(0xffffffffu, vals[j], o);
+      for (int o = 16; o > 0; o >>= 1) facc_merge(vals[j], facc_shfl_down(vals[j], o));
+    FAcc* red = reinterpret_cast<FAcc*>(sb + SL.red_off);
     if (lane == 0)
 #pragma unroll
       for (int j = 0; j < 2 + 2 * KTRIAL; ++j) red[q * (2 + 2 * KTRIAL) + j] = vals[j];
     epi_sync();
     double* prow = part + (size_t)blockIdx.x * part_stride;
     if (et < 2 + 2 * KTRIAL) {
-      double s = 0.0;
-      for (int w = 0; w < 4; ++w) s += red[w * (2 + 2 * KTRIAL) + et];
+      FAcc sum;
+      for (int w = 0; w < 4; ++w) facc_merge(sum, red[w * (2 + 2 * KTRIAL) + et]);
+      const double v = facc_value(sum);
       const int tslot = nslots(r);
-      if (et < 2) prow[et] = s;
-      else prow[tslot + et - 2] = ((et - 2) / 2 < ntr) ? s : 0.0;
+      if (et < 2) prow[et] = v;
+      else prow[tslot + et - 2] = ((et - 2) / 2 < ntr) ? v : 0.0;
     }
     if (et < r) {
-      prow[slot_g(et)] = gacc;
-      prow[slot_gabs(r, et)] = gabs;
+      prow[slot_g(et)] = facc_value(gacc);
+      prow[slot_gabs(r, et)] = facc_value(gabs);
     }
     // inertia Gram: row c of the M = 64 accumulator is TMEM lane
     // 32 (c / 16) + c % 16, i.e. lanes 0-15 of quadrant c / 16
@@ -562,6 +562,10 @@ cudaError_t TcLast::setup(const float* W_fp32, int M_, int H_, int C_, int r_, b
     e = cudaMalloc(&Bl, bbytes);
     if (e != cudaSuccess) return e;
   }
+  // rows c >= C of the B operand stay zero (the hidden layer writes c < C)
+  e = cudaMemsetAsync(Bh, 0, bbytes, s);
+  if (e == cudaSuccess && bf16) e = cudaMemsetAsync(Bl, 0, bbytes, s);
+  if (e != cudaSuccess) return e;
   e = cudaMalloc(&err, sizeof(int));
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(err, 0, sizeof(int), s);
@@ -586,14 +590,14 @@ void TcLast::release() {
 
 void TcLast::launch(const float* Z, int CPs, const float* bias, int nj, float* u, float* J,
                     float* ut, double* part, int part_stride, const LastArgs& la,
-                    cudaStream_t s) const {
+                    cudaStream_t s, bool packed) const {
   const int n = Cp * H;
   if (bf16) {
-    pack_kernel<true><<<(n + 255) / 256, 256, 0, s>>>(Z, H, C, CPs, Cp, Bh, Bl);
+    if (!packed) pack_kernel<true><<<(n + 255) / 256, 256, 0, s>>>(Z, H, C, CPs, Cp, Bh, Bl);
     tc_last_kernel<true><<<grid, TNT, smem, s>>>(mapW, mapBh, mapBl, bias, M, H, C, Cp, nj, u,
                                                  J, ut, part, part_stride, la, err);
   } else {
-    pack_kernel<false><<<(n + 255) / 256, 256, 0, s>>>(Z, H, C, CPs, Cp, Bh, nullptr);
+    if (!packed) pack_kernel<false><<<(n + 255) / 256, 256, 0, s>>>(Z, H, C, CPs, Cp, Bh, nullptr);
     tc_last_kernel<false><<<grid, TNT, smem, s>>>(mapW, mapBh, mapBl, bias, M, H, C, Cp, nj,
                                                   u, J, ut, part, part_stride, la, err);
   }

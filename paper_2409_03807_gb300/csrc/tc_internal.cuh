@@ -23,8 +23,12 @@ struct TcLast {
   void release();
   // Z: last hidden layer, unit-major [H][CPs] (FP32); same outputs and
   // partial-row layout as launch_last_layer
+  // packed: the B operand was already written by the last hidden layer
+  // (launch_hidden_layer with bkind()), so the packing kernel is skipped
   void launch(const float* Z, int CPs, const float* bias, int nj, float* u, float* J, float* ut,
-              double* part, int part_stride, const LastArgs& la, cudaStream_t s) const;
+              double* part, int part_stride, const LastArgs& la, cudaStream_t s,
+              bool packed = false) const;
+  int bkind() const { return bf16 ? 1 : 2; }
   ~TcLast() { release(); }
 };
 

@@ -171,5 +171,32 @@ __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
+// Double-float accumulator: value = hi + lo, additions by Knuth's TwoSum
+// (the rounding error of each FP32 addition is carried exactly into lo), so
+// long sums keep about 2^-44 relative accuracy without FP64 instructions
+// (GB300 issues a warp-wide FP64 instruction in about 64 cycles per
+// sub-partition).
+struct FAcc {
+  float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void facc_add(FAcc& a, float x) {
+  const float s = a.hi + x;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (x - bb);
+  a.hi = s;
+  a.lo += err;
+}
+__device__ __forceinline__ void facc_merge(FAcc& a, const FAcc& b) {
+  facc_add(a, b.hi);
+  a.lo += b.lo;
+}
+__device__ __forceinline__ FAcc facc_shfl_down(const FAcc& a, int o) {
+  FAcc b;
+  b.hi = __shfl_down_sync(0xffffffffu, a.hi, o);
+  b.lo = __shfl_down_sync(0xffffffffu, a.lo, o);
+  return b;
+}
+__device__ __forceinline__ double facc_value(const FAcc& a) { return (double)a.hi + (double)a.lo; }
+
 }  // namespace tc
 }  // namespace lsn
