@@ -117,6 +117,36 @@ def dist_setup():
     return world, rank, local
 
 
+def workload_config(args, p, world):
+    """The `config` object of the JSON line (both arms)."""
+    c = p.config
+    W, K = args.warmup, args.steps
+    return {"workload": args.workload,
+            "mesh": f"{c.dims[0]}x{c.dims[1]}x{c.dims[2]} nodes, {p.ne} tets, n={p.n}",
+            "r": c.r, "decoder": "-".join(map(str, p.widths)),
+            "cubature": len(p.cub_idx), "dt": c.dt, "tol_inf": c.eps,
+            "precision": args.precision + " (FP64 Cholesky + line search)",
+            "frames": f"{W + 1}..{W + K}",
+            "l2": "flushed between steps (256 MiB write, outside events)",
+            "parallelism": "replicas" if world > 1 else "1 GPU"}
+
+
+def aggregate_time(total_ms, world, device=None):
+    """Timed-region milliseconds of the whole job: the maximum over ranks
+    (every rank runs its own replica; the slowest one sets the job time)."""
+    if world <= 1:
+        return total_ms
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, total_ms):
+    """Whole-job throughput: the steps of all ranks over the job time."""
+    return world * steps / (total_ms / 1000.0)
+
+
 def oracle_run(p, frames, budget_s):
     """Run the FP64 CPU oracle for up to `frames` frames or `budget_s` seconds.
     Returns (frames done, seconds, positions per frame)."""
@@ -164,7 +194,7 @@ def run_reference(args, world, rank):
             "n_gpus": world, "steps": steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * el / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload},
+            "config": workload_config(args, p, world),
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"frames {args.warmup + 1}..{args.warmup + steps} of "
                                        f"{args.workload} (FP64 NumPy oracle, implicit Euler)"},
@@ -262,12 +292,9 @@ def run_ours(args, world, rank, local):
     total_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
     prof_timed = ctx.get_profile()
     launches = sum(v[0] for v in prof_timed.values())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = aggregate_time(total_ms, world, dev)
     ms_per_step = total_ms / K
-    value = world * K / (total_ms / 1000.0)
+    value = job_value(world, K, total_ms)
 
     # kernel durations: the first frames of the timed region replayed from the
     # same state with CUDA events around every kernel class (host-driven loop)
@@ -333,27 +360,31 @@ def run_ours(args, world, rank, local):
                "kind": "oracle",
                "sample": f"frames 1..{done} of {args.workload} from rest "
                          f"(FP64 NumPy oracle, {secs:.1f} s)"}
-        f = min(done, W)
-        if f >= 1:
+        # GPU positions of every frame the oracle reached: the warm-up frames,
+        # then a replay of the timed frames from the snapshot (untimed)
+        gq = dict(warm_q)
+        last = min(done, W + K)
+        if last > W:
+            ctx.set_state(*snap)
+            for k in range(W + 1, last + 1):
+                do_step(k, z_dev)
+                gq[k] = ctx.get_positions()
+        errs = {}
+        for f in range(1, last + 1):
             uo = qs[f - 1] - p.X0.ravel()
-            ug = warm_q[f] - p.X0.ravel()
-            err = {"frame": f, "rel_displacement_error": float(
-                np.linalg.norm(ug - uo) / max(np.linalg.norm(uo), 1e-300))}
+            errs[f] = float(np.linalg.norm(gq[f] - p.X0.ravel() - uo) /
+                            max(np.linalg.norm(uo), 1e-300))
+        if errs:
+            fmax = max(errs, key=errs.get)
+            err = {"frames": f"1..{last}", "max_rel_displacement_error": errs[fmax],
+                   "at_frame": fmax, "last_frame_error": errs[last]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
                 "steps": K, "warmup": W, "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.precision], "data": "synthetic",
-                "config": {"workload": args.workload,
-                           "mesh": f"{c.dims[0]}x{c.dims[1]}x{c.dims[2]} nodes, {p.ne} tets, "
-                                   f"n={p.n}",
-                           "r": c.r, "decoder": "-".join(map(str, p.widths)),
-                           "cubature": len(p.cub_idx), "dt": c.dt, "tol_inf": c.eps,
-                           "precision": args.precision + " (FP64 Cholesky + line search)",
-                           "frames": f"{W + 1}..{W + K}",
-                           "l2": "flushed between steps (256 MiB write, outside events)",
-                           "parallelism": "replicas" if world > 1 else "1 GPU"},
+                "config": workload_config(args, p, world),
                 "newton_iters_per_step": iters / K, "ls_trials_per_step": trials / K,
                 "newton_iters_per_s": iters / (total_ms / 1000.0),
                 "exits": {str(k): v for k, v in sorted(exits.items())},

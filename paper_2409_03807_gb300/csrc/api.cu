@@ -330,8 +330,11 @@ struct Engine : EngineBase {
     // FP64: the plain Armijo test of the paper's line search.  Lower
     // precisions accept a step whose energy rise stays within the rounding
     // scale of the energy evaluation, so the solve can reach their floor.
-    h.eta_scale = c->precision == LSN_PREC_FP64 ? 0.0 : 8.0 * unit;
-    h.floor_scale = 64.0 * unit;
+    // (TF32: the unit itself is coarse, so the slack and the floor stay within
+    // two units of the energy / gradient scale)
+    const bool tf32 = c->precision == LSN_PREC_TF32;
+    h.eta_scale = c->precision == LSN_PREC_FP64 ? 0.0 : (tf32 ? 2.0 : 8.0) * unit;
+    h.floor_scale = (tf32 ? 2.0 : 64.0) * unit;
     h.r = r;
     h.max_ls = c->max_ls;
     h.max_newton = c->max_newton;
