@@ -117,6 +117,24 @@ def dist_setup():
     return world, rank, local
 
 
+def measured_traffic(cls, workload, precision):
+    """DRAM bytes per launch from the ncu capture recorded in
+    profiles/traffic.json, or None when there is none or the kernel's source
+    has changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    ent = json.load(open(path)).get(f"{cls}|{workload}|{precision}")
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    if not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return ent["bytes"] if sha == ent["sha256_16"] else None
+
+
 def workload_config(args, p, world):
     """The `config` object of the JSON line (both arms)."""
     c = p.config
@@ -345,7 +363,8 @@ def run_ours(args, world, rank, local):
     achieved = ab / (avg_ms / 1000.0) / 1e9 if ab and avg_ms > 0 else None
     roofline = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak,
                 "peak_source": peak_src, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None,
+                "traffic": measured_traffic(dominant, args.workload, args.precision),
                 "avg_launch_us": avg_ms * 1000.0, "launches": launches_dom,
                 "algorithmic_bytes_per_launch": ab,
                 "share_of_kernel_time": ms_dom / replay_ms if replay_ms > 0 else None,
