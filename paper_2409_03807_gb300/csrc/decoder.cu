@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 
 #include "lsn_internal.cuh"
+#include "pdl.cuh"
 
 #include <algorithm>
 
@@ -199,6 +200,7 @@ __global__ void __launch_bounds__(KP * HBM) hidden_kernel(const Real* __restrict
   Real* Zs = Ws + HBM * w_stride<Real>();
   const int t = threadIdx.x, q = t % KP, row = t / KP;
   const int m0 = blockIdx.x * HBM, m = m0 + row;
+  pdl_wait();
   const Real bm = m < M ? b[m] : Real(0);
   Real acc[4 * CQ];
   skinny_gemm<Real, CQ, HBM>(W, M, K, Zin, CPs, m0, Ws, Zs, acc);
@@ -438,8 +440,8 @@ void run_hidden(const Real* W, const Real* b, int M, int K, const Real* Zin, int
                          (int)sm);
     set = sm;
   }
-  hidden_kernel<Real, CQ><<<(M + HBM - 1) / HBM, KP * HBM, sm, s>>>(W, b, M, K, Zin, C, CPs,
-                                                                    nj, Zout, Bh, Bl, bkind);
+  launch_pdl(hidden_kernel<Real, CQ>, dim3((M + HBM - 1) / HBM), dim3(KP * HBM), sm, s, W, b,
+             M, K, Zin, C, CPs, nj, Zout, Bh, Bl, bkind);
 }
 
 template <typename Real, int CQ>

@@ -42,6 +42,7 @@
 #include <cuda_bf16.h>
 
 #include "lsn_internal.cuh"
+#include "pdl.cuh"
 #include "tc_ptx.cuh"
 
 #include <algorithm>
@@ -836,6 +837,7 @@ __global__ void __launch_bounds__(NT, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tbase_s;
+  pdl_wait();  // u, J and the trial displacements come from the output layer
   // energies and gradient partials in double-float (FP32 TwoSum) accumulators
   FAcc eacc, eabs, etr[KTRIAL], atr[KTRIAL], gacc, gabs;
   // TT <= ET tets per tile (small cubature sets use small tiles, more CTAs)
@@ -1089,8 +1091,8 @@ cudaError_t launch_element_tc(const ElemArgs& ea, const float* u, const float* J
       if (e != cudaSuccess) return e;
       set_bf = sm;
     }
-    tcel::element_tc_kernel<true><<<grid, tcel::NT, sm, s>>>(
-        ea, u, J, ut, part, nslots_total(ea.r), element_tc_tile(ea.S, num_sms_cached()), err);
+    return launch_pdl(tcel::element_tc_kernel<true>, dim3(grid), dim3(tcel::NT), sm, s, ea, u, J,
+                      ut, part, nslots_total(ea.r), element_tc_tile(ea.S, num_sms_cached()), err);
   } else {
     const size_t sm = tcel::smem_bytes<false>(ea.r);
     if (sm > set_tf) {
@@ -1099,8 +1101,9 @@ cudaError_t launch_element_tc(const ElemArgs& ea, const float* u, const float* J
       if (e != cudaSuccess) return e;
       set_tf = sm;
     }
-    tcel::element_tc_kernel<false><<<grid, tcel::NT, sm, s>>>(
-        ea, u, J, ut, part, nslots_total(ea.r), element_tc_tile(ea.S, num_sms_cached()), err);
+    return launch_pdl(tcel::element_tc_kernel<false>, dim3(grid), dim3(tcel::NT), sm, s, ea, u,
+                      J, ut, part, nslots_total(ea.r), element_tc_tile(ea.S, num_sms_cached()),
+                      err);
   }
   return cudaGetLastError();
 }

@@ -15,6 +15,7 @@
 // after every pass, decides, and writes the points of the next pass.
 // Single-block kernels; r <= 64.
 #include "lsn_internal.cuh"
+#include "pdl.cuh"
 
 #include <cstddef>
 
@@ -34,6 +35,7 @@ __global__ void reduce_partials_kernel(const double* __restrict__ A, int rowsA,
                                        const double* __restrict__ B, int rowsB, int splitB,
                                        int split, int ncols, double* __restrict__ out) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  pdl_wait();
   if (warp >= ncols) return;
   const int c = warp;
   double s = 0.0;
@@ -177,6 +179,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_direction_kernel(
   __shared__ double s_base;
   DevSolver* sv = &svs;
   const int t = threadIdx.x;
+  pdl_wait();
   // ---- parallel load of the state (scalars, z, d) and of E, g, gabs, trials
   {
     const double* src = reinterpret_cast<const double*>(gsv);
@@ -422,8 +425,8 @@ __global__ void begin_step_kernel(const double* __restrict__ X0,
 void launch_reduce_partials(const double* A, int rowsA, const double* B, int rowsB,
                             int splitB, int split, int ncols, double* out, cudaStream_t s) {
   const int threads = 256, warps = threads / 32;
-  reduce_partials_kernel<<<(ncols + warps - 1) / warps, threads, 0, s>>>(
-      A, rowsA, B, rowsB, splitB, split, ncols, out);
+  launch_pdl(reduce_partials_kernel, dim3((ncols + warps - 1) / warps), dim3(threads), 0, s, A,
+             rowsA, B, rowsB, splitB, split, ncols, out);
 }
 
 template <typename Real>
@@ -434,7 +437,8 @@ void launch_solve_begin(DevSolver* sv, Real* Z0, int C, int eval_only, cudaStrea
 template <typename Real>
 void launch_select_direction(DevSolver* sv, const double* sys, Real* Z0,
                              unsigned long long cond, int use_cond, cudaStream_t s) {
-  select_direction_kernel<Real><<<1, SEL_THREADS, 0, s>>>(sv, sys, Z0, cond, use_cond);
+  launch_pdl(select_direction_kernel<Real>, dim3(1), dim3(SEL_THREADS), 0, s, sv, sys, Z0, cond,
+             use_cond);
 }
 
 template <typename Real>

@@ -30,6 +30,7 @@
 #include <cstring>
 
 #include "lsn_internal.cuh"
+#include "pdl.cuh"
 #include "tc_ptx.cuh"
 #include "tc_internal.cuh"
 
@@ -196,6 +197,7 @@ __global__ void __launch_bounds__(TNT, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tbase_s;
+  pdl_wait();  // the packed columns and the row data come from earlier kernels
 
   if (warp == 0) {
     // ------------------------------------------------ TMA producer
@@ -594,12 +596,12 @@ void TcLast::launch(const float* Z, int CPs, const float* bias, int nj, float* u
   const int n = Cp * H;
   if (bf16) {
     if (!packed) pack_kernel<true><<<(n + 255) / 256, 256, 0, s>>>(Z, H, C, CPs, Cp, Bh, Bl);
-    tc_last_kernel<true><<<grid, TNT, smem, s>>>(mapW, mapBh, mapBl, bias, M, H, C, Cp, nj, u,
-                                                 J, ut, part, part_stride, la, err);
+    launch_pdl(tc_last_kernel<true>, dim3(grid), dim3(TNT), smem, s, mapW, mapBh, mapBl, bias, M,
+               H, C, Cp, nj, u, J, ut, part, part_stride, la, err);
   } else {
     if (!packed) pack_kernel<false><<<(n + 255) / 256, 256, 0, s>>>(Z, H, C, CPs, Cp, Bh, nullptr);
-    tc_last_kernel<false><<<grid, TNT, smem, s>>>(mapW, mapBh, mapBl, bias, M, H, C, Cp, nj,
-                                                  u, J, ut, part, part_stride, la, err);
+    launch_pdl(tc_last_kernel<false>, dim3(grid), dim3(TNT), smem, s, mapW, mapBh, mapBl, bias,
+               M, H, C, Cp, nj, u, J, ut, part, part_stride, la, err);
   }
 }
 
