@@ -236,7 +236,9 @@ struct Engine : EngineBase {
   LastArgs la;
   ElemArgs ea;
   TcLast tcl;          // tensor-core output layer (TF32 / BF16 forms)
-  bool use_tc = false;
+  bool use_tc = false;       // TF32 / BF16 form: tensor-core element contraction
+  bool use_tc_last = false;  // ... and tensor-core output layer (hidden width allows TMA)
+  int* tc_err = nullptr;     // device flag: a bounded wait of a tensor-core kernel ran out
 
   explicit Engine(lsn_ctx* ctx) : c(ctx) {
     cudaStream_t s = c->stream;
@@ -281,9 +283,22 @@ struct Engine : EngineBase {
     use_tc = sizeof(Real) == 4 &&
              (c->precision == LSN_PREC_TF32 || c->precision == LSN_PREC_BF16);
     if (use_tc) {
-      ck(tcl.setup(reinterpret_cast<const float*>(dW[L - 1]), n, c->widths[L - 1], C, r,
-                   c->precision == LSN_PREC_BF16, c->num_sms, s));
-      grid_dec = tcl.grid;
+      tc_err = dalloc<int>(1);
+      ck(cudaMemsetAsync(tc_err, 0, sizeof(int), s));
+      // the TMA row pitch (hidden width x element size) must be a multiple of
+      // 16 bytes; otherwise the FP32 CUDA-core output layer serves this form
+      const cudaError_t te = tcl.setup(reinterpret_cast<const float*>(dW[L - 1]), n,
+                                       c->widths[L - 1], C, r,
+                                       c->precision == LSN_PREC_BF16, c->num_sms, s);
+      if (te == cudaSuccess) {
+        use_tc_last = true;
+        grid_dec = tcl.grid;
+      } else if (te == cudaErrorInvalidValue) {
+        cudaGetLastError();
+        tcl.release();
+      } else {
+        ck(te);
+      }
     }
     element_grids(S, r, c->num_sms, gfull, genergy);
     if (use_tc) {  // one complete partial row per CTA (trial energies included)
@@ -361,6 +376,7 @@ struct Engine : EngineBase {
     dfree(cwv);
     dfree(part_dec);
     dfree(part_el);
+    dfree(tc_err);
     dfree(sys);
     dfree(sv);
   }
@@ -382,7 +398,7 @@ struct Engine : EngineBase {
     for (int l = 0; l < L - 1; ++l) {
       const int M = c->widths[l + 1], K = c->widths[l];
       // the last hidden layer also writes the tensor-core output layer's operand
-      const bool pack = use_tc && l == L - 2;
+      const bool pack = use_tc_last && l == L - 2;
       launch_hidden_layer<Real>(dW[l], db[l], M, K, in, C, nj, Z[cur], s,
                                 pack ? tcl.Bh : nullptr, pack ? tcl.Bl : nullptr,
                                 pack ? tcl.bkind() : 0);
@@ -398,7 +414,7 @@ struct Engine : EngineBase {
     Profiler& P = c->prof;
     const Real* h = hidden(s, prof);
     if (prof) P.begin(LSN_K_DECODER_LAST);
-    if (use_tc)
+    if (use_tc_last)
       tcl.launch(reinterpret_cast<const float*>(h), zstride(C),
                  reinterpret_cast<const float*>(db[L - 1]), nj, reinterpret_cast<float*>(u),
                  reinterpret_cast<float*>(J), reinterpret_cast<float*>(ut), part_dec, nst, la,
@@ -411,7 +427,7 @@ struct Engine : EngineBase {
     if (use_tc)
       ck(launch_element_tc(ea, reinterpret_cast<const float*>(u),
                            reinterpret_cast<const float*>(J), reinterpret_cast<const float*>(ut),
-                           part_el, gfull, c->precision == LSN_PREC_BF16, tcl.err, s));
+                           part_el, gfull, c->precision == LSN_PREC_BF16, tc_err, s));
     else
       launch_element<Real>(ea, u, J, ut, part_el, gfull, genergy, s);
     if (prof) P.end(LSN_K_ELEMENT);
@@ -424,10 +440,11 @@ struct Engine : EngineBase {
 
   int device_error(cudaStream_t s) override {
     if (!use_tc) return 0;
-    int h = 0;
-    ck(cudaMemcpyAsync(&h, tcl.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int h[2] = {0, 0};
+    ck(cudaMemcpyAsync(&h[0], tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (use_tc_last) ck(cudaMemcpyAsync(&h[1], tcl.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     ck(cudaStreamSynchronize(s));
-    return h;
+    return h[0] | h[1];
   }
 
   void finish(double dt) override {

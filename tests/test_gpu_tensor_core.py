@@ -123,3 +123,62 @@ def test_tc_dynamics_trajectory(pkg, prec):
         err = rel(ctx.get_positions() - p.X0.ravel(), sim.q - p.X0.ravel())
         assert err < (1e-3 if prec == "bf16" else 3e-3), (k, err)
     ctx.close()
+
+
+def _ctx_and_oracle(pkg, mesh, widths, prec, cub=None, cn=None, round_last=True):
+    from oracle.decoder import Decoder
+    from oracle.reduced import ReducedModel
+    from workloads import xavier_decoder
+    Ws, bs = xavier_decoder(widths, 0)
+    ctx = pkg.Context()
+    ctx.set_mesh(mesh.X0, mesh.tets)
+    ctx.set_material(1e5, 0.45, 1000.0, (0.0, 0.0, -9.8))
+    if cub is not None:
+        ctx.set_cubature(*cub)
+    if cn is not None:
+        ctx.set_constraints(cn, mesh.X0[cn])
+    ctx.set_decoder(Ws, bs, 1e-2, prec)
+    Wo = [*Ws[:-1], round_bf16(Ws[-1])] if (prec == "bf16" and round_last) else Ws
+    m = ReducedModel(mesh.X0, mesh.tets, Decoder(Wo, bs, 1e-2), 1e5, 0.45, 1000.0,
+                     (0.0, 0.0, -9.8), None if cub is None else cub[0],
+                     None if cub is None else cub[1], cn)
+    return ctx, m
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_tc_single_tet_and_r1(pkg, prec):
+    """One tet, one constrained vertex, r = 1 (N padded to 16 in the MMAs)."""
+    X0 = np.array([[0, 0, 0], [0.1, 0, 0], [0, 0.1, 0], [0, 0, 0.1]], float)
+    mesh = type("M", (), {"X0": X0, "tets": np.array([[0, 1, 2, 3]], np.int32)})
+    ctx, m = _ctx_and_oracle(pkg, mesh, [1, 8, 12], prec, cn=np.array([0], np.int32))
+    t = TOL[prec]
+    for z in (np.array([0.8]), np.array([-1.3])):
+        E, g, K = ctx.eval(z)
+        E0, g0, K0 = m.eval(z)
+        assert abs(E - E0) <= t["E"] * max(1.0, abs(E0))
+        assert rel(g, g0) < t["g"] and rel(K, K0) < t["K"], (rel(g, g0), rel(K, K0))
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_tc_ragged_tiles_and_fp32_output_layer_fallback(pkg, prec):
+    """Hidden width 13 (TMA row pitch not a multiple of 16 bytes): the output
+    layer runs on the FP32 CUDA-core kernel with the FP32 weights, the element
+    contraction on the tensor cores; one cubature tet and a ragged half set."""
+    from workloads import make_bar
+    mesh = make_bar(5, 4, 3, 0.05)
+    for cub in [(np.array([7], np.int32), np.array([3.5])),
+                (np.arange(0, mesh.ne, 2, dtype=np.int32), np.full((mesh.ne + 1) // 2, 2.0))]:
+        ctx, m = _ctx_and_oracle(pkg, mesh, [7, 13, 3 * mesh.nv], prec, cub=cub,
+                                 round_last=False)
+        m.set_dynamics(0.02, mesh.X0.ravel() + 1e-3)
+        ctx.set_dynamics(0.02, mesh.X0.ravel() + 1e-3)
+        z = np.random.default_rng(3).standard_normal(7)
+        x, J = ctx.decode(z)
+        x0, J0 = m.positions_jac(z)
+        assert rel(J, J0) < 1e-5  # FP32 output layer
+        E, g, K = ctx.eval(z)
+        E0, g0, K0 = m.eval(z)
+        assert abs(E - E0) <= 1e-4 * max(1.0, abs(E0))
+        assert rel(g, g0) < 2e-3 and rel(K, K0) < TOL[prec]["K"], (rel(g, g0), rel(K, K0))
+        ctx.close()
