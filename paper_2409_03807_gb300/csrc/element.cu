@@ -895,6 +895,15 @@ __global__ void __launch_bounds__(NT, 1)
         const int slot = t >> 3, c8 = t & 7;
         const int lt = slot % C::CH, cb0 = slot / C::CH;
         const bool live_t = lt < nb;
+        // byte offsets of the tet's nine operand entries (K = 9 lt + m) within
+        // a column row: the swizzle XOR uses c & 7 = c8, fixed for the thread
+        uint32_t koff[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+          const int k = lt * 9 + m, kb = k / C::EPB, kin = k - kb * C::EPB;
+          koff[m] = BF ? kb * KBB + ((((uint32_t)kin >> 3) ^ (uint32_t)c8) << 4) + (kin & 7) * 2
+                       : kb * KBB + ((((uint32_t)kin >> 2) ^ (uint32_t)c8) << 4) + (kin & 3) * 4;
+        }
         TetData<float> td;
         int vv[4] = {0, 0, 0, 0};
         if (live_t) {
@@ -921,15 +930,13 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
             for (int m = 0; m < 9; ++m) Cv[m] = 0.f;
           }
+          uint8_t* orow = op + (uint32_t)c * 128u;  // operand row c (128-byte rows)
 #pragma unroll
           for (int m = 0; m < 9; ++m) {
-            const int k = lt * 9 + m, kb = k / C::EPB, kin = k - kb * C::EPB;
             if (BF)
-              *reinterpret_cast<__nv_bfloat16*>(op + kb * KBB + sw128_offset(c, kin >> 3) +
-                                                (kin & 7) * 2) = __float2bfloat16_rn(Cv[m]);
+              *reinterpret_cast<__nv_bfloat16*>(orow + koff[m]) = __float2bfloat16_rn(Cv[m]);
             else
-              *reinterpret_cast<float*>(op + kb * KBB + sw128_offset(c, kin >> 2) +
-                                        (kin & 3) * 4) = Cv[m];
+              *reinterpret_cast<float*>(orow + koff[m]) = Cv[m];
           }
           Gp[lt * r + c] = gp;
         }
