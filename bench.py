@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="time budget of the CPU-oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--train", action="store_true",
+                    help="time decoder training steps (lsn_train_step) instead of the solve")
     ap.add_argument("--replay", type=int, default=10,
                     help="timed frames replayed with per-kernel CUDA events")
     return ap.parse_args()
@@ -176,6 +178,9 @@ def oracle_run(p, frames, budget_s):
     t0 = time.perf_counter()
     done = 0
     for k in range(1, frames + 1):
+        if not (c.dt > 0):  # quasi-static: every solve from the rest state
+            sim = ReducedSimulator(model_from_problem(p), c.dt, eps=c.eps,
+                                   max_newton=c.max_newton, max_ls=c.max_ls, c=c.armijo_c)
         sim.step(p.targets(k))
         qs.append(sim.q.copy())
         done = k
@@ -201,6 +206,9 @@ def run_reference(args, world, rank):
     t1 = time.perf_counter()
     steps = 0
     for k in range(args.warmup + 1, args.warmup + args.steps + 1):
+        if not (c.dt > 0):  # quasi-static: every solve from the rest state
+            sim = ReducedSimulator(model_from_problem(p), c.dt, eps=c.eps,
+                                   max_newton=c.max_newton, max_ls=c.max_ls, c=c.armijo_c)
         sim.step(p.targets(k))
         steps += 1
         if time.perf_counter() - t1 > budget:
@@ -273,6 +281,15 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
 
+    # quasi-static workloads: every step is a solve from the rest state z = 0
+    # (the state is restored before the step, outside the timed events)
+    quasi_static = not (c.dt > 0)
+    rest = ctx.get_state()
+
+    def restart():
+        if quasi_static:
+            ctx.set_state(*rest)
+
     def do_step(k, z_out):
         ctx.set_constraints(None, targets[k - 1])
         return ctx.step(dt=c.dt, z_out=z_out)
@@ -280,6 +297,7 @@ def run_ours(args, world, rank, local):
     # warm-up frames 1..W
     warm_q = {}
     for k in range(1, W + 1):
+        restart()
         do_step(k, z_dev)
         warm_q[k] = ctx.get_positions()
     snap = ctx.get_state()
@@ -296,6 +314,7 @@ def run_ours(args, world, rank, local):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     for i, k in enumerate(range(W + 1, W + K + 1)):
+        restart()
         with torch.cuda.stream(stream):
             flush.fill_(float(i))
             ev0[i].record(stream)
@@ -322,6 +341,7 @@ def run_ours(args, world, rank, local):
     ctx.reset_profile()
     torch.cuda.synchronize()
     for i, k in enumerate(range(W + 1, W + KR + 1)):
+        restart()
         with torch.cuda.stream(stream):
             flush.fill_(float(i))
         do_step(k, z_dev)
@@ -341,6 +361,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(W + 1, W + K + 1):
+        restart()
         ctx.set_constraints(None, pin_t[k - 1])
         ctx.step(dt=c.dt, z_out=z_host)
         ctx.get_positions(q_host)
@@ -390,6 +411,7 @@ def run_ours(args, world, rank, local):
         if last > W:
             ctx.set_state(*snap)
             for k in range(W + 1, last + 1):
+                restart()
                 do_step(k, z_dev)
                 gq[k] = ctx.get_positions()
         errs = {}
@@ -422,9 +444,67 @@ def run_ours(args, world, rank, local):
         torch.distributed.destroy_process_group()
 
 
+def run_train(args, world, rank, local):
+    """Decoder-training throughput: Adam steps of L = L_C + 1e-3 L_LS on a
+    batch of 64 seeded smooth displacement fields (twist and bend along the
+    bar), 512 cubature tets, FP32 trainer."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2409_03807_gb300.build import build
+    build()
+    import paper_2409_03807_gb300 as pkg
+    from workloads import build_problem, draw_cubature
+    name = args.workload if args.workload != WORKLOAD else "bar_train_44544"
+    p = build_problem(name)
+    c = p.config
+    rng = np.random.default_rng(2)
+    X = p.X0
+    L = X[:, 0].max()
+    Q = []
+    for _ in range(64):
+        tw, bd = rng.uniform(0, 0.3), rng.uniform(0, 0.05)
+        s = X[:, 0] / L
+        d = np.zeros_like(X)
+        yc, zc = X[:, 1] - X[:, 1].mean(), X[:, 2] - X[:, 2].mean()
+        d[:, 1] = (np.cos(tw * s) - 1) * yc - np.sin(tw * s) * zc
+        d[:, 2] = np.sin(tw * s) * yc + (np.cos(tw * s) - 1) * zc - bd * s * s * L
+        Q.append((X + d).ravel())
+    Q = torch.tensor(np.array(Q), dtype=torch.float64, device="cuda")
+    S = c.cubature if c.cubature > 0 else 512
+    cub, w = draw_cubature(p.ne, S, c.cubature_seed)
+    ctx = pkg.Context()
+    ctx.set_mesh(p.X0, p.tets)
+    ctx.set_material(c.youngs, c.poisson, c.density, c.gravity)
+    ctx.set_decoder(p.Ws, p.bs, c.out_scale, "fp32")
+    r, n = c.r, p.n
+    ctx.train_init((rng.standard_normal((r, n)) / np.sqrt(n)).astype(np.float32),
+                   np.zeros(r, np.float32), cub, w)
+    for _ in range(args.warmup):
+        ctx.train_step(Q, 1e-3, 1e-4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        losses = ctx.train_step(Q, 1e-3, 1e-4)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    ctx.close()
+    if rank == 0:
+        print(json.dumps({"metric": "decoder training steps/s (batch 64, L_C + L_LS, Adam)",
+                          "value": args.steps / el, "unit": "steps/s", "n_gpus": 1,
+                          "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True,
+                          "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": name, "n": p.n, "decoder": "-".join(
+                              map(str, p.widths)), "cubature": S, "batch": 64},
+                          "last_losses": list(losses)}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
+    if args.train:
+        run_train(args, world, rank, local)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
