@@ -65,13 +65,27 @@ enum lsn_status {
 
 /* Arithmetic of the decoder, Jacobian and J_e^T H_e J_e contraction.  The
  * r x r Cholesky and the line-search energy comparison are FP64 in every
- * mode; energies, gradients and partial sums are accumulated in FP64. */
+ * mode; energies, gradients and partial sums are accumulated in FP64 (or, in
+ * the tensor-core kernels, in double-float FP32 pairs summed in FP64).
+ *
+ * Tensor-core forms (tcgen05, FP32 accumulation in TMEM): the decoder output
+ * layer + Jacobian, the inertia Hessian J^T M J / dt^2 and the element
+ * contraction sum_e w_e J_e^T Hproj_e J_e.  Hidden layers, per-element
+ * energies, stresses, PSD projection and the gradient stay FP32.
+ *   TF32: W_L and the hidden activations rounded to TF32; Gram operands TF32.
+ *   BF16: W_L stored in BF16 (rounded once, at lsn_set_decoder time), the
+ *         activations entered as a two-term BF16 split (so only W_L is
+ *         rounded), Gram operands BF16.  The rounding of W_L changes the model
+ *         by about 1e-3 relative; the form agrees with the FP64 evaluation of
+ *         its own BF16 weights to FP32 accuracy.
+ * The tensor-core output layer needs the last hidden width times the element
+ * size (2 / 4 bytes) to be a multiple of 16 bytes; otherwise the FP32
+ * CUDA-core output layer is used with the FP32 weights. */
 enum lsn_precision {
   LSN_PREC_FP64 = 0, /* everything in FP64                                 */
   LSN_PREC_FP32 = 1, /* plain FP32 on CUDA cores                           */
-  LSN_PREC_TF32 = 2, /* decoder last layer + contraction on tensor cores,
-                        TF32 inputs, FP32 accumulation; rest FP32            */
-  LSN_PREC_BF16 = 3  /* as TF32 with BF16 inputs                           */
+  LSN_PREC_TF32 = 2, /* tensor-core form, TF32 operands (see above)        */
+  LSN_PREC_BF16 = 3  /* tensor-core form, BF16 weights (see above)         */
 };
 
 typedef struct {
