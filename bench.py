@@ -447,7 +447,8 @@ def run_ours(args, world, rank, local):
 def run_train(args, world, rank, local):
     """Decoder-training throughput: Adam steps of L = L_C + 1e-3 L_LS on a
     batch of 64 seeded smooth displacement fields (twist and bend along the
-    bar), 512 cubature tets, FP32 trainer."""
+    bar), 512 cubature tets; the trainer follows --precision (FP64, FP32, or
+    FP32 with TF32 tensor-core matrix products for the tensor-core forms)."""
     import torch
     torch.cuda.set_device(local)
     from paper_2409_03807_gb300.build import build
@@ -475,7 +476,8 @@ def run_train(args, world, rank, local):
     ctx = pkg.Context()
     ctx.set_mesh(p.X0, p.tets)
     ctx.set_material(c.youngs, c.poisson, c.density, c.gravity)
-    ctx.set_decoder(p.Ws, p.bs, c.out_scale, "fp32")
+    # tensor-core forms train with TF32 tensor-core matrix products
+    ctx.set_decoder(p.Ws, p.bs, c.out_scale, args.precision)
     r, n = c.r, p.n
     ctx.train_init((rng.standard_normal((r, n)) / np.sqrt(n)).astype(np.float32),
                    np.zeros(r, np.float32), cub, w)
@@ -493,7 +495,9 @@ def run_train(args, world, rank, local):
                           "value": args.steps / el, "unit": "steps/s", "n_gpus": 1,
                           "steps": args.steps, "warmup": args.warmup,
                           "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True,
-                          "dtype": "f32", "data": "synthetic",
+                          "dtype": {"fp64": "f64", "fp32": "f32"}.get(args.precision,
+                                                                      "tf32"),
+                          "data": "synthetic",
                           "config": {"workload": name, "n": p.n, "decoder": "-".join(
                               map(str, p.widths)), "cubature": S, "batch": 64},
                           "last_losses": list(losses)}), flush=True)

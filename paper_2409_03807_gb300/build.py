@@ -56,7 +56,7 @@ def build(verbose=False, jobs=None):
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
         return LIB
-    cmd = [_nvcc(), *ARCH, "-shared", "--cudart=static", "-o", LIB, *objs]
+    cmd = [_nvcc(), *ARCH, "-shared", "--cudart=static", "-o", LIB, *objs, "-lcublas"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

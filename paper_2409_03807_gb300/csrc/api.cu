@@ -1226,7 +1226,11 @@ int lsn_train_init(lsn_ctx* c, const float* enc_W, const float* enc_b, const int
     ts.inc.insert(ts.inc.end(), lists[v].begin(), lists[v].end());
   }
   // initial parameters: encoder, then the context's decoder
-  std::unique_ptr<TrainerBase> tr(TrainerBase::create(c->precision == LSN_PREC_FP64, ts));
+  // the tensor-core forms train with TF32 tensor-core matrix products
+  const int tmode = c->precision == LSN_PREC_FP64 ? 1
+                    : (c->precision == LSN_PREC_TF32 || c->precision == LSN_PREC_BF16) ? 2
+                                                                                      : 0;
+  std::unique_ptr<TrainerBase> tr(TrainerBase::create(tmode, ts));
   std::vector<double> theta(tr->nparams);
   std::copy(enc_W, enc_W + (size_t)r * c->n, theta.begin() + tr->off[0]);
   std::copy(enc_b, enc_b + r, theta.begin() + tr->off[1]);

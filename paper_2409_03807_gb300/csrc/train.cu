@@ -25,6 +25,7 @@
 // of the element Hessian, evaluated with forward-mode dual numbers.
 //
 // Matrices are row-major; one sample's columns are contiguous.
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -738,6 +739,30 @@ __global__ void x0_rows_kernel(const double* __restrict__ X0, const int* __restr
 template <typename Real>
 struct Trainer : TrainerBase {
   TrainSetup ts;
+  // TF32 tensor-core GEMMs (cuBLAS) for the plain matrix products of the
+  // forward and backward passes; otherwise the CUDA-core kernel above
+  bool tf32 = false;
+  cublasHandle_t blas = nullptr;
+
+  // C[m][n] = alpha sum_k A(m,k) B(k,n) + beta C[m][n] with the strides of
+  // gemm(); as column-major, C^T (N x M, ld ldc) = op(B) op(A)
+  void mm(cudaStream_t s, int M, int N, int K, Real alpha, const Real* A, long long sam,
+          long long sak, const Real* B, long long sbk, long long sbn, Real beta, Real* C,
+          long long ldc) {
+    if (!tf32 || M <= 0 || N <= 0 || K <= 0 || sizeof(Real) != 4) {
+      gemm<Real>(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, ldc);
+      return;
+    }
+    const cublasOperation_t opB = sbn == 1 ? CUBLAS_OP_N : CUBLAS_OP_T;
+    const cublasOperation_t opA = sak == 1 ? CUBLAS_OP_N : CUBLAS_OP_T;
+    const int ldb = (int)(sbn == 1 ? sbk : sbn), lda = (int)(sak == 1 ? sam : sak);
+    const float a = (float)alpha, b = (float)beta;
+    if (cublasSetStream(blas, s) != CUBLAS_STATUS_SUCCESS ||
+        cublasGemmEx(blas, opB, opA, N, M, K, &a, B, CUDA_R_32F, ldb, A, CUDA_R_32F, lda, &b, C,
+                     CUDA_R_32F, (int)ldc, CUBLAS_COMPUTE_32F_FAST_TF32,
+                     CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+      throw CudaFail{cudaErrorUnknown};
+  }
   std::vector<void*> sbufs, bbufs;   // static / per-batch allocations
   Real *theta = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr;
   long long step = 0;
@@ -782,9 +807,11 @@ struct Trainer : TrainerBase {
   ~Trainer() override {
     for (void* p : bbufs) cudaFree(p);
     for (void* p : sbufs) cudaFree(p);
+    if (blas) cublasDestroy(blas);
   }
 
   void init_device(const double* theta_host) override {
+    if (tf32 && cublasCreate(&blas) != CUBLAS_STATUS_SUCCESS) throw CudaFail{cudaErrorUnknown};
     theta = alloc<Real>(sbufs, nparams);
     grad = alloc<Real>(sbufs, nparams);
     am = alloc<Real>(sbufs, nparams);
@@ -902,7 +929,7 @@ struct Trainer : TrainerBase {
     so_init_kernel<Real><<<blocks(r * NC), 256, 0, s>>>(Z, r, B, Cs, Y[0]);
     for (int l = 0; l + 1 < L; ++l) {
       const int M = ts.widths[l + 1], K = ts.widths[l];
-      gemm<Real>(s, M, (int)NC, K, Real(1), theta + off[2 + 2 * l], K, 1, Y[l], NC, 1, Real(0),
+      mm(s, M, (int)NC, K, Real(1), theta + off[2 + 2 * l], K, 1, Y[l], NC, 1, Real(0),
                  Zh[l], NC);
       so_act_kernel<Real><<<blocks((long long)M * B), 256, 0, s>>>(Zh[l], theta + off[3 + 2 * l],
                                                                    M, B, r, Cs, Y[l + 1]);
@@ -910,7 +937,7 @@ struct Trainer : TrainerBase {
     const int Hc = ts.widths[L - 1];
     gather_rows_kernel<Real><<<blocks((long long)ts.RS * Hc), 256, 0, s>>>(
         theta + off[2 + 2 * (L - 1)], theta + off[3 + 2 * (L - 1)], rows, ts.RS, Hc, WS, bS);
-    gemm<Real>(s, ts.RS, (int)NC, Hc, Real(1), WS, Hc, 1, Y[L - 1], NC, 1, Real(0), XS, NC);
+    mm(s, ts.RS, (int)NC, Hc, Real(1), WS, Hc, 1, Y[L - 1], NC, 1, Real(0), XS, NC);
     const long long warps = (long long)ts.S * B;
     elem_hess_kernel<Real><<<blocks(warps * 32, 128), 128, 0, s>>>(elem_ctx(B), contrib);
     sum_hess_kernel<Real><<<blocks((long long)B * P), 256, 0, s>>>(contrib, ts.S, B, P, Hs);
@@ -937,25 +964,25 @@ struct Trainer : TrainerBase {
     tck(cudaMemsetAsync(grad, 0, sizeof(Real) * nparams, s));
     // ---- reconstruction loss (Eq. 3) and its gradient
     snapshots_kernel<Real><<<blocks((long long)n * B), 256, 0, s>>>(q, ts.X0, n, B, D);
-    gemm<Real>(s, r, B, n, one, theta + off[0], n, 1, D, B, 1, zero, Z, B);
+    mm(s, r, B, n, one, theta + off[0], n, 1, D, B, 1, zero, Z, B);
     bias_add_kernel<Real><<<blocks((long long)r * B), 256, 0, s>>>(Z, theta + off[1], r, B);
     const Real* hin = Z;
     for (int l = 0; l + 1 < L; ++l) {
       const int M = ts.widths[l + 1], K = ts.widths[l];
-      gemm<Real>(s, M, B, K, one, theta + off[2 + 2 * l], K, 1, hin, B, 1, zero, A[l], B);
+      mm(s, M, B, K, one, theta + off[2 + 2 * l], K, 1, hin, B, 1, zero, A[l], B);
       bias_elu_kernel<Real><<<blocks((long long)M * B), 256, 0, s>>>(
           A[l], theta + off[3 + 2 * l], M, B, Hh[l]);
       hin = Hh[l];
     }
     const int Hc = ts.widths[L - 1];
-    gemm<Real>(s, n, B, Hc, one, theta + off[2 + 2 * (L - 1)], Hc, 1, hin, B, 1, zero, OUT, B);
+    mm(s, n, B, Hc, one, theta + off[2 + 2 * (L - 1)], Hc, 1, hin, B, 1, zero, OUT, B);
     const int rb = 256;
     recon_kernel<Real><<<rb, 256, 0, s>>>(OUT, theta + off[3 + 2 * (L - 1)], D, ts.mass, n, B,
                                           (Real)ts.scale, dOUT, rpart);
-    gemm<Real>(s, n, Hc, B, one, dOUT, B, 1, hin, 1, B, zero, grad + off[2 + 2 * (L - 1)], Hc);
+    mm(s, n, Hc, B, one, dOUT, B, 1, hin, 1, B, zero, grad + off[2 + 2 * (L - 1)], Hc);
     rowsum_kernel<Real><<<blocks(n), 256, 0, s>>>(dOUT, n, B, B, 1, 0, one,
                                                   grad + off[3 + 2 * (L - 1)], 0);
-    gemm<Real>(s, Hc, B, n, one, theta + off[2 + 2 * (L - 1)], 1, Hc, dOUT, B, 1, zero, dH, B);
+    mm(s, Hc, B, n, one, theta + off[2 + 2 * (L - 1)], 1, Hc, dOUT, B, 1, zero, dH, B);
     Real* dcur = dH;
     Real* dnext = dH2;
     for (int l = L - 2; l >= 0; --l) {
@@ -963,13 +990,13 @@ struct Trainer : TrainerBase {
       elu_back_kernel<Real><<<blocks((long long)M * B), 256, 0, s>>>(A[l], dcur,
                                                                      (long long)M * B);
       const Real* hprev = l == 0 ? Z : Hh[l - 1];
-      gemm<Real>(s, M, K, B, one, dcur, B, 1, hprev, 1, B, zero, grad + off[2 + 2 * l], K);
+      mm(s, M, K, B, one, dcur, B, 1, hprev, 1, B, zero, grad + off[2 + 2 * l], K);
       rowsum_kernel<Real><<<blocks(M), 256, 0, s>>>(dcur, M, B, B, 1, 0, one,
                                                     grad + off[3 + 2 * l], 0);
-      gemm<Real>(s, K, B, M, one, theta + off[2 + 2 * l], 1, K, dcur, B, 1, zero, dnext, B);
+      mm(s, K, B, M, one, theta + off[2 + 2 * l], 1, K, dcur, B, 1, zero, dnext, B);
       std::swap(dcur, dnext);
     }
-    gemm<Real>(s, r, n, B, one, dcur, B, 1, D, 1, B, zero, grad + off[0], n);
+    mm(s, r, n, B, one, dcur, B, 1, D, 1, B, zero, grad + off[0], n);
     rowsum_kernel<Real><<<blocks(r), 256, 0, s>>>(dcur, r, B, B, 1, 0, one, grad + off[1], 0);
     // ---- Lipschitz loss (Eq. 9) on the cubature Hessians
     double lls = 0.0;
@@ -983,22 +1010,22 @@ struct Trainer : TrainerBase {
                                                                       gk);
       row_adjoint_kernel<Real><<<blocks((long long)ts.RS * B, 128), 128, 0, s>>>(
           inc_ptr, inc, ts.RS, ts.S, B, r, P, Cs, (Real)ts.scale, gx, gJ, gk, Gbar, dXS);
-      gemm<Real>(s, ts.RS, Hc, (int)NC, one, dXS, NC, 1, Y[L - 1], 1, NC, zero, dWS, Hc);
+      mm(s, ts.RS, Hc, (int)NC, one, dXS, NC, 1, Y[L - 1], 1, NC, zero, dWS, Hc);
       rowsum_kernel<Real><<<blocks(ts.RS), 256, 0, s>>>(dXS, ts.RS, (int)NC, B, Cs, 0, one, dbS,
                                                         0);
       scatter_rows_kernel<Real><<<blocks((long long)ts.RS * Hc), 256, 0, s>>>(
           dWS, dbS, rows, ts.RS, Hc, lam, grad + off[2 + 2 * (L - 1)],
           grad + off[3 + 2 * (L - 1)]);
-      gemm<Real>(s, Hc, (int)NC, ts.RS, one, WS, 1, Hc, dXS, NC, 1, zero, dY, NC);
+      mm(s, Hc, (int)NC, ts.RS, one, WS, 1, Hc, dXS, NC, 1, zero, dY, NC);
       for (int l = L - 2; l >= 0; --l) {
         const int M = ts.widths[l + 1], K = ts.widths[l];
         so_act_back_kernel<Real><<<blocks((long long)M * B), 256, 0, s>>>(
             Zh[l], theta + off[3 + 2 * l], dY, M, B, r, Cs, dZh);
-        gemm<Real>(s, M, K, (int)NC, lam, dZh, NC, 1, Y[l], 1, NC, one, grad + off[2 + 2 * l], K);
+        mm(s, M, K, (int)NC, lam, dZh, NC, 1, Y[l], 1, NC, one, grad + off[2 + 2 * l], K);
         rowsum_kernel<Real><<<blocks(M), 256, 0, s>>>(dZh, M, (int)NC, B, Cs, 0, lam,
                                                       grad + off[3 + 2 * l], 1);
         if (l > 0)
-          gemm<Real>(s, K, (int)NC, M, one, theta + off[2 + 2 * l], 1, K, dZh, NC, 1, zero, dY,
+          mm(s, K, (int)NC, M, one, theta + off[2 + 2 * l], 1, K, dZh, NC, 1, zero, dY,
                      NC);
       }
       std::vector<double> lp(B);
@@ -1031,9 +1058,11 @@ struct Trainer : TrainerBase {
 
 }  // namespace
 
-TrainerBase* TrainerBase::create(bool fp64, const TrainSetup& ts) {
-  if (fp64) return new Trainer<double>(ts);
-  return new Trainer<float>(ts);
+TrainerBase* TrainerBase::create(int mode, const TrainSetup& ts) {
+  if (mode == 1) return new Trainer<double>(ts);
+  Trainer<float>* t = new Trainer<float>(ts);
+  t->tf32 = mode == 2;
+  return t;
 }
 
 }  // namespace lsn

@@ -35,7 +35,8 @@ struct TrainerBase {
   std::vector<long long> off;    // offsets of Ew, eb, W_1, b_1, ...
   int L = 0, P = 0, Cs = 0;
   virtual ~TrainerBase() {}
-  static TrainerBase* create(bool fp64, const TrainSetup& ts);
+  // mode 0: FP32 (CUDA cores), 1: FP64, 2: FP32 with TF32 tensor-core GEMMs
+  static TrainerBase* create(int mode, const TrainSetup& ts);
   virtual void init_device(const double* theta_host) = 0;
   // losses[3] = L_C, L_LS, L; gradient kept on the device
   virtual void evaluate(const double* q_dev, int B, double lambda_ls, double* losses,
