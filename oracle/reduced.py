@@ -113,6 +113,11 @@ class ReducedModel:
     def energy(self, z):
         return self.energy_x(self.positions(z))
 
+    def energy_grad(self, z):
+        """E and the reduced gradient g = J^T dE/dx (no Hessian; L-BFGS)."""
+        x, J = self.positions_jac(z)
+        return self.energy_x(x), J.T @ self.full_gradient_x(x)
+
     def full_gradient_x(self, x):
         """dE/dx as an assembled n-vector (used by pins and the full space)."""
         ge = fem.element_gradient(x.reshape(-1, 3), self.tets, self.DmInv,
