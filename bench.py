@@ -7,7 +7,8 @@ implicit Euler dt = 1/60, r = 16, decoder 16-256-256-256-9720 (seeded Xavier
 weights, output scale 1e-2), 256 cubature tets drawn uniformly by seed with
 weights 14976/256, Stable Neo-Hookean E = 1e5 Pa, nu = 0.45, rho = 1000.
 
-A step is one implicit-Euler time step solved by projective Newton to
+A step is one implicit-Euler time step solved by projective Newton (default;
+--optimizer lbfgs: L-BFGS with gradient-only passes) to
 ||g||_inf < 1e-5 (or its precision-floor / iteration-cap exit): decoder +
 Jacobian, element kernel + contraction, Cholesky, line search, until exit.
 Inputs (constraint targets of every frame, decoder weights, mesh) are
@@ -47,6 +48,10 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["fp64", "fp32", "tf32", "bf16"],
                     help="bf16 (default): BF16 weights and tensor-core contractions, FP32 "
                          "element math, FP64 Cholesky and energy comparison")
+    ap.add_argument("--optimizer", default="newton", choices=["newton", "lbfgs"],
+                    help="newton (default): projective Newton; lbfgs: L-BFGS (Sec. 5), "
+                         "gradient-only passes")
+    ap.add_argument("--history", type=int, default=10, help="L-BFGS history size")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="time budget of the CPU-oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -146,6 +151,8 @@ def workload_config(args, p, world):
             "r": c.r, "decoder": "-".join(map(str, p.widths)),
             "cubature": len(p.cub_idx), "dt": c.dt, "tol_inf": c.eps,
             "precision": args.precision + " (FP64 Cholesky + line search)",
+            "optimizer": (f"L-BFGS (history {args.history})" if args.optimizer == "lbfgs"
+                          else "projective Newton"),
             "frames": f"{W + 1}..{W + K}",
             "l2": "flushed between steps (256 MiB write, outside events)",
             "parallelism": "replicas" if world > 1 else "1 GPU"}
@@ -167,20 +174,26 @@ def job_value(world, steps, total_ms):
     return world * steps / (total_ms / 1000.0)
 
 
-def oracle_run(p, frames, budget_s):
-    """Run the FP64 CPU oracle for up to `frames` frames or `budget_s` seconds.
-    Returns (frames done, seconds, positions per frame)."""
+def oracle_sim(p, args):
+    """The FP64 CPU oracle's simulator with the optimiser of the run."""
     from oracle.reduced import model_from_problem, ReducedSimulator
     c = p.config
-    sim = ReducedSimulator(model_from_problem(p), c.dt, eps=c.eps,
-                           max_newton=c.max_newton, max_ls=c.max_ls, c=c.armijo_c)
+    return ReducedSimulator(model_from_problem(p), c.dt, eps=c.eps, max_newton=c.max_newton,
+                            max_ls=c.max_ls, c=c.armijo_c, optimizer=args.optimizer,
+                            history=args.history)
+
+
+def oracle_run(p, args, frames, budget_s):
+    """Run the FP64 CPU oracle for up to `frames` frames or `budget_s` seconds.
+    Returns (frames done, seconds, positions per frame)."""
+    c = p.config
+    sim = oracle_sim(p, args)
     qs = []
     t0 = time.perf_counter()
     done = 0
     for k in range(1, frames + 1):
         if not (c.dt > 0):  # quasi-static: every solve from the rest state
-            sim = ReducedSimulator(model_from_problem(p), c.dt, eps=c.eps,
-                                   max_newton=c.max_newton, max_ls=c.max_ls, c=c.armijo_c)
+            sim = oracle_sim(p, args)
         sim.step(p.targets(k))
         qs.append(sim.q.copy())
         done = k
@@ -198,17 +211,14 @@ def run_reference(args, world, rank):
     c = p.config
     budget = 150.0
     # timed: frames after the warm-up, continuing the same trajectory
-    from oracle.reduced import model_from_problem, ReducedSimulator
-    sim = ReducedSimulator(model_from_problem(p), c.dt, eps=c.eps, max_newton=c.max_newton,
-                           max_ls=c.max_ls, c=c.armijo_c)
+    sim = oracle_sim(p, args)
     for k in range(1, args.warmup + 1):
         sim.step(p.targets(k))
     t1 = time.perf_counter()
     steps = 0
     for k in range(args.warmup + 1, args.warmup + args.steps + 1):
         if not (c.dt > 0):  # quasi-static: every solve from the rest state
-            sim = ReducedSimulator(model_from_problem(p), c.dt, eps=c.eps,
-                                   max_newton=c.max_newton, max_ls=c.max_ls, c=c.armijo_c)
+            sim = oracle_sim(p, args)
         sim.step(p.targets(k))
         steps += 1
         if time.perf_counter() - t1 > budget:
@@ -273,7 +283,8 @@ def run_ours(args, world, rank, local):
     c = p.config
     W, K = args.warmup, args.steps
     stream = torch.cuda.Stream(dev)
-    ctx = pkg.context_from_problem(p, precision=args.precision, device=local, stream=stream)
+    ctx = pkg.context_from_problem(p, precision=args.precision, device=local, stream=stream,
+                                   optimizer=args.optimizer, history=args.history)
     frames = W + K
     targets = torch.tensor(np.stack([p.targets(k) for k in range(1, frames + 1)]),
                            dtype=torch.float64, device=dev)
@@ -399,7 +410,7 @@ def run_ours(args, world, rank, local):
     cpu = None
     err = None
     if rank == 0 and not args.no_cpu_baseline:
-        done, secs, qs = oracle_run(p, max(W, 200), args.cpu_seconds)
+        done, secs, qs = oracle_run(p, args, max(W, 200), args.cpu_seconds)
         cpu = {"value": done / secs, "unit": "steps/s", "cores": os.cpu_count(),
                "kind": "oracle",
                "sample": f"frames 1..{done} of {args.workload} from rest "

@@ -56,6 +56,8 @@ enum lsn_status {
                               diagonal-shift retries                          */
   LSN_PRECISION_FLOOR = 4, /* line search stalled at the rounding level of the
                               chosen precision while ||g||_inf < 100 tol       */
+  LSN_SADDLE = 5,          /* L-BFGS: no positive curvature along the accepted
+                              step (s^T y <= 0; exit II of Sec. 5)             */
   LSN_ERR_ARG = -1,        /* invalid argument or size                         */
   LSN_ERR_CUDA = -2,       /* CUDA runtime error                               */
   LSN_ERR_NONFINITE = -3,  /* NaN / Inf in inputs or in the reduced system     */
@@ -149,6 +151,26 @@ int lsn_set_decoder(lsn_ctx* ctx, int nlayers, const int* widths,
 int lsn_set_solver(lsn_ctx* ctx, double tol_inf, int max_newton, int max_ls,
                    double armijo_c);
 
+/* Optimiser of the solves (Sec. 5 and the Supplement's projective Newton
+ * tests).  Both share the evaluation passes, the Armijo backtracking line
+ * search, the tolerance and the caps of lsn_set_solver (max_newton caps the
+ * iterations of either).
+ *   LSN_OPT_NEWTON (default): projective Newton, d = -K^-1 g with the
+ *     Gauss-Newton reduced Hessian K (FP64 Cholesky).
+ *   LSN_OPT_LBFGS: L-BFGS, d = -H g by the two-loop recursion over the
+ *     `history` (1..32) most recent curvature pairs s = alpha d,
+ *     y = g(z + s) - g(z), initial matrix (s^T y / y^T y) I of the newest
+ *     pair (identity while the history is empty).  Its passes evaluate E and
+ *     g only (no per-element Hessian, eigen-decomposition or K).  Exits:
+ *     LSN_OK (I), LSN_SADDLE (II: s^T y <= 0 at a gradient above tol),
+ *     LSN_LS_FAILED (III), LSN_NOT_CONVERGED (IV), as well as
+ *     LSN_PRECISION_FLOOR in the FP32 / tensor-core forms.  A direction
+ *     with g.d >= 0 in rounding restarts from -g with an empty history.
+ * The history is cleared at the start of every solve.  Takes effect at the
+ * next call that evaluates (the device engine is rebuilt). */
+enum lsn_optimizer { LSN_OPT_NEWTON = 0, LSN_OPT_LBFGS = 1 };
+int lsn_set_optimizer(lsn_ctx* ctx, int kind, int history);
+
 /* Execution of a solve: mode 0 (default) launches the whole Newton loop as
  * one CUDA graph whose conditional WHILE node repeats an evaluation pass
  * until the device-side solver stops it; mode 1 drives the same kernels from
@@ -183,7 +205,9 @@ int lsn_get_positions(lsn_ctx* ctx, double* x_out);
  * reduced energy E, the
  * reduced gradient g (r) and the Gauss-Newton reduced Hessian K (r x r,
  * row-major) for the current dynamics setting (dt, qbar from the last
- * lsn_step or lsn_set_dynamics).  Outputs are host pointers; any may be NULL. */
+ * lsn_step or lsn_set_dynamics).  Outputs are host pointers; any may be NULL.
+ * With LSN_OPT_LBFGS selected and K == NULL, E and g come from the
+ * gradient-only pass that the L-BFGS solve uses. */
 int lsn_eval(lsn_ctx* ctx, const double* z, double* E, double* g, double* K);
 
 /* Parity hook for the inertia term: sets dt and qbar (n, host or device)

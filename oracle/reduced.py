@@ -220,10 +220,12 @@ def newton_solve(model, z0, eps, max_newton=1024, max_ls=128, c=1e-4,
 
 
 class ReducedSimulator:
-    """Implicit Euler stepping (Eq. 2) or a quasi-static solve (dt = 0)."""
+    """Implicit Euler stepping (Eq. 2) or a quasi-static solve (dt = 0), each
+    step solved by projective Newton or (optimizer="lbfgs") by L-BFGS."""
 
     def __init__(self, model, dt, z0=None, eps=1e-5, max_newton=1024,
-                 max_ls=128, c=1e-4):
+                 max_ls=128, c=1e-4, optimizer="newton", history=10):
+        self.optimizer, self.history = optimizer, history
         self.m = model
         self.dt = float(dt)
         r = model.dec.r
@@ -240,8 +242,13 @@ class ReducedSimulator:
             m.set_dynamics(self.dt, self.q + self.dt * self.v + self.dt ** 2 * g)
         else:
             m.set_dynamics(0.0, None)
-        z, st = newton_solve(m, self.z, self.eps, self.max_newton, self.max_ls,
-                             self.c)
+        if self.optimizer == "lbfgs":
+            from .lbfgs import lbfgs_solve
+            z, st = lbfgs_solve(m, self.z, self.eps, self.history, self.max_newton,
+                                self.max_ls, self.c)
+        else:
+            z, st = newton_solve(m, self.z, self.eps, self.max_newton, self.max_ls,
+                                 self.c)
         self.z = z
         qn = m.positions(z)
         if self.dt > 0.0:

@@ -8,9 +8,9 @@ without the built library raises.
 """
 from ._native import (Context, LsnError, LsnStats, load, exported_symbols, PRECISIONS,
                       LSN_OK, LSN_NOT_CONVERGED, LSN_LS_FAILED, LSN_NOT_SPD,
-                      LSN_PRECISION_FLOOR)
+                      LSN_PRECISION_FLOOR, LSN_SADDLE, OPTIMIZERS)
 from .problem import context_from_problem
 
 __all__ = ["Context", "LsnError", "LsnStats", "load", "exported_symbols", "PRECISIONS",
            "context_from_problem", "LSN_OK", "LSN_NOT_CONVERGED", "LSN_LS_FAILED",
-           "LSN_NOT_SPD", "LSN_PRECISION_FLOOR"]
+           "LSN_NOT_SPD", "LSN_PRECISION_FLOOR", "LSN_SADDLE", "OPTIMIZERS"]

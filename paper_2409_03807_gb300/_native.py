@@ -14,6 +14,8 @@ import numpy as np
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblsn.so")
 
 LSN_OK, LSN_NOT_CONVERGED, LSN_LS_FAILED, LSN_NOT_SPD, LSN_PRECISION_FLOOR = 0, 1, 2, 3, 4
+LSN_SADDLE = 5
+OPTIMIZERS = {"newton": 0, "lbfgs": 1}
 LSN_ERR_ARG, LSN_ERR_CUDA, LSN_ERR_NONFINITE, LSN_ERR_STATE, LSN_ERR_OOM = -1, -2, -3, -4, -5
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 
@@ -49,6 +51,7 @@ _SIGS = {
                         ctypes.c_void_p, ctypes.c_double, ctypes.c_int],
     "lsn_set_solver": [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                        ctypes.c_double],
+    "lsn_set_optimizer": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
     "lsn_set_state": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "lsn_set_dynamics": [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p],
     "lsn_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
@@ -221,6 +224,10 @@ class Context:
         return self._check(self.lib.lsn_set_solver(self.h, tol_inf, max_newton, max_ls,
                                                    armijo_c))
 
+    def set_optimizer(self, kind="newton", history=10):
+        """kind: "newton" (projective Newton) or "lbfgs"; history: L-BFGS pairs."""
+        return self._check(self.lib.lsn_set_optimizer(self.h, OPTIMIZERS[kind], history))
+
     def set_state(self, z=None, q=None, v=None):
         z, q, v = _f64(z), _f64(q), _f64(v)
         return self._check(self.lib.lsn_set_state(self.h, _ptr(z), _ptr(q), _ptr(v)))
@@ -253,12 +260,15 @@ class Context:
         self._check(self.lib.lsn_get_positions(self.h, _ptr(out)))
         return out
 
-    def eval(self, z):
+    def eval(self, z, want_K=True):
+        """E, g, K at z (K None when want_K is False: with the L-BFGS optimiser
+        E and g then come from its gradient-only pass)."""
         z = _f64(z)
         E = np.zeros(1)
         g = np.zeros(self.r)
-        K = np.zeros((self.r, self.r))
-        self._check(self.lib.lsn_eval(self.h, _ptr(z), _ptr(E), _ptr(g), _ptr(K)))
+        K = np.zeros((self.r, self.r)) if want_K else None
+        self._check(self.lib.lsn_eval(self.h, _ptr(z), _ptr(E), _ptr(g),
+                                      _ptr(K) if want_K else None))
         return float(E[0]), g, K
 
     def get_trace(self, max_entries=128):

@@ -148,6 +148,8 @@ struct EngineBase {
   virtual int device_error(cudaStream_t) { return 0; }
   DevSolver* sv = nullptr;
   double* sys = nullptr;
+  int kind = 0;       // optimiser of the solves: 0 projective Newton, 1 L-BFGS
+  int pass_kind = 0;  // passes issued by pass(): 0 full (E, g, K), 1 gradient-only
   // CUDA graph of the whole solve loop (conditional WHILE node)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -194,6 +196,7 @@ struct lsn_ctx {
   // solver controls
   double tol = 1e-5, armijo_c = 1e-4;
   int max_newton = 1024, max_ls = 128;
+  int opt_kind = LSN_OPT_NEWTON, hist_m = 10;  // optimiser and L-BFGS history size
   // state
   double* q = nullptr;
   double* v = nullptr;
@@ -239,6 +242,8 @@ struct Engine : EngineBase {
   bool use_tc = false;       // TF32 / BF16 form: tensor-core element contraction
   bool use_tc_last = false;  // ... and tensor-core output layer (hidden width allows TMA)
   int* tc_err = nullptr;     // device flag: a bounded wait of a tensor-core kernel ran out
+  DevHistory* hist = nullptr;  // L-BFGS curvature pairs
+  int ggrid = 0;               // CTAs of the gradient-only element kernel
 
   explicit Engine(lsn_ctx* ctx) : c(ctx) {
     cudaStream_t s = c->stream;
@@ -306,7 +311,10 @@ struct Engine : EngineBase {
       genergy = 0;
     }
     part_dec = dalloc<double>((size_t)grid_dec * nst);
-    part_el = dalloc<double>((size_t)(gfull + genergy) * nst);
+    kind = pass_kind = c->opt_kind;
+    ggrid = element_grad_grid(S, c->num_sms);
+    hist = dalloc<DevHistory>(1);
+    part_el = dalloc<double>((size_t)std::max(gfull + genergy, ggrid) * nst);
     sys = dalloc<double>(nst);
     sv = dalloc<DevSolver>(1);
     ck(cudaMemsetAsync(sv, 0, sizeof(DevSolver), s));
@@ -353,6 +361,9 @@ struct Engine : EngineBase {
     h.r = r;
     h.max_ls = c->max_ls;
     h.max_newton = c->max_newton;
+    h.kind = kind;
+    h.hist_m = c->hist_m;
+    h.gamma = 1.0;
     h.status = -1;
     ck(cudaMemcpyAsync(sv, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     ck(cudaStreamSynchronize(s));
@@ -377,6 +388,7 @@ struct Engine : EngineBase {
     dfree(part_dec);
     dfree(part_el);
     dfree(tc_err);
+    dfree(hist);
     dfree(sys);
     dfree(sv);
   }
@@ -423,6 +435,17 @@ struct Engine : EngineBase {
       launch_last_layer<Real>(dW[L - 1], db[L - 1], n, c->widths[L - 1], h, C, nj, u, J, ut,
                               part_dec, nst, la, grid_dec, s);
     if (prof) P.end(LSN_K_DECODER_LAST);
+    if (pass_kind == 1) {  // L-BFGS: energies and gradient only
+      if (prof) P.begin(LSN_K_ELEMENT);
+      launch_element_grad<Real>(ea, u, J, ut, part_el, ggrid, s);
+      if (prof) P.end(LSN_K_ELEMENT);
+      if (prof) P.begin(LSN_K_SOLVE, 2);
+      launch_reduce_partials(part_dec, grid_dec, part_el, ggrid, -1, nslots(r), nst, sys, s,
+                             slot_K(r), npairs(r));
+      launch_select_lbfgs<Real>(sv, hist, sys, Z0, cond, use_cond, s);
+      if (prof) P.end(LSN_K_SOLVE);
+      return;
+    }
     if (prof) P.begin(LSN_K_ELEMENT);
     if (use_tc)
       ck(launch_element_tc(ea, reinterpret_cast<const float*>(u),
@@ -545,14 +568,18 @@ void ensure_graph(lsn_ctx* c) {
 
 // One solve from the current device z: graph launch (default) or host loop
 // (when kernel-event profiling is on).
-void run_solve(lsn_ctx* c, int eval_only) {
+// eval_pass: for eval_only, the pass kind to evaluate with (0 full, 1
+// gradient-only); solves use the engine's optimiser.
+void run_solve(lsn_ctx* c, int eval_only, int eval_pass = -1) {
   EngineBase* e = c->eng.get();
   cudaStream_t s = c->stream;
+  const int want = (eval_only && eval_pass >= 0) ? eval_pass : e->kind;
   e->begin(eval_only);
-  if (c->prof.mask == 0 && c->use_graph) {
+  if (c->prof.mask == 0 && c->use_graph && want == e->kind) {
     ensure_graph(c);
     ck(cudaGraphLaunch(e->exec, s));
   } else {
+    e->pass_kind = want;
     for (int guard = 0; guard < 4 * (c->max_newton + 2) * (c->max_ls + 2); ++guard) {
       e->pass(s, 0, 0);
       ck(cudaMemcpyAsync(c->pinned_status, &e->sv->running, sizeof(int),
@@ -560,6 +587,7 @@ void run_solve(lsn_ctx* c, int eval_only) {
       ck(cudaStreamSynchronize(s));
       if (!c->pinned_status[0]) break;
     }
+    e->pass_kind = e->kind;
   }
 }
 
@@ -877,6 +905,16 @@ int lsn_set_solver(lsn_ctx* c, double tol_inf, int max_newton, int max_ls, doubl
   return LSN_OK;
 }
 
+int lsn_set_optimizer(lsn_ctx* c, int kind, int history) {
+  if (!c) return LSN_ERR_ARG;
+  if ((kind != LSN_OPT_NEWTON && kind != LSN_OPT_LBFGS) || history < 1 || history > MHIST)
+    return fail(c, LSN_ERR_ARG, "set_optimizer: invalid optimiser or history size");
+  if (kind != c->opt_kind || history != c->hist_m) c->dirty = true;
+  c->opt_kind = kind;
+  c->hist_m = history;
+  return LSN_OK;
+}
+
 int lsn_set_execution(lsn_ctx* c, int mode) {
   if (!c || mode < 0 || mode > 1) return LSN_ERR_ARG;
   c->use_graph = mode == 0;
@@ -968,7 +1006,8 @@ int lsn_eval(lsn_ctx* c, const double* z, double* E, double* g, double* K) {
                        cudaMemcpyDeviceToHost, c->stream));
     ck(cudaStreamSynchronize(c->stream));
   }
-  run_solve(c, 1);
+  // the L-BFGS passes carry no reduced Hessian: K comes from a full pass
+  run_solve(c, 1, (c->opt_kind == LSN_OPT_LBFGS && !K) ? 1 : 0);
   std::vector<double> sys(nslots(r));
   ck(cudaMemcpyAsync(sys.data(), c->eng->sys, sizeof(double) * sys.size(),
                      cudaMemcpyDeviceToHost, c->stream));

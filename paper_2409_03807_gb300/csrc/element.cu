@@ -1034,6 +1034,152 @@ __global__ void __launch_bounds__(NT, 1)
 
 }  // namespace tcel
 
+// ------------------------------------------------------------------------
+// Gradient-only form (the passes of the L-BFGS solve, Sec. 5): per tet the
+// energy, its first derivative P and the KTRIAL trial energies (one tet per
+// thread), then g += sum_e J_e^T ge_e with ge_e = w_e V_e dPsi/dx_e, the 12
+// values (vertex a >= 1, component i) sum_j P_ij Dm^-1_{a-1,j} and their
+// negated sum for vertex 0, held in shared memory while groups of r threads
+// (one subspace column each) stream the tets' J rows, coalesced along the
+// columns.  No Hessian, eigen-decomposition or K contraction.  Each CTA
+// writes one complete partial row: E, sum |E terms|, g, gabs and the trial
+// energies (the K slots are not written).
+namespace gradel {
+constexpr int ET = 128;
+
+template <typename Real>
+__global__ void __launch_bounds__(ET) element_grad_kernel(ElemArgs ea, const Real* __restrict__ u,
+                                                          const Real* __restrict__ J,
+                                                          const Real* __restrict__ ut,
+                                                          double* __restrict__ part,
+                                                          int part_stride) {
+  __shared__ Real ge[ET][13];
+  __shared__ int4 tvs[ET];
+  __shared__ double red[2 + 2 * KTRIAL][ET];
+  const int t = threadIdx.x, r = ea.r;
+  const int G = ET / r;  // column groups
+  const int grp = t / r, c = t - grp * r;
+  const bool active = grp < G;
+  const Real mu = (Real)ea.mu, lam = (Real)ea.lam;
+  const Real oma = (Real)(-0.75 * ea.mu / ea.lam);  // 1 - a
+  double eacc = 0.0, eabs = 0.0, gacc = 0.0, gabs = 0.0;
+  double tacc[KTRIAL], tabs[KTRIAL];
+#pragma unroll
+  for (int j = 0; j < KTRIAL; ++j) tacc[j] = tabs[j] = 0.0;
+  const int ntiles = (ea.S + ET - 1) / ET;
+  pdl_wait();
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int e = tile * ET + t;
+    const int nt = min(ET, ea.S - tile * ET);
+    if (e < ea.S) {
+      int4 tv;
+      Real Dmi[3][3], wv, H[3][3];
+      load_tet<Real>(ea, e, tv, Dmi, wv);
+      disp_grad<Real>(u, tv, Dmi, H);
+      Invariants<Real> iv;
+      invariants<Real>(H, iv);
+      const double pe = (double)(wv * snh_psi<Real>(iv, mu, lam, oma));
+      eacc += pe;
+      eabs += fabs(pe);
+      const Real Ic = iv.Ic3 + Real(3);
+      const Real dl = iv.Ic3 / (Real(4) * (Ic + Real(1)));
+      const Real lJ = lam * iv.Jm1;
+      Real P[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const Real Fij = H[i][j] + (i == j ? Real(1) : Real(0));
+          P[i][j] = wv * (mu * dl * Fij + lJ * iv.cof[i][j] +
+                          Real(0.75) * mu *
+                              (H[i][j] + H[j][i] - (i == j ? iv.trH : Real(0)) - iv.cofH[i][j]));
+        }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        Real s0 = Real(0);
+#pragma unroll
+        for (int a = 1; a < 4; ++a) {
+          const Real v = P[i][0] * Dmi[a - 1][0] + P[i][1] * Dmi[a - 1][1] +
+                         P[i][2] * Dmi[a - 1][2];
+          ge[t][3 * a + i] = v;
+          s0 += v;
+        }
+        ge[t][i] = -s0;
+      }
+      tvs[t] = tv;
+#pragma unroll
+      for (int j = 0; j < KTRIAL; ++j) {
+        Real Ht[3][3];
+        disp_grad<Real>(ut + (size_t)j * ea.n, tv, Dmi, Ht);
+        Invariants<Real> ivt;
+        invariants<Real>(Ht, ivt);
+        const double pt = (double)(wv * snh_psi<Real>(ivt, mu, lam, oma));
+        tacc[j] += pt;
+        tabs[j] += fabs(pt);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) ge[t][k] = Real(0);
+      tvs[t] = make_int4(0, 0, 0, 0);
+    }
+    __syncthreads();
+    if (active) {
+      Real sg = Real(0), sa = Real(0);
+#pragma unroll 4
+      for (int lt = grp; lt < nt; lt += G) {
+        const int4 tv = tvs[lt];
+        const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
+        Real gp = Real(0);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            gp += ge[lt][3 * a + i] * __ldg(J + (size_t)(3 * vv[a] + i) * r + c);
+        sg += gp;
+        sa += fabs(gp);
+      }
+      gacc += (double)sg;
+      gabs += (double)sa;
+    }
+    __syncthreads();
+  }
+  red[0][t] = eacc;
+  red[1][t] = eabs;
+#pragma unroll
+  for (int j = 0; j < KTRIAL; ++j) {
+    red[2 + 2 * j][t] = tacc[j];
+    red[3 + 2 * j][t] = tabs[j];
+  }
+  __syncthreads();
+  for (int h = ET / 2; h > 0; h >>= 1) {
+    if (t < h) {
+#pragma unroll
+      for (int k = 0; k < 2 + 2 * KTRIAL; ++k) red[k][t] += red[k][t + h];
+    }
+    __syncthreads();
+  }
+  double* prow = part + (size_t)blockIdx.x * part_stride;
+  if (t == 0) {
+    prow[0] = red[0][0];
+    prow[1] = red[1][0];
+  }
+  if (t < 2 * KTRIAL) prow[nslots(r) + t] = red[2 + t][0];
+  __syncthreads();
+  red[0][t] = active ? gacc : 0.0;
+  red[1][t] = active ? gabs : 0.0;
+  __syncthreads();
+  if (t < r) {  // the column groups in fixed order
+    double s0 = 0.0, a0 = 0.0;
+    for (int q = 0; q < G; ++q) {
+      s0 += red[0][q * r + t];
+      a0 += red[1][q * r + t];
+    }
+    prow[slot_g(t)] = s0;
+    prow[slot_gabs(r, t)] = a0;
+  }
+}
+}  // namespace gradel
+
 }  // namespace
 
 // Small cubature sets use 64-tet tiles so that more CTAs share the work.
@@ -1115,6 +1261,22 @@ cudaError_t launch_element_tc(const ElemArgs& ea, const float* u, const float* J
   return cudaGetLastError();
 }
 
+int element_grad_grid(int S, int num_sms) {
+  const int tiles = (S + gradel::ET - 1) / gradel::ET;
+  return std::max(1, std::min(tiles, 8 * num_sms));
+}
+
+template <typename Real>
+void launch_element_grad(const ElemArgs& ea, const Real* u, const Real* J, const Real* ut,
+                         double* part, int grid, cudaStream_t s) {
+  launch_pdl(gradel::element_grad_kernel<Real>, dim3(grid), dim3(gradel::ET), 0, s, ea, u, J,
+             ut, part, nslots_total(ea.r));
+}
+
+template void launch_element_grad<float>(const ElemArgs&, const float*, const float*,
+                                         const float*, double*, int, cudaStream_t);
+template void launch_element_grad<double>(const ElemArgs&, const double*, const double*,
+                                          const double*, double*, int, cudaStream_t);
 template void launch_element<float>(const ElemArgs&, const float*, const float*, const float*,
                                     double*, int, int, cudaStream_t);
 template void launch_element<double>(const ElemArgs&, const double*, const double*,

@@ -11,6 +11,7 @@ constexpr int RMAX = 64;           // largest subspace dimension
 constexpr int KTRIAL = 3;          // extra line-search step lengths per pass
 constexpr int GEMM_BK = 32;        // k-chunk of the decoder GEMM tiles
 constexpr int TRACE = 128;         // Newton iterations kept in the solve trace
+constexpr int MHIST = 32;          // largest L-BFGS history (curvature pairs)
 
 // Number of upper-triangle entries of an r x r symmetric matrix.
 __host__ __device__ inline int npairs(int r) { return r * (r + 1) / 2; }
@@ -57,12 +58,26 @@ struct DevSolver {
   int running;         // the solve loop continues
   int stall;           // iterations without a 10 % drop of ||g||_inf
   int passes;          // evaluation passes of this solve
-  int pad_;
+  int kind;            // optimiser: 0 projective Newton, 1 L-BFGS
+  int hist_m;          // L-BFGS: history size m
+  int hist_n;          // L-BFGS: stored curvature pairs
+  int hist_head;       // L-BFGS: ring slot of the oldest pair
+  int pair_pending;    // L-BFGS: a step was taken; its pair is formed at the next gradient
+  int pad_[2];
+  double gamma;        // L-BFGS: initial scaling s^T y / y^T y of the newest pair
   double z[RMAX];      // current iterate
   double d[RMAX];      // Newton direction
   double g[RMAX];      // reduced gradient at z
   // per-iteration history of the current solve (first TRACE iterations)
   double trace_g[TRACE], trace_E[TRACE], trace_gabs[TRACE], trace_alpha[TRACE];
+};
+
+// L-BFGS curvature pairs (s_i, y_i) of the current solve, a ring of
+// DevSolver::hist_m slots, and the reduced gradient at z (for y = g' - g).
+struct DevHistory {
+  double gz[RMAX];
+  double S[MHIST][RMAX], Y[MHIST][RMAX];
+  double rho[MHIST];   // 1 / s_i^T y_i
 };
 
 // ---------------------------------------------------------------- launchers
@@ -125,15 +140,25 @@ void element_grids(int S, int r, int num_sms, int& gfull, int& genergy);
 // writing one complete partial row (elastic slots and trial energies) of
 // nslots_total(r) doubles; err receives a nonzero code if a bounded wait ran out.
 int element_tc_grid(int S, int num_sms);
+// Gradient-only element kernel of the L-BFGS passes (any precision form):
+// `grid` CTAs, each writing the E, g, gabs and trial-energy slots of one
+// partial row (stride nslots_total(r)); the K slots are not written.
+int element_grad_grid(int S, int num_sms);
+template <typename Real>
+void launch_element_grad(const ElemArgs& ea, const Real* u, const Real* J, const Real* ut,
+                         double* part, int grid, cudaStream_t s);
 cudaError_t launch_element_tc(const ElemArgs& ea, const float* u, const float* J,
                               const float* ut, double* part, int grid, bool bf16, int* err,
                               cudaStream_t s);
 
 // solve.cu
 // out[c] = sum over rows of A (all rows) and of B: rows [0, splitB) for
-// c < split, rows [splitB, rowsB) for c >= split.  Fixed order.
+// c < split, rows [splitB, rowsB) for c >= split (splitB < 0: all rows for
+// every column).  Fixed order.  Columns [gap0, gap0 + gapn) are skipped (out
+// left unchanged there).
 void launch_reduce_partials(const double* A, int rowsA, const double* B, int rowsB,
-                            int splitB, int split, int ncols, double* out, cudaStream_t s);
+                            int splitB, int split, int ncols, double* out, cudaStream_t s,
+                            int gap0 = 0, int gapn = 0);
 // Z0 is the first layer's input [r][zstride(C)]: column 0 the point y0,
 // columns 1..r the identity, columns r+1..r+KTRIAL the trial points.
 template <typename Real>
@@ -141,6 +166,11 @@ void launch_solve_begin(DevSolver* sv, Real* Z0, int C, int eval_only, cudaStrea
 template <typename Real>
 void launch_select_direction(DevSolver* sv, const double* sys, Real* Z0,
                              unsigned long long cond, int use_cond, cudaStream_t s);
+// L-BFGS counterpart of launch_select_direction: the same line search and
+// exits, the direction from the two-loop recursion over the history.
+template <typename Real>
+void launch_select_lbfgs(DevSolver* sv, DevHistory* hist, const double* sys, Real* Z0,
+                         unsigned long long cond, int use_cond, cudaStream_t s);
 template <typename Real>
 void launch_finish_positions(const double* X0, const Real* u, int n, double dt, double* q,
                              double* v, cudaStream_t s);

@@ -33,11 +33,12 @@ __device__ __forceinline__ int upper_index(int i, int j, int r) {
 // shuffle tree: the summation order does not depend on scheduling.
 __global__ void reduce_partials_kernel(const double* __restrict__ A, int rowsA,
                                        const double* __restrict__ B, int rowsB, int splitB,
-                                       int split, int ncols, double* __restrict__ out) {
+                                       int split, int ncols, double* __restrict__ out, int gap0,
+                                       int gapn) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   pdl_wait();
-  if (warp >= ncols) return;
-  const int c = warp;
+  if (warp >= ncols - gapn) return;
+  const int c = warp < gap0 ? warp : warp + gapn;  // columns [gap0, gap0 + gapn) skipped
   double s = 0.0;
   for (int b = lane; b < rowsA; b += 32) s += A[(size_t)b * ncols + c];
   // splitB < 0: every B row carries every column
@@ -78,6 +79,10 @@ __global__ void solve_begin_kernel(DevSolver* sv, Real* Z0, int C, int eval_only
     sv->g_best = 1e300;
     sv->alpha_base = 1.0;
     sv->eval_only = eval_only;
+    sv->hist_n = 0;
+    sv->hist_head = 0;
+    sv->pair_pending = 0;
+    sv->gamma = 1.0;
   }
   const int CPs = zstride(C);
   for (int e = threadIdx.x; e < CPs * r; e += blockDim.x) {
@@ -162,6 +167,106 @@ __device__ bool block_cholesky(double (*L)[RMAX + 1], double* invd, int r, int* 
   return true;
 }
 
+// Line-search decision on the energies of the pass (lane 0 of warp 0):
+// at_z = -2: the final re-evaluation at z is done; -1: keep backtracking
+// along d (or a final pass at z is queued); 0: a shorter step was taken, the
+// next pass evaluates at the new z; 1: the pass point y0 is the current z
+// (sys holds E and g there).  stepped = 1 when a step was accepted.
+__device__ void line_search_decide(DevSolver* sv, DevSolver* gsv, const double* sE,
+                                   const double* sT, int& at_z, int& stepped) {
+  at_z = 1;
+  stepped = 0;
+  sv->passes += 1;
+  if (sv->final_pass) {
+    sv->final_pass = 0;
+    sv->running = 0;
+    at_z = -2;
+  } else if (sv->have_dir) {
+    int acc = -1;
+    for (int j = 0; j <= KTRIAL; ++j) {
+      if (sv->ls_iter >= sv->max_ls) break;
+      sv->ls_iter += 1;
+      sv->ls_trials += 1;
+      const double a = ldexp(sv->alpha_base, -j);
+      const double Et = j == 0 ? sE[0] : sT[2 * (j - 1)];
+      const double Ea = j == 0 ? sE[1] : sT[2 * (j - 1) + 1];
+      const double eta = sv->eta_scale * (Ea + sv->Eabs);
+      if (isfinite(Et) && Et <= sv->E + sv->armijo_c * a * sv->gd + eta) {
+        acc = j;
+        break;
+      }
+    }
+    if (acc >= 0) {
+      const double a = ldexp(sv->alpha_base, -acc);
+      sv->alpha_taken = a;
+      if (sv->iters < TRACE) gsv->trace_alpha[sv->iters] = a;
+      sv->iters += 1;
+      sv->have_dir = 0;
+      at_z = acc == 0 ? 1 : 0;
+      stepped = 1;
+    } else if (sv->ls_iter >= sv->max_ls) {
+      sv->status = (sv->grad_inf < 100.0 * sv->tol) ? 4 : 2;  // PRECISION_FLOOR : LS_FAILED
+      sv->have_dir = 0;
+      sv->final_pass = 1;  // positions must be re-evaluated at z
+      at_z = -1;
+    } else {
+      sv->alpha_base = ldexp(sv->alpha_base, -(KTRIAL + 1));
+      at_z = -1;  // keep backtracking along d
+    }
+  }
+}
+
+// Exit tests at the current z (warp 0; lane 0 writes the state): records E,
+// ||g||_inf, the rounding scale of g and the trace entry, updates the stall
+// counter, and returns the solve's exit status or -1 to continue.  `finite`
+// carries the caller's finiteness check of further data (the reduced
+// Hessian); `saddle` is the L-BFGS curvature exit.
+__device__ int gradient_exits(DevSolver* sv, DevSolver* gsv, const double* sE, const double* sg,
+                              const double* sga, int r, bool finite, bool saddle) {
+  const int t = threadIdx.x;
+  double gm = 0.0, ga = 0.0;
+  for (int i = t; i < r; i += 32) {
+    const double gi = sg[i];
+    gm = fmax(gm, fabs(gi));
+    ga = fmax(ga, sga[i]);
+    finite = finite && isfinite(gi);
+  }
+  const double ginf = __all_sync(0xffffffffu, finite) ? warp_max(gm) : -1.0;
+  const double gabs_max = warp_max(ga);
+  const double E = sE[0];
+  int stall = 0;
+  if (t == 0) {
+    sv->E = E;
+    sv->Eabs = sE[1];
+    sv->grad_inf = ginf;
+    sv->gabs_max = gabs_max;
+    if (!sv->eval_only) {
+      if (sv->iters < TRACE) {
+        gsv->trace_g[sv->iters] = ginf;
+        gsv->trace_E[sv->iters] = E;
+        gsv->trace_gabs[sv->iters] = gabs_max;
+        gsv->trace_alpha[sv->iters] = 0.0;
+      }
+      // stall counter: iterations since ||g||_inf last dropped by 10 %
+      if (ginf <= 0.9 * sv->g_best) {
+        sv->g_best = ginf;
+        sv->stall = 0;
+      } else {
+        sv->stall += 1;
+      }
+    }
+    stall = sv->stall;
+  }
+  stall = __shfl_sync(0xffffffffu, stall, 0);
+  if (sv->eval_only) return 0;
+  if (ginf < 0.0 || !isfinite(E)) return -3;                     // LSN_ERR_NONFINITE
+  if (ginf < sv->tol) return 0;                                  // LSN_OK
+  if (saddle) return 5;                                          // LSN_SADDLE
+  if (stall >= 4 && ginf <= sv->floor_scale * gabs_max) return 4;  // PRECISION_FLOOR
+  if (sv->iters >= sv->max_newton) return 1;                     // LSN_NOT_CONVERGED
+  return -1;
+}
+
 // Warp-0 state logic around a block-wide FP64 Cholesky (SEL_THREADS threads,
 // one CTA): the line-search decision on the trial energies of the pass, the
 // exit tests, and (when a new direction is due) d = -K^-1 g with diagonal
@@ -209,46 +314,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_direction_kernel(
     const double* sT = ssys + 2 + 2 * r;        // trial (E_j, Eabs_j)
     // ------------------------------------------------ line-search decision
     int at_z = 1, stepped = 0;
-    if (t == 0) {
-      sv->passes += 1;
-      if (sv->final_pass) {
-        sv->final_pass = 0;
-        sv->running = 0;
-        at_z = -2;
-      } else if (sv->have_dir) {
-        int acc = -1;
-        for (int j = 0; j <= KTRIAL; ++j) {
-          if (sv->ls_iter >= sv->max_ls) break;
-          sv->ls_iter += 1;
-          sv->ls_trials += 1;
-          const double a = ldexp(sv->alpha_base, -j);
-          const double Et = j == 0 ? sE[0] : sT[2 * (j - 1)];
-          const double Ea = j == 0 ? sE[1] : sT[2 * (j - 1) + 1];
-          const double eta = sv->eta_scale * (Ea + sv->Eabs);
-          if (isfinite(Et) && Et <= sv->E + sv->armijo_c * a * sv->gd + eta) {
-            acc = j;
-            break;
-          }
-        }
-        if (acc >= 0) {
-          const double a = ldexp(sv->alpha_base, -acc);
-          sv->alpha_taken = a;
-          if (sv->iters < TRACE) gsv->trace_alpha[sv->iters] = a;
-          sv->iters += 1;
-          sv->have_dir = 0;
-          at_z = acc == 0 ? 1 : 0;
-          stepped = 1;
-        } else if (sv->ls_iter >= sv->max_ls) {
-          sv->status = (sv->grad_inf < 100.0 * sv->tol) ? 4 : 2;  // PRECISION_FLOOR : LS_FAILED
-          sv->have_dir = 0;
-          sv->final_pass = 1;  // positions must be re-evaluated at z
-          at_z = -1;
-        } else {
-          sv->alpha_base = ldexp(sv->alpha_base, -(KTRIAL + 1));
-          at_z = -1;  // keep backtracking along d
-        }
-      }
-    }
+    if (t == 0) line_search_decide(sv, gsv, sE, sT, at_z, stepped);
     at_z = __shfl_sync(0xffffffffu, at_z, 0);
     stepped = __shfl_sync(0xffffffffu, stepped, 0);
     __syncwarp();
@@ -265,48 +331,10 @@ __global__ void __launch_bounds__(SEL_THREADS) select_direction_kernel(
       write_pass_points<Real>(sv, Z0, 0.0, false);
     } else {
       // ------------------------------------------- sys holds E, g, K at z
-      double gm = 0.0, ga = 0.0;
       bool finite = true;
-      for (int i = t; i < r; i += 32) {
-        const double gi = sg[i];
-        y[i] = -gi;
-        gm = fmax(gm, fabs(gi));
-        ga = fmax(ga, sga[i]);
-        finite = finite && isfinite(gi);
-      }
+      for (int i = t; i < r; i += 32) y[i] = -sg[i];
       for (int e = t; e < r * r; e += 32) finite = finite && isfinite(L[e / r][e % r]);
-      const double ginf = __all_sync(0xffffffffu, finite) ? warp_max(gm) : -1.0;
-      const double gabs_max = warp_max(ga);
-      const double E = sE[0];
-      int stall = 0;
-      if (t == 0) {
-        sv->E = E;
-        sv->Eabs = sE[1];
-        sv->grad_inf = ginf;
-        sv->gabs_max = gabs_max;
-        if (!sv->eval_only) {
-          if (sv->iters < TRACE) {
-            gsv->trace_g[sv->iters] = ginf;
-            gsv->trace_E[sv->iters] = E;
-            gsv->trace_gabs[sv->iters] = gabs_max;
-            gsv->trace_alpha[sv->iters] = 0.0;
-          }
-          // stall counter: iterations since ||g||_inf last dropped by 10 %
-          if (ginf <= 0.9 * sv->g_best) {
-            sv->g_best = ginf;
-            sv->stall = 0;
-          } else {
-            sv->stall += 1;
-          }
-        }
-        stall = sv->stall;
-      }
-      stall = __shfl_sync(0xffffffffu, stall, 0);
-      if (sv->eval_only) status = 0;
-      else if (ginf < 0.0 || !isfinite(E)) status = -3;              // LSN_ERR_NONFINITE
-      else if (ginf < sv->tol) status = 0;                           // LSN_OK
-      else if (stall >= 4 && ginf <= sv->floor_scale * gabs_max) status = 4;  // PRECISION_FLOOR
-      else if (sv->iters >= sv->max_newton) status = 1;              // LSN_NOT_CONVERGED
+      status = gradient_exits(sv, gsv, sE, sg, sga, r, finite, false);
       if (status != -1) {
         if (t == 0) {
           if (!sv->eval_only) sv->status = status;
@@ -396,6 +424,176 @@ __global__ void __launch_bounds__(SEL_THREADS) select_direction_kernel(
   if (want_cond && use_cond && t == 0) cudaGraphSetConditional(cond, cond_val);
 }
 
+// L-BFGS state logic (Sec. 5: the optimiser of the main results, exits I-IV).
+// The same passes, line search and exit tests as the Newton solve; the
+// direction is d = -H g by the two-loop recursion (Nocedal & Wright,
+// Algorithm 7.4) over the hist_n most recent curvature pairs, H0 = gamma I
+// with gamma = s^T y / y^T y of the newest pair (1 while the history is
+// empty).  The pair of an accepted step, s = alpha d and y = g(z + s) - g(z),
+// is formed at the next gradient at z; s^T y <= 0 (no positive curvature
+// along the step) ends the solve with exit II, LSN_SADDLE, unless that
+// gradient already meets the tolerance.  A direction that is not a descent
+// direction in rounding (g.d >= 0) restarts from d = -g with an empty history.
+// The history is staged in shared memory by all SEL_THREADS threads; the
+// logic and the recursion run in warp 0 (FP64, lanes own entries i, i + 32).
+template <typename Real>
+__global__ void __launch_bounds__(SEL_THREADS) select_lbfgs_kernel(
+    DevSolver* gsv, DevHistory* gh, const double* __restrict__ sys, Real* Z0,
+    unsigned long long cond, int use_cond) {
+  __shared__ double hS[MHIST][RMAX], hY[MHIST][RMAX];
+  __shared__ double hrho[MHIST], ha[MHIST];
+  __shared__ double sgz[RMAX];
+  __shared__ double ssys[2 + 2 * RMAX + 2 * KTRIAL];
+  __shared__ __align__(16) DevSolver svs;
+  DevSolver* sv = &svs;
+  const int t = threadIdx.x;
+  pdl_wait();
+  {
+    const double* src = reinterpret_cast<const double*>(gsv);
+    double* dst = reinterpret_cast<double*>(&svs);
+    for (int e = t; e < SV_SCALAR_WORDS + 2 * RMAX; e += SEL_THREADS) dst[e] = src[e];
+  }
+  __syncthreads();
+  const int r = sv->r, m = sv->hist_m, hn = sv->hist_n, head = sv->hist_head;
+  const int tslot = nslots(r);
+  for (int e = t; e < 2 + 2 * r; e += SEL_THREADS) ssys[e] = sys[e];
+  for (int e = t; e < 2 * KTRIAL; e += SEL_THREADS) ssys[2 + 2 * r + e] = sys[tslot + e];
+  for (int e = t; e < hn * r; e += SEL_THREADS) {
+    const int k = e / r, i = e - k * r, slot = (head + k) % m;
+    hS[slot][i] = gh->S[slot][i];
+    hY[slot][i] = gh->Y[slot][i];
+  }
+  for (int k = t; k < hn; k += SEL_THREADS) hrho[(head + k) % m] = gh->rho[(head + k) % m];
+  for (int i = t; i < r; i += SEL_THREADS) sgz[i] = gh->gz[i];
+  __syncthreads();
+  int cond_val = 1;
+  if (t < 32) {
+    const double* sE = ssys;
+    const double* sg = ssys + 2;
+    const double* sga = ssys + 2 + r;
+    const double* sT = ssys + 2 + 2 * r;
+    int at_z = 1, stepped = 0;
+    if (t == 0) line_search_decide(sv, gsv, sE, sT, at_z, stepped);
+    at_z = __shfl_sync(0xffffffffu, at_z, 0);
+    stepped = __shfl_sync(0xffffffffu, stepped, 0);
+    __syncwarp();
+    if (stepped) {  // z += alpha d; the pair is formed at the gradient of the new z
+      for (int i = t; i < r; i += 32) sv->z[i] += sv->alpha_taken * sv->d[i];
+      if (t == 0) sv->pair_pending = 1;
+      __syncwarp();
+    }
+    if (at_z == -2) {
+      cond_val = 0;
+    } else if (at_z == -1) {
+      write_pass_points<Real>(sv, Z0, sv->alpha_base, sv->status == -1);
+      if (t == 0) sv->running = 1;
+    } else if (at_z == 0) {
+      write_pass_points<Real>(sv, Z0, 0.0, false);
+    } else {
+      // ------------------------------------------- sys holds E, g at z
+      bool saddle = false;
+      const int i0 = t, i1 = t + 32;
+      if (!sv->eval_only) {
+        if (sv->pair_pending) {
+          const double a = sv->alpha_taken;
+          const double s0 = i0 < r ? a * sv->d[i0] : 0.0, s1 = i1 < r ? a * sv->d[i1] : 0.0;
+          const double y0 = i0 < r ? sg[i0] - sgz[i0] : 0.0;
+          const double y1 = i1 < r ? sg[i1] - sgz[i1] : 0.0;
+          const double sy = warp_sum(s0 * y0 + s1 * y1);
+          const double yy = warp_sum(y0 * y0 + y1 * y1);
+          if (sy > 0.0 && isfinite(sy) && isfinite(yy)) {
+            const int slot = hn < m ? (head + hn) % m : head;
+            if (i0 < r) {
+              hS[slot][i0] = s0; hY[slot][i0] = y0;
+              gh->S[slot][i0] = s0; gh->Y[slot][i0] = y0;
+            }
+            if (i1 < r) {
+              hS[slot][i1] = s1; hY[slot][i1] = y1;
+              gh->S[slot][i1] = s1; gh->Y[slot][i1] = y1;
+            }
+            if (t == 0) {
+              hrho[slot] = 1.0 / sy;
+              gh->rho[slot] = 1.0 / sy;
+              if (hn < m) sv->hist_n = hn + 1;
+              else sv->hist_head = (head + 1) % m;
+              sv->gamma = sy / yy;
+            }
+          } else {
+            saddle = true;
+          }
+          if (t == 0) sv->pair_pending = 0;
+        }
+        for (int i = t; i < r; i += 32) gh->gz[i] = sg[i];
+      }
+      __syncwarp();
+      const int status = gradient_exits(sv, gsv, sE, sg, sga, r, true, saddle);
+      if (status != -1) {
+        if (t == 0) {
+          if (!sv->eval_only) sv->status = status;
+          sv->running = 0;
+        }
+        cond_val = 0;
+      } else {
+        // two-loop recursion: q = g; newest to oldest a_k = rho_k s_k.q,
+        // q -= a_k y_k; q *= gamma; oldest to newest b = rho_k y_k.q,
+        // q += (a_k - b) s_k; d = -q
+        const int n2 = sv->hist_n, h2 = sv->hist_head;
+        double q0 = i0 < r ? sg[i0] : 0.0, q1 = i1 < r ? sg[i1] : 0.0;
+        for (int k = n2 - 1; k >= 0; --k) {
+          const int slot = (h2 + k) % m;
+          const double sk0 = i0 < r ? hS[slot][i0] : 0.0, sk1 = i1 < r ? hS[slot][i1] : 0.0;
+          const double ak = hrho[slot] * warp_sum(sk0 * q0 + sk1 * q1);
+          if (t == 0) ha[k] = ak;
+          if (i0 < r) q0 -= ak * hY[slot][i0];
+          if (i1 < r) q1 -= ak * hY[slot][i1];
+        }
+        __syncwarp();
+        const double gm = n2 > 0 ? sv->gamma : 1.0;
+        q0 *= gm;
+        q1 *= gm;
+        for (int k = 0; k < n2; ++k) {
+          const int slot = (h2 + k) % m;
+          const double yk0 = i0 < r ? hY[slot][i0] : 0.0, yk1 = i1 < r ? hY[slot][i1] : 0.0;
+          const double b = hrho[slot] * warp_sum(yk0 * q0 + yk1 * q1);
+          const double c = ha[k] - b;
+          if (i0 < r) q0 += c * hS[slot][i0];
+          if (i1 < r) q1 += c * hS[slot][i1];
+        }
+        const double g0 = i0 < r ? sg[i0] : 0.0, g1 = i1 < r ? sg[i1] : 0.0;
+        double gd = -warp_sum(g0 * q0 + g1 * q1);
+        if (!(gd < 0.0)) {  // not a descent direction in rounding: restart
+          q0 = g0;
+          q1 = g1;
+          gd = -warp_sum(g0 * g0 + g1 * g1);
+          if (t == 0) {
+            sv->hist_n = 0;
+            sv->hist_head = 0;
+          }
+        }
+        if (i0 < r) sv->d[i0] = -q0;
+        if (i1 < r) sv->d[i1] = -q1;
+        if (t == 0) {
+          sv->gd = gd;
+          sv->alpha_base = 1.0;
+          sv->ls_iter = 0;
+          sv->have_dir = 1;
+          sv->running = 1;
+        }
+        __syncwarp();
+        write_pass_points<Real>(sv, Z0, 1.0, true);
+      }
+    }
+    for (int i = t; i < r; i += 32) gsv->g[i] = sg[i];
+  }
+  __syncthreads();
+  {
+    const double* src = reinterpret_cast<const double*>(&svs);
+    double* dst = reinterpret_cast<double*>(gsv);
+    for (int e = t; e < SV_SCALAR_WORDS + 2 * RMAX; e += SEL_THREADS) dst[e] = src[e];
+  }
+  if (use_cond && t == 0) cudaGraphSetConditional(cond, cond_val);
+}
+
 template <typename Real>
 __global__ void finish_positions_kernel(const double* __restrict__ X0,
                                         const Real* __restrict__ u, int n, double dt,
@@ -423,10 +621,11 @@ __global__ void begin_step_kernel(const double* __restrict__ X0,
 }  // namespace
 
 void launch_reduce_partials(const double* A, int rowsA, const double* B, int rowsB,
-                            int splitB, int split, int ncols, double* out, cudaStream_t s) {
+                            int splitB, int split, int ncols, double* out, cudaStream_t s,
+                            int gap0, int gapn) {
   const int threads = 256, warps = threads / 32;
-  launch_pdl(reduce_partials_kernel, dim3((ncols + warps - 1) / warps), dim3(threads), 0, s, A,
-             rowsA, B, rowsB, splitB, split, ncols, out);
+  launch_pdl(reduce_partials_kernel, dim3((ncols - gapn + warps - 1) / warps), dim3(threads), 0,
+             s, A, rowsA, B, rowsB, splitB, split, ncols, out, gap0, gapn);
 }
 
 template <typename Real>
@@ -439,6 +638,13 @@ void launch_select_direction(DevSolver* sv, const double* sys, Real* Z0,
                              unsigned long long cond, int use_cond, cudaStream_t s) {
   launch_pdl(select_direction_kernel<Real>, dim3(1), dim3(SEL_THREADS), 0, s, sv, sys, Z0, cond,
              use_cond);
+}
+
+template <typename Real>
+void launch_select_lbfgs(DevSolver* sv, DevHistory* hist, const double* sys, Real* Z0,
+                         unsigned long long cond, int use_cond, cudaStream_t s) {
+  launch_pdl(select_lbfgs_kernel<Real>, dim3(1), dim3(SEL_THREADS), 0, s, sv, hist, sys, Z0,
+             cond, use_cond);
 }
 
 template <typename Real>
@@ -457,6 +663,8 @@ void launch_begin_step(const double* X0, const double* q, const double* v, int n
   template void launch_solve_begin<R>(DevSolver*, R*, int, int, cudaStream_t);           \
   template void launch_select_direction<R>(DevSolver*, const double*, R*,                \
                                            unsigned long long, int, cudaStream_t);       \
+  template void launch_select_lbfgs<R>(DevSolver*, DevHistory*, const double*, R*,       \
+                                       unsigned long long, int, cudaStream_t);           \
   template void launch_finish_positions<R>(const double*, const R*, int, double,         \
                                            double*, double*, cudaStream_t);
 LSN_INST(float)

@@ -2,7 +2,8 @@
 from ._native import Context
 
 
-def context_from_problem(p, precision="fp32", device=0, stream=None, tol=None):
+def context_from_problem(p, precision="fp32", device=0, stream=None, tol=None,
+                         optimizer="newton", history=10):
     """p is a ``workloads.Problem``; returns a ready ``Context``."""
     c = p.config
     ctx = Context(device, stream)
@@ -13,5 +14,7 @@ def context_from_problem(p, precision="fp32", device=0, stream=None, tol=None):
     ctx.set_constraints(p.cnodes, p.targets(0))
     ctx.set_decoder(p.Ws, p.bs, c.out_scale, precision)
     ctx.set_solver(c.eps if tol is None else tol, c.max_newton, c.max_ls, c.armijo_c)
+    if optimizer != "newton":
+        ctx.set_optimizer(optimizer, history)
     ctx.set_state()
     return ctx

@@ -17,7 +17,8 @@ def test_header_declares_the_solver_calls():
     names = _declared()
     for n in ["lsn_create", "lsn_destroy", "lsn_last_error", "lsn_set_mesh",
               "lsn_set_material", "lsn_set_constraints", "lsn_set_cubature",
-              "lsn_set_ground", "lsn_set_decoder", "lsn_set_solver", "lsn_set_state",
+              "lsn_set_ground", "lsn_set_decoder", "lsn_set_solver", "lsn_set_optimizer",
+              "lsn_set_state",
               "lsn_step", "lsn_get_positions", "lsn_eval"]:
         assert n in names
 
