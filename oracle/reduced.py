@@ -16,6 +16,12 @@ inertial guess qbar = q^k + dt v^k + dt^2 g (reading of Eq. 1's "inertial
 guess determined by previous configurations and the external force") and
 quasi-static solves as the potential -sum m_v g . x_v.
 
+Ground contact (optional, off by default): the penalty
+    E_c = k/2 sum_v min(0, x_{v,z} - h)^2
+on every vertex (Sec. 5's collision examples use a penalty; reading: plane
+z = h, stiffness k, no mass weighting), with gradient k min(0, x_z - h) and
+Gauss-Newton Hessian J^T diag(k [x_z < h]) J (the penalty's own Hessian).
+
 Gradient:  g(z) = sum_e w_e J_e^T g_e + J^T M (x - qbar) / dt^2   (Eq. 11 form)
 Hessian:   K(z) = sum_e w_e J_e^T Hproj_e J_e + J^T M J / dt^2   (Gauss-Newton:
            the term sum_k dE/dx_k d2x_k/dz2 is dropped; reading).
@@ -71,10 +77,26 @@ class ReducedModel:
         self.dt = 0.0
         self.qbar = None
         self.chunk = chunk
+        self.ground_h, self.ground_k = 0.0, 0.0
 
     # -- problem data ----------------------------------------------------
     def set_targets(self, targets):
         self.targets = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
+
+    def set_ground(self, height, stiffness):
+        self.ground_h, self.ground_k = float(height), float(stiffness)
+
+    def _ground(self, x):
+        """Penalty energy, its x-gradient and its diagonal x-Hessian."""
+        n = x.shape[0]
+        g = np.zeros(n)
+        h = np.zeros(n)
+        if self.ground_k > 0.0:
+            pen = np.minimum(0.0, x[2::3] - self.ground_h)
+            g[2::3] = self.ground_k * pen
+            h[2::3] = np.where(pen < 0.0, self.ground_k, 0.0)
+            return 0.5 * self.ground_k * float(pen @ pen), g, h
+        return 0.0, g, h
 
     def set_dynamics(self, dt, qbar):
         self.dt = float(dt)
@@ -108,7 +130,7 @@ class ReducedModel:
         else:
             E -= float(np.sum(self.mass[:, None] * self.gravity[None, :]
                               * x.reshape(-1, 3)))
-        return E
+        return E + self._ground(x)[0]
 
     def energy(self, z):
         return self.energy_x(self.positions(z))
@@ -128,7 +150,7 @@ class ReducedModel:
             g += m * (x - self.qbar) / self.dt ** 2
         else:
             g -= (self.mass[:, None] * self.gravity[None, :]).ravel()
-        return g
+        return g + self._ground(x)[1]
 
     def eval(self, z):
         """E, reduced gradient g (r), Gauss-Newton reduced Hessian K (r, r)."""
@@ -157,6 +179,10 @@ class ReducedModel:
             K += (J.T * m) @ J / self.dt ** 2
         else:
             g -= J.T @ (self.mass[:, None] * self.gravity[None, :]).ravel()
+        _, gc, hc = self._ground(x)
+        if self.ground_k > 0.0:
+            g += J.T @ gc
+            K += (J.T * hc) @ J
         return E, g, 0.5 * (K + K.T)
 
 

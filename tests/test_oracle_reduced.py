@@ -142,3 +142,43 @@ def test_quasistatic_bar_solve_converges():
     assert np.max(np.abs(m.eval(sim.z)[1])) < p.config.eps
     # gravity pulls the free end down
     assert (sim.q.reshape(-1, 3)[:, 2] - p.X0[:, 2]).mean() < 0
+
+
+def test_ground_penalty_closed_form_under_rigid_translation():
+    """x = X0 + z e_z (one linear layer, a rigid vertical translation: no
+    elastic energy, no gravity): E = k/2 N_below (z - h)^2, g = k N_below
+    (z - h), K = k N_below, with N_below the bottom layer of nodes (z = 0)
+    when 0 < h - z < 0.05."""
+    mesh = make_bar(6, 3, 3, 0.05)
+    n = 3 * mesh.nv
+    W = np.zeros((n, 1), np.float32)
+    W[2::3, 0] = 100.0                       # output scale 1e-2: dx_z/dz = 1
+    dec = Decoder([W], [np.zeros(n, np.float32)], 1e-2)
+    m = ReducedModel(mesh.X0, mesh.tets, dec, 1e5, 0.45, 1000.0, (0.0, 0.0, 0.0))
+    k, h, z = 3e4, 0.01, -0.025
+    m.set_ground(h, k)
+    nb = int(np.sum(mesh.X0[:, 2] == 0.0))
+    assert nb == 6 * 3
+    E, g, K = m.eval(np.array([z]))
+    pen = z - h
+    assert E == pytest.approx(0.5 * k * nb * pen ** 2, rel=1e-12)
+    assert g[0] == pytest.approx(k * nb * pen, rel=1e-12)
+    assert K[0, 0] == pytest.approx(k * nb, rel=1e-12)
+    # above the plane the penalty vanishes
+    E0, g0, K0 = m.eval(np.array([0.02]))
+    assert E0 == pytest.approx(0.0, abs=1e-12) and abs(g0[0]) < 1e-9 and K0[0, 0] < 1e-6
+
+
+@pytest.mark.parametrize("dyn", [False, True])
+def test_gradient_with_ground_contact_matches_central_differences(dyn):
+    m = tiny_model(dyn)
+    m.set_ground(0.06, 2e4)                  # a plane through the bar's second node layer
+    z = np.random.default_rng(4).standard_normal(4) * 0.5
+    E, g, _ = m.eval(z)
+    assert m._ground(m.positions(z))[0] > 0.0
+    h = 1e-6
+    for k in range(4):
+        e = np.zeros(4)
+        e[k] = h
+        fd = (m.energy(z + e) - m.energy(z - e)) / (2 * h)
+        assert fd == pytest.approx(g[k], rel=1e-6, abs=1e-8)
