@@ -145,6 +145,18 @@ int lsn_set_decoder(lsn_ctx* ctx, int nlayers, const int* widths,
                     const float* const* W, const float* const* b,
                     double out_scale, int precision);
 
+/* Affine modes (optional; off by default): 12 coordinates appended to z,
+ * z = (z_nn, M row-major (9), t (3)), with
+ *   x(z) = X0 + out_scale * f(z_nn) + Phi z_aff,   u_v += M (X0_v - center) + t,
+ * a linear map in parallel with the network, so that a free body can
+ * translate and (to first order) rotate.  The columns of J for these
+ * coordinates are the constant Phi; constrained DOFs still follow their
+ * targets.  Every z array of the ABI then has widths[0] + 12 entries (at
+ * most 64).  Call after lsn_set_decoder; enable = 0 turns them off; center
+ * (3 doubles, host) is ignored then.  Decoder training (lsn_train_*) uses
+ * the network alone. */
+int lsn_set_affine_modes(lsn_ctx* ctx, int enable, const double* center);
+
 /* Newton controls: exit when ||g||_inf < tol_inf (Supplement, convergence
  * condition), at most max_newton iterations (Sec. 5: 1024) and max_ls line
  * search trials per iteration (Sec. 5: 128), Armijo constant armijo_c. */

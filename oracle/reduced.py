@@ -16,6 +16,15 @@ inertial guess qbar = q^k + dt v^k + dt^2 g (reading of Eq. 1's "inertial
 guess determined by previous configurations and the external force") and
 quasi-static solves as the potential -sum m_v g . x_v.
 
+Affine modes (optional, off by default): a linear map in parallel with the
+network (the "neural + linear in parallel" construction of prior subspace
+methods that the paper's related work names; reading for free bodies, which
+the network alone cannot translate or rotate):
+    x(z) = X0 + s f(z_nn) + Phi z_aff,   z = (z_nn, z_aff), z_aff in R^12,
+    u_v = M (X0_v - c) + t,   z_aff = (M_00, M_01, ..., M_22, t_0, t_1, t_2),
+with c a fixed centre (the rest centroid); Phi is constant, so its columns
+of J are Phi itself.
+
 Ground contact (optional, off by default): the penalty
     E_c = k/2 sum_v min(0, x_{v,z} - h)^2
 on every vertex (Sec. 5's collision examples use a penalty; reading: plane
@@ -52,7 +61,7 @@ CONVERGED, MAX_ITERS, LS_FAILED, NOT_SPD = 0, 1, 2, 3
 
 class ReducedModel:
     def __init__(self, X0, tets, decoder, youngs, poisson, rho, gravity,
-                 cub_idx=None, cub_w=None, cnodes=None, chunk=65536):
+                 cub_idx=None, cub_w=None, cnodes=None, chunk=65536, affine_center=None):
         self.X0 = np.asarray(X0, dtype=np.float64)
         self.tets_all = np.asarray(tets, dtype=np.int64)
         self.nv = self.X0.shape[0]
@@ -78,6 +87,15 @@ class ReducedModel:
         self.qbar = None
         self.chunk = chunk
         self.ground_h, self.ground_k = 0.0, 0.0
+        self.r_nn = decoder.r
+        self.Phi = None
+        if affine_center is not None:
+            dX = self.X0 - np.asarray(affine_center, dtype=np.float64)
+            self.Phi = np.zeros((self.n, 12))
+            for a in range(3):
+                self.Phi[a::3, 3 * a:3 * a + 3] = dX      # d u_{v,a} / d M_{a,b}
+                self.Phi[a::3, 9 + a] = 1.0               # d u_{v,a} / d t_a
+        self.r = self.r_nn + (12 if self.Phi is not None else 0)
 
     # -- problem data ----------------------------------------------------
     def set_targets(self, targets):
@@ -104,13 +122,20 @@ class ReducedModel:
 
     # -- subspace map with constraints ------------------------------------
     def positions(self, z):
-        x = self.X0.ravel() + self.dec.out(z)
+        z = np.asarray(z, dtype=np.float64)
+        x = self.X0.ravel() + self.dec.out(z[:self.r_nn])
+        if self.Phi is not None:
+            x = x + self.Phi @ z[self.r_nn:]
         x[self.cdofs] = self.targets.ravel()
         return x
 
     def positions_jac(self, z):
-        o, J = self.dec.out_jac(z)
+        z = np.asarray(z, dtype=np.float64)
+        o, J = self.dec.out_jac(z[:self.r_nn])
         x = self.X0.ravel() + o
+        if self.Phi is not None:
+            x = x + self.Phi @ z[self.r_nn:]
+            J = np.hstack([J, self.Phi])
         x[self.cdofs] = self.targets.ravel()
         J[self.cdofs, :] = 0.0
         return x, J
@@ -250,14 +275,14 @@ class ReducedSimulator:
     step solved by projective Newton or (optimizer="lbfgs") by L-BFGS."""
 
     def __init__(self, model, dt, z0=None, eps=1e-5, max_newton=1024,
-                 max_ls=128, c=1e-4, optimizer="newton", history=10):
+                 max_ls=128, c=1e-4, optimizer="newton", history=10, v0=None):
         self.optimizer, self.history = optimizer, history
         self.m = model
         self.dt = float(dt)
-        r = model.dec.r
+        r = model.r
         self.z = np.zeros(r) if z0 is None else np.asarray(z0, np.float64)
         self.q = model.positions(self.z)
-        self.v = np.zeros_like(self.q)
+        self.v = np.zeros_like(self.q) if v0 is None else np.asarray(v0, np.float64).copy()
         self.eps, self.max_newton, self.max_ls, self.c = eps, max_newton, max_ls, c
 
     def step(self, targets):
@@ -284,8 +309,13 @@ class ReducedSimulator:
 
 
 def model_from_problem(p, chunk=65536):
-    """Oracle model for a ``workloads.Problem``."""
+    """Oracle model for a ``workloads.Problem`` (with its affine modes and
+    ground plane when the workload has them)."""
     c = p.config
     dec = Decoder(p.Ws, p.bs, c.out_scale)
-    return ReducedModel(p.X0, p.tets, dec, c.youngs, c.poisson, c.density,
-                        c.gravity, p.cub_idx, p.cub_w, p.cnodes, chunk=chunk)
+    m = ReducedModel(p.X0, p.tets, dec, c.youngs, c.poisson, c.density,
+                     c.gravity, p.cub_idx, p.cub_w, p.cnodes, chunk=chunk,
+                     affine_center=getattr(p, "affine_center", None))
+    if getattr(c, "ground_k", 0.0) > 0.0:
+        m.set_ground(c.ground_h, c.ground_k)
+    return m

@@ -52,6 +52,7 @@ _SIGS = {
     "lsn_set_solver": [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                        ctypes.c_double],
     "lsn_set_optimizer": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
+    "lsn_set_affine_modes": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "lsn_set_state": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "lsn_set_dynamics": [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p],
     "lsn_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
@@ -158,6 +159,8 @@ class Context:
             raise LsnError(rc, "lsn_create failed")
         self.h = h
         self.r = None
+        self.r_nn = None
+        self.affine = False
         self.n = None
 
     def close(self):
@@ -215,7 +218,8 @@ class Context:
         wa = (ctypes.c_int * len(widths))(*widths)
         Wp = (ctypes.c_void_p * len(Ws))(*[W.ctypes.data for W in Ws])
         bp = (ctypes.c_void_p * len(bs))(*[b.ctypes.data for b in bs])
-        self.r = widths[0]
+        self.r_nn = widths[0]
+        self.r = widths[0] + (12 if self.affine else 0)  # the library keeps the affine flag
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         return self._check(self.lib.lsn_set_decoder(self.h, len(Ws), wa, Wp, bp,
                                                     float(out_scale), prec))
@@ -223,6 +227,13 @@ class Context:
     def set_solver(self, tol_inf, max_newton=1024, max_ls=128, armijo_c=1e-4):
         return self._check(self.lib.lsn_set_solver(self.h, tol_inf, max_newton, max_ls,
                                                    armijo_c))
+
+    def set_affine_modes(self, center=None):
+        """12 affine coordinates appended to z (center: 3 floats), or off (None)."""
+        c = None if center is None else _f64(center)
+        self._check(self.lib.lsn_set_affine_modes(self.h, 0 if center is None else 1, _ptr(c)))
+        self.affine = center is not None
+        self.r = self.r_nn + (12 if self.affine else 0)
 
     def set_optimizer(self, kind="newton", history=10):
         """kind: "newton" (projective Newton) or "lbfgs"; history: L-BFGS pairs."""

@@ -187,6 +187,9 @@ struct lsn_ctx {
   double* cub_w = nullptr;
   // ground
   double ground_h = 0.0, ground_k = 0.0;
+  // affine modes in parallel with the network (12 extra coordinates of z)
+  bool affine = false;
+  double acen[3] = {0.0, 0.0, 0.0};
   // decoder (host copy)
   bool have_decoder = false;
   std::vector<int> widths;
@@ -224,6 +227,9 @@ struct lsn_ctx {
 
 namespace {
 
+// dimension of z: the network's input width, plus 12 with affine modes
+int subspace_r(const lsn_ctx* c) { return c->widths[0] + (c->affine ? 12 : 0); }
+
 // ----------------------------------------------------------------- engine
 template <typename Real>
 struct Engine : EngineBase {
@@ -243,11 +249,12 @@ struct Engine : EngineBase {
   bool use_tc_last = false;  // ... and tensor-core output layer (hidden width allows TMA)
   int* tc_err = nullptr;     // device flag: a bounded wait of a tensor-core kernel ran out
   DevHistory* hist = nullptr;  // L-BFGS curvature pairs
+  double* Zd = nullptr;        // FP64 copy of the pass points (affine modes)
   int ggrid = 0;               // CTAs of the gradient-only element kernel
 
   explicit Engine(lsn_ctx* ctx) : c(ctx) {
     cudaStream_t s = c->stream;
-    r = c->widths[0];
+    r = subspace_r(c);
     L = (int)c->widths.size() - 1;
     n = c->n;
     S = c->S > 0 ? c->S : c->ne;
@@ -331,6 +338,14 @@ struct Engine : EngineBase {
     la.ground_h = c->ground_h;
     la.ground_k = c->ground_k;
     la.X0 = c->X0;
+    la.aff0 = c->affine ? c->widths[0] : -1;
+    la.zcps = zstride(C);
+    if (c->affine) {
+      Zd = dalloc<double>((size_t)zstride(C) * r);
+      ck(cudaMemsetAsync(Zd, 0, sizeof(double) * zstride(C) * r, s));
+    }
+    la.zaff = c->affine ? Zd + (size_t)c->widths[0] * zstride(C) : nullptr;
+    for (int i = 0; i < 3; ++i) la.acen[i] = c->acen[i];
     ea.S = S;
     ea.r = r;
     ea.n = n;
@@ -363,6 +378,7 @@ struct Engine : EngineBase {
     h.max_newton = c->max_newton;
     h.kind = kind;
     h.hist_m = c->hist_m;
+    h.zd = Zd;
     h.gamma = 1.0;
     h.status = -1;
     ck(cudaMemcpyAsync(sv, &h, sizeof(h), cudaMemcpyHostToDevice, s));
@@ -389,6 +405,7 @@ struct Engine : EngineBase {
     dfree(part_el);
     dfree(tc_err);
     dfree(hist);
+    dfree(Zd);
     dfree(sys);
     dfree(sv);
   }
@@ -847,8 +864,9 @@ int lsn_set_decoder(lsn_ctx* c, int nlayers, const int* widths, const float* con
   if (!c) return LSN_ERR_ARG;
   if (c->n == 0) return fail(c, LSN_ERR_STATE, "set_decoder: call lsn_set_mesh first");
   if (nlayers < 1 || !widths || !W || !b) return fail(c, LSN_ERR_ARG, "set_decoder: bad layers");
-  if (widths[0] < 1 || widths[0] > RMAX)
-    return fail(c, LSN_ERR_ARG, "set_decoder: subspace dimension must be in [1, 64]");
+  if (widths[0] < 1 || widths[0] + (c->affine ? 12 : 0) > RMAX)
+    return fail(c, LSN_ERR_ARG,
+                "set_decoder: subspace dimension (with affine modes) must be in [1, 64]");
   if (widths[nlayers] != c->n)
     return fail(c, LSN_ERR_ARG, "set_decoder: last width must equal 3 * nv");
   if (precision < LSN_PREC_FP64 || precision > LSN_PREC_BF16)
@@ -874,7 +892,23 @@ int lsn_set_decoder(lsn_ctx* c, int nlayers, const int* widths, const float* con
   c->precision = precision;
   c->have_decoder = true;
   c->dirty = true;
-  c->z0.assign(widths[0], 0.0);
+  c->z0.assign(subspace_r(c), 0.0);
+  c->z_pending = true;
+  return LSN_OK;
+}
+
+int lsn_set_affine_modes(lsn_ctx* c, int enable, const double* center) {
+  if (!c) return LSN_ERR_ARG;
+  if (!c->have_decoder) return fail(c, LSN_ERR_STATE, "set_affine_modes: set the decoder first");
+  if (enable && (!center || !std::isfinite(center[0]) || !std::isfinite(center[1]) ||
+                 !std::isfinite(center[2])))
+    return fail(c, LSN_ERR_ARG, "set_affine_modes: bad centre");
+  if (enable && c->widths[0] + 12 > RMAX)
+    return fail(c, LSN_ERR_ARG, "set_affine_modes: network input width + 12 exceeds 64");
+  c->affine = enable != 0;
+  for (int i = 0; i < 3; ++i) c->acen[i] = enable ? center[i] : 0.0;
+  c->dirty = true;
+  c->z0.assign(subspace_r(c), 0.0);
   c->z_pending = true;
   return LSN_OK;
 }
@@ -949,7 +983,7 @@ int lsn_set_state(lsn_ctx* c, const double* z, const double* q, const double* v)
   LSN_GUARD_BEGIN
   int rc = prepare(c);
   if (rc != LSN_OK) return rc;
-  const int r = c->widths[0];
+  const int r = subspace_r(c);
   cudaStream_t s = c->stream;
   if (z) {
     upload(&c->eng->sv->z[0], z, sizeof(double) * r, s);
@@ -999,7 +1033,7 @@ int lsn_eval(lsn_ctx* c, const double* z, double* E, double* g, double* K) {
   LSN_GUARD_BEGIN
   int rc = prepare(c);
   if (rc != LSN_OK) return rc;
-  const int r = c->widths[0];
+  const int r = subspace_r(c);
   if (z) {
     upload(&c->eng->sv->z[0], z, sizeof(double) * r, c->stream);
     ck(cudaMemcpyAsync(c->z0.data(), &c->eng->sv->z[0], sizeof(double) * r,
@@ -1033,8 +1067,8 @@ int lsn_decode(lsn_ctx* c, const double* z, double* x_out, double* J_out) {
   int rc = prepare(c);
   if (rc != LSN_OK) return rc;
   if (z) {
-    upload(&c->eng->sv->z[0], z, sizeof(double) * c->widths[0], c->stream);
-    ck(cudaMemcpyAsync(c->z0.data(), &c->eng->sv->z[0], sizeof(double) * c->widths[0],
+    upload(&c->eng->sv->z[0], z, sizeof(double) * subspace_r(c), c->stream);
+    ck(cudaMemcpyAsync(c->z0.data(), &c->eng->sv->z[0], sizeof(double) * subspace_r(c),
                        cudaMemcpyDeviceToHost, c->stream));
     ck(cudaStreamSynchronize(c->stream));
   }
@@ -1052,7 +1086,7 @@ int lsn_step(lsn_ctx* c, const double* z_in, double dt, double* z_out, lsn_stats
   int rc = prepare(c);
   if (rc != LSN_OK) return rc;
   cudaStream_t s = c->stream;
-  const int r = c->widths[0];
+  const int r = subspace_r(c);
   if (!c->q_valid) {  // q = x(current z), v = 0
     rc = lsn_set_state(c, nullptr, nullptr, nullptr);
     if (rc != LSN_OK) return rc;
@@ -1154,7 +1188,7 @@ int lsn_get_state(lsn_ctx* c, double* z, double* q, double* v) {
   LSN_GUARD_BEGIN
   int rc = prepare(c);
   if (rc != LSN_OK) return rc;
-  if (z) download(z, &c->eng->sv->z[0], sizeof(double) * c->widths[0], c->stream);
+  if (z) download(z, &c->eng->sv->z[0], sizeof(double) * subspace_r(c), c->stream);
   if (q) download(q, c->q, sizeof(double) * c->n, c->stream);
   if (v) download(v, c->v, sizeof(double) * c->n, c->stream);
   ck(cudaStreamSynchronize(c->stream));

@@ -251,6 +251,21 @@ __device__ __forceinline__ void row_terms(const LastArgs& la, double inv_dt2, in
   }
 }
 
+// Affine modes: the displacement M (X0_v - c) + t of DOF (v, comp) at the
+// pass point of column `col` (FP64 copy of the point), and the constant
+// Jacobian entry of affine coordinate k (0..8: M row-major, 9..11: t).
+__device__ __forceinline__ double affine_disp(const LastArgs& la, int comp, const double (&dX)[3],
+                                              int col) {
+  const double* Za = la.zaff;
+  const int s = la.zcps;
+  return Za[(3 * comp) * s + col] * dX[0] + Za[(3 * comp + 1) * s + col] * dX[1] +
+         Za[(3 * comp + 2) * s + col] * dX[2] + Za[(9 + comp) * s + col];
+}
+__device__ __forceinline__ double affine_jac(int comp, const double (&dX)[3], int k) {
+  if (k < 9) return (k / 3 == comp) ? dX[k - 3 * comp] : 0.0;
+  return (k - 9 == comp) ? 1.0 : 0.0;
+}
+
 // ------------------------------------------------------------ output layer
 constexpr int LBM = 64;        // rows per tile of the output layer
 constexpr int LNT = KP * LBM;  // threads per CTA
@@ -299,6 +314,7 @@ __global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
     const int v = m / 3, comp = m - 3 * v;
     // per-row constants, fetched before the GEMM
     double mv = 0.0, ub = 0.0, x0 = 0.0, bm = 0.0;
+    double dX[3] = {0.0, 0.0, 0.0};  // X0_v - c of the affine modes
     int slot = -1;
     if (live) {
       mv = la.mass[v];
@@ -306,6 +322,8 @@ __global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
       x0 = la.X0[m];
       slot = la.cslot[v];
       bm = (double)b[m];
+      if (la.aff0 >= 0)
+        for (int k = 0; k < 3; ++k) dX[k] = la.X0[3 * v + k] - la.acen[k];
     }
     Real acc[RQ];
     skinny_gemm<Real, CQ, LBM>(W, M, K, Zin, CPs, m0, Ws, Zs, acc);
@@ -313,10 +331,14 @@ __global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
     const double cu = (live && slot >= 0) ? la.cu[3 * slot + comp] : 0.0;
     // value at y0 and the row terms
     double u0 = la.scale * ((double)acc[0] + bm);
+    if (la.aff0 >= 0 && live) u0 += affine_disp(la, comp, dX, 0);
     if (slot >= 0) u0 = cu;
     const Real u0r = (Real)u0;
     double e = 0.0, gv = 0.0, kv = 0.0;
-    if (live) row_terms(la, inv_dt2, comp, mv, ub, x0, (double)u0r, e, gv, kv);
+    // (with affine modes the row terms take the unrounded displacement: a free
+    // body's u is large, and its rounding would swamp the inertia force)
+    if (live)
+      row_terms(la, inv_dt2, comp, mv, ub, x0, la.aff0 >= 0 ? u0 : (double)u0r, e, gv, kv);
     if (q == 0) {
       if (live) {
         u_out[m] = u0r;
@@ -330,7 +352,11 @@ __global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
 #pragma unroll
     for (int c = 1; c < RQ; ++c) {
       if ((c % KP) != q || c >= nj) continue;
-      const Real jv = (live && slot < 0) ? (Real)(la.scale * (double)acc[c]) : Real(0);
+      const bool aff = la.aff0 >= 0 && c - 1 >= la.aff0;
+      const Real jv = (live && slot < 0)
+                          ? (Real)(aff ? affine_jac(comp, dX, c - 1 - la.aff0)
+                                       : la.scale * (double)acc[c])
+                          : Real(0);
       if (live) J_out[(size_t)m * r + (c - 1)] = jv;
       Js[row * OS + (c - 1)] = jv;
     }
@@ -340,11 +366,12 @@ __global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
 #pragma unroll
       for (int c = 0; c < RQ; ++c)
         if (c == nj + q - 1) ut = la.scale * ((double)acc[c] + bm);
+      if (la.aff0 >= 0) ut += affine_disp(la, comp, dX, nj + q - 1);
       if (slot >= 0) ut = cu;
       const Real utr = (Real)ut;
       u_trial[(size_t)(q - 1) * M + m] = utr;
       double et, g2, k2;
-      row_terms(la, inv_dt2, comp, mv, ub, x0, (double)utr, et, g2, k2);
+      row_terms(la, inv_dt2, comp, mv, ub, x0, la.aff0 >= 0 ? ut : (double)utr, et, g2, k2);
       etr += et;
       atr += fabs(et);
     }

@@ -65,6 +65,7 @@ struct DevSolver {
   int pair_pending;    // L-BFGS: a step was taken; its pair is formed at the next gradient
   int pad_[2];
   double gamma;        // L-BFGS: initial scaling s^T y / y^T y of the newest pair
+  double* zd;          // FP64 copy of the pass points [r][zstride(C)] (affine modes) or null
   double z[RMAX];      // current iterate
   double d[RMAX];      // Newton direction
   double g[RMAX];      // reduced gradient at z
@@ -107,6 +108,12 @@ struct LastArgs {            // data of the output-layer epilogue
   double grav[3];
   double ground_h, ground_k; // ground plane, k = 0 off
   const double* X0;          // rest positions (n)
+  // affine modes (aff0 < 0: none): coordinates aff0 .. aff0 + 11 of z are
+  // (M row-major, t) with u_v += M (X0_v - acen) + t; zaff points at row aff0
+  // of the FP64 copy of the pass points (column stride zcps)
+  int aff0, zcps;
+  const double* zaff;
+  double acen[3];
 };
 
 // Activations are unit-major Z[k][c] with column stride zstride(C).

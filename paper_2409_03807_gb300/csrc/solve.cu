@@ -60,6 +60,7 @@ __device__ void write_pass_points(DevSolver* sv, Real* Z0, double a0, bool with_
     const double v = sv->z[i] + a * sv->d[i];
     const int col = j == 0 ? 0 : r + j;
     Z0[i * CPs + col] = (Real)v;
+    if (sv->zd) sv->zd[i * CPs + col] = v;
   }
 }
 
@@ -85,10 +86,12 @@ __global__ void solve_begin_kernel(DevSolver* sv, Real* Z0, int C, int eval_only
     sv->gamma = 1.0;
   }
   const int CPs = zstride(C);
+  double* zd = sv->zd;
   for (int e = threadIdx.x; e < CPs * r; e += blockDim.x) {
     const int i = e / CPs, c = e - i * CPs;
-    Z0[e] = c >= C ? Real(0)
-                   : ((c == 0 || c > r) ? (Real)sv->z[i] : (i == c - 1 ? Real(1) : Real(0)));
+    const double v = c >= C ? 0.0 : ((c == 0 || c > r) ? sv->z[i] : (i == c - 1 ? 1.0 : 0.0));
+    Z0[e] = (Real)v;
+    if (zd) zd[e] = v;
   }
 }
 

@@ -106,6 +106,48 @@ __device__ __forceinline__ void row_terms_tc(const LastArgs& la, float inv_dt2, 
   }
 }
 
+// Affine modes, in FP64 (a free body's displacement is large: its FP32
+// rounding times the body's m / dt^2 would swamp the inertia force): the
+// displacement M (X0_v - c) + t of DOF (v, comp) at the pass point of column
+// `col`, and the constant Jacobian entry of affine coordinate k (0..8: M
+// row-major, 9..11: t).
+__device__ __forceinline__ double affine_disp_tc(const LastArgs& la, int comp,
+                                                 const double (&dX)[3], int col) {
+  const double* Za = la.zaff;
+  const int s = la.zcps;
+  return Za[(3 * comp) * s + col] * dX[0] + Za[(3 * comp + 1) * s + col] * dX[1] +
+         Za[(3 * comp + 2) * s + col] * dX[2] + Za[(9 + comp) * s + col];
+}
+// The row terms of row_terms_tc with the displacement difference taken in
+// FP64 (rows of a body with affine modes)
+__device__ __forceinline__ void row_terms_tc_aff(const LastArgs& la, float inv_dt2, int comp,
+                                                 float mv, double ubar, double x0, double u,
+                                                 float& e, float& gv, float& kv) {
+  if (inv_dt2 > 0.f) {
+    const float diff = (float)(u - ubar);
+    e = 0.5f * inv_dt2 * mv * diff * diff;
+    gv = inv_dt2 * mv * diff;
+    kv = inv_dt2 * mv;
+  } else {
+    e = (float)(-(double)mv * la.grav[comp] * u);
+    gv = -mv * (float)la.grav[comp];
+    kv = 0.f;
+  }
+  if (la.ground_k > 0.0 && comp == 2) {
+    const float gk = (float)la.ground_k;
+    const float pen = (float)(x0 + u - la.ground_h);
+    if (pen < 0.f) {
+      e += 0.5f * gk * pen * pen;
+      gv += gk * pen;
+      kv += gk;
+    }
+  }
+}
+__device__ __forceinline__ double affine_jac(int comp, const double (&dX)[3], int k) {
+  if (k < 9) return (k / 3 == comp) ? dX[k - 3 * comp] : 0.0;
+  return (k - 9 == comp) ? 1.0 : 0.0;
+}
+
 // Z[k][c] (unit-major, column stride CPs) -> B operand rows c < Cp, K-major
 template <bool BF>
 __global__ void pack_kernel(const float* __restrict__ Z, int H, int C, int CPs, int Cp,
@@ -324,6 +366,7 @@ __global__ void __launch_bounds__(TNT, 1)
       const bool live = m < M;
       const int v = m / 3, comp = m - 3 * v;
       float mv = 0.f, ub = 0.f, x0 = 0.f, bm = 0.f;
+      double dX[3] = {0.0, 0.0, 0.0};  // X0_v - c of the affine modes
       int slot = -1;
       if (live) {
         mv = (float)la.mass[v];
@@ -331,6 +374,8 @@ __global__ void __launch_bounds__(TNT, 1)
         x0 = (float)la.X0[m];
         slot = la.cslot[v];
         bm = b[m];
+        if (la.aff0 >= 0)
+          for (int k = 0; k < 3; ++k) dX[k] = la.X0[3 * v + k] - la.acen[k];
       }
       const int ab = i & 1;
       // every decision to stop is taken by all 128 epilogue threads together
@@ -356,10 +401,16 @@ __global__ void __launch_bounds__(TNT, 1)
           const int c = c0 + j;
           const float a = __uint_as_float(vv[j]);
           if (c == 0) {
-            const float u0r = slot >= 0 ? cu : scale * (a + bm);
+            const bool aff = la.aff0 >= 0 && live && slot < 0;
+            const double u0d = aff ? (double)(scale * (a + bm)) + affine_disp_tc(la, comp, dX, 0)
+                                   : 0.0;
+            const float u0r = slot >= 0 ? cu : (aff ? (float)u0d : scale * (a + bm));
             float e = 0.f, kv = 0.f;
             if (live) {
-              row_terms_tc(la, inv_dt2, comp, mv, ub, x0, u0r, e, gv, kv);
+              if (aff)
+                row_terms_tc_aff(la, inv_dt2, comp, mv, la.ubar[m], la.X0[m], u0d, e, gv, kv);
+              else
+                row_terms_tc(la, inv_dt2, comp, mv, ub, x0, u0r, e, gv, kv);
               u_out[m] = u0r;
               facc_add(eacc, e);
               facc_add(eabs, fabsf(e));
@@ -369,7 +420,10 @@ __global__ void __launch_bounds__(TNT, 1)
             // Jacobian row into the staging tile; sqrt(kv) J row into the
             // Gram operand (K-major: operand row = column, K = tile row)
             const int cc = c - 1;
-            const float jv = jlive ? scale * a : 0.f;
+            const float jv = !jlive ? 0.f
+                             : (la.aff0 >= 0 && cc >= la.aff0)
+                                 ? (float)affine_jac(comp, dX, cc - la.aff0)
+                                 : scale * a;
             Js[row * JS + cc] = jv;
             if (jok) {
               const float gval = wk * jv;
@@ -386,10 +440,16 @@ __global__ void __launch_bounds__(TNT, 1)
             }
           } else if (c >= nj && c < C && live) {
             const int tj = c - nj;
-            const float utr = slot >= 0 ? cu : scale * (a + bm);
+            const bool aff = la.aff0 >= 0 && slot < 0;
+            const double utd =
+                aff ? (double)(scale * (a + bm)) + affine_disp_tc(la, comp, dX, c) : 0.0;
+            const float utr = slot >= 0 ? cu : (aff ? (float)utd : scale * (a + bm));
             u_trial[(size_t)tj * M + m] = utr;
             float et2, g2, k2;
-            row_terms_tc(la, inv_dt2, comp, mv, ub, x0, utr, et2, g2, k2);
+            if (aff)
+              row_terms_tc_aff(la, inv_dt2, comp, mv, la.ubar[m], la.X0[m], utd, et2, g2, k2);
+            else
+              row_terms_tc(la, inv_dt2, comp, mv, ub, x0, utr, et2, g2, k2);
 #pragma unroll
             for (int x = 0; x < KTRIAL; ++x)
               if (x == tj) {

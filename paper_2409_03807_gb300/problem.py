@@ -13,8 +13,12 @@ def context_from_problem(p, precision="fp32", device=0, stream=None, tol=None,
         ctx.set_cubature(p.cub_idx, p.cub_w)
     ctx.set_constraints(p.cnodes, p.targets(0))
     ctx.set_decoder(p.Ws, p.bs, c.out_scale, precision)
+    if getattr(p, "affine_center", None) is not None:
+        ctx.set_affine_modes(p.affine_center)
+    if getattr(c, "ground_k", 0.0) > 0.0:
+        ctx.set_ground(c.ground_h, c.ground_k)
     ctx.set_solver(c.eps if tol is None else tol, c.max_newton, c.max_ls, c.armijo_c)
     if optimizer != "newton":
         ctx.set_optimizer(optimizer, history)
-    ctx.set_state()
+    ctx.set_state(v=getattr(p, "v0", None))
     return ctx

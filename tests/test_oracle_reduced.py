@@ -182,3 +182,65 @@ def test_gradient_with_ground_contact_matches_central_differences(dyn):
         e[k] = h
         fd = (m.energy(z + e) - m.energy(z - e)) / (2 * h)
         assert fd == pytest.approx(g[k], rel=1e-6, abs=1e-8)
+
+
+def _affine_model(zero_network, gravity=(0.0, 0.0, 0.0), seed=0):
+    mesh = make_bar(6, 3, 3, 0.05)
+    n = 3 * mesh.nv
+    Ws, bs = xavier_decoder([4, 16, 16, n], seed)
+    if zero_network:
+        Ws[-1] = np.zeros_like(Ws[-1])
+    c = mesh.X0.mean(0)
+    m = ReducedModel(mesh.X0, mesh.tets, Decoder(Ws, bs, 1e-2), 1e5, 0.45, 1000.0, gravity,
+                     affine_center=c)
+    return m, mesh, c
+
+
+def test_affine_modes_map_closed_form():
+    """Network output zero: z_aff = (M, t) moves every vertex to
+    X0 + M (X0 - c) + t, so every tet has F = I + M and the elastic energy is
+    V_total Psi(I + M); a pure translation costs nothing."""
+    from oracle import snh
+    m, mesh, c = _affine_model(True)
+    assert m.r == 4 + 12
+    rng = np.random.default_rng(3)
+    M = 0.05 * rng.standard_normal((3, 3))
+    t = rng.standard_normal(3)
+    z = np.concatenate([rng.standard_normal(4), M.ravel(), t])
+    x = m.positions(z).reshape(-1, 3)
+    assert np.allclose(x, mesh.X0 + (mesh.X0 - c) @ M.T + t, rtol=0, atol=1e-14)
+    mu, lam = snh.lame(1e5, 0.45)
+    vol = fem.rest_shape(mesh.X0, mesh.tets)[1]
+    psi = float(snh.psi(np.eye(3) + M, mu, lam))
+    assert m.energy(z) == pytest.approx(vol.sum() * psi, rel=1e-10)
+    zt = np.concatenate([np.zeros(4 + 9), t])
+    assert abs(m.energy(zt)) < 1e-9
+
+
+def test_affine_jacobian_columns_match_central_differences():
+    m, _, _ = _affine_model(False)
+    z = np.random.default_rng(5).standard_normal(16) * 0.3
+    _, J = m.positions_jac(z)
+    h = 1e-6
+    for k in range(16):
+        e = np.zeros(16)
+        e[k] = h
+        fd = (m.positions(z + e) - m.positions(z - e)) / (2 * h)
+        assert np.allclose(J[:, k], fd, rtol=1e-6, atol=1e-9), k
+
+
+def test_affine_free_fall_is_exact_projectile_motion():
+    """Network output zero, no contact: one implicit-Euler step from rest with
+    a uniform initial velocity v0 lands on x = X0 + dt v0 + dt^2 g (the
+    inertial guess is reachable at zero elastic energy), and v becomes
+    v0 + dt g."""
+    g = np.array([0.0, 0.0, -9.8])
+    m, mesh, _ = _affine_model(True, gravity=tuple(g))
+    v0 = np.tile([0.3, -0.2, 0.5], mesh.nv)
+    dt = 0.01
+    sim = ReducedSimulator(m, dt, eps=1e-10, v0=v0)
+    st = sim.step(np.zeros((0, 3)))
+    assert st.status == CONVERGED
+    assert np.allclose(sim.q, mesh.X0.ravel() + dt * v0 + dt * dt * np.tile(g, mesh.nv),
+                       rtol=0, atol=1e-11)
+    assert np.allclose(sim.v, v0 + dt * np.tile(g, mesh.nv), rtol=0, atol=1e-9)
