@@ -147,8 +147,11 @@ def workload_config(args, p, world):
     c = p.config
     W, K = args.warmup, args.steps
     return {"workload": args.workload,
-            "mesh": f"{c.dims[0]}x{c.dims[1]}x{c.dims[2]} nodes, {p.ne} tets, n={p.n}",
-            "r": c.r, "decoder": "-".join(map(str, p.widths)),
+            "mesh": (f"voxel torus R={c.torus[0]} a={c.torus[1]} h={c.h}, {p.ne} tets, n={p.n}, "
+                     f"ground k={c.ground_k:g}" if c.mesh == "torus" else
+                     f"{c.dims[0]}x{c.dims[1]}x{c.dims[2]} nodes, {p.ne} tets, n={p.n}"),
+            "r": subspace_dim(p), "decoder": "-".join(map(str, p.widths)),
+            "affine_modes": 12 if p.affine_center is not None else 0,
             "cubature": len(p.cub_idx), "dt": c.dt, "tol_inf": c.eps,
             "precision": args.precision + " (FP64 Cholesky + line search)",
             "optimizer": (f"L-BFGS (history {args.history})" if args.optimizer == "lbfgs"
@@ -180,7 +183,7 @@ def oracle_sim(p, args):
     c = p.config
     return ReducedSimulator(model_from_problem(p), c.dt, eps=c.eps, max_newton=c.max_newton,
                             max_ls=c.max_ls, c=c.armijo_c, optimizer=args.optimizer,
-                            history=args.history)
+                            history=args.history, v0=p.v0)
 
 
 def oracle_run(p, args, frames, budget_s):
@@ -240,11 +243,16 @@ def run_reference(args, world, rank):
 
 
 # --------------------------------------------------------------------- ours
+def subspace_dim(p):
+    """Dimension of z: the network's input width (+ 12 affine modes)."""
+    return p.config.r + (12 if p.affine_center is not None else 0)
+
+
 def algorithmic_bytes(cls, p, precision):
     """Bytes one launch of kernel class `cls` must move at minimum (each datum
     once): weights and inputs read, outputs written."""
     c = p.config
-    n, r, H = p.n, c.r, p.widths[-2]
+    n, r, H = p.n, subspace_dim(p), p.widths[-2]
     b = 8 if precision == "fp64" else 4
     w = 2 if precision == "bf16" else b          # stored bytes of W_L
     C = r + 4                                    # value, r tangents, 3 trial columns
@@ -288,7 +296,7 @@ def run_ours(args, world, rank, local):
     frames = W + K
     targets = torch.tensor(np.stack([p.targets(k) for k in range(1, frames + 1)]),
                            dtype=torch.float64, device=dev)
-    z_dev = torch.zeros(c.r, dtype=torch.float64, device=dev)
+    z_dev = torch.zeros(subspace_dim(p), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
 
@@ -367,7 +375,7 @@ def run_ours(args, world, rank, local):
     ctx.set_state(*snap)
     pin_t = torch.empty((frames, p.cnodes.shape[0], 3), dtype=torch.float64).pin_memory()
     pin_t.copy_(targets.cpu())
-    z_host = torch.zeros(c.r, dtype=torch.float64).pin_memory()
+    z_host = torch.zeros(subspace_dim(p), dtype=torch.float64).pin_memory()
     q_host = torch.zeros(p.n, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -380,7 +388,7 @@ def run_ours(args, world, rank, local):
     e2e_s = time.perf_counter() - t0
     e2e = {"value": world * K / e2e_s, "unit": "steps/s",
            "h2d_bytes_per_step": int(p.cnodes.shape[0] * 3 * 8),
-           "d2h_bytes_per_step": int(c.r * 8 + p.n * 8)}
+           "d2h_bytes_per_step": int(subspace_dim(p) * 8 + p.n * 8)}
 
     replay_ms = sum(v[2] for v in prof.values())
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")

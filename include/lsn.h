@@ -55,7 +55,10 @@ enum lsn_status {
   LSN_NOT_SPD = 3,         /* reduced Hessian not positive definite after the
                               diagonal-shift retries                          */
   LSN_PRECISION_FLOOR = 4, /* line search stalled at the rounding level of the
-                              chosen precision while ||g||_inf < 100 tol       */
+                              chosen precision while ||g||_inf < 100 tol (FP32
+                              and tensor-core forms: also after 4 iterations
+                              without a 10 % drop of ||g||_inf whose accepted
+                              steps were all shorter than 2^-10)              */
   LSN_SADDLE = 5,          /* L-BFGS: no positive curvature along the accepted
                               step (s^T y <= 0; exit II of Sec. 5)             */
   LSN_ERR_ARG = -1,        /* invalid argument or size                         */
@@ -147,11 +150,13 @@ int lsn_set_decoder(lsn_ctx* ctx, int nlayers, const int* widths,
 
 /* Affine modes (optional; off by default): 12 coordinates appended to z,
  * z = (z_nn, M row-major (9), t (3)), with
- *   x(z) = X0 + out_scale * f(z_nn) + Phi z_aff,   u_v += M (X0_v - center) + t,
- * a linear map in parallel with the network, so that a free body can
- * translate and (to first order) rotate.  The columns of J for these
- * coordinates are the constant Phi; constrained DOFs still follow their
- * targets.  Every z array of the ABI then has widths[0] + 12 entries (at
+ *   x(z) = X0 + out_scale * (f(z_nn) + Phi z_aff),
+ *   i.e. u_v += out_scale * (M (X0_v - center) + t),
+ * a linear map in parallel with the network (inside the same output scale,
+ * so that one gradient tolerance suits both kinds of coordinate), so that a
+ * free body can translate and (to first order) rotate.  The columns of J
+ * for these coordinates are the constant out_scale * Phi; constrained DOFs
+ * still follow their targets.  Every z array of the ABI then has widths[0] + 12 entries (at
  * most 64).  Call after lsn_set_decoder; enable = 0 turns them off; center
  * (3 doubles, host) is ignored then.  Decoder training (lsn_train_*) uses
  * the network alone. */

@@ -20,10 +20,15 @@ Affine modes (optional, off by default): a linear map in parallel with the
 network (the "neural + linear in parallel" construction of prior subspace
 methods that the paper's related work names; reading for free bodies, which
 the network alone cannot translate or rotate):
-    x(z) = X0 + s f(z_nn) + Phi z_aff,   z = (z_nn, z_aff), z_aff in R^12,
-    u_v = M (X0_v - c) + t,   z_aff = (M_00, M_01, ..., M_22, t_0, t_1, t_2),
-with c a fixed centre (the rest centroid); Phi is constant, so its columns
-of J are Phi itself.
+    x(z) = X0 + s (f(z_nn) + Phi z_aff),   z = (z_nn, z_aff), z_aff in R^12,
+    s Phi z_aff:  u_v = s (M (X0_v - c) + t),
+    z_aff = (M_00, M_01, ..., M_22, t_0, t_1, t_2),
+with c a fixed centre (the rest centroid) and s the decoder's output scale
+(the affine coordinates share the network coordinates' scale, so that one
+gradient tolerance suits both: in metres, the translation coordinate's
+curvature is the body's whole m / dt^2 and its gradient stalls at the
+rounding of E above the usual tolerance); s Phi is constant, so it is also
+their columns of J.
 
 Ground contact (optional, off by default): the penalty
     E_c = k/2 sum_v min(0, x_{v,z} - h)^2
@@ -95,6 +100,7 @@ class ReducedModel:
             for a in range(3):
                 self.Phi[a::3, 3 * a:3 * a + 3] = dX      # d u_{v,a} / d M_{a,b}
                 self.Phi[a::3, 9 + a] = 1.0               # d u_{v,a} / d t_a
+            self.Phi *= decoder.scale
         self.r = self.r_nn + (12 if self.Phi is not None else 0)
 
     # -- problem data ----------------------------------------------------

@@ -251,9 +251,10 @@ __device__ __forceinline__ void row_terms(const LastArgs& la, double inv_dt2, in
   }
 }
 
-// Affine modes: the displacement M (X0_v - c) + t of DOF (v, comp) at the
-// pass point of column `col` (FP64 copy of the point), and the constant
-// Jacobian entry of affine coordinate k (0..8: M row-major, 9..11: t).
+// Affine modes (scaled by the output scale, like the network): the unscaled
+// displacement M (X0_v - c) + t of DOF (v, comp) at the pass point of column
+// `col` (FP64 copy of the point), and the unscaled constant Jacobian entry of
+// affine coordinate k (0..8: M row-major, 9..11: t).
 __device__ __forceinline__ double affine_disp(const LastArgs& la, int comp, const double (&dX)[3],
                                               int col) {
   const double* Za = la.zaff;
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
     const double cu = (live && slot >= 0) ? la.cu[3 * slot + comp] : 0.0;
     // value at y0 and the row terms
     double u0 = la.scale * ((double)acc[0] + bm);
-    if (la.aff0 >= 0 && live) u0 += affine_disp(la, comp, dX, 0);
+    if (la.aff0 >= 0 && live) u0 += la.scale * affine_disp(la, comp, dX, 0);
     if (slot >= 0) u0 = cu;
     const Real u0r = (Real)u0;
     double e = 0.0, gv = 0.0, kv = 0.0;
@@ -354,8 +355,8 @@ __global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
       if ((c % KP) != q || c >= nj) continue;
       const bool aff = la.aff0 >= 0 && c - 1 >= la.aff0;
       const Real jv = (live && slot < 0)
-                          ? (Real)(aff ? affine_jac(comp, dX, c - 1 - la.aff0)
-                                       : la.scale * (double)acc[c])
+                          ? (Real)(la.scale * (aff ? affine_jac(comp, dX, c - 1 - la.aff0)
+                                                   : (double)acc[c]))
                           : Real(0);
       if (live) J_out[(size_t)m * r + (c - 1)] = jv;
       Js[row * OS + (c - 1)] = jv;
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
 #pragma unroll
       for (int c = 0; c < RQ; ++c)
         if (c == nj + q - 1) ut = la.scale * ((double)acc[c] + bm);
-      if (la.aff0 >= 0) ut += affine_disp(la, comp, dX, nj + q - 1);
+      if (la.aff0 >= 0) ut += la.scale * affine_disp(la, comp, dX, nj + q - 1);
       if (slot >= 0) ut = cu;
       const Real utr = (Real)ut;
       u_trial[(size_t)(q - 1) * M + m] = utr;

@@ -63,7 +63,8 @@ struct DevSolver {
   int hist_n;          // L-BFGS: stored curvature pairs
   int hist_head;       // L-BFGS: ring slot of the oldest pair
   int pair_pending;    // L-BFGS: a step was taken; its pair is formed at the next gradient
-  int pad_[2];
+  int tiny_steps;      // consecutive accepted steps with alpha < 2^-10
+  int pad_;
   double gamma;        // L-BFGS: initial scaling s^T y / y^T y of the newest pair
   double* zd;          // FP64 copy of the pass points [r][zstride(C)] (affine modes) or null
   double z[RMAX];      // current iterate

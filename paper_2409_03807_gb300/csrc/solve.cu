@@ -84,6 +84,7 @@ __global__ void solve_begin_kernel(DevSolver* sv, Real* Z0, int C, int eval_only
     sv->hist_head = 0;
     sv->pair_pending = 0;
     sv->gamma = 1.0;
+    sv->tiny_steps = 0;
   }
   const int CPs = zstride(C);
   double* zd = sv->zd;
@@ -202,6 +203,7 @@ __device__ void line_search_decide(DevSolver* sv, DevSolver* gsv, const double* 
     if (acc >= 0) {
       const double a = ldexp(sv->alpha_base, -acc);
       sv->alpha_taken = a;
+      sv->tiny_steps = a < 0x1p-10 ? sv->tiny_steps + 1 : 0;
       if (sv->iters < TRACE) gsv->trace_alpha[sv->iters] = a;
       sv->iters += 1;
       sv->have_dir = 0;
@@ -266,6 +268,10 @@ __device__ int gradient_exits(DevSolver* sv, DevSolver* gsv, const double* sE, c
   if (ginf < sv->tol) return 0;                                  // LSN_OK
   if (saddle) return 5;                                          // LSN_SADDLE
   if (stall >= 4 && ginf <= sv->floor_scale * gabs_max) return 4;  // PRECISION_FLOOR
+  // reduced-precision forms: the line search keeps accepting only tiny steps
+  // (the energy or the reduced Hessian is resolved no better than this)
+  if (sv->eta_scale > 0.0 && stall >= 4 && sv->tiny_steps >= 4 && ginf < 100.0 * sv->tol)
+    return 4;
   if (sv->iters >= sv->max_newton) return 1;                     // LSN_NOT_CONVERGED
   return -1;
 }

@@ -108,9 +108,10 @@ __device__ __forceinline__ void row_terms_tc(const LastArgs& la, float inv_dt2, 
 
 // Affine modes, in FP64 (a free body's displacement is large: its FP32
 // rounding times the body's m / dt^2 would swamp the inertia force): the
-// displacement M (X0_v - c) + t of DOF (v, comp) at the pass point of column
-// `col`, and the constant Jacobian entry of affine coordinate k (0..8: M
-// row-major, 9..11: t).
+// unscaled displacement M (X0_v - c) + t of DOF (v, comp) at the pass point
+// of column `col`, and the unscaled constant Jacobian entry of affine
+// coordinate k (0..8: M row-major, 9..11: t); both enter times the output
+// scale.
 __device__ __forceinline__ double affine_disp_tc(const LastArgs& la, int comp,
                                                  const double (&dX)[3], int col) {
   const double* Za = la.zaff;
@@ -402,8 +403,9 @@ __global__ void __launch_bounds__(TNT, 1)
           const float a = __uint_as_float(vv[j]);
           if (c == 0) {
             const bool aff = la.aff0 >= 0 && live && slot < 0;
-            const double u0d = aff ? (double)(scale * (a + bm)) + affine_disp_tc(la, comp, dX, 0)
-                                   : 0.0;
+            const double u0d =
+                aff ? (double)(scale * (a + bm)) + la.scale * affine_disp_tc(la, comp, dX, 0)
+                    : 0.0;
             const float u0r = slot >= 0 ? cu : (aff ? (float)u0d : scale * (a + bm));
             float e = 0.f, kv = 0.f;
             if (live) {
@@ -422,7 +424,7 @@ __global__ void __launch_bounds__(TNT, 1)
             const int cc = c - 1;
             const float jv = !jlive ? 0.f
                              : (la.aff0 >= 0 && cc >= la.aff0)
-                                 ? (float)affine_jac(comp, dX, cc - la.aff0)
+                                 ? (float)(la.scale * affine_jac(comp, dX, cc - la.aff0))
                                  : scale * a;
             Js[row * JS + cc] = jv;
             if (jok) {
@@ -442,7 +444,8 @@ __global__ void __launch_bounds__(TNT, 1)
             const int tj = c - nj;
             const bool aff = la.aff0 >= 0 && slot < 0;
             const double utd =
-                aff ? (double)(scale * (a + bm)) + affine_disp_tc(la, comp, dX, c) : 0.0;
+                aff ? (double)(scale * (a + bm)) + la.scale * affine_disp_tc(la, comp, dX, c)
+                    : 0.0;
             const float utr = slot >= 0 ? cu : (aff ? (float)utd : scale * (a + bm));
             u_trial[(size_t)tj * M + m] = utr;
             float et2, g2, k2;

@@ -50,10 +50,11 @@ def test_positions_jacobian_with_affine_modes(pkg, prec):
     t = TOL[prec]
     assert rel(x - p.X0.ravel(), x_ref - p.X0.ravel()) < 10 * t["x"]
     assert rel(J, J_ref) < 10 * t["J"]
-    # the affine columns are the constant map itself
+    # the affine columns are the constant map itself (times the output scale)
+    s = p.config.out_scale
     dX = p.X0 - p.affine_center
-    assert np.allclose(J[2::3, r - 12 + 6:r - 12 + 9], dX, rtol=0, atol=1e-6)
-    assert np.allclose(J[0::3, r - 1], 0.0) and np.allclose(J[2::3, r - 1], 1.0)
+    assert np.allclose(J[2::3, r - 12 + 6:r - 12 + 9], s * dX, rtol=0, atol=1e-8)
+    assert np.allclose(J[0::3, r - 1], 0.0) and np.allclose(J[2::3, r - 1], s)
     ctx.close()
 
 
@@ -70,7 +71,7 @@ def test_energy_gradient_hessian_with_affine_modes_and_contact(pkg, prec):
     r = c.r + 12
     for _ in range(2):
         z = rng.standard_normal(r) * 0.2
-        z[r - 1] = -0.2          # translate down into the ground
+        z[r - 1] = -2.0          # translate down (2 cm) into the ground
         assert m._ground(m.positions(z))[0] > 0.0
         E, g, K = ctx.eval(z)
         E_ref, g_ref, K_ref = m.eval(z)
