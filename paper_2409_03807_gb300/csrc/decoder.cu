@@ -271,7 +271,8 @@ __device__ __forceinline__ double affine_jac(int comp, const double (&dX)[3], in
 constexpr int LBM = 64;        // rows per tile of the output layer
 constexpr int LNT = KP * LBM;  // threads per CTA
 
-template <typename Real, int CQ>
+// AFF: the body has affine modes (a separate instantiation)
+template <typename Real, int CQ, bool AFF>
 __global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
                                                    const Real* __restrict__ b, int M, int K,
                                                    const Real* __restrict__ Zin, int C,
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
       x0 = la.X0[m];
       slot = la.cslot[v];
       bm = (double)b[m];
-      if (la.aff0 >= 0)
+      if (AFF)
         for (int k = 0; k < 3; ++k) dX[k] = la.X0[3 * v + k] - la.acen[k];
     }
     Real acc[RQ];
@@ -332,14 +333,14 @@ __global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
     const double cu = (live && slot >= 0) ? la.cu[3 * slot + comp] : 0.0;
     // value at y0 and the row terms
     double u0 = la.scale * ((double)acc[0] + bm);
-    if (la.aff0 >= 0 && live) u0 += la.scale * affine_disp(la, comp, dX, 0);
+    if (AFF && live) u0 += la.scale * affine_disp(la, comp, dX, 0);
     if (slot >= 0) u0 = cu;
     const Real u0r = (Real)u0;
     double e = 0.0, gv = 0.0, kv = 0.0;
     // (with affine modes the row terms take the unrounded displacement: a free
     // body's u is large, and its rounding would swamp the inertia force)
     if (live)
-      row_terms(la, inv_dt2, comp, mv, ub, x0, la.aff0 >= 0 ? u0 : (double)u0r, e, gv, kv);
+      row_terms(la, inv_dt2, comp, mv, ub, x0, AFF ? u0 : (double)u0r, e, gv, kv);
     if (q == 0) {
       if (live) {
         u_out[m] = u0r;
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
 #pragma unroll
     for (int c = 1; c < RQ; ++c) {
       if ((c % KP) != q || c >= nj) continue;
-      const bool aff = la.aff0 >= 0 && c - 1 >= la.aff0;
+      const bool aff = AFF && c - 1 >= la.aff0;
       const Real jv = (live && slot < 0)
                           ? (Real)(la.scale * (aff ? affine_jac(comp, dX, c - 1 - la.aff0)
                                                    : (double)acc[c]))
@@ -367,12 +368,12 @@ __global__ void __launch_bounds__(LNT) last_kernel(const Real* __restrict__ W,
 #pragma unroll
       for (int c = 0; c < RQ; ++c)
         if (c == nj + q - 1) ut = la.scale * ((double)acc[c] + bm);
-      if (la.aff0 >= 0) ut += la.scale * affine_disp(la, comp, dX, nj + q - 1);
+      if (AFF) ut += la.scale * affine_disp(la, comp, dX, nj + q - 1);
       if (slot >= 0) ut = cu;
       const Real utr = (Real)ut;
       u_trial[(size_t)(q - 1) * M + m] = utr;
       double et, g2, k2;
-      row_terms(la, inv_dt2, comp, mv, ub, x0, la.aff0 >= 0 ? ut : (double)utr, et, g2, k2);
+      row_terms(la, inv_dt2, comp, mv, ub, x0, AFF ? ut : (double)utr, et, g2, k2);
       etr += et;
       atr += fabs(et);
     }
@@ -479,12 +480,18 @@ void run_last(const Real* W, const Real* b, int M, int K, const Real* Zin, int C
   const size_t sm = last_smem<Real>(la.r, CPs);
   static size_t set = 0;
   if (sm > set) {
-    cudaFuncSetAttribute(last_kernel<Real, CQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sm);
+    cudaFuncSetAttribute(last_kernel<Real, CQ, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(last_kernel<Real, CQ, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     set = sm;
   }
-  last_kernel<Real, CQ><<<grid, LNT, sm, s>>>(W, b, M, K, Zin, C, CPs, nj, u_out, J_out,
-                                              u_trial, part, stride, la);
+  if (la.aff0 >= 0)
+    last_kernel<Real, CQ, true><<<grid, LNT, sm, s>>>(W, b, M, K, Zin, C, CPs, nj, u_out, J_out,
+                                                      u_trial, part, stride, la);
+  else
+    last_kernel<Real, CQ, false><<<grid, LNT, sm, s>>>(W, b, M, K, Zin, C, CPs, nj, u_out,
+                                                       J_out, u_trial, part, stride, la);
 }
 
 }  // namespace

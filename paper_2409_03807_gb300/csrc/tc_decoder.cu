@@ -195,7 +195,9 @@ __host__ __device__ inline TcSmem tc_smem_layout(bool bf, int Cp, int r) {
   return L;
 }
 
-template <bool BF>
+// AFF: the body has affine modes (a separate instantiation, so the rows of
+// the other workloads carry none of their FP64 registers)
+template <bool BF, bool AFF>
 __global__ void __launch_bounds__(TNT, 1)
     tc_last_kernel(const __grid_constant__ CUtensorMap mapW,
                    const __grid_constant__ CUtensorMap mapBh,
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(TNT, 1)
         x0 = (float)la.X0[m];
         slot = la.cslot[v];
         bm = b[m];
-        if (la.aff0 >= 0)
+        if (AFF)
           for (int k = 0; k < 3; ++k) dX[k] = la.X0[3 * v + k] - la.acen[k];
       }
       const int ab = i & 1;
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(TNT, 1)
           const int c = c0 + j;
           const float a = __uint_as_float(vv[j]);
           if (c == 0) {
-            const bool aff = la.aff0 >= 0 && live && slot < 0;
+            const bool aff = AFF && live && slot < 0;
             const double u0d =
                 aff ? (double)(scale * (a + bm)) + la.scale * affine_disp_tc(la, comp, dX, 0)
                     : 0.0;
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(TNT, 1)
             // Gram operand (K-major: operand row = column, K = tile row)
             const int cc = c - 1;
             const float jv = !jlive ? 0.f
-                             : (la.aff0 >= 0 && cc >= la.aff0)
+                             : (AFF && cc >= la.aff0)
                                  ? (float)(la.scale * affine_jac(comp, dX, cc - la.aff0))
                                  : scale * a;
             Js[row * JS + cc] = jv;
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(TNT, 1)
             }
           } else if (c >= nj && c < C && live) {
             const int tj = c - nj;
-            const bool aff = la.aff0 >= 0 && slot < 0;
+            const bool aff = AFF && slot < 0;
             const double utd =
                 aff ? (double)(scale * (a + bm)) + la.scale * affine_disp_tc(la, comp, dX, c)
                     : 0.0;
@@ -639,8 +641,15 @@ cudaError_t TcLast::setup(const float* W_fp32, int M_, int H_, int C_, int r_, b
   if (!make_map(&mapW, wsrc, bf16, H, M, TBM) || !make_map(&mapBh, Bh, bf16, H, Cp, Cp) ||
       !make_map(&mapBl, bf16 ? Bl : Bh, bf16, H, Cp, Cp))
     return cudaErrorInvalidValue;
-  if (bf16) e = cudaFuncSetAttribute(tc_last_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  else e = cudaFuncSetAttribute(tc_last_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int sm_i = (int)smem;
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (bf16) {
+    e = cudaFuncSetAttribute(tc_last_kernel<true, false>, at, sm_i);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tc_last_kernel<true, true>, at, sm_i);
+  } else {
+    e = cudaFuncSetAttribute(tc_last_kernel<false, false>, at, sm_i);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tc_last_kernel<false, true>, at, sm_i);
+  }
   return e;
 }
 
@@ -657,14 +666,17 @@ void TcLast::launch(const float* Z, int CPs, const float* bias, int nj, float* u
                     float* ut, double* part, int part_stride, const LastArgs& la,
                     cudaStream_t s, bool packed) const {
   const int n = Cp * H;
+  const bool aff = la.aff0 >= 0;
   if (bf16) {
     if (!packed) pack_kernel<true><<<(n + 255) / 256, 256, 0, s>>>(Z, H, C, CPs, Cp, Bh, Bl);
-    launch_pdl(tc_last_kernel<true>, dim3(grid), dim3(TNT), smem, s, mapW, mapBh, mapBl, bias, M,
-               H, C, Cp, nj, u, J, ut, part, part_stride, la, err);
+    launch_pdl(aff ? tc_last_kernel<true, true> : tc_last_kernel<true, false>, dim3(grid),
+               dim3(TNT), smem, s, mapW, mapBh, mapBl, bias, M, H, C, Cp, nj, u, J, ut, part,
+               part_stride, la, err);
   } else {
     if (!packed) pack_kernel<false><<<(n + 255) / 256, 256, 0, s>>>(Z, H, C, CPs, Cp, Bh, nullptr);
-    launch_pdl(tc_last_kernel<false>, dim3(grid), dim3(TNT), smem, s, mapW, mapBh, mapBl, bias,
-               M, H, C, Cp, nj, u, J, ut, part, part_stride, la, err);
+    launch_pdl(aff ? tc_last_kernel<false, true> : tc_last_kernel<false, false>, dim3(grid),
+               dim3(TNT), smem, s, mapW, mapBh, mapBl, bias, M, H, C, Cp, nj, u, J, ut, part,
+               part_stride, la, err);
   }
 }
 
