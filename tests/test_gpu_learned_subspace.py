@@ -132,13 +132,18 @@ def _train_and_measure(pkg, data, lam, steps, r=8):
         iters += st["newton_iters"]
         errs.append(rel(sc.get_positions() - mesh.X0.ravel(), qh - mesh.X0.ravel()))
     sc.close()
-    return dict(Lc=lc, lip=lip, iters=iters, err=max(errs))
+    return dict(Lc=lc, lip=lip, iters=iters, err=max(errs), Ws=Ws_t, bs=bs_t, eb=eb_t)
 
 
-def test_learned_subspace_gains(pkg, data):
-    untrained = _train_and_measure(pkg, data, 0.0, 0)
-    vanilla = _train_and_measure(pkg, data, 0.0, 3000)
-    lipschitz = _train_and_measure(pkg, data, 1e-6, 3000)
+@pytest.fixture(scope="module")
+def trained(pkg, data):
+    return {"untrained": _train_and_measure(pkg, data, 0.0, 0),
+            "vanilla": _train_and_measure(pkg, data, 0.0, 3000),
+            "lipschitz": _train_and_measure(pkg, data, 1e-6, 3000)}
+
+
+def test_learned_subspace_gains(trained):
+    untrained, vanilla, lipschitz = (trained[k] for k in ("untrained", "vanilla", "lipschitz"))
     for name, m in (("untrained", untrained), ("vanilla", vanilla), ("lipschitz", lipschitz)):
         print(f"{name:10s} L_C {m['Lc']:.3e}  Lip {m['lip']:.3e}  Newton iters {m['iters']:4d}"
               f"  max subspace error vs full space {m['err']:.3e}")
@@ -148,3 +153,46 @@ def test_learned_subspace_gains(pkg, data):
     assert vanilla["err"] < 0.1 and lipschitz["err"] < 0.1
     assert max(vanilla["err"], lipschitz["err"]) < 0.2 * untrained["err"]
     assert lipschitz["iters"] <= 1.25 * vanilla["iters"]
+
+
+def test_lbfgs_exit_shares_per_tolerance(pkg, data, trained):
+    """The Supplement's exit table: L-BFGS (FP32 form, the paper's optimiser)
+    on 40 implicit-Euler frames of the bar (far face twisted 0 -> 1.2 rad and
+    bent 0 -> 0.15 rad over 30 frames, then held), for each tolerance and for
+    the vanilla and the Lipschitz-trained decoder: the share of frames ending
+    with each exit (I converged, II saddle, III line search, IV iteration
+    cap, and the FP32 form's precision floor), the mean ||g||_inf at exit and
+    the mean iterations per frame.  Printed (pytest -s); checked: every frame
+    ends with one of these exits and every trajectory stays finite."""
+    mesh, cn, targets, Q, held, Qh = data
+    names = {0: "I", 5: "II", 2: "III", 1: "IV", 4: "floor"}
+    rows = []
+    for eps in (1e-4, 1e-5, 1e-6):
+        for which in ("lipschitz", "vanilla"):
+            t = trained[which]
+            sc = pkg.Context()
+            sc.set_mesh(mesh.X0, mesh.tets)
+            sc.set_material(E_, NU, RHO, GRAV)
+            sc.set_constraints(cn, targets(0.0, 0.0))
+            sc.set_decoder(t["Ws"], t["bs"], SCALE, "fp32")
+            sc.set_solver(eps, 1024, 128, 1e-4)
+            sc.set_optimizer("lbfgs", 10)
+            sc.set_state(t["eb"].astype(np.float64))
+            exits, gs, its = {}, [], []
+            for k in range(1, 41):
+                a = min(k / 30.0, 1.0)
+                sc.set_constraints(None, targets(1.2 * a, 0.15 * a))
+                rc, st, _ = sc.step(dt=1.0 / 60.0)
+                assert rc in names, (k, rc, st)
+                assert np.all(np.isfinite(sc.get_positions()))
+                exits[names[rc]] = exits.get(names[rc], 0) + 1
+                gs.append(st["grad_inf"])
+                its.append(st["newton_iters"])
+            sc.close()
+            share = {n: 100.0 * exits.get(n, 0) / 40 for n in ("I", "II", "III", "IV", "floor")}
+            rows.append((eps, which, share, float(np.mean(gs)), float(np.mean(its))))
+    print("\n eps     subspace    I      II     III    IV   floor   mean|g|exit  iters/frame")
+    for eps, which, sh, g, it in rows:
+        print(f" {eps:.0e}  {which:9s} " + " ".join(f"{sh[n]:5.1f}%" for n in
+                                                   ("I", "II", "III", "IV", "floor")) +
+              f"   {g:.2e}   {it:7.1f}")
