@@ -301,7 +301,8 @@ struct Engine : EngineBase {
       // 16 bytes; otherwise the FP32 CUDA-core output layer serves this form
       const cudaError_t te = tcl.setup(reinterpret_cast<const float*>(dW[L - 1]), n,
                                        c->widths[L - 1], C, r,
-                                       c->precision == LSN_PREC_BF16, c->num_sms, s);
+                                       c->precision == LSN_PREC_BF16, c->num_sms, s,
+                                       c->affine);
       if (te == cudaSuccess) {
         use_tc_last = true;
         grid_dec = tcl.grid;

@@ -179,14 +179,15 @@ struct TcSmem {  // byte offsets from the 1024-aligned base
       total;
 };
 
-__host__ __device__ inline TcSmem tc_smem_layout(bool bf, int Cp, int r) {
+// split: the Gram operand buffers hold a BF16 hi and lo part each
+__host__ __device__ inline TcSmem tc_smem_layout(bool bf, int Cp, int r, bool split) {
   TcSmem L;
   L.a_bytes = TBM * 128;
   L.bh_off = L.a_bytes;
   L.bl_off = L.bh_off + Cp * 128;
   L.stage_bytes = L.a_bytes + Cp * 128 * (bf ? 2 : 1);
   L.jt_off = TST * L.stage_bytes;
-  L.jt_bytes = GM * TBM * (bf ? 2 : 4);
+  L.jt_bytes = GM * TBM * (bf ? 2 : 4) * (split ? 2 : 1);
   L.js_off = L.jt_off + 2 * L.jt_bytes;
   const uint32_t js_bytes = TBM * (r + 4) * 4;
   L.gv_off = (L.js_off + js_bytes + 15) & ~15u;
@@ -214,7 +215,12 @@ __global__ void __launch_bounds__(TNT, 1)
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* sb = smem_raw + (base - raw);
   const int r = la.r;
-  const TcSmem SL = tc_smem_layout(BF, Cp, r);
+  // bodies with affine modes take the inertia Gram from a two-term BF16 split
+  // of sqrt(kv) J (hi hi^T + hi lo^T + lo hi^T): the reduced Hessian of a free
+  // body spans its whole m / dt^2 and the network curvatures, and one BF16
+  // rounding of the operand leaves too little of the small ones
+  constexpr bool SPLIT = BF && AFF;
+  const TcSmem SL = tc_smem_layout(BF, Cp, r, SPLIT);
   constexpr int EPB = BF ? 64 : 32;  // K values per 128-byte block
   const int nkb = (H + EPB - 1) / EPB;
   const int ntiles = (M + TBM - 1) / TBM;
@@ -289,8 +295,16 @@ __global__ void __launch_bounds__(TNT, 1)
           for (int ks = 0; ks < 4; ++ks) {
             const uint64_t d = sdesc_sw128(jt + kb * GM * 128 + ks * 32);
             const uint32_t acc = (j > 0 || kb > 0 || ks > 0) ? 1u : 0u;
-            if (BF) mma_bf16(tbase + COL_GRAM, d, d, idg, acc);
-            else mma_tf32(tbase + COL_GRAM, d, d, idg, acc);
+            if (BF) {
+              mma_bf16(tbase + COL_GRAM, d, d, idg, acc);
+              if (SPLIT) {
+                const uint64_t dl = sdesc_sw128(jt + SL.jt_bytes / 2 + kb * GM * 128 + ks * 32);
+                mma_bf16(tbase + COL_GRAM, d, dl, idg, 1u);
+                mma_bf16(tbase + COL_GRAM, dl, d, idg, 1u);
+              }
+            } else {
+              mma_tf32(tbase + COL_GRAM, d, d, idg, acc);
+            }
           }
         mma_commit(&jempty[jb]);
       };
@@ -433,9 +447,12 @@ __global__ void __launch_bounds__(TNT, 1)
               const float gval = wk * jv;
               if (BF) {
                 const int kb = row >> 6, kin = row & 63;
-                *reinterpret_cast<__nv_bfloat16*>(jt + kb * GM * 128 +
-                                                  sw128_offset(cc, kin >> 3) + (kin & 7) * 2) =
-                    __float2bfloat16_rn(gval);
+                const uint32_t off = kb * GM * 128 + sw128_offset(cc, kin >> 3) + (kin & 7) * 2;
+                const __nv_bfloat16 hi = __float2bfloat16_rn(gval);
+                *reinterpret_cast<__nv_bfloat16*>(jt + off) = hi;
+                if (SPLIT)
+                  *reinterpret_cast<__nv_bfloat16*>(jt + SL.jt_bytes / 2 + off) =
+                      __float2bfloat16_rn(gval - __bfloat162float(hi));
               } else {
                 const int kb = row >> 5, kin = row & 31;
                 *reinterpret_cast<float*>(jt + kb * GM * 128 + sw128_offset(cc, kin >> 2) +
@@ -596,8 +613,9 @@ bool make_map(CUtensorMap* map, const void* ptr, bool bf, int inner, int outer, 
 }  // namespace
 
 cudaError_t TcLast::setup(const float* W_fp32, int M_, int H_, int C_, int r_, bool bf16_,
-                          int num_sms, cudaStream_t s) {
+                          int num_sms, cudaStream_t s, bool aff_) {
   release();
+  aff = aff_;
   M = M_;
   H = H_;
   C = C_;
@@ -610,7 +628,7 @@ cudaError_t TcLast::setup(const float* W_fp32, int M_, int H_, int C_, int r_, b
   if (Cp > 96 || r > 64 || (H * (bf16 ? 2 : 4)) % 16 != 0) return cudaErrorInvalidValue;
   const int ntiles = (M + TBM - 1) / TBM;
   grid = std::max(1, std::min(ntiles, num_sms));
-  const TcSmem L = tc_smem_layout(bf16, Cp, r);
+  const TcSmem L = tc_smem_layout(bf16, Cp, r, bf16 && aff);
   smem = L.total + 1024;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e;
@@ -666,7 +684,7 @@ void TcLast::launch(const float* Z, int CPs, const float* bias, int nj, float* u
                     float* ut, double* part, int part_stride, const LastArgs& la,
                     cudaStream_t s, bool packed) const {
   const int n = Cp * H;
-  const bool aff = la.aff0 >= 0;
+  // the instantiation (and its shared-memory layout) follows the setup flag
   if (bf16) {
     if (!packed) pack_kernel<true><<<(n + 255) / 256, 256, 0, s>>>(Z, H, C, CPs, Cp, Bh, Bl);
     launch_pdl(aff ? tc_last_kernel<true, true> : tc_last_kernel<true, false>, dim3(grid),

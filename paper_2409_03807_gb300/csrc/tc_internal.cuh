@@ -17,9 +17,11 @@ struct TcLast {
   int M = 0, H = 0, C = 0, Cp = 0, r = 0, grid = 0;
   size_t smem = 0;
   bool bf16 = false;
+  bool aff = false;  // affine modes: the epilogue adds them (and, in the BF16
+                     // form, the inertia Gram operand is a hi + lo BF16 split)
   // W_fp32: the output layer's FP32 weights (M x H, row-major, device)
   cudaError_t setup(const float* W_fp32, int M, int H, int C, int r, bool bf16, int num_sms,
-                    cudaStream_t s);
+                    cudaStream_t s, bool aff = false);
   void release();
   // Z: last hidden layer, unit-major [H][CPs] (FP32); same outputs and
   // partial-row layout as launch_last_layer
