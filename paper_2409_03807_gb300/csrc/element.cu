@@ -1047,7 +1047,10 @@ __global__ void __launch_bounds__(NT, 1)
 namespace gradel {
 constexpr int ET = 128;
 
-template <typename Real>
+// VEC (FP32, r a multiple of 4): each thread of a group takes four adjacent
+// columns and loads them as one float4 per J row (a quarter of the load
+// instructions of the one-column mapping).
+template <typename Real, bool VEC>
 __global__ void __launch_bounds__(ET) element_grad_kernel(ElemArgs ea, const Real* __restrict__ u,
                                                           const Real* __restrict__ J,
                                                           const Real* __restrict__ ut,
@@ -1056,10 +1059,16 @@ __global__ void __launch_bounds__(ET) element_grad_kernel(ElemArgs ea, const Rea
   __shared__ Real ge[ET][13];
   __shared__ int4 tvs[ET];
   __shared__ double red[2 + 2 * KTRIAL][ET];
+  __shared__ double redv[VEC ? 2 : 1][VEC ? 4 * ET : 1];
   const int t = threadIdx.x, r = ea.r;
   const int G = ET / r;  // column groups
   const int grp = t / r, c = t - grp * r;
   const bool active = grp < G;
+  const int Q = VEC ? r / 4 : 1;  // column quads (VEC)
+  const int G4 = ET / Q;
+  const int grp4 = t / Q, cq = t - grp4 * Q;
+  const bool active4 = VEC && grp4 < G4;
+  double gacc4[4] = {0.0, 0.0, 0.0, 0.0}, gabs4[4] = {0.0, 0.0, 0.0, 0.0};
   const Real mu = (Real)ea.mu, lam = (Real)ea.lam;
   const Real oma = (Real)(-0.75 * ea.mu / ea.lam);  // 1 - a
   double eacc = 0.0, eabs = 0.0, gacc = 0.0, gabs = 0.0;
@@ -1123,7 +1132,40 @@ __global__ void __launch_bounds__(ET) element_grad_kernel(ElemArgs ea, const Rea
       tvs[t] = make_int4(0, 0, 0, 0);
     }
     __syncthreads();
-    if (active) {
+    if (VEC) {
+      // four columns per thread: one 16-byte load per J row
+      if (active4) {
+        float sg[4] = {0.f, 0.f, 0.f, 0.f}, sa[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int lt = grp4; lt < nt; lt += G4) {
+          const int4 tv = tvs[lt];
+          const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
+          float gp[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              const float4 jv = __ldg(reinterpret_cast<const float4*>(
+                  J + (size_t)(3 * vv[a] + i) * r + 4 * cq));
+              const float w = (float)ge[lt][3 * a + i];
+              gp[0] += w * jv.x;
+              gp[1] += w * jv.y;
+              gp[2] += w * jv.z;
+              gp[3] += w * jv.w;
+            }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            sg[k] += gp[k];
+            sa[k] += fabsf(gp[k]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          gacc4[k] += (double)sg[k];
+          gabs4[k] += (double)sa[k];
+        }
+      }
+    } else if (active) {
       Real sg = Real(0), sa = Real(0);
 #pragma unroll 4
       for (int lt = grp; lt < nt; lt += G) {
@@ -1165,6 +1207,25 @@ __global__ void __launch_bounds__(ET) element_grad_kernel(ElemArgs ea, const Rea
   }
   if (t < 2 * KTRIAL) prow[nslots(r) + t] = red[2 + t][0];
   __syncthreads();
+  if (VEC) {
+    // thread (grp4, cq) holds columns 4 cq .. 4 cq + 3 of group grp4
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      redv[0][4 * t + k] = active4 ? gacc4[k] : 0.0;
+      redv[1][4 * t + k] = active4 ? gabs4[k] : 0.0;
+    }
+    __syncthreads();
+    if (t < r) {  // column t = 4 cq + k: entry 4 (q Q + cq) + k of group q
+      double s0 = 0.0, a0 = 0.0;
+      for (int q = 0; q < G4; ++q) {
+        s0 += redv[0][4 * q * Q + t];
+        a0 += redv[1][4 * q * Q + t];
+      }
+      prow[slot_g(t)] = s0;
+      prow[slot_gabs(r, t)] = a0;
+    }
+    return;
+  }
   red[0][t] = active ? gacc : 0.0;
   red[1][t] = active ? gabs : 0.0;
   __syncthreads();
@@ -1269,8 +1330,12 @@ int element_grad_grid(int S, int num_sms) {
 template <typename Real>
 void launch_element_grad(const ElemArgs& ea, const Real* u, const Real* J, const Real* ut,
                          double* part, int grid, cudaStream_t s) {
-  launch_pdl(gradel::element_grad_kernel<Real>, dim3(grid), dim3(gradel::ET), 0, s, ea, u, J,
-             ut, part, nslots_total(ea.r));
+  if (sizeof(Real) == 4 && ea.r % 4 == 0)
+    launch_pdl(gradel::element_grad_kernel<Real, sizeof(Real) == 4>, dim3(grid),
+               dim3(gradel::ET), 0, s, ea, u, J, ut, part, nslots_total(ea.r));
+  else
+    launch_pdl(gradel::element_grad_kernel<Real, false>, dim3(grid), dim3(gradel::ET), 0, s, ea,
+               u, J, ut, part, nslots_total(ea.r));
 }
 
 template void launch_element_grad<float>(const ElemArgs&, const float*, const float*,
