@@ -227,6 +227,30 @@ int lsn_get_positions(lsn_ctx* ctx, double* x_out);
  * gradient-only pass that the L-BFGS solve uses. */
 int lsn_eval(lsn_ctx* ctx, const double* z, double* E, double* g, double* K);
 
+/* Optimised cubature (Sec. 4.3: the cubature set and weights are fitted on
+ * the initial subspace, after von Tycowicz et al. 2013; Sec. 5.3 discusses
+ * the cubature count).  At the K subspace points z (K x r, host or device;
+ * r includes the affine modes) every tet e of the mesh gives the r reduced
+ * elastic forces a_{k,e} = J_e(z_k)^T d(V_e Psi(F_e))/dx_e (unit weight;
+ * constrained rows of J are zero).
+ *
+ * lsn_tet_forces: the matrix A ((K r) x ne, row k r + i, column e,
+ * row-major FP64; host or device) of these forces (parity hook).
+ *
+ * lsn_select_cubature: each snapshot's r rows of A and of the full force
+ * b = A 1 are divided by ||b_k||; the non-negative least-squares fit
+ * min ||A w - b||, w >= 0, by the Lawson-Hanson active-set method (the
+ * column with the largest entry of A^T (b - A w) enters the active set per
+ * outer iteration), stopped once S columns are active.  Writes the active
+ * tets in ascending order to idx, their weights to w (host, room for S
+ * each), their number to *count (<= S) and ||A w - b|| / ||b|| to
+ * *rel_residual (may be NULL).  The result feeds lsn_set_cubature or the
+ * training cubature of lsn_train_init.  The solver's current z is kept.
+ * Device memory: K r ne doubles for A. */
+int lsn_tet_forces(lsn_ctx* ctx, const double* z, int K, double* A);
+int lsn_select_cubature(lsn_ctx* ctx, const double* z, int K, int S, int32_t* idx, double* w,
+                        int* count, double* rel_residual);
+
 /* Parity hook for the inertia term: sets dt and qbar (n, host or device)
  * directly, as lsn_step would. dt == 0 selects the quasi-static objective. */
 int lsn_set_dynamics(lsn_ctx* ctx, double dt, const double* qbar);

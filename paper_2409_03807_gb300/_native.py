@@ -53,6 +53,10 @@ _SIGS = {
                        ctypes.c_double],
     "lsn_set_optimizer": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
     "lsn_set_affine_modes": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "lsn_tet_forces": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "lsn_select_cubature": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                            ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                            ctypes.c_void_p],
     "lsn_set_state": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "lsn_set_dynamics": [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p],
     "lsn_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
@@ -162,6 +166,7 @@ class Context:
         self.r_nn = None
         self.affine = False
         self.n = None
+        self.ne = None
 
     def close(self):
         if self.h:
@@ -187,6 +192,7 @@ class Context:
         tets = _i32(tets)
         self.keep = (X0, tets)
         self.n = 3 * X0.shape[0]
+        self.ne = int(tets.shape[0])
         return self._check(self.lib.lsn_set_mesh(self.h, _ptr(X0), X0.shape[0], _ptr(tets),
                                                  tets.shape[0]))
 
@@ -234,6 +240,29 @@ class Context:
         self._check(self.lib.lsn_set_affine_modes(self.h, 0 if center is None else 1, _ptr(c)))
         self.affine = center is not None
         self.r = self.r_nn + (12 if self.affine else 0)
+
+    def tet_forces(self, Z, A=None):
+        """Per-tet reduced elastic forces at the points Z (K x r): (K r) x ne."""
+        Z = _f64(Z)
+        K = int(Z.shape[0])
+        if A is None:
+            A = np.zeros((K * self.r, self.ne))
+        self._check(self.lib.lsn_tet_forces(self.h, _ptr(Z), K, _ptr(A)))
+        return A
+
+    def select_cubature(self, Z, S):
+        """Optimised cubature for the points Z (K x r): (tet indices, weights,
+        relative residual of the force fit)."""
+        Z = _f64(Z)
+        idx = np.zeros(S, np.int32)
+        w = np.zeros(S)
+        cnt = ctypes.c_int()
+        rel = np.zeros(1)
+        self._check(self.lib.lsn_select_cubature(self.h, _ptr(Z), int(Z.shape[0]), int(S),
+                                                 _ptr(idx), _ptr(w), ctypes.byref(cnt),
+                                                 _ptr(rel)))
+        k = cnt.value
+        return idx[:k].copy(), w[:k].copy(), float(rel[0])
 
     def set_optimizer(self, kind="newton", history=10):
         """kind: "newton" (projective Newton) or "lbfgs"; history: L-BFGS pairs."""

@@ -142,6 +142,9 @@ struct EngineBase {
   virtual void begin(int eval_only) = 0;   // reset the device solve state
   virtual void finish(double dt) = 0;      // q, v from the positions at z
   virtual void decode_to_host(double* x, double* J) = 0;
+  // per-tet reduced elastic forces of every mesh tet at the point of the
+  // last pass into A (r rows of ne, device)
+  virtual void tet_forces(double* A) = 0;
   virtual int kernels_per_pass() const = 0;
   // nonzero when a bounded wait inside a tensor-core kernel ran out (reads a
   // device flag; call after the stream's work is queued)
@@ -492,6 +495,12 @@ struct Engine : EngineBase {
     c->prof.begin(LSN_K_SOLVE);
     launch_finish_positions<Real>(c->X0, u, n, dt, c->q, c->v, c->stream);
     c->prof.end(LSN_K_SOLVE);
+  }
+
+  void tet_forces(double* A) override {
+    launch_tet_forces<Real>(c->tets, c->dminv, c->vol, c->ne, r, u, J, ea.mu, ea.lam, A,
+                            c->stream);
+    ck(cudaGetLastError());
   }
 
   void decode_to_host(double* x, double* Jh) override {
@@ -1061,6 +1070,97 @@ int lsn_eval(lsn_ctx* c, const double* z, double* E, double* g, double* K) {
   return LSN_OK;
   LSN_GUARD_END
 }
+
+}  // extern "C"
+
+namespace {
+// A (K r x ne, device) of the per-tet reduced elastic forces at the K points
+// z (host or device); the solver's current z is restored afterwards
+void tet_force_matrix(lsn_ctx* c, const double* z, int K, double* Ad) {
+  const int r = subspace_r(c);
+  cudaStream_t s = c->stream;
+  std::vector<double> zsave(r);
+  ck(cudaMemcpyAsync(zsave.data(), &c->eng->sv->z[0], sizeof(double) * r,
+                     cudaMemcpyDeviceToHost, s));
+  ck(cudaStreamSynchronize(s));
+  const bool zdev = is_device_ptr(z);
+  for (int k = 0; k < K; ++k) {
+    ck(cudaMemcpyAsync(&c->eng->sv->z[0], z + (size_t)k * r, sizeof(double) * r,
+                       zdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    run_solve(c, 1, 0);
+    c->eng->tet_forces(Ad + (size_t)k * r * c->ne);
+  }
+  ck(cudaMemcpyAsync(&c->eng->sv->z[0], zsave.data(), sizeof(double) * r,
+                     cudaMemcpyHostToDevice, s));
+  ck(cudaStreamSynchronize(s));
+}
+}  // namespace
+
+extern "C" {
+
+int lsn_tet_forces(lsn_ctx* c, const double* z, int K, double* A) {
+  if (!c) return LSN_ERR_ARG;
+  if (!z || !A || K < 1) return fail(c, LSN_ERR_ARG, "tet_forces: bad arguments");
+  LSN_GUARD_BEGIN
+  int rc = prepare(c);
+  if (rc != LSN_OK) return rc;
+  const size_t cnt = (size_t)K * subspace_r(c) * c->ne;
+  const bool adev = is_device_ptr(A);
+  double* Ad = adev ? A : dalloc<double>(cnt);
+  try {
+    tet_force_matrix(c, z, K, Ad);
+    if (!adev) {
+      ck(cudaMemcpyAsync(A, Ad, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+      ck(cudaStreamSynchronize(c->stream));
+    }
+  } catch (...) {
+    if (!adev) dfree(Ad);
+    throw;
+  }
+  if (!adev) dfree(Ad);
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_select_cubature(lsn_ctx* c, const double* z, int K, int S, int32_t* idx, double* w,
+                        int* count, double* rel_residual) {
+  if (!c) return LSN_ERR_ARG;
+  if (!z || !idx || !w || !count || K < 1 || S < 1)
+    return fail(c, LSN_ERR_ARG, "select_cubature: bad arguments");
+  LSN_GUARD_BEGIN
+  int rc = prepare(c);
+  if (rc != LSN_OK) return rc;
+  if (S > c->ne) return fail(c, LSN_ERR_ARG, "select_cubature: S exceeds the tet count");
+  const int r = subspace_r(c), m = K * r;
+  double* Ad = dalloc<double>((size_t)m * c->ne);
+  std::vector<int> P;
+  std::vector<double> xP, b;
+  double rel = 0.0;
+  cudaError_t e = cudaSuccess;
+  try {
+    tet_force_matrix(c, z, K, Ad);
+    e = cubature_normalise(Ad, m, c->ne, r, b, c->stream);
+    if (e == cudaSuccess) e = cubature_nnls(Ad, m, c->ne, b, S, P, xP, rel, c->stream);
+  } catch (...) {
+    dfree(Ad);
+    throw;
+  }
+  dfree(Ad);
+  ck(e);
+  // ascending tet order (the cubature gather reads the mesh in that order)
+  std::vector<int> ord(P.size());
+  for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+  std::sort(ord.begin(), ord.end(), [&](int a, int bb) { return P[a] < P[bb]; });
+  for (size_t i = 0; i < ord.size(); ++i) {
+    idx[i] = P[ord[i]];
+    w[i] = xP[ord[i]];
+  }
+  *count = (int)P.size();
+  if (rel_residual) *rel_residual = rel;
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
 
 int lsn_decode(lsn_ctx* c, const double* z, double* x_out, double* J_out) {
   if (!c) return LSN_ERR_ARG;

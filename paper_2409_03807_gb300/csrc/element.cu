@@ -1241,6 +1241,64 @@ __global__ void __launch_bounds__(ET) element_grad_kernel(ElemArgs ea, const Rea
 }
 }  // namespace gradel
 
+// ------------------------------------------------------------------------
+// Per-tet reduced elastic forces for the cubature fit (Sec. 4.3): for every
+// tet e of the mesh (unit weight) the r values J_e^T dP_e/dx_e, P_e = V_e
+// Psi(F_e), written to A[i * ne + e] (one row per subspace column, coalesced
+// along the tets).  One thread per tet.
+template <typename Real>
+__global__ void __launch_bounds__(128) tet_force_kernel(const int4* __restrict__ tets,
+                                                        const double* __restrict__ dminv,
+                                                        const double* __restrict__ vol, int ne,
+                                                        int r, const Real* __restrict__ u,
+                                                        const Real* __restrict__ J, Real mu,
+                                                        Real lam, double* __restrict__ A) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const int4 tv = tets[e];
+  Real Dmi[3][3], H[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) Dmi[a][b] = (Real)dminv[(3 * a + b) * ne + e];
+  const Real wv = (Real)vol[e];
+  disp_grad<Real>(u, tv, Dmi, H);
+  Invariants<Real> iv;
+  invariants<Real>(H, iv);
+  const Real Ic = iv.Ic3 + Real(3);
+  const Real dl = iv.Ic3 / (Real(4) * (Ic + Real(1)));
+  const Real lJ = lam * iv.Jm1;
+  Real ge[12];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Real P[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const Real Fij = H[i][j] + (i == j ? Real(1) : Real(0));
+      P[j] = wv * (mu * dl * Fij + lJ * iv.cof[i][j] +
+                   Real(0.75) * mu *
+                       (H[i][j] + H[j][i] - (i == j ? iv.trH : Real(0)) - iv.cofH[i][j]));
+    }
+    Real s0 = Real(0);
+#pragma unroll
+    for (int a = 1; a < 4; ++a) {
+      const Real v = P[0] * Dmi[a - 1][0] + P[1] * Dmi[a - 1][1] + P[2] * Dmi[a - 1][2];
+      ge[3 * a + i] = v;
+      s0 += v;
+    }
+    ge[i] = -s0;
+  }
+  const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
+  for (int c = 0; c < r; ++c) {
+    Real acc = Real(0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) acc += ge[3 * a + i] * J[(size_t)(3 * vv[a] + i) * r + c];
+    A[(size_t)c * ne + e] = (double)acc;
+  }
+}
+
 }  // namespace
 
 // Small cubature sets use 64-tet tiles so that more CTAs share the work.
@@ -1321,6 +1379,20 @@ cudaError_t launch_element_tc(const ElemArgs& ea, const float* u, const float* J
   }
   return cudaGetLastError();
 }
+
+template <typename Real>
+void launch_tet_forces(const int4* tets, const double* dminv, const double* vol, int ne, int r,
+                       const Real* u, const Real* J, double mu, double lam, double* A,
+                       cudaStream_t s) {
+  tet_force_kernel<Real><<<(ne + 127) / 128, 128, 0, s>>>(tets, dminv, vol, ne, r, u, J,
+                                                          (Real)mu, (Real)lam, A);
+}
+template void launch_tet_forces<float>(const int4*, const double*, const double*, int, int,
+                                       const float*, const float*, double, double, double*,
+                                       cudaStream_t);
+template void launch_tet_forces<double>(const int4*, const double*, const double*, int, int,
+                                        const double*, const double*, double, double, double*,
+                                        cudaStream_t);
 
 int element_grad_grid(int S, int num_sms) {
   const int tiles = (S + gradel::ET - 1) / gradel::ET;

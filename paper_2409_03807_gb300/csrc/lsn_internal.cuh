@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace lsn {
 
 constexpr int RMAX = 64;           // largest subspace dimension
@@ -152,12 +154,29 @@ int element_tc_grid(int S, int num_sms);
 // `grid` CTAs, each writing the E, g, gabs and trial-energy slots of one
 // partial row (stride nslots_total(r)); the K slots are not written.
 int element_grad_grid(int S, int num_sms);
+// Per-tet reduced elastic forces of every mesh tet (unit weight) for the
+// cubature fit: A[i * ne + e] = (J_e^T dP_e/dx_e)_i, i < r (FP64 output).
+template <typename Real>
+void launch_tet_forces(const int4* tets, const double* dminv, const double* vol, int ne, int r,
+                       const Real* u, const Real* J, double mu, double lam, double* A,
+                       cudaStream_t s);
 template <typename Real>
 void launch_element_grad(const ElemArgs& ea, const Real* u, const Real* J, const Real* ut,
                          double* part, int grid, cudaStream_t s);
 cudaError_t launch_element_tc(const ElemArgs& ea, const float* u, const float* J,
                               const float* ut, double* part, int grid, bool bf16, int* err,
                               cudaStream_t s);
+
+// cubature.cu: optimised cubature fit on the per-tet force matrix A
+// ([m][ne] row-major, device, FP64; rows of r per snapshot).  normalise:
+// b = A 1, each snapshot's rows of A and b divided by ||b_k||.  nnls:
+// Lawson-Hanson active set stopped at S active columns; P the active tets,
+// xP their weights, rel = ||A_P xP - b|| / ||b||.
+cudaError_t cubature_normalise(double* A, int m, int ne, int r, std::vector<double>& b,
+                               cudaStream_t s);
+cudaError_t cubature_nnls(const double* A, int m, int ne, const std::vector<double>& b, int S,
+                          std::vector<int>& P, std::vector<double>& xP, double& rel,
+                          cudaStream_t s);
 
 // solve.cu
 // out[c] = sum over rows of A (all rows) and of B: rows [0, splitB) for
