@@ -52,6 +52,8 @@ def parse():
                     help="newton (default): projective Newton; lbfgs: L-BFGS (Sec. 5), "
                          "gradient-only passes")
     ap.add_argument("--history", type=int, default=10, help="L-BFGS history size")
+    ap.add_argument("--r", type=int, default=None,
+                    help="override the workload's subspace dimension (r-sweep)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="time budget of the CPU-oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -210,7 +212,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     from workloads import build_problem
-    p = build_problem(args.workload)
+    p = load_problem(args)
     c = p.config
     budget = 150.0
     # timed: frames after the warm-up, continuing the same trajectory
@@ -243,6 +245,16 @@ def run_reference(args, world, rank):
 
 
 # --------------------------------------------------------------------- ours
+def load_problem(args):
+    """The workload, with the subspace dimension overridden by --r."""
+    import dataclasses
+    from workloads import build_problem, CONFIGS
+    c = CONFIGS[args.workload]
+    if args.r is not None:
+        c = dataclasses.replace(c, r=args.r)
+    return build_problem(c)
+
+
 def subspace_dim(p):
     """Dimension of z: the network's input width (+ 12 affine modes)."""
     return p.config.r + (12 if p.affine_center is not None else 0)
@@ -287,7 +299,7 @@ def run_ours(args, world, rank, local):
     import paper_2409_03807_gb300 as pkg
     from workloads import build_problem
 
-    p = build_problem(args.workload)
+    p = load_problem(args)
     c = p.config
     W, K = args.warmup, args.steps
     stream = torch.cuda.Stream(dev)
