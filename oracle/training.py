@@ -17,6 +17,16 @@ Hessian obtained by automatic differentiation as in the paper (Sec. 5).
 Only the rows of the decoder that the cubature tets touch enter Pt, so the
 Hessian evaluates the last layer on those rows only (same function).
 
+Unsupervised setting (Eq. 4, Sec. 3.2), over a batch of given samples
+z_1..z_B (the caller draws them from N(0, I)):
+    L_P   = 1/B sum_b Pt(x(z_b))                                      (potential loss)
+    L_R   = 1/(B(B-1)) sum_{i != j} log(||x(z_i) - x(z_j)||_M / (sigma ||z_i - z_j||))^2
+    L_U   = L_P + lambda L_R                                            (Eq. 4)
+with the same cubature elastic potential Pt as the Lipschitz loss (reading:
+the paper's P, with S = every tet as the exact case) and the expectations
+taken as batch means over all ordered pairs (reading).  The encoder takes
+no part (its gradient is zero).
+
 Parameters are one flat float64 vector, in the order
     Ew (r x n, row-major), eb (r), then per decoder layer W_l (out x in), b_l.
 
@@ -135,6 +145,32 @@ class TrainProblem:
         H = torch.stack([self.hessian(P, Zs[b], create_graph=create_graph) for b in range(B)])
         Lls = lipschitz_loss(H, Zs)
         return Lc, Lls, Lc + lam_ls * Lls, Zs, H
+
+
+def unsupervised_losses(tp, theta, Z, lam, sigma):
+    """(L_P, L_R, L_U) of Eq. 4 for parameters theta (torch, flat) and the
+    samples Z (B, r)."""
+    P = tp.unpack(theta)
+    B = Z.shape[0]
+    rows = torch.tensor(tp.rows, dtype=torch.long)
+    Lp = sum(tp.cubature_potential(tp.decode(P, Z[b], rows)) for b in range(B)) / B
+    X = tp.decode(P, Z)
+    dX = X[:, None] - X[None, :]
+    dm = (tp.massdof * dX * dX).sum(dim=2)                 # ||x_i - x_j||_M^2
+    dz = ((Z[:, None] - Z[None, :]) ** 2).sum(dim=2)
+    off = ~torch.eye(B, dtype=torch.bool)
+    ell = 0.5 * torch.log(dm[off]) - np.log(sigma) - 0.5 * torch.log(dz[off])
+    Lr = (ell * ell).sum() / (B * (B - 1))
+    return Lp, Lr, Lp + lam * Lr
+
+
+def unsupervised_loss_and_grad(tp, theta_np, Z_np, lam, sigma):
+    """float64 losses (L_P, L_R, L_U) and the gradient of L_U."""
+    theta = torch.tensor(theta_np, dtype=torch_dtype, requires_grad=True)
+    Z = torch.tensor(Z_np, dtype=torch_dtype)
+    Lp, Lr, L = unsupervised_losses(tp, theta, Z, lam, sigma)
+    (g,) = torch.autograd.grad(L, theta)
+    return (float(Lp.detach()), float(Lr.detach()), float(L.detach())), g.numpy()
 
 
 def lipschitz_loss(H, Z):

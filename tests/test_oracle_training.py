@@ -113,3 +113,53 @@ def test_parameter_gradient_by_central_differences(setup, lam_ls):
         Lm = loss_and_grad(tp, tm_, Q, lam_ls, Z_samples=Z)[0][2]
         fd = (Lp - Lm) / (2 * h)
         assert fd == pytest.approx(g[k], rel=1e-5, abs=1e-8 * max(1.0, abs(L)))
+
+
+def test_unsupervised_losses_against_independent_sums(setup):
+    """Eq. 4: L_P equals the numpy oracle's cubature elastic energy at the
+    decoded positions; L_R equals a double loop over ordered pairs."""
+    from oracle.training import unsupervised_losses
+    tp, theta, Q, Ws, bs = setup
+    dec = Decoder([np.asarray(W, np.float64) for W in Ws], [np.asarray(b) for b in bs], tp.scale)
+    Z = np.random.default_rng(5).standard_normal((4, 3))
+    lam, sigma = 0.3, 0.02
+    Lp, Lr, L = (float(v) for v in unsupervised_losses(tp, torch.tensor(theta), torch.tensor(Z),
+                                                       lam, sigma))
+    tl = tp.ctets_local.numpy()
+    DmInv = tp.cDmInv.numpy()
+    cw = tp.cw.numpy()
+    Ep = 0.0
+    X = []
+    for z in Z:
+        x = tp.X0.ravel() + dec.out(z)
+        X.append(x)
+        xv = x[tp.rows].reshape(-1, 3)
+        Ep += float(np.sum(cw * fem.element_energy(xv, tl, DmInv, np.ones(len(tl)), tp.mu, tp.lam)))
+    assert Lp == pytest.approx(Ep / 4, rel=1e-12)
+    m = np.repeat(tp.mass, 3)
+    acc = 0.0
+    for i in range(4):
+        for j in range(4):
+            if i != j:
+                d = np.sqrt(np.sum(m * (X[i] - X[j]) ** 2))
+                acc += np.log(d / (sigma * np.linalg.norm(Z[i] - Z[j]))) ** 2
+    assert Lr == pytest.approx(acc / 12, rel=1e-12)
+    assert L == pytest.approx(Lp + lam * Lr, rel=1e-14)
+
+
+def test_unsupervised_gradient_matches_central_differences(setup):
+    from oracle.training import unsupervised_loss_and_grad
+    tp, theta, Q, Ws, bs = setup
+    Z = np.random.default_rng(6).standard_normal((4, 3))
+    (Lp, Lr, L), g = unsupervised_loss_and_grad(tp, theta, Z, 0.3, 0.02)
+    n_enc = tp.sizes[0] + tp.sizes[1]
+    assert np.all(g[:n_enc] == 0.0)          # the encoder takes no part
+    rng = np.random.default_rng(101)
+    for k in rng.choice(np.arange(n_enc, theta.size), 8, replace=False):
+        h = 1e-6 * max(1.0, abs(theta[k]))
+        tp_, tm_ = theta.copy(), theta.copy()
+        tp_[k] += h
+        tm_[k] -= h
+        fd = (unsupervised_loss_and_grad(tp, tp_, Z, 0.3, 0.02)[0][2] -
+              unsupervised_loss_and_grad(tp, tm_, Z, 0.3, 0.02)[0][2]) / (2 * h)
+        assert fd == pytest.approx(g[k], rel=1e-5, abs=1e-8 * max(1.0, abs(L)))
