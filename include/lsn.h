@@ -308,6 +308,22 @@ int lsn_train_eval(lsn_ctx* ctx, const double* q, int B, double lambda_ls,
  * gradient of L for the batch q; losses as in lsn_train_eval. */
 int lsn_train_step(lsn_ctx* ctx, const double* q, int B, double lambda_ls,
                    double lr, double* losses);
+/* Unsupervised construction (Eq. 4, Sec. 3.2) at the B samples z (B x r,
+ * host or device; the caller draws them from N(0, I)), with the Lipschitz
+ * loss of Eq. 9 at the same samples (Eq. 10 in the unsupervised setting; the
+ * paper estimates the Lipschitz term from Gaussian subspace samples there):
+ *   L_P = 1/B sum_b Pt(x(z_b))          (the cubature elastic potential above)
+ *   L_R = 1/(B(B-1)) sum_{i != j} log(||x(z_i) - x(z_j)||_M / (sigma ||z_i - z_j||))^2
+ *   L_U = L_P + lambda L_R,   L = L_U + lambda_ls L_LS
+ * losses[0..4] = L_P, L_R, L_U, L_LS, L (host, may be NULL); grad (of L) as
+ * in lsn_train_eval (the encoder's entries are zero).  lambda, lambda_ls >=
+ * 0, sigma > 0; the samples must be distinct (L_R is reported for B >= 2;
+ * B >= 2 is required when lambda or lambda_ls is positive). */
+int lsn_train_eval_unsup(lsn_ctx* ctx, const double* z, int B, double lambda, double sigma,
+                         double lambda_ls, double* losses, double* grad);
+/* One Adam step (as lsn_train_step) on the gradient of L. */
+int lsn_train_step_unsup(lsn_ctx* ctx, const double* z, int B, double lambda, double sigma,
+                         double lambda_ls, double lr, double* losses);
 /* Cubature Hessians Ht at the B subspace points z (B x r, host) into H
  * (B x r x r, host), with the trainer's current decoder. */
 int lsn_train_hessians(lsn_ctx* ctx, const double* z, int B, double* H);

@@ -164,13 +164,20 @@ def unsupervised_losses(tp, theta, Z, lam, sigma):
     return Lp, Lr, Lp + lam * Lr
 
 
-def unsupervised_loss_and_grad(tp, theta_np, Z_np, lam, sigma):
-    """float64 losses (L_P, L_R, L_U) and the gradient of L_U."""
+def unsupervised_loss_and_grad(tp, theta_np, Z_np, lam, sigma, lam_ls=0.0):
+    """float64 losses (L_P, L_R, L_U, L_LS, L = L_U + lam_ls L_LS) and the
+    gradient of L; L_LS (Eq. 9) at the same samples, held fixed."""
     theta = torch.tensor(theta_np, dtype=torch_dtype, requires_grad=True)
     Z = torch.tensor(Z_np, dtype=torch_dtype)
-    Lp, Lr, L = unsupervised_losses(tp, theta, Z, lam, sigma)
+    Lp, Lr, Lu = unsupervised_losses(tp, theta, Z, lam, sigma)
+    Lls = torch.zeros((), dtype=torch_dtype)
+    if lam_ls != 0.0 and Z.shape[0] >= 2:
+        P = tp.unpack(theta)
+        H = torch.stack([tp.hessian(P, Z[b], create_graph=True) for b in range(Z.shape[0])])
+        Lls = lipschitz_loss(H, Z)
+    L = Lu + lam_ls * Lls
     (g,) = torch.autograd.grad(L, theta)
-    return (float(Lp.detach()), float(Lr.detach()), float(L.detach())), g.numpy()
+    return tuple(float(v.detach()) for v in (Lp, Lr, Lu, Lls, L)), g.numpy()
 
 
 def lipschitz_loss(H, Z):

@@ -83,6 +83,12 @@ _SIGS = {
     "lsn_train_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                        ctypes.c_double, ctypes.c_void_p],
     "lsn_train_hessians": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "lsn_train_eval_unsup": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                             ctypes.c_void_p],
+    "lsn_train_step_unsup": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_void_p],
     "lsn_train_apply": [ctypes.c_void_p],
     "lsn_element_system_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -384,6 +390,26 @@ class Context:
         losses = np.zeros(3)
         self._check(self.lib.lsn_train_step(self.h, _ptr(q), int(q.shape[0]), float(lambda_ls),
                                             float(lr), _ptr(losses)))
+        return tuple(losses)
+
+    def train_eval_unsup(self, Z, lam, sigma, lambda_ls=0.0, grad=None, want_grad=True):
+        """Eq. 4 (+ lambda_ls Eq. 9) at the samples Z (B x r):
+        (L_P, L_R, L_U, L_LS, L), gradient of L."""
+        Z = _f64(Z)
+        losses = np.zeros(5)
+        if grad is None and want_grad:
+            grad = np.zeros(self.train_num_params())
+        self._check(self.lib.lsn_train_eval_unsup(self.h, _ptr(Z), int(Z.shape[0]), float(lam),
+                                                  float(sigma), float(lambda_ls), _ptr(losses),
+                                                  _ptr(grad)))
+        return tuple(losses), grad
+
+    def train_step_unsup(self, Z, lam, sigma, lr, lambda_ls=0.0):
+        Z = _f64(Z)
+        losses = np.zeros(5)
+        self._check(self.lib.lsn_train_step_unsup(self.h, _ptr(Z), int(Z.shape[0]), float(lam),
+                                                  float(sigma), float(lambda_ls), float(lr),
+                                                  _ptr(losses)))
         return tuple(losses)
 
     def train_hessians(self, Z):

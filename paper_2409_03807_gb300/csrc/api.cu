@@ -1522,6 +1522,67 @@ int lsn_train_step(lsn_ctx* c, const double* q, int B, double lambda_ls, double 
   LSN_GUARD_END
 }
 
+int lsn_train_eval_unsup(lsn_ctx* c, const double* z, int B, double lambda, double sigma,
+                         double lambda_ls, double* losses, double* grad) {
+  int rc = train_ready(c);
+  if (rc != LSN_OK) return rc;
+  if (!z || B < 1 || !(lambda >= 0.0) || !(sigma > 0.0) || !(lambda_ls >= 0.0) ||
+      ((lambda > 0.0 || lambda_ls > 0.0) && B < 2))
+    return fail(c, LSN_ERR_ARG, "train_eval_unsup: bad arguments");
+  LSN_GUARD_BEGIN
+  const int r = c->widths[0];
+  std::vector<double> zh((size_t)B * r);
+  if (is_device_ptr(z)) {
+    ck(cudaMemcpyAsync(zh.data(), z, sizeof(double) * zh.size(), cudaMemcpyDeviceToHost,
+                       c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+  } else {
+    std::copy(z, z + zh.size(), zh.begin());
+  }
+  for (int b = 0; b < B; ++b)
+    for (int a = 0; a < b; ++a) {
+      bool same = true;
+      for (int k = 0; k < r && same; ++k) same = zh[(size_t)a * r + k] == zh[(size_t)b * r + k];
+      if (same) return fail(c, LSN_ERR_ARG, "train_eval_unsup: repeated sample");
+    }
+  double l[5];
+  try {
+    c->trainer->evaluate_unsup(zh.data(), B, lambda, sigma, lambda_ls, l, c->stream);
+  } catch (...) {
+    return fail(c, LSN_ERR_CUDA, "train_eval_unsup: CUDA error in the training kernels");
+  }
+  if (losses) std::copy(l, l + 5, losses);
+  if (grad) {
+    std::vector<double> h(c->trainer->nparams);
+    try {
+      c->trainer->get_grad(h.data());
+    } catch (...) {
+      return fail(c, LSN_ERR_CUDA, "train_eval_unsup: CUDA error reading the gradient");
+    }
+    if (is_device_ptr(grad)) host_to_user(h, grad, c->stream);
+    else std::copy(h.begin(), h.end(), grad);
+  }
+  return std::isfinite(l[4]) ? LSN_OK
+                             : fail(c, LSN_ERR_NONFINITE, "train_eval_unsup: non-finite loss");
+  LSN_GUARD_END
+}
+
+int lsn_train_step_unsup(lsn_ctx* c, const double* z, int B, double lambda, double sigma,
+                         double lambda_ls, double lr, double* losses) {
+  if (!(lr > 0.0)) return fail(c, LSN_ERR_ARG, "train_step_unsup: lr must be > 0");
+  int rc = lsn_train_eval_unsup(c, z, B, lambda, sigma, lambda_ls, losses, nullptr);
+  if (rc != LSN_OK) return rc;
+  LSN_GUARD_BEGIN
+  try {
+    c->trainer->adam(lr, c->stream);
+  } catch (...) {
+    return fail(c, LSN_ERR_CUDA, "train_step_unsup: CUDA error in the Adam update");
+  }
+  ck(cudaStreamSynchronize(c->stream));
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
 int lsn_train_hessians(lsn_ctx* c, const double* z, int B, double* H) {
   int rc = train_ready(c);
   if (rc != LSN_OK) return rc;

@@ -697,6 +697,113 @@ __global__ void row_adjoint_kernel(const int* __restrict__ inc_ptr, const int* _
       out[1 + r + p] = scale * sg * (c == d ? Real(1) : Real(2)) * Gbar[b * P + p];
 }
 
+// ------------------------------------------------ unsupervised loss (Eq. 4)
+// Potential term: per (cubature tet, sample) the weighted energy w V Psi(F)
+// and its 12 position derivatives, from the decoder output OUT (n x B, raw,
+// before bias and scale) on the cubature rows.  Psi and dPsi/dF are written
+// in Hd = F - I (as in the solver's element kernels).
+template <typename Real>
+__global__ void unsup_elem_kernel(const int4* __restrict__ tets, const Real* __restrict__ dminv,
+                                  const Real* __restrict__ wv, const int* __restrict__ rows,
+                                  const Real* __restrict__ X0S, const Real* __restrict__ OUT,
+                                  const Real* __restrict__ bias, int S, int B, Real scale,
+                                  Real mu, Real lam, Real alpha, double* __restrict__ epart,
+                                  Real* __restrict__ gx) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)S * B) return;
+  const int b = (int)(id / S), e = (int)(id % S);
+  const int4 tv = tets[e];
+  const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
+  Real xv[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int lr = 3 * vv[a] + i, gr = rows[lr];
+      xv[a][i] = X0S[lr] + scale * (OUT[(long long)gr * B + b] + bias[gr]);
+    }
+  Real Dm[3][3], H[3][3];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Dm[k / 3][k % 3] = dminv[k * S + e];
+  // Hd = Ds Dm^-1 - I, Ds the edge matrix of the deformed tet
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Real v = Real(0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) v += (xv[a + 1][i] - xv[0][i]) * Dm[a][j];
+      H[i][j] = v - (i == j ? Real(1) : Real(0));
+    }
+  Real trH = H[0][0] + H[1][1] + H[2][2], nrm = Real(0), cofH[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      nrm += H[i][j] * H[i][j];
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+      cofH[i][j] = H[i1][j1] * H[i2][j2] - H[i1][j2] * H[i2][j1];
+    }
+  const Real Ic3 = Real(2) * trH + nrm;
+  const Real m2 = cofH[0][0] + cofH[1][1] + cofH[2][2];
+  const Real detH = H[0][0] * cofH[0][0] + H[0][1] * cofH[0][1] + H[0][2] * cofH[0][2];
+  const Real Jm1 = trH + m2 + detH;
+  const Real oma = Real(1) - alpha;
+  const Real w = wv[e];
+  const Real psi = Real(0.5) * mu * Ic3 - Real(0.5) * mu * log1p(Ic3 * Real(0.25)) +
+                   Real(0.5) * lam * Jm1 * (Jm1 + Real(2) * oma);
+  epart[id] = (double)(w * psi);
+  const Real dl = Ic3 / (Real(4) * (Ic3 + Real(4)));
+  Real* g = gx + id * 12;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Real P[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const Real Fij = H[i][j] + (i == j ? Real(1) : Real(0));
+      const Real cofF = (i == j ? Real(1) + trH : Real(0)) - H[j][i] + cofH[i][j];
+      P[j] = w * (mu * dl * Fij + lam * Jm1 * cofF +
+                  Real(0.75) * mu * (H[i][j] + H[j][i] - (i == j ? trH : Real(0)) - cofH[i][j]));
+    }
+    Real s0 = Real(0);
+#pragma unroll
+    for (int a = 1; a < 4; ++a) {
+      const Real v = P[0] * Dm[a - 1][0] + P[1] * Dm[a - 1][1] + P[2] * Dm[a - 1][2];
+      g[3 * a + i] = v;
+      s0 += v;
+    }
+    g[i] = -s0;
+  }
+}
+
+// dOUT[row][b] += coef * sum over the tets at the row's vertex of their
+// derivative (fixed order along the incidence list)
+template <typename Real>
+__global__ void unsup_row_kernel(const int* __restrict__ inc_ptr, const int* __restrict__ inc,
+                                 const int* __restrict__ rows, int RS, int S, int B,
+                                 const Real* __restrict__ gx, Real coef,
+                                 Real* __restrict__ dOUT) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)RS * B) return;
+  const int lr = (int)(id / B), b = (int)(id % B);
+  const int vtx = lr / 3, comp = lr % 3;
+  Real sx = Real(0);
+  for (int q = inc_ptr[vtx]; q < inc_ptr[vtx + 1]; ++q) {
+    const int tet = inc[q] >> 2, slot = inc[q] & 3;
+    sx += gx[((long long)b * S + tet) * 12 + 3 * slot + comp];
+  }
+  dOUT[(long long)rows[lr] * B + b] += coef * sx;
+}
+
+// Y[row][b] = c m_{row / 3} X[row][b]
+template <typename Real>
+__global__ void mass_rows_kernel(const Real* __restrict__ X, const double* __restrict__ mass,
+                                 int n, int B, Real c, Real* __restrict__ Yo) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)n * B) return;
+  Yo[i] = c * (Real)mass[(i / B) / 3] * X[i];
+}
+
 template <typename Real>
 __global__ void adam_kernel(Real* __restrict__ th, const Real* __restrict__ g,
                             Real* __restrict__ m, Real* __restrict__ v, long long N, Real lr,
@@ -776,7 +883,8 @@ struct Trainer : TrainerBase {
   Real *WS = nullptr, *bS = nullptr, *dWS = nullptr, *dbS = nullptr, *XS = nullptr,
        *dXS = nullptr, *dY = nullptr, *dZh = nullptr, *contrib = nullptr, *gx = nullptr,
        *gJ = nullptr, *gk = nullptr, *Gbar = nullptr;
-  double *Hs = nullptr, *lpart = nullptr, *rpart = nullptr;
+  double *Hs = nullptr, *lpart = nullptr, *rpart = nullptr, *epart = nullptr;
+  Real *Gm = nullptr, *Cm = nullptr;  // B x B Gram and repulsion coefficients (Eq. 4)
 
   template <typename T>
   T* alloc(std::vector<void*>& keep, size_t count) {
@@ -898,6 +1006,9 @@ struct Trainer : TrainerBase {
     Hs = alloc<double>(bbufs, (size_t)B * P);
     lpart = alloc<double>(bbufs, B);
     rpart = alloc<double>(bbufs, 1024);
+    Gm = alloc<Real>(bbufs, (size_t)B * B);
+    Cm = alloc<Real>(bbufs, (size_t)B * B);
+    epart = alloc<double>(bbufs, (size_t)B * ts.S);
     Bcap = B;
   }
 
@@ -999,6 +1110,24 @@ struct Trainer : TrainerBase {
     mm(s, r, n, B, one, dcur, B, 1, D, 1, B, zero, grad + off[0], n);
     rowsum_kernel<Real><<<blocks(r), 256, 0, s>>>(dcur, r, B, B, 1, 0, one, grad + off[1], 0);
     // ---- Lipschitz loss (Eq. 9) on the cubature Hessians
+    const double lls = lipschitz_part(B, lambda_ls, s);
+    std::vector<double> rp(rb);
+    tck(cudaMemcpyAsync(rp.data(), rpart, sizeof(double) * rb, cudaMemcpyDeviceToHost, s));
+    tck(cudaStreamSynchronize(s));
+    tck(cudaGetLastError());
+    double lc = 0.0;
+    for (double v : rp) lc += v;
+    lc /= B;
+    losses[0] = lc;
+    losses[1] = lls;
+    losses[2] = lc + lambda_ls * lls;
+  }
+
+  // Eq. 9 at the samples held in Z (r x B): returns L_LS and adds
+  // lambda_ls dL_LS/dtheta to the gradient (the samples held fixed)
+  double lipschitz_part(int B, double lambda_ls, cudaStream_t s) {
+    const int r = ts.widths[0], Hc = ts.widths[L - 1];
+    const Real one = Real(1), zero = Real(0);
     double lls = 0.0;
     if (lambda_ls != 0.0 && B >= 2) {
       const Real lam = (Real)lambda_ls;
@@ -1033,16 +1162,127 @@ struct Trainer : TrainerBase {
       tck(cudaStreamSynchronize(s));
       for (int b = 0; b < B; ++b) lls += lp[b];
     }
-    std::vector<double> rp(rb);
-    tck(cudaMemcpyAsync(rp.data(), rpart, sizeof(double) * rb, cudaMemcpyDeviceToHost, s));
+    return lls;
+  }
+
+  // decoder forward of the samples held in Z (r x B) to OUT (n x B)
+  const Real* forward_out(int B, cudaStream_t s) {
+    const Real one = Real(1), zero = Real(0);
+    const Real* hin = Z;
+    for (int l = 0; l + 1 < L; ++l) {
+      const int M = ts.widths[l + 1], K = ts.widths[l];
+      mm(s, M, B, K, one, theta + off[2 + 2 * l], K, 1, hin, B, 1, zero, A[l], B);
+      bias_elu_kernel<Real><<<blocks((long long)M * B), 256, 0, s>>>(
+          A[l], theta + off[3 + 2 * l], M, B, Hh[l]);
+      hin = Hh[l];
+    }
+    const int Hc = ts.widths[L - 1];
+    mm(s, ts.n, B, Hc, one, theta + off[2 + 2 * (L - 1)], Hc, 1, hin, B, 1, zero, OUT, B);
+    return hin;
+  }
+
+  // gradient of the decoder parameters from the adjoint dOUT (n x B) of OUT
+  void backward_from_out(int B, const Real* hin, cudaStream_t s) {
+    const Real one = Real(1), zero = Real(0);
+    const int n = ts.n, Hc = ts.widths[L - 1];
+    mm(s, n, Hc, B, one, dOUT, B, 1, hin, 1, B, zero, grad + off[2 + 2 * (L - 1)], Hc);
+    rowsum_kernel<Real><<<blocks(n), 256, 0, s>>>(dOUT, n, B, B, 1, 0, one,
+                                                  grad + off[3 + 2 * (L - 1)], 0);
+    mm(s, Hc, B, n, one, theta + off[2 + 2 * (L - 1)], 1, Hc, dOUT, B, 1, zero, dH, B);
+    Real* dcur = dH;
+    Real* dnext = dH2;
+    for (int l = L - 2; l >= 0; --l) {
+      const int M = ts.widths[l + 1], K = ts.widths[l];
+      elu_back_kernel<Real><<<blocks((long long)M * B), 256, 0, s>>>(A[l], dcur,
+                                                                     (long long)M * B);
+      const Real* hprev = l == 0 ? Z : Hh[l - 1];
+      mm(s, M, K, B, one, dcur, B, 1, hprev, 1, B, zero, grad + off[2 + 2 * l], K);
+      rowsum_kernel<Real><<<blocks(M), 256, 0, s>>>(dcur, M, B, B, 1, 0, one,
+                                                    grad + off[3 + 2 * l], 0);
+      if (l > 0)
+        mm(s, K, B, M, one, theta + off[2 + 2 * l], 1, K, dcur, B, 1, zero, dnext, B);
+      std::swap(dcur, dnext);
+    }
+  }
+
+  void evaluate_unsup(const double* z, int B, double lambda, double sigma, double lambda_ls,
+                      double* losses, cudaStream_t s) override {
+    ensure_batch(B);
+    const int r = ts.widths[0], n = ts.n, S = ts.S;
+    const Real one = Real(1), zero = Real(0);
+    const double sc = ts.scale;
+    tck(cudaMemsetAsync(grad, 0, sizeof(Real) * nparams, s));
+    std::vector<Real> zt((size_t)r * B);
+    for (int b = 0; b < B; ++b)
+      for (int i = 0; i < r; ++i) zt[(size_t)i * B + b] = (Real)z[(size_t)b * r + i];
+    tck(cudaMemcpyAsync(Z, zt.data(), sizeof(Real) * zt.size(), cudaMemcpyHostToDevice, s));
+    const Real* hin = forward_out(B, s);
+    // repulsion: Gram G = OUT^T M OUT, ||x_i - x_j||_M^2 = s^2 (G_ii + G_jj - 2 G_ij)
+    double lr_sum = 0.0;
+    std::vector<double> cmat((size_t)B * B, 0.0);
+    if (B >= 2) {
+      mass_rows_kernel<Real><<<blocks((long long)n * B), 256, 0, s>>>(OUT, ts.mass, n, B, one, D);
+      mm(s, B, B, n, one, OUT, 1, B, D, B, 1, zero, Gm, B);
+      std::vector<Real> G((size_t)B * B);
+      tck(cudaMemcpyAsync(G.data(), Gm, sizeof(Real) * G.size(), cudaMemcpyDeviceToHost, s));
+      tck(cudaStreamSynchronize(s));
+      const double np = (double)B * (B - 1);
+      std::vector<double> c((size_t)B * B, 0.0);
+      for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) {
+          if (i == j) continue;
+          const double dm = sc * sc * ((double)G[i * B + i] + (double)G[j * B + j] -
+                                       2.0 * (double)G[i * B + j]);
+          double dz = 0.0;
+          for (int k = 0; k < r; ++k) {
+            const double d = z[(size_t)i * r + k] - z[(size_t)j * r + k];
+            dz += d * d;
+          }
+          const double ell = 0.5 * std::log(dm) - std::log(sigma) - 0.5 * std::log(dz);
+          lr_sum += ell * ell;
+          c[(size_t)i * B + j] = ell / (np * dm);  // dL_R / d(dm_ij)
+        }
+      // dL_R/dOUT_i = sum_j (c_ij + c_ji) 2 s^2 M (OUT_i - OUT_j): OUT times
+      // (diag(row sums of C + C^T) - (C + C^T))
+      for (int i = 0; i < B; ++i) {
+        double d = 0.0;
+        for (int j = 0; j < B; ++j) {
+          if (i == j) continue;
+          const double cs = c[(size_t)i * B + j] + c[(size_t)j * B + i];
+          cmat[(size_t)j * B + i] = -cs;  // column i: sample i's adjoint
+          d += cs;
+        }
+        cmat[(size_t)i * B + i] = d;
+      }
+      lr_sum /= np;
+      std::vector<Real> cr(cmat.begin(), cmat.end());
+      tck(cudaMemcpyAsync(Cm, cr.data(), sizeof(Real) * cr.size(), cudaMemcpyHostToDevice, s));
+      mm(s, n, B, B, one, OUT, B, 1, Cm, B, 1, zero, D, B);
+      mass_rows_kernel<Real><<<blocks((long long)n * B), 256, 0, s>>>(
+          D, ts.mass, n, B, (Real)(2.0 * lambda * sc * sc), dOUT);
+    } else {
+      tck(cudaMemsetAsync(dOUT, 0, sizeof(Real) * (size_t)n * B, s));
+    }
+    // potential: per (tet, sample) energies and derivatives on the cubature rows
+    unsup_elem_kernel<Real><<<blocks((long long)S * B, 128), 128, 0, s>>>(
+        ctl, cdminv, cwv, rows, X0S, OUT, theta + off[3 + 2 * (L - 1)], S, B, (Real)sc,
+        (Real)ts.mu, (Real)ts.lam, (Real)ts.alpha, epart, gx);
+    unsup_row_kernel<Real><<<blocks((long long)ts.RS * B, 128), 128, 0, s>>>(
+        inc_ptr, inc, rows, ts.RS, S, B, gx, (Real)(sc / B), dOUT);
+    backward_from_out(B, hin, s);
+    const double lls = lipschitz_part(B, lambda_ls, s);
+    std::vector<double> ep((size_t)S * B);
+    tck(cudaMemcpyAsync(ep.data(), epart, sizeof(double) * ep.size(), cudaMemcpyDeviceToHost, s));
     tck(cudaStreamSynchronize(s));
     tck(cudaGetLastError());
-    double lc = 0.0;
-    for (double v : rp) lc += v;
-    lc /= B;
-    losses[0] = lc;
-    losses[1] = lls;
-    losses[2] = lc + lambda_ls * lls;
+    double lp = 0.0;
+    for (double v : ep) lp += v;
+    lp /= B;
+    losses[0] = lp;
+    losses[1] = lr_sum;
+    losses[2] = lp + lambda * lr_sum;
+    losses[3] = lls;
+    losses[4] = losses[2] + lambda_ls * lls;
   }
 
   void adam(double lr, cudaStream_t s) override {

@@ -41,6 +41,12 @@ struct TrainerBase {
   // losses[3] = L_C, L_LS, L; gradient kept on the device
   virtual void evaluate(const double* q_dev, int B, double lambda_ls, double* losses,
                         cudaStream_t s) = 0;
+  // unsupervised loss of Eq. 4 at the samples z (B x r, host), with the
+  // Lipschitz loss of Eq. 9 at the same samples: losses[5] = L_P, L_R,
+  // L_U = L_P + lambda L_R, L_LS, L_U + lambda_ls L_LS; gradient of the last
+  // kept on the device
+  virtual void evaluate_unsup(const double* z, int B, double lambda, double sigma,
+                              double lambda_ls, double* losses, cudaStream_t s) = 0;
   // Ht (B x P upper, row-major) at the subspace points z (B x r), host arrays
   virtual void hessians_host(const double* z, int B, double* Hs, cudaStream_t s) = 0;
   virtual void adam(double lr, cudaStream_t s) = 0;

@@ -151,7 +151,8 @@ def test_unsupervised_gradient_matches_central_differences(setup):
     from oracle.training import unsupervised_loss_and_grad
     tp, theta, Q, Ws, bs = setup
     Z = np.random.default_rng(6).standard_normal((4, 3))
-    (Lp, Lr, L), g = unsupervised_loss_and_grad(tp, theta, Z, 0.3, 0.02)
+    (Lp, Lr, Lu, Lls, L), g = unsupervised_loss_and_grad(tp, theta, Z, 0.3, 0.02, 1e-3)
+    assert L == pytest.approx(Lu + 1e-3 * Lls, rel=1e-14) and Lls > 0.0
     n_enc = tp.sizes[0] + tp.sizes[1]
     assert np.all(g[:n_enc] == 0.0)          # the encoder takes no part
     rng = np.random.default_rng(101)
@@ -160,6 +161,6 @@ def test_unsupervised_gradient_matches_central_differences(setup):
         tp_, tm_ = theta.copy(), theta.copy()
         tp_[k] += h
         tm_[k] -= h
-        fd = (unsupervised_loss_and_grad(tp, tp_, Z, 0.3, 0.02)[0][2] -
-              unsupervised_loss_and_grad(tp, tm_, Z, 0.3, 0.02)[0][2]) / (2 * h)
+        fd = (unsupervised_loss_and_grad(tp, tp_, Z, 0.3, 0.02, 1e-3)[0][4] -
+              unsupervised_loss_and_grad(tp, tm_, Z, 0.3, 0.02, 1e-3)[0][4]) / (2 * h)
         assert fd == pytest.approx(g[k], rel=1e-5, abs=1e-8 * max(1.0, abs(L)))
