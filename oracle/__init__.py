@@ -19,7 +19,7 @@ decoder   the MLP subspace map f(z), its forward-mode Jacobian and its
           second-order tangents.
 reduced   the reduced objective E(z) of Eq. 2, its gradient and Gauss-Newton
           Hessian, Cholesky + Armijo Newton, implicit Euler stepping.
-fullspace full-space projective Newton on Eq. 1 (the subspace-error judge
+fullspace full-space projective Newton on Eq. 1 (the reference for the subspace error
           and snapshot generator).
 training  reconstruction loss (Eq. 3), cubature subspace Hessian (Sec. 4.3),
           Lipschitz loss (Eq. 9), combined loss (Eq. 10), Lip estimate

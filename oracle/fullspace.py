@@ -1,6 +1,6 @@
 """Full-space implicit Euler / quasi-static solve of Eq. 1 (Sec. 3.1) by
-projective Newton with Armijo backtracking: the fallback, the judge of
-subspace error, and the snapshot generator for decoder training (Sec. 3.2,
+projective Newton with Armijo backtracking: the fallback, the reference for
+the subspace error, and the snapshot generator for decoder training (Sec. 3.2,
 supervised setting).
 
 Every tet is used with weight 1.  Constrained DOFs are held at their targets
