@@ -129,10 +129,13 @@ class TrainProblem:
         return torch.autograd.functional.hessian(f, z, create_graph=create_graph)
 
     # -- losses ----------------------------------------------------------
-    def losses(self, theta, Q, lam_ls, create_graph=False, Z_samples=None):
+    def losses(self, theta, Q, lam_ls, create_graph=False, Z_samples=None, order=2):
         """(L_C, L_LS, L, Z, H) for parameters theta (torch, flat) and snapshot
         positions Q (B, n).  The L_LS samples are z_i = g(q_i) without gradient
-        (or the given Z_samples, which finite-difference checks hold fixed)."""
+        (or the given Z_samples, which finite-difference checks hold fixed).
+        order 0: the Lipschitz loss of the potential itself (the Supplement's
+        order-o family, o = 0), 1/(B(B-1)) sum_{i != j} (Pt_i - Pt_j)^2 /
+        ||z_i - z_j||^2; order 2: Eq. 9."""
         P = self.unpack(theta)
         Z = self.encode(P, Q)
         X = self.decode(P, Z)
@@ -142,6 +145,15 @@ class TrainProblem:
         B = Q.shape[0]
         if lam_ls == 0.0 or B < 2:
             return Lc, torch.zeros((), dtype=torch_dtype), Lc, Zs, None
+        if order == 0:
+            rows = torch.tensor(self.rows, dtype=torch.long)
+            Pz = torch.stack([self.cubature_potential(self.decode(P, Zs[b], rows))
+                              for b in range(B)])
+            dP = Pz[:, None] - Pz[None, :]
+            dz = ((Zs[:, None] - Zs[None, :]) ** 2).sum(dim=2)
+            off = ~torch.eye(B, dtype=torch.bool)
+            L0 = (dP[off] ** 2 / dz[off]).sum() / (B * (B - 1))
+            return Lc, L0, Lc + lam_ls * L0, Zs, None
         H = torch.stack([self.hessian(P, Zs[b], create_graph=create_graph) for b in range(B)])
         Lls = lipschitz_loss(H, Zs)
         return Lc, Lls, Lc + lam_ls * Lls, Zs, H
@@ -203,13 +215,14 @@ def lipschitz_estimate(H, Z):
     return best
 
 
-def loss_and_grad(tp, theta_np, Q_np, lam_ls, Z_samples=None):
+def loss_and_grad(tp, theta_np, Q_np, lam_ls, Z_samples=None, order=2):
     """float64 losses and the gradient of L w.r.t. the flat parameters (the
     L_LS samples held fixed, as in training)."""
     theta = torch.tensor(theta_np, dtype=torch_dtype, requires_grad=True)
     Q = torch.tensor(Q_np, dtype=torch_dtype)
     Zf = None if Z_samples is None else torch.tensor(Z_samples, dtype=torch_dtype)
-    Lc, Lls, L, Z, H = tp.losses(theta, Q, lam_ls, create_graph=True, Z_samples=Zf)
+    Lc, Lls, L, Z, H = tp.losses(theta, Q, lam_ls, create_graph=True, Z_samples=Zf,
+                                 order=order)
     (g,) = torch.autograd.grad(L, theta)
     return ((float(Lc.detach()), float(Lls.detach()), float(L.detach())), g.numpy(),
             Z.numpy(), None if H is None else H.detach().numpy())

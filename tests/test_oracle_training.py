@@ -164,3 +164,32 @@ def test_unsupervised_gradient_matches_central_differences(setup):
         fd = (unsupervised_loss_and_grad(tp, tp_, Z, 0.3, 0.02, 1e-3)[0][4] -
               unsupervised_loss_and_grad(tp, tm_, Z, 0.3, 0.02, 1e-3)[0][4]) / (2 * h)
         assert fd == pytest.approx(g[k], rel=1e-5, abs=1e-8 * max(1.0, abs(L)))
+
+
+def test_zeroth_order_lipschitz_loss(setup):
+    """L_LS,0 equals a double loop over the numpy oracle's cubature energies
+    at the encoded samples, and its gradient (samples held fixed) central
+    differences."""
+    tp, theta, Q, Ws, bs = setup
+    (Lc, L0, L), g, Z, _ = loss_and_grad(tp, theta, Q, 0.7, order=0)
+    dec = Decoder([np.asarray(W, np.float64) for W in Ws], [np.asarray(b) for b in bs], tp.scale)
+    tl, DmInv, cw = tp.ctets_local.numpy(), tp.cDmInv.numpy(), tp.cw.numpy()
+    E = []
+    for z in Z:
+        xv = (tp.X0.ravel() + dec.out(z))[tp.rows].reshape(-1, 3)
+        E.append(float(np.sum(cw * fem.element_energy(xv, tl, DmInv, np.ones(len(tl)), tp.mu,
+                                                      tp.lam))))
+    B = len(E)
+    ref = sum((E[i] - E[j]) ** 2 / np.sum((Z[i] - Z[j]) ** 2)
+              for i in range(B) for j in range(B) if i != j) / (B * (B - 1))
+    assert L0 == pytest.approx(ref, rel=1e-10)
+    assert L == pytest.approx(Lc + 0.7 * L0, rel=1e-14)
+    rng = np.random.default_rng(102)
+    for k in rng.choice(theta.size, 6, replace=False):
+        h = 1e-6 * max(1.0, abs(theta[k]))
+        tp_, tm_ = theta.copy(), theta.copy()
+        tp_[k] += h
+        tm_[k] -= h
+        fd = (loss_and_grad(tp, tp_, Q, 0.7, Z_samples=Z, order=0)[0][2] -
+              loss_and_grad(tp, tm_, Q, 0.7, Z_samples=Z, order=0)[0][2]) / (2 * h)
+        assert fd == pytest.approx(g[k], rel=1e-5, abs=1e-8 * max(1.0, abs(L)))
