@@ -324,6 +324,15 @@ int lsn_train_eval_unsup(lsn_ctx* ctx, const double* z, int B, double lambda, do
 /* One Adam step (as lsn_train_step) on the gradient of L. */
 int lsn_train_step_unsup(lsn_ctx* ctx, const double* z, int B, double lambda, double sigma,
                          double lambda_ls, double lr, double* losses);
+/* Order of the Lipschitz loss in lsn_train_eval / lsn_train_step (the
+ * Supplement's family L_LS,o of Lipschitz losses of the o-th derivative of
+ * the potential in z): 2 (default) is Eq. 9 on the cubature Hessians; 0 is
+ * 1/(B(B-1)) sum_{i != j} (Pt(z_i) - Pt(z_j))^2 / ||z_i - z_j||^2 with the
+ * same cubature potential and samples (for the ablation of the order).
+ * Other orders: LSN_ERR_ARG.  Applies to the current and later trainers;
+ * the unsupervised calls always use order 2. */
+int lsn_set_lipschitz_order(lsn_ctx* ctx, int order);
+
 /* Cubature Hessians Ht at the B subspace points z (B x r, host) into H
  * (B x r x r, host), with the trainer's current decoder. */
 int lsn_train_hessians(lsn_ctx* ctx, const double* z, int B, double* H);

@@ -83,6 +83,7 @@ _SIGS = {
     "lsn_train_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                        ctypes.c_double, ctypes.c_void_p],
     "lsn_train_hessians": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "lsn_set_lipschitz_order": [ctypes.c_void_p, ctypes.c_int],
     "lsn_train_eval_unsup": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                              ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                              ctypes.c_void_p],
@@ -411,6 +412,9 @@ class Context:
                                                   float(sigma), float(lambda_ls), float(lr),
                                                   _ptr(losses)))
         return tuple(losses)
+
+    def set_lipschitz_order(self, order):
+        return self._check(self.lib.lsn_set_lipschitz_order(self.h, int(order)))
 
     def train_hessians(self, Z):
         Z = np.ascontiguousarray(Z, np.float64)

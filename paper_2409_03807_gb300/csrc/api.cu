@@ -222,6 +222,7 @@ struct lsn_ctx {
   long long passes_total = 0;
   // decoder training (lsn_train_*)
   std::unique_ptr<TrainerBase> trainer;
+  int lip_order = 2;  // order of the Lipschitz loss in training (0 or 2)
   int* tr_cub_idx = nullptr;
   double* tr_cub_w = nullptr;
   double* tr_q = nullptr;
@@ -1405,6 +1406,7 @@ int lsn_train_init(lsn_ctx* c, const float* enc_W, const float* enc_b, const int
                     : (c->precision == LSN_PREC_TF32 || c->precision == LSN_PREC_BF16) ? 2
                                                                                       : 0;
   std::unique_ptr<TrainerBase> tr(TrainerBase::create(tmode, ts));
+  tr->lip_order = c->lip_order;
   std::vector<double> theta(tr->nparams);
   std::copy(enc_W, enc_W + (size_t)r * c->n, theta.begin() + tr->off[0]);
   std::copy(enc_b, enc_b + r, theta.begin() + tr->off[1]);
@@ -1581,6 +1583,15 @@ int lsn_train_step_unsup(lsn_ctx* c, const double* z, int B, double lambda, doub
   ck(cudaStreamSynchronize(c->stream));
   return LSN_OK;
   LSN_GUARD_END
+}
+
+int lsn_set_lipschitz_order(lsn_ctx* c, int order) {
+  if (!c) return LSN_ERR_ARG;
+  if (order != 0 && order != 2)
+    return fail(c, LSN_ERR_ARG, "set_lipschitz_order: orders 0 and 2 are supported");
+  c->lip_order = order;
+  if (c->trainer) c->trainer->lip_order = order;
+  return LSN_OK;
 }
 
 int lsn_train_hessians(lsn_ctx* c, const double* z, int B, double* H) {

@@ -782,7 +782,7 @@ template <typename Real>
 __global__ void unsup_row_kernel(const int* __restrict__ inc_ptr, const int* __restrict__ inc,
                                  const int* __restrict__ rows, int RS, int S, int B,
                                  const Real* __restrict__ gx, Real coef,
-                                 Real* __restrict__ dOUT) {
+                                 const Real* __restrict__ coefb, Real* __restrict__ dOUT) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (long long)RS * B) return;
   const int lr = (int)(id / B), b = (int)(id % B);
@@ -792,7 +792,7 @@ __global__ void unsup_row_kernel(const int* __restrict__ inc_ptr, const int* __r
     const int tet = inc[q] >> 2, slot = inc[q] & 3;
     sx += gx[((long long)b * S + tet) * 12 + 3 * slot + comp];
   }
-  dOUT[(long long)rows[lr] * B + b] += coef * sx;
+  dOUT[(long long)rows[lr] * B + b] += coef * (coefb ? coefb[b] : Real(1)) * sx;
 }
 
 // Y[row][b] = c m_{row / 3} X[row][b]
@@ -1109,8 +1109,10 @@ struct Trainer : TrainerBase {
     }
     mm(s, r, n, B, one, dcur, B, 1, D, 1, B, zero, grad + off[0], n);
     rowsum_kernel<Real><<<blocks(r), 256, 0, s>>>(dcur, r, B, B, 1, 0, one, grad + off[1], 0);
-    // ---- Lipschitz loss (Eq. 9) on the cubature Hessians
-    const double lls = lipschitz_part(B, lambda_ls, s);
+    // ---- Lipschitz loss on the cubature Hessians (Eq. 9), or of the
+    // potential itself (order 0)
+    const double lls = lip_order == 0 ? lipschitz0_part(B, lambda_ls, hin, s)
+                                      : lipschitz_part(B, lambda_ls, s);
     std::vector<double> rp(rb);
     tck(cudaMemcpyAsync(rp.data(), rpart, sizeof(double) * rb, cudaMemcpyDeviceToHost, s));
     tck(cudaStreamSynchronize(s));
@@ -1165,6 +1167,49 @@ struct Trainer : TrainerBase {
     return lls;
   }
 
+  // The zeroth-order Lipschitz loss at the samples held in Z, with OUT (and
+  // the activations) of the decoder forward at them: returns L_LS,0 and adds
+  // lambda_ls dL_LS,0/dtheta to the decoder blocks of the gradient (the
+  // samples held fixed: nothing flows into the encoder).
+  double lipschitz0_part(int B, double lambda_ls, const Real* hin, cudaStream_t s) {
+    if (lambda_ls == 0.0 || B < 2) return 0.0;
+    const int r = ts.widths[0], S = ts.S;
+    const double sc = ts.scale;
+    unsup_elem_kernel<Real><<<blocks((long long)S * B, 128), 128, 0, s>>>(
+        ctl, cdminv, cwv, rows, X0S, OUT, theta + off[3 + 2 * (L - 1)], S, B, (Real)sc,
+        (Real)ts.mu, (Real)ts.lam, (Real)ts.alpha, epart, gx);
+    std::vector<double> ep((size_t)S * B);
+    std::vector<Real> zt((size_t)r * B);
+    tck(cudaMemcpyAsync(ep.data(), epart, sizeof(double) * ep.size(), cudaMemcpyDeviceToHost, s));
+    tck(cudaMemcpyAsync(zt.data(), Z, sizeof(Real) * zt.size(), cudaMemcpyDeviceToHost, s));
+    tck(cudaStreamSynchronize(s));
+    std::vector<double> Pb(B, 0.0), cb(B, 0.0);
+    for (int b = 0; b < B; ++b)
+      for (int e = 0; e < S; ++e) Pb[b] += ep[(size_t)b * S + e];
+    const double np = (double)B * (B - 1);
+    double l0 = 0.0;
+    for (int i = 0; i < B; ++i)
+      for (int j = 0; j < B; ++j) {
+        if (i == j) continue;
+        double dz = 0.0;
+        for (int k = 0; k < r; ++k) {
+          const double d = (double)zt[(size_t)k * B + i] - (double)zt[(size_t)k * B + j];
+          dz += d * d;
+        }
+        const double dp = Pb[i] - Pb[j];
+        l0 += dp * dp / dz;
+        cb[i] += 4.0 * dp / (np * dz);  // both orders of the pair (i, j)
+      }
+    l0 /= np;
+    std::vector<Real> cr(cb.begin(), cb.end());
+    tck(cudaMemcpyAsync(Cm, cr.data(), sizeof(Real) * B, cudaMemcpyHostToDevice, s));
+    tck(cudaMemsetAsync(dOUT, 0, sizeof(Real) * (size_t)ts.n * B, s));
+    unsup_row_kernel<Real><<<blocks((long long)ts.RS * B, 128), 128, 0, s>>>(
+        inc_ptr, inc, rows, ts.RS, S, B, gx, (Real)(lambda_ls * sc), Cm, dOUT);
+    backward_from_out(B, hin, s, true);
+    return l0;
+  }
+
   // decoder forward of the samples held in Z (r x B) to OUT (n x B)
   const Real* forward_out(int B, cudaStream_t s) {
     const Real one = Real(1), zero = Real(0);
@@ -1182,12 +1227,13 @@ struct Trainer : TrainerBase {
   }
 
   // gradient of the decoder parameters from the adjoint dOUT (n x B) of OUT
-  void backward_from_out(int B, const Real* hin, cudaStream_t s) {
-    const Real one = Real(1), zero = Real(0);
+  // (accumulate: add to the gradient instead of overwriting the decoder blocks)
+  void backward_from_out(int B, const Real* hin, cudaStream_t s, bool accumulate = false) {
+    const Real one = Real(1), zero = Real(0), beta = accumulate ? one : zero;
     const int n = ts.n, Hc = ts.widths[L - 1];
-    mm(s, n, Hc, B, one, dOUT, B, 1, hin, 1, B, zero, grad + off[2 + 2 * (L - 1)], Hc);
+    mm(s, n, Hc, B, one, dOUT, B, 1, hin, 1, B, beta, grad + off[2 + 2 * (L - 1)], Hc);
     rowsum_kernel<Real><<<blocks(n), 256, 0, s>>>(dOUT, n, B, B, 1, 0, one,
-                                                  grad + off[3 + 2 * (L - 1)], 0);
+                                                  grad + off[3 + 2 * (L - 1)], accumulate);
     mm(s, Hc, B, n, one, theta + off[2 + 2 * (L - 1)], 1, Hc, dOUT, B, 1, zero, dH, B);
     Real* dcur = dH;
     Real* dnext = dH2;
@@ -1196,9 +1242,9 @@ struct Trainer : TrainerBase {
       elu_back_kernel<Real><<<blocks((long long)M * B), 256, 0, s>>>(A[l], dcur,
                                                                      (long long)M * B);
       const Real* hprev = l == 0 ? Z : Hh[l - 1];
-      mm(s, M, K, B, one, dcur, B, 1, hprev, 1, B, zero, grad + off[2 + 2 * l], K);
+      mm(s, M, K, B, one, dcur, B, 1, hprev, 1, B, beta, grad + off[2 + 2 * l], K);
       rowsum_kernel<Real><<<blocks(M), 256, 0, s>>>(dcur, M, B, B, 1, 0, one,
-                                                    grad + off[3 + 2 * l], 0);
+                                                    grad + off[3 + 2 * l], accumulate);
       if (l > 0)
         mm(s, K, B, M, one, theta + off[2 + 2 * l], 1, K, dcur, B, 1, zero, dnext, B);
       std::swap(dcur, dnext);
@@ -1268,7 +1314,7 @@ struct Trainer : TrainerBase {
         ctl, cdminv, cwv, rows, X0S, OUT, theta + off[3 + 2 * (L - 1)], S, B, (Real)sc,
         (Real)ts.mu, (Real)ts.lam, (Real)ts.alpha, epart, gx);
     unsup_row_kernel<Real><<<blocks((long long)ts.RS * B, 128), 128, 0, s>>>(
-        inc_ptr, inc, rows, ts.RS, S, B, gx, (Real)(sc / B), dOUT);
+        inc_ptr, inc, rows, ts.RS, S, B, gx, (Real)(sc / B), nullptr, dOUT);
     backward_from_out(B, hin, s);
     const double lls = lipschitz_part(B, lambda_ls, s);
     std::vector<double> ep((size_t)S * B);

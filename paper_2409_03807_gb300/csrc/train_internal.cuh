@@ -34,6 +34,7 @@ struct TrainerBase {
   long long nparams = 0;
   std::vector<long long> off;    // offsets of Ew, eb, W_1, b_1, ...
   int L = 0, P = 0, Cs = 0;
+  int lip_order = 2;  // Lipschitz loss of the potential's Hessian (2) or of the potential (0)
   virtual ~TrainerBase() {}
   // mode 0: FP32 (CUDA cores), 1: FP64, 2: FP32 with TF32 tensor-core GEMMs
   static TrainerBase* create(int mode, const TrainSetup& ts);

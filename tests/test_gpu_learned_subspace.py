@@ -90,7 +90,7 @@ def _unpack(th, widths, n):
     return Ew, eb, Ws, bs
 
 
-def _train_and_measure(pkg, data, lam, steps, r=8):
+def _train_and_measure(pkg, data, lam, steps, r=8, order=2):
     import torch
     mesh, cn, targets, Q, held, Qh = data
     n = 3 * mesh.nv
@@ -107,6 +107,7 @@ def _train_and_measure(pkg, data, lam, steps, r=8):
     ctx.set_material(E_, NU, RHO, GRAV)
     ctx.set_decoder(Ws, bs, SCALE, "fp32")
     ctx.train_init(Ew, eb, cub, np.full(64, mesh.ne / 64))
+    ctx.set_lipschitz_order(order)
     rs = np.random.default_rng(3)
     for _ in range(steps):
         ctx.train_step(Q[rs.choice(Q.shape[0], 16, replace=False)], lam, 1e-3)
@@ -196,3 +197,42 @@ def test_lbfgs_exit_shares_per_tolerance(pkg, data, trained):
         print(f" {eps:.0e}  {which:9s} " + " ".join(f"{sh[n]:5.1f}%" for n in
                                                    ("I", "II", "III", "IV", "floor")) +
               f"   {g:.2e}   {it:7.1f}")
+
+
+def test_lipschitz_order_ablation(pkg, data, trained):
+    """The Supplement's ablation of the Lipschitz loss's order: training with
+    the zeroth-order loss (potential differences) against the paper's
+    second-order one (Hessian differences, Eq. 9) and no Lipschitz term.
+    lambda_0 puts the zeroth-order term at the weight the second-order term
+    has at the untrained decoder.  Printed: L_C, the Hessian Lipschitz
+    estimate (Eq. 7) and Newton iterations on the held-out loads; checked:
+    the second-order loss gives the lowest Hessian Lipschitz estimate."""
+    import torch
+    mesh, cn, targets, Q, held, Qh = data
+    r = 8
+    n = 3 * mesh.nv
+    widths = [r, 64, 64, n]
+    Ws, bs = xavier_decoder(widths, 0)
+    _, sv, Vt = np.linalg.svd(Q - mesh.X0.ravel(), full_matrices=False)
+    Ew = (Vt[:r] / sv[:r, None] * np.sqrt(Q.shape[0])).astype(np.float32)
+    eb = np.zeros(r, np.float32)
+    rng = np.random.default_rng(1)
+    cub = np.sort(rng.choice(mesh.ne, 64, replace=False)).astype(np.int32)
+    scale = {}
+    for order in (0, 2):
+        ctx = pkg.Context()
+        ctx.set_mesh(mesh.X0, mesh.tets)
+        ctx.set_material(E_, NU, RHO, GRAV)
+        ctx.set_decoder(Ws, bs, SCALE, "fp32")
+        ctx.train_init(Ew, eb, cub, np.full(64, mesh.ne / 64))
+        ctx.set_lipschitz_order(order)
+        scale[order] = ctx.train_eval(Q[:16], 1.0, want_grad=False)[0][1]
+        ctx.close()
+    lam0 = 1e-6 * scale[2] / scale[0]
+    zeroth = _train_and_measure(pkg, data, lam0, 3000, order=0)
+    van, second = trained["vanilla"], trained["lipschitz"]
+    print(f"\n lambda_0 {lam0:.3e}")
+    for name, m in (("vanilla", van), ("order 0", zeroth), ("order 2", second)):
+        print(f" {name:8s} L_C {m['Lc']:.3e}  Lip[Hessian] {m['lip']:.3e}  "
+              f"Newton iters {m['iters']:4d}  max error {m['err']:.3e}")
+    assert second["lip"] < min(van["lip"], zeroth["lip"])

@@ -148,3 +148,20 @@ def test_autograd_function_and_adam_lower_the_loss(pkg):
     l1 = ctx.train_eval(Q, 1e-3, want_grad=False)[0][2]
     assert l1 < 0.5 * l0
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
+def test_zeroth_order_lipschitz_loss_matches_oracle(pkg, prec):
+    """lsn_set_lipschitz_order(0): losses and gradient of L_C + lambda L_LS,0."""
+    mesh, widths, cub, w, Ws, bs, Ew, eb, Q, tp, theta = make_case()
+    ctx = gpu_ctx(pkg, mesh, Ws, bs, Ew, eb, cub, w, prec)
+    ctx.set_lipschitz_order(0)
+    th = ctx.train_get_params()
+    (lc, l0, L), g = ctx.train_eval(Q, 0.7)
+    (lc0, l00, L0), g0, _, _ = loss_and_grad(tp, th, Q, 0.7, order=0)
+    tl, tg = {"fp64": (1e-8, 1e-8), "fp32": (1e-4, 2e-3), "tf32": (2e-3, 3e-2)}[prec]
+    assert lc == pytest.approx(lc0, rel=tl)
+    assert l0 == pytest.approx(l00, rel=tl, abs=1e-12)
+    assert L == pytest.approx(L0, rel=tl)
+    assert rel(g, g0) < tg, rel(g, g0)
+    ctx.close()
