@@ -107,3 +107,45 @@ def test_argument_errors(pkg):
         ctx.set_cubature(np.array([0, mesh.ne], np.int32), np.ones(2))
     assert e.value.code == -1
     ctx.close()
+
+
+def test_argument_errors_of_the_optimiser_cubature_and_training_calls(pkg):
+    ctx = pkg.Context()
+    mesh = make_bar(4, 3, 3, 0.05)
+    ctx.set_mesh(mesh.X0, mesh.tets)
+    ctx.set_material(1e5, 0.45, 1000.0, (0, 0, -9.8))
+    # affine modes need a decoder, and fit in r <= 64 with it
+    with pytest.raises(pkg.LsnError) as e:
+        ctx.set_affine_modes(mesh.X0.mean(0))
+    assert e.value.code == -4
+    Ws, bs = xavier_decoder([60, 8, 3 * mesh.nv], 0)
+    ctx.set_decoder(Ws, bs, 1e-2)
+    with pytest.raises(pkg.LsnError) as e:
+        ctx.set_affine_modes(mesh.X0.mean(0))     # 60 + 12 > 64
+    assert e.value.code == -1
+    Ws, bs = xavier_decoder([4, 8, 3 * mesh.nv], 0)
+    ctx.set_decoder(Ws, bs, 1e-2)
+    for kind, hist in (("lbfgs", 0), ("lbfgs", 33)):
+        with pytest.raises(pkg.LsnError) as e:
+            ctx.set_optimizer(kind, hist)
+        assert e.value.code == -1
+    with pytest.raises(KeyError):
+        ctx.set_optimizer("sgd", 10)
+    ctx.set_state()
+    Z = np.random.default_rng(0).standard_normal((2, 4)) * 0.1
+    with pytest.raises(pkg.LsnError) as e:
+        ctx.select_cubature(Z, mesh.ne + 1)
+    assert e.value.code == -1
+    # training: unsupported Lipschitz order, repeated unsupervised samples
+    with pytest.raises(pkg.LsnError) as e:
+        ctx.set_lipschitz_order(1)
+    assert e.value.code == -1
+    ctx.train_init(np.zeros((4, 3 * mesh.nv), np.float32), np.zeros(4, np.float32),
+                   np.arange(8, dtype=np.int32), np.ones(8))
+    with pytest.raises(pkg.LsnError) as e:
+        ctx.train_eval_unsup(np.vstack([Z[0], Z[0]]), 0.1, 0.05)
+    assert e.value.code == -1
+    with pytest.raises(pkg.LsnError) as e:
+        ctx.train_eval_unsup(Z, 0.1, 0.0)           # sigma must be positive
+    assert e.value.code == -1
+    ctx.close()
