@@ -125,3 +125,61 @@ def test_unsupervised_training_on_the_torus(pkg):
     print(f" untrained Newton iters/step {it_u:.2f}")
     assert van[1][0] < van[0][0] and lip[1][0] < lip[0][0]
     assert it_l <= it_v
+
+
+def test_unsupervised_training_at_the_full_torus(pkg):
+    """torus_drop_200k (200,928 tets, n = 119,268, r = 32 + 12 affine modes,
+    decoder 32-512x3-n, its 1,024 cubature tets): 300 Adam steps of the
+    unsupervised loss (batch 16, lambda 0.1, sigma 0.05) without and with
+    the Lipschitz term (lambda_LS = 1) on the FP32 trainer, then 24 frames of
+    the FP32 reduced solve (free fall and the first contacts) with the
+    untrained and the two trained decoders.  Printed: losses and Newton
+    iterations per step; checked: the potential loss drops and every solve
+    step ends converged or at the FP32 form's precision floor."""
+    p = build_problem("torus_drop_200k")
+    c = p.config
+    r = c.r
+
+    def train(lam_ls, steps=300):
+        ctx = pkg.Context()
+        ctx.set_mesh(p.X0, p.tets)
+        ctx.set_material(c.youngs, c.poisson, c.density, c.gravity)
+        ctx.set_decoder(p.Ws, p.bs, c.out_scale, "fp32")
+        ctx.train_init(np.zeros((r, p.n), np.float32), np.zeros(r, np.float32), p.cub_idx,
+                       p.cub_w)
+        rng = np.random.default_rng(3)
+        Zt = rng.standard_normal((16, r))
+        l0 = ctx.train_eval_unsup(Zt, 0.1, 0.05, lam_ls, want_grad=False)[0]
+        for _ in range(steps):
+            ctx.train_step_unsup(rng.standard_normal((16, r)), 0.1, 0.05, 1e-3, lam_ls)
+        l1 = ctx.train_eval_unsup(Zt, 0.1, 0.05, lam_ls, want_grad=False)[0]
+        th = ctx.train_get_params()
+        ctx.close()
+        o = r * p.n + r
+        Ws, bs = [], []
+        for a, b in zip(p.widths[:-1], p.widths[1:]):
+            Ws.append(th[o:o + a * b].reshape(b, a).astype(np.float32))
+            o += a * b
+            bs.append(th[o:o + b].astype(np.float32))
+            o += b
+        return l0, l1, Ws, bs
+
+    def solve(Ws_, bs_):
+        pp = dataclasses.replace(p, Ws=Ws_, bs=bs_)
+        sc = pkg.context_from_problem(pp, precision="fp32")
+        its = []
+        for k in range(1, 25):
+            rc, st, _ = sc.step(dt=c.dt)
+            assert rc in (pkg.LSN_OK, pkg.LSN_PRECISION_FLOOR), (k, st)
+            its.append(st["newton_iters"])
+        sc.close()
+        return float(np.mean(its))
+
+    van = train(0.0)
+    lip = train(1.0)
+    it_u, it_v, it_l = solve(p.Ws, p.bs), solve(van[2], van[3]), solve(lip[2], lip[3])
+    print(f"\n full torus: untrained {it_u:.2f} Newton iterations / step")
+    for name, t, it in (("vanilla", van, it_v), ("lipschitz", lip, it_l)):
+        print(f" {name:9s} L_P {t[0][0]:.3e} -> {t[1][0]:.3e}  L_R {t[0][1]:.3e} -> "
+              f"{t[1][1]:.3e}  L_LS {t[1][3]:.3e}  Newton iterations / step {it:.2f}")
+    assert van[1][0] < van[0][0] and lip[1][0] < lip[0][0]
