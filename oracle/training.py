@@ -135,7 +135,8 @@ class TrainProblem:
         (or the given Z_samples, which finite-difference checks hold fixed).
         order 0: the Lipschitz loss of the potential itself (the Supplement's
         order-o family, o = 0), 1/(B(B-1)) sum_{i != j} (Pt_i - Pt_j)^2 /
-        ||z_i - z_j||^2; order 2: Eq. 9."""
+        ||z_i - z_j||^2; order 1: the same with the reduced gradients
+        dPt/dz (squared Euclidean norm of the difference); order 2: Eq. 9."""
         P = self.unpack(theta)
         Z = self.encode(P, Q)
         X = self.decode(P, Z)
@@ -154,6 +155,20 @@ class TrainProblem:
             off = ~torch.eye(B, dtype=torch.bool)
             L0 = (dP[off] ** 2 / dz[off]).sum() / (B * (B - 1))
             return Lc, L0, Lc + lam_ls * L0, Zs, None
+        if order == 1:
+            rows = torch.tensor(self.rows, dtype=torch.long)
+            G = []
+            for b in range(B):
+                zb = Zs[b].clone().requires_grad_(True)
+                pb = self.cubature_potential(self.decode(P, zb, rows))
+                (gb,) = torch.autograd.grad(pb, zb, create_graph=True)
+                G.append(gb)
+            G = torch.stack(G)
+            dG = ((G[:, None] - G[None, :]) ** 2).sum(dim=2)
+            dz = ((Zs[:, None] - Zs[None, :]) ** 2).sum(dim=2)
+            off = ~torch.eye(B, dtype=torch.bool)
+            L1 = (dG[off] / dz[off]).sum() / (B * (B - 1))
+            return Lc, L1, Lc + lam_ls * L1, Zs, None
         H = torch.stack([self.hessian(P, Zs[b], create_graph=create_graph) for b in range(B)])
         Lls = lipschitz_loss(H, Zs)
         return Lc, Lls, Lc + lam_ls * Lls, Zs, H

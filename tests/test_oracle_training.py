@@ -193,3 +193,32 @@ def test_zeroth_order_lipschitz_loss(setup):
         fd = (loss_and_grad(tp, tp_, Q, 0.7, Z_samples=Z, order=0)[0][2] -
               loss_and_grad(tp, tm_, Q, 0.7, Z_samples=Z, order=0)[0][2]) / (2 * h)
         assert fd == pytest.approx(g[k], rel=1e-5, abs=1e-8 * max(1.0, abs(L)))
+
+
+def test_first_order_lipschitz_loss(setup):
+    """L_LS,1 equals a double loop over the numpy oracle's reduced elastic
+    gradients sum_e w_e J_e^T g_e at the encoded samples; its gradient
+    (samples held fixed) central differences."""
+    tp, theta, Q, Ws, bs = setup
+    (Lc, L1, L), g, Z, _ = loss_and_grad(tp, theta, Q, 0.7, order=1)
+    dec = Decoder([np.asarray(W, np.float64) for W in Ws], [np.asarray(b) for b in bs], tp.scale)
+    tl, DmInv, cw = tp.ctets_local.numpy(), tp.cDmInv.numpy(), tp.cw.numpy()
+    G = []
+    for z in Z:
+        o, J = dec.out_jac(z, tp.rows)
+        xv = (tp.X0.ravel()[tp.rows] + o).reshape(-1, 3)
+        ge = fem.element_gradient(xv, tl, DmInv, np.ones(len(tl)), tp.mu, tp.lam)
+        G.append(np.einsum("e,eki,ek->i", cw, J[fem.element_dofs(tl)], ge))
+    B = len(G)
+    ref = sum(np.sum((G[i] - G[j]) ** 2) / np.sum((Z[i] - Z[j]) ** 2)
+              for i in range(B) for j in range(B) if i != j) / (B * (B - 1))
+    assert L1 == pytest.approx(ref, rel=1e-10)
+    rng = np.random.default_rng(103)
+    for k in rng.choice(theta.size, 6, replace=False):
+        h = 1e-6 * max(1.0, abs(theta[k]))
+        tp_, tm_ = theta.copy(), theta.copy()
+        tp_[k] += h
+        tm_[k] -= h
+        fd = (loss_and_grad(tp, tp_, Q, 0.7, Z_samples=Z, order=1)[0][2] -
+              loss_and_grad(tp, tm_, Q, 0.7, Z_samples=Z, order=1)[0][2]) / (2 * h)
+        assert fd == pytest.approx(g[k], rel=1e-5, abs=1e-8 * max(1.0, abs(L)))
