@@ -326,9 +326,10 @@ int lsn_train_step_unsup(lsn_ctx* ctx, const double* z, int B, double lambda, do
                          double lambda_ls, double lr, double* losses);
 /* Order of the Lipschitz loss in lsn_train_eval / lsn_train_step (the
  * Supplement's family L_LS,o of Lipschitz losses of the o-th derivative of
- * the potential in z): 2 (default) is Eq. 9 on the cubature Hessians; 0 is
- * 1/(B(B-1)) sum_{i != j} (Pt(z_i) - Pt(z_j))^2 / ||z_i - z_j||^2 with the
- * same cubature potential and samples (for the ablation of the order).
+ * the potential in z): 2 (default) is Eq. 9 on the cubature Hessians; 1 is
+ * 1/(B(B-1)) sum_{i != j} ||dPt/dz(z_i) - dPt/dz(z_j)||^2 / ||z_i - z_j||^2;
+ * 0 is the same with Pt(z_i) - Pt(z_j); all with the same cubature
+ * potential and samples (for the ablation of the order).
  * Other orders: LSN_ERR_ARG.  Applies to the current and later trainers;
  * the unsupervised calls always use order 2. */
 int lsn_set_lipschitz_order(lsn_ctx* ctx, int order);

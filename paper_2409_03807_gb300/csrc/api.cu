@@ -1587,8 +1587,8 @@ int lsn_train_step_unsup(lsn_ctx* c, const double* z, int B, double lambda, doub
 
 int lsn_set_lipschitz_order(lsn_ctx* c, int order) {
   if (!c) return LSN_ERR_ARG;
-  if (order != 0 && order != 2)
-    return fail(c, LSN_ERR_ARG, "set_lipschitz_order: orders 0 and 2 are supported");
+  if (order < 0 || order > 2)
+    return fail(c, LSN_ERR_ARG, "set_lipschitz_order: orders 0, 1 and 2 are supported");
   c->lip_order = order;
   if (c->trainer) c->trainer->lip_order = order;
   return LSN_OK;

@@ -496,6 +496,77 @@ __global__ void __launch_bounds__(128) elem_hess_kernel(ElemCtx<Real> ec, Real* 
 }
 
 // Hs[b][p] = sum_e contrib[(b S + e) P + p]  (fixed order)
+// First-order Lipschitz loss (the Supplement's order-o family, o = 1).
+// Forward: per (tet, sample) the contribution w V P : G_e[:, c] of the tet to
+// the reduced gradient dPt/dz_c (lane c), contrib[(b S + e) r + c].
+template <typename Real>
+__global__ void __launch_bounds__(128) grad1_kernel(ElemCtx<Real> ec, Real* __restrict__ contrib) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= ec.S * ec.B) return;
+  const int b = warp / ec.S, e = warp % ec.S;
+  Real F[9], Dc[12], Gc[9], wv;
+  int rowi[12];
+  load_elem(ec, e, b, lane, F, Dc, Gc, rowi, wv);
+  ElemD<Real> ed;
+  elem_derivs(F, ec.mu, ec.lam, ec.alpha, ed);
+  if (lane < ec.r) {
+    Real s = Real(0);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) s += ed.P[a] * Gc[a];
+    contrib[((long long)b * ec.S + e) * ec.r + lane] = wv * s;
+  }
+}
+
+// Backward: with gbar_b = dL/d(dPt/dz)(z_b) (B x r), the adjoints of the
+// tet's rows: value rows gx = w V B^T A dF with dF = sum_c gbar_c G_e[:, c],
+// tangent rows gJ[k][c] = gbar_c g_k (g_k the element gradient rows).
+template <typename Real>
+__global__ void __launch_bounds__(128) elem_back1_kernel(ElemCtx<Real> ec,
+                                                         const Real* __restrict__ gbar,
+                                                         Real* __restrict__ gx,
+                                                         Real* __restrict__ gJ) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= ec.S * ec.B) return;
+  const int b = warp / ec.S, e = warp % ec.S;
+  Real F[9], Dc[12], Gc[9], wv;
+  int rowi[12];
+  load_elem(ec, e, b, lane, F, Dc, Gc, rowi, wv);
+  ElemD<Real> ed;
+  elem_derivs(F, ec.mu, ec.lam, ec.alpha, ed);
+  const Real gb = lane < ec.r ? gbar[b * ec.r + lane] : Real(0);
+  Real dF[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    Real v = gb * Gc[a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    dF[a] = v;
+  }
+  Real AdF[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    Real v = Real(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v += ed.A[9 * a + k] * dF[k];
+    AdF[a] = v;
+  }
+  const long long w = (long long)b * ec.S + e;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Real gk = Real(0), gxv = Real(0);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        gk += ed.P[3 * i + j] * Dc[3 * a + j];
+        gxv += AdF[3 * i + j] * Dc[3 * a + j];
+      }
+      const int k = 3 * a + i;
+      if (lane == 0) gx[w * 12 + k] = wv * gxv;
+      if (lane < ec.r) gJ[(w * 12 + k) * ec.r + lane] = gb * wv * gk;
+    }
+}
+
 template <typename Real>
 __global__ void sum_hess_kernel(const Real* __restrict__ contrib, int S, int B, int P,
                                 double* __restrict__ Hs) {
@@ -885,6 +956,7 @@ struct Trainer : TrainerBase {
        *gJ = nullptr, *gk = nullptr, *Gbar = nullptr;
   double *Hs = nullptr, *lpart = nullptr, *rpart = nullptr, *epart = nullptr;
   Real *Gm = nullptr, *Cm = nullptr;  // B x B Gram and repulsion coefficients (Eq. 4)
+  Real* G1 = nullptr;                 // B x r adjoint of the reduced gradients (order 1)
 
   template <typename T>
   T* alloc(std::vector<void*>& keep, size_t count) {
@@ -1007,6 +1079,7 @@ struct Trainer : TrainerBase {
     lpart = alloc<double>(bbufs, B);
     rpart = alloc<double>(bbufs, 1024);
     Gm = alloc<Real>(bbufs, (size_t)B * B);
+    G1 = alloc<Real>(bbufs, (size_t)B * r);
     Cm = alloc<Real>(bbufs, (size_t)B * B);
     epart = alloc<double>(bbufs, (size_t)B * ts.S);
     Bcap = B;
@@ -1112,7 +1185,7 @@ struct Trainer : TrainerBase {
     // ---- Lipschitz loss on the cubature Hessians (Eq. 9), or of the
     // potential itself (order 0)
     const double lls = lip_order == 0 ? lipschitz0_part(B, lambda_ls, hin, s)
-                                      : lipschitz_part(B, lambda_ls, s);
+                                      : lipschitz_part(B, lambda_ls, s, lip_order);
     std::vector<double> rp(rb);
     tck(cudaMemcpyAsync(rp.data(), rpart, sizeof(double) * rb, cudaMemcpyDeviceToHost, s));
     tck(cudaStreamSynchronize(s));
@@ -1127,7 +1200,10 @@ struct Trainer : TrainerBase {
 
   // Eq. 9 at the samples held in Z (r x B): returns L_LS and adds
   // lambda_ls dL_LS/dtheta to the gradient (the samples held fixed)
-  double lipschitz_part(int B, double lambda_ls, cudaStream_t s) {
+  // order 2: Eq. 9 on the cubature Hessians; order 1: the same family on
+  // the reduced gradients (the second-order columns of the pass carry zero
+  // adjoints then)
+  double lipschitz_part(int B, double lambda_ls, cudaStream_t s, int order = 2) {
     const int r = ts.widths[0], Hc = ts.widths[L - 1];
     const Real one = Real(1), zero = Real(0);
     double lls = 0.0;
@@ -1135,10 +1211,47 @@ struct Trainer : TrainerBase {
       const Real lam = (Real)lambda_ls;
       const long long NC = (long long)B * Cs;
       hessians(B, s);
-      lls_kernel<Real><<<B, 128, 0, s>>>(Hs, Z, B, r, P, Gbar, lpart);
       const long long warps = (long long)ts.S * B;
-      elem_back_kernel<Real><<<blocks(warps * 32, 128), 128, 0, s>>>(elem_ctx(B), Gbar, gx, gJ,
-                                                                      gk);
+      double l1 = 0.0;
+      if (order == 1) {
+        grad1_kernel<Real><<<blocks(warps * 32, 128), 128, 0, s>>>(elem_ctx(B), contrib);
+        sum_hess_kernel<Real><<<blocks((long long)B * r), 256, 0, s>>>(contrib, ts.S, B, r, Hs);
+        std::vector<double> gh((size_t)B * r);
+        std::vector<Real> zt((size_t)r * B);
+        tck(cudaMemcpyAsync(gh.data(), Hs, sizeof(double) * gh.size(), cudaMemcpyDeviceToHost,
+                            s));
+        tck(cudaMemcpyAsync(zt.data(), Z, sizeof(Real) * zt.size(), cudaMemcpyDeviceToHost, s));
+        tck(cudaStreamSynchronize(s));
+        const double np = (double)B * (B - 1);
+        std::vector<Real> gbar((size_t)B * r, Real(0));
+        std::vector<double> acc((size_t)B * r, 0.0);
+        for (int i = 0; i < B; ++i)
+          for (int j = 0; j < B; ++j) {
+            if (i == j) continue;
+            double dz = 0.0, dg = 0.0;
+            for (int k = 0; k < r; ++k) {
+              const double d = (double)zt[(size_t)k * B + i] - (double)zt[(size_t)k * B + j];
+              dz += d * d;
+              const double q = gh[(size_t)i * r + k] - gh[(size_t)j * r + k];
+              dg += q * q;
+            }
+            l1 += dg / dz;
+            for (int k = 0; k < r; ++k)  // both orders of the pair (i, j)
+              acc[(size_t)i * r + k] +=
+                  4.0 * (gh[(size_t)i * r + k] - gh[(size_t)j * r + k]) / (np * dz);
+          }
+        l1 /= np;
+        for (size_t q = 0; q < acc.size(); ++q) gbar[q] = (Real)acc[q];
+        tck(cudaMemcpyAsync(G1, gbar.data(), sizeof(Real) * gbar.size(), cudaMemcpyHostToDevice,
+                            s));
+        tck(cudaMemsetAsync(gk, 0, sizeof(Real) * (size_t)B * ts.S * 12, s));
+        tck(cudaMemsetAsync(Gbar, 0, sizeof(Real) * (size_t)B * P, s));
+        elem_back1_kernel<Real><<<blocks(warps * 32, 128), 128, 0, s>>>(elem_ctx(B), G1, gx, gJ);
+      } else {
+        lls_kernel<Real><<<B, 128, 0, s>>>(Hs, Z, B, r, P, Gbar, lpart);
+        elem_back_kernel<Real><<<blocks(warps * 32, 128), 128, 0, s>>>(elem_ctx(B), Gbar, gx,
+                                                                        gJ, gk);
+      }
       row_adjoint_kernel<Real><<<blocks((long long)ts.RS * B, 128), 128, 0, s>>>(
           inc_ptr, inc, ts.RS, ts.S, B, r, P, Cs, (Real)ts.scale, gx, gJ, gk, Gbar, dXS);
       mm(s, ts.RS, Hc, (int)NC, one, dXS, NC, 1, Y[L - 1], 1, NC, zero, dWS, Hc);
@@ -1159,10 +1272,14 @@ struct Trainer : TrainerBase {
           mm(s, K, (int)NC, M, one, theta + off[2 + 2 * l], 1, K, dZh, NC, 1, zero, dY,
                      NC);
       }
-      std::vector<double> lp(B);
-      tck(cudaMemcpyAsync(lp.data(), lpart, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
-      tck(cudaStreamSynchronize(s));
-      for (int b = 0; b < B; ++b) lls += lp[b];
+      if (order == 1) {
+        lls = l1;
+      } else {
+        std::vector<double> lp(B);
+        tck(cudaMemcpyAsync(lp.data(), lpart, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+        tck(cudaStreamSynchronize(s));
+        for (int b = 0; b < B; ++b) lls += lp[b];
+      }
     }
     return lls;
   }

@@ -151,15 +151,20 @@ def test_autograd_function_and_adam_lower_the_loss(pkg):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
-def test_zeroth_order_lipschitz_loss_matches_oracle(pkg, prec):
-    """lsn_set_lipschitz_order(0): losses and gradient of L_C + lambda L_LS,0."""
+@pytest.mark.parametrize("order", [0, 1])
+def test_lower_order_lipschitz_losses_match_oracle(pkg, prec, order):
+    """lsn_set_lipschitz_order(0 or 1): losses and gradient of
+    L_C + lambda L_LS,o (the first-order gradient sums large cancelling
+    adjoints like the second-order one: 0.2 in the FP32 forms)."""
     mesh, widths, cub, w, Ws, bs, Ew, eb, Q, tp, theta = make_case()
     ctx = gpu_ctx(pkg, mesh, Ws, bs, Ew, eb, cub, w, prec)
-    ctx.set_lipschitz_order(0)
+    ctx.set_lipschitz_order(order)
     th = ctx.train_get_params()
     (lc, l0, L), g = ctx.train_eval(Q, 0.7)
-    (lc0, l00, L0), g0, _, _ = loss_and_grad(tp, th, Q, 0.7, order=0)
+    (lc0, l00, L0), g0, _, _ = loss_and_grad(tp, th, Q, 0.7, order=order)
     tl, tg = {"fp64": (1e-8, 1e-8), "fp32": (1e-4, 2e-3), "tf32": (2e-3, 3e-2)}[prec]
+    if order == 1 and prec != "fp64":
+        tg = 0.2
     assert lc == pytest.approx(lc0, rel=tl)
     assert l0 == pytest.approx(l00, rel=tl, abs=1e-12)
     assert L == pytest.approx(L0, rel=tl)
