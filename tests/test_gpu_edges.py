@@ -137,9 +137,10 @@ def test_argument_errors_of_the_optimiser_cubature_and_training_calls(pkg):
         ctx.select_cubature(Z, mesh.ne + 1)
     assert e.value.code == -1
     # training: unsupported Lipschitz order, repeated unsupervised samples
-    with pytest.raises(pkg.LsnError) as e:
-        ctx.set_lipschitz_order(1)
-    assert e.value.code == -1
+    for order in (-1, 3):                         # orders 0, 1 and 2 exist
+        with pytest.raises(pkg.LsnError) as e:
+            ctx.set_lipschitz_order(order)
+        assert e.value.code == -1
     ctx.train_init(np.zeros((4, 3 * mesh.nv), np.float32), np.zeros(4, np.float32),
                    np.arange(8, dtype=np.int32), np.ones(8))
     with pytest.raises(pkg.LsnError) as e:
