@@ -251,6 +251,45 @@ int lsn_tet_forces(lsn_ctx* ctx, const double* z, int K, double* A);
 int lsn_select_cubature(lsn_ctx* ctx, const double* z, int K, int S, int32_t* idx, double* w,
                         int* count, double* rel_residual);
 
+/* Full-space solve (the comparison for the reduced solve; Sec. 3.1, Eq. 1
+ * minimised over all n DOFs, every tet at unit weight).  The method is
+ * projective Newton: per-tet PSD projection of d2Psi/dF2, the same as in the
+ * reduced solve.  It uses the same Armijo backtracking, the tolerance and
+ * caps of lsn_set_solver, and the same exit codes.  Constrained DOFs are
+ * held at their lsn_set_constraints targets.  The ground penalty is not part
+ * of this solve: with a ground set, lsn_fullspace_step returns
+ * LSN_ERR_STATE.
+ *
+ * Newton directions solve the projected Hessian (+ M / dt^2) system on the
+ * free DOFs by Jacobi-preconditioned conjugate gradients, stopped at
+ * |r| <= cg_rtol |r_0| or after max_cg iterations (rounded up to a multiple
+ * of 16).  The Hessian is applied matrix-free per tet.  A breakdown
+ * (non-positive curvature) ends the solve with LSN_NOT_SPD.  With FP32
+ * element math, the line search accepts an energy rise within the rounding
+ * of the element sums.  With FP32 element math, LSN_PRECISION_FLOOR is
+ * returned in three cases.  (1) ||g||_inf has gone 4 iterations without a
+ * 10 % drop while below 100 tol or within 64 u max_i sum |element
+ * contributions to g_i|.  (2) ||g||_inf has gone 16 iterations without such
+ * a drop.  (3) The line search failed at such a gradient.
+ *
+ * lsn_fullspace_setup: allocates the solver, discarding any previous one.
+ * Requires lsn_set_mesh and lsn_set_material.  precision is LSN_PREC_FP64 or
+ * LSN_PREC_FP32 (element math; vectors and sums are FP64); 0 <= cg_rtol < 1;
+ * max_cg >= 1.  The solver keeps its own full state, independent of the
+ * reduced solve's, starting at q = X0, v = 0.  Device memory: about
+ * 13 n doubles plus 43 ne Real values.
+ * lsn_fullspace_set_state: q, v (n each, host or device; NULL: X0 and 0).
+ * lsn_fullspace_step: one implicit-Euler step (dt > 0: q_bar = q + dt v +
+ * dt^2 g, then v = (q' - q) / dt) or quasi-static solve (dt == 0, gravity as
+ * the potential -sum m g.x).  Writes q' to q_out (n, host or device; may be
+ * NULL), stats (may be NULL; energy is the full-space objective at q'), and
+ * the total number of CG iterations to cg_iters (may be NULL).  Returns the
+ * exit status (>= 0) or an error. */
+int lsn_fullspace_setup(lsn_ctx* ctx, int precision, double cg_rtol, int max_cg);
+int lsn_fullspace_set_state(lsn_ctx* ctx, const double* q, const double* v);
+int lsn_fullspace_step(lsn_ctx* ctx, double dt, double* q_out, lsn_stats* stats,
+                       long long* cg_iters);
+
 /* Parity hook for the inertia term: sets dt and qbar (n, host or device)
  * directly, as lsn_step would. dt == 0 selects the quasi-static objective. */
 int lsn_set_dynamics(lsn_ctx* ctx, double dt, const double* qbar);

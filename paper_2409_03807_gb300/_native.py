@@ -57,6 +57,10 @@ _SIGS = {
     "lsn_select_cubature": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                             ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                             ctypes.c_void_p],
+    "lsn_fullspace_setup": [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int],
+    "lsn_fullspace_set_state": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "lsn_fullspace_step": [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                           ctypes.POINTER(LsnStats), ctypes.POINTER(ctypes.c_longlong)],
     "lsn_set_state": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "lsn_set_dynamics": [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p],
     "lsn_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
@@ -270,6 +274,29 @@ class Context:
                                                  _ptr(rel)))
         k = cnt.value
         return idx[:k].copy(), w[:k].copy(), float(rel[0])
+
+    def fullspace_setup(self, precision="fp64", cg_rtol=1e-4, max_cg=4096):
+        """Full-space comparison solve: element math "fp64" or "fp32"."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        return self._check(self.lib.lsn_fullspace_setup(self.h, prec, float(cg_rtol),
+                                                        int(max_cg)))
+
+    def fullspace_set_state(self, q=None, v=None):
+        q, v = _f64(q), _f64(v)
+        return self._check(self.lib.lsn_fullspace_set_state(self.h, _ptr(q), _ptr(v)))
+
+    def fullspace_step(self, dt=0.0, q_out=None):
+        """Returns (exit status, stats dict with "cg_iters", q_out)."""
+        if q_out is None:
+            q_out = np.zeros(self.n)
+        st = LsnStats()
+        cg = ctypes.c_longlong()
+        rc = self.lib.lsn_fullspace_step(self.h, float(dt), _ptr(q_out), ctypes.byref(st),
+                                         ctypes.byref(cg))
+        self._check(rc, allow_positive=True)
+        d = st.as_dict()
+        d["cg_iters"] = int(cg.value)
+        return rc, d, q_out
 
     def set_optimizer(self, kind="newton", history=10):
         """kind: "newton" (projective Newton) or "lbfgs"; history: L-BFGS pairs."""

@@ -227,6 +227,10 @@ struct lsn_ctx {
   double* tr_cub_w = nullptr;
   double* tr_q = nullptr;
   long long tr_qcap = 0;
+  // full-space comparison solve (lsn_fullspace_*): its own q, v
+  std::unique_ptr<FullSpaceBase> fs;
+  double fs_rtol = 1e-4;
+  int fs_max_cg = 4096;
 };
 
 namespace {
@@ -687,6 +691,7 @@ void lsn_destroy(lsn_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   c->eng.reset();
+  c->fs.reset();
   c->trainer.reset();
   dfree(c->tr_cub_idx);
   dfree(c->tr_cub_w);
@@ -709,6 +714,7 @@ int lsn_set_mesh(lsn_ctx* c, const double* X0, int nv, const int32_t* tets, int 
   LSN_GUARD_BEGIN
   ck(cudaSetDevice(c->device));
   c->eng.reset();
+  c->fs.reset();
   free_mesh(c);
   cudaStream_t s = c->stream;
   c->nv = nv;
@@ -1159,6 +1165,112 @@ int lsn_select_cubature(lsn_ctx* c, const double* z, int K, int S, int32_t* idx,
   *count = (int)P.size();
   if (rel_residual) *rel_residual = rel;
   return LSN_OK;
+  LSN_GUARD_END
+}
+
+}  // extern "C"
+
+namespace {
+FsArgs fullspace_args(const lsn_ctx* c) {
+  FsArgs a;
+  a.nv = c->nv;
+  a.n = c->n;
+  a.ne = c->ne;
+  a.X0 = c->X0;
+  a.tets = c->tets;
+  a.dminv = c->dminv;
+  a.vol = c->vol;
+  a.mass = c->mass;
+  a.cslot = c->cslot;
+  a.cu = c->cu;
+  a.mu = c->youngs / (2.0 * (1.0 + c->poisson));
+  a.lam = c->youngs * c->poisson / ((1.0 + c->poisson) * (1.0 - 2.0 * c->poisson));
+  for (int k = 0; k < 3; ++k) a.grav[k] = c->grav[k];
+  a.tol = c->tol;
+  a.armijo_c = c->armijo_c;
+  a.cg_rtol = c->fs_rtol;
+  a.max_newton = c->max_newton;
+  a.max_ls = c->max_ls;
+  a.max_cg = c->fs_max_cg;
+  return a;
+}
+}  // namespace
+
+extern "C" {
+
+int lsn_fullspace_setup(lsn_ctx* c, int precision, double cg_rtol, int max_cg) {
+  if (!c) return LSN_ERR_ARG;
+  if (c->n == 0) return fail(c, LSN_ERR_STATE, "fullspace_setup: call lsn_set_mesh first");
+  if (!c->have_material)
+    return fail(c, LSN_ERR_STATE, "fullspace_setup: call lsn_set_material first");
+  if (precision != LSN_PREC_FP64 && precision != LSN_PREC_FP32)
+    return fail(c, LSN_ERR_ARG, "fullspace_setup: precision must be LSN_PREC_FP64 or FP32");
+  if (!(cg_rtol >= 0.0 && cg_rtol < 1.0) || max_cg < 1)
+    return fail(c, LSN_ERR_ARG, "fullspace_setup: need 0 <= cg_rtol < 1 and max_cg >= 1");
+  LSN_GUARD_BEGIN
+  c->fs.reset();
+  c->fs_rtol = cg_rtol;
+  c->fs_max_cg = max_cg;
+  FullSpaceBase* f = nullptr;
+  cudaError_t e = make_fullspace(precision == LSN_PREC_FP64, fullspace_args(c), c->num_sms,
+                                 c->stream, &f);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  c->fs.reset(f);
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_fullspace_set_state(lsn_ctx* c, const double* q, const double* v) {
+  if (!c) return LSN_ERR_ARG;
+  if (!c->fs) return fail(c, LSN_ERR_STATE, "fullspace_set_state: call lsn_fullspace_setup first");
+  LSN_GUARD_BEGIN
+  cudaStream_t s = c->stream;
+  if (q) upload(c->fs->positions(), q, sizeof(double) * c->n, s);
+  else ck(cudaMemcpyAsync(c->fs->positions(), c->X0, sizeof(double) * c->n,
+                          cudaMemcpyDeviceToDevice, s));
+  if (v) upload(c->fs->velocities(), v, sizeof(double) * c->n, s);
+  else ck(cudaMemsetAsync(c->fs->velocities(), 0, sizeof(double) * c->n, s));
+  ck(cudaStreamSynchronize(s));
+  ck(cudaGetLastError());
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_fullspace_step(lsn_ctx* c, double dt, double* q_out, lsn_stats* stats,
+                       long long* cg_iters) {
+  if (!c) return LSN_ERR_ARG;
+  if (!(dt >= 0.0) || !std::isfinite(dt))
+    return fail(c, LSN_ERR_ARG, "fullspace_step: dt must be >= 0");
+  if (!c->fs) return fail(c, LSN_ERR_STATE, "fullspace_step: call lsn_fullspace_setup first");
+  if (c->ground_k > 0.0)
+    return fail(c, LSN_ERR_STATE, "fullspace_step: the ground penalty is not part of this solve");
+  auto t0 = std::chrono::steady_clock::now();
+  LSN_GUARD_BEGIN
+  FsResult res;
+  cudaError_t e = c->fs->step(fullspace_args(c), dt, res, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  if (res.status == LSN_ERR_NONFINITE)
+    return fail(c, LSN_ERR_NONFINITE, "fullspace_step: non-finite energy or gradient");
+  if (q_out) {
+    if (is_device_ptr(q_out))
+      ck(cudaMemcpyAsync(q_out, c->fs->positions(), sizeof(double) * c->n,
+                         cudaMemcpyDeviceToDevice, c->stream));
+    else
+      ck(cudaMemcpyAsync(q_out, c->fs->positions(), sizeof(double) * c->n,
+                         cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+  }
+  auto t1 = std::chrono::steady_clock::now();
+  if (stats) {
+    stats->newton_iters = res.newton_iters;
+    stats->ls_trials = res.ls_trials;
+    stats->exit = res.status;
+    stats->grad_inf = res.grad_inf;
+    stats->energy = res.energy;
+    stats->ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  }
+  if (cg_iters) *cg_iters = res.cg_iters;
+  return res.status;
   LSN_GUARD_END
 }
 

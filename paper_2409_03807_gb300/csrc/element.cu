@@ -1299,6 +1299,246 @@ __global__ void __launch_bounds__(128) tet_force_kernel(const int4* __restrict__
   }
 }
 
+// ------------------------------------------------------------- full space
+// Full-space projective Newton (Eq. 1 over all n DOFs, every tet at unit
+// weight): the comparison solve of the reduced method.  The projected element
+// Hessian is kept in factored form, Hproj_e = A_e^T A_e, with A_e the map of
+// element_item_td applied to the tet's four vertex displacements (in place of
+// four rows of J), so a Hessian-vector product is A_e^T (A_e v_e) per tet,
+// scattered with FP64 atomics.  The per-tet factor data (U, V, the scaled
+// scaling modes and the twist / flip scales: FS_NF values) are stored
+// structure-of-arrays [FS_NF][ne] at each Newton iterate.
+namespace fullsp {
+constexpr int NT = 64;   // tets per CTA of the evaluation kernel
+constexpr int HT = 128;  // threads of the Hessian-vector and energy kernels
+
+// Sums a and b over the CTA (NTH threads) and stores them at out[0], out[1].
+template <int NTH>
+__device__ __forceinline__ void block_sum2(double a, double b, double* out) {
+  __shared__ double sh[2][NTH / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sh[0][w] = a;
+    sh[1][w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = 0; k < NTH / 32; ++k) {
+      s0 += sh[0][k];
+      s1 += sh[1][k];
+    }
+    out[0] = s0;
+    out[1] = s1;
+  }
+}
+
+// Adjoint of element_item_td: f = A_e^T Cv as forces on the tet's four
+// vertices.  The eigen coordinates Cv give S in the (U, V) frame, the
+// perturbation of F is U S V^T, and its vertex forces follow from D.
+template <typename Real>
+__device__ __forceinline__ void item_adjoint(const TetData<Real>& td, const Real (&Cv)[9],
+                                             Real (&f)[4][3]) {
+  Real S[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) S[a][b] = Real(0);
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) S[a][a] += td.As[3 * m + a] * Cv[m];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    const Real tw = td.tf[i] * Cv[3 + i], fl = td.tf[3 + i] * Cv[6 + i];
+    S[j][k] += tw + fl;
+    S[k][j] += fl - tw;
+  }
+  Real US[3][3], Gb[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      US[i][b] = td.U[3 * i] * S[0][b] + td.U[3 * i + 1] * S[1][b] + td.U[3 * i + 2] * S[2][b];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      Gb[i][c] = US[i][0] * td.V[3 * c] + US[i][1] * td.V[3 * c + 1] + US[i][2] * td.V[3 * c + 2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      f[a][i] = td.D[3 * a] * Gb[i][0] + td.D[3 * a + 1] * Gb[i][1] + td.D[3 * a + 2] * Gb[i][2];
+}
+
+// Evaluation at the Newton iterate u = q - X0: per tet the energy (summed
+// per CTA into part[2 b], part[2 b + 1] = sum |terms|), the gradient
+// scattered into g (and |contributions| into gabs: the rounding scale of
+// each g_i), the factor data into fac and the diagonal of A_e^T A_e (the
+// Jacobi preconditioner) scattered into diag.  g, gabs and diag are zeroed
+// by the caller.  ea.S = ne, ea.dminv / ea.wv the tets' Dm^-1 and volumes.
+template <typename Real>
+__global__ void __launch_bounds__(NT) fs_elem_kernel(ElemArgs ea, const Real* __restrict__ u,
+                                                     Real* __restrict__ fac,
+                                                     double* __restrict__ g,
+                                                     double* __restrict__ gabs,
+                                                     double* __restrict__ diag,
+                                                     double* __restrict__ part) {
+  __shared__ ElemTile<Real, NT> tl;
+  const int t = threadIdx.x;
+  const int ne = ea.S;
+  const Real mu = (Real)ea.mu, lam = (Real)ea.lam;
+  const Real oma = (Real)(-0.75 * ea.mu / ea.lam);  // 1 - a
+  double eacc = 0.0, eabs = 0.0;
+  for (int e0 = blockIdx.x * NT; e0 < ne; e0 += gridDim.x * NT) {
+    const int e = e0 + t;
+    Real pe;
+    // each thread writes and reads back only its own slot of the tile
+    element_phase1<Real, NT>(ea, u, e, t, tl, mu, lam, oma, pe);
+    if (e >= ne) continue;
+    eacc += (double)pe;
+    eabs += fabs((double)pe);
+    TetData<Real> td;
+    load_tet_data<Real, NT>(tl, t, td);
+    const int4 tv = ea.tets[e];
+    const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const Real fa = td.D[3 * a] * td.p[3 * i] + td.D[3 * a + 1] * td.p[3 * i + 1] +
+                        td.D[3 * a + 2] * td.p[3 * i + 2];
+        atomicAdd(&g[3 * vv[a] + i], (double)fa);
+        atomicAdd(&gabs[3 * vv[a] + i], fabs((double)fa));
+      }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      fac[(size_t)k * ne + e] = td.U[k];
+      fac[(size_t)(9 + k) * ne + e] = td.V[k];
+      fac[(size_t)(18 + k) * ne + e] = td.As[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) fac[(size_t)(27 + k) * ne + e] = td.tf[k];
+    // diagonal entries |A_e e_(a,i)|^2
+    for (int a = 0; a < 4; ++a)
+      for (int i = 0; i < 3; ++i) {
+        Real jv[4][3];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) jv[b][k] = (b == a && k == i) ? Real(1) : Real(0);
+        Real Cv[9], gp = Real(0);
+        element_item_td<Real>(td, jv, Cv, gp);
+        Real s = Real(0);
+#pragma unroll
+        for (int m = 0; m < 9; ++m) s += Cv[m] * Cv[m];
+        atomicAdd(&diag[3 * vv[a] + i], (double)s);
+      }
+  }
+  block_sum2<NT>(eacc, eabs, part + 2 * blockIdx.x);
+}
+
+// y += sum_e A_e^T A_e p_e (skipped once *done is set).
+template <typename Real>
+__global__ void __launch_bounds__(HT) fs_hv_kernel(const int4* __restrict__ tets,
+                                                   const Real* __restrict__ dminv, int ne,
+                                                   const Real* __restrict__ fac,
+                                                   const double* __restrict__ p,
+                                                   double* __restrict__ y,
+                                                   const int* __restrict__ done) {
+  if (*done) return;
+  for (int e = blockIdx.x * HT + threadIdx.x; e < ne; e += gridDim.x * HT) {
+    const int4 tv = tets[e];
+    const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
+    TetData<Real> td;
+    Real Dmi[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Dmi[a][b] = dminv[(size_t)(3 * a + b) * ne + e];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      td.D[j] = -(Dmi[0][j] + Dmi[1][j] + Dmi[2][j]);
+#pragma unroll
+      for (int a = 1; a < 4; ++a) td.D[3 * a + j] = Dmi[a - 1][j];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      td.p[k] = Real(0);
+      td.U[k] = fac[(size_t)k * ne + e];
+      td.V[k] = fac[(size_t)(9 + k) * ne + e];
+      td.As[k] = fac[(size_t)(18 + k) * ne + e];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) td.tf[k] = fac[(size_t)(27 + k) * ne + e];
+    Real jv[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) jv[a][i] = (Real)p[3 * vv[a] + i];
+    Real Cv[9], gp = Real(0), f[4][3];
+    element_item_td<Real>(td, jv, Cv, gp);
+    item_adjoint<Real>(td, Cv, f);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) atomicAdd(&y[3 * vv[a] + i], (double)f[a][i]);
+  }
+}
+
+// Elastic energy at q + alpha d (line-search trials), summed per CTA into
+// part[2 b] and part[2 b + 1] = sum |terms|.
+template <typename Real>
+__global__ void __launch_bounds__(HT) fs_energy_kernel(
+    const int4* __restrict__ tets, const Real* __restrict__ dminv, const Real* __restrict__ wv,
+    int ne, const double* __restrict__ q, const double* __restrict__ X0,
+    const double* __restrict__ d, double alpha, double mu_d, double lam_d,
+    double* __restrict__ part) {
+  const Real mu = (Real)mu_d, lam = (Real)lam_d;
+  const Real oma = (Real)(-0.75 * mu_d / lam_d);
+  double eacc = 0.0, eabs = 0.0;
+  for (int e = blockIdx.x * HT + threadIdx.x; e < ne; e += gridDim.x * HT) {
+    const int4 tv = tets[e];
+    const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
+    Real uu[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int k = 3 * vv[a] + i;
+        uu[a][i] = (Real)(q[k] - X0[k] + alpha * d[k]);
+      }
+    Real Dmi[3][3], H[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Dmi[a][b] = dminv[(size_t)(3 * a + b) * ne + e];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Real s = Real(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s += (uu[a + 1][i] - uu[0][i]) * Dmi[a][j];
+        H[i][j] = s;
+      }
+    Invariants<Real> iv;
+    invariants<Real>(H, iv);
+    const double pe = (double)(wv[e] * snh_psi<Real>(iv, mu, lam, oma));
+    eacc += pe;
+    eabs += fabs(pe);
+  }
+  block_sum2<HT>(eacc, eabs, part + 2 * blockIdx.x);
+}
+}  // namespace fullsp
+
 }  // namespace
 
 // Small cubature sets use 64-tet tiles so that more CTAs share the work.
@@ -1393,6 +1633,45 @@ template void launch_tet_forces<float>(const int4*, const double*, const double*
 template void launch_tet_forces<double>(const int4*, const double*, const double*, int, int,
                                         const double*, const double*, double, double, double*,
                                         cudaStream_t);
+
+int fs_grid(int ne, int threads, int num_sms) {
+  return std::max(1, std::min((ne + threads - 1) / threads, 8 * num_sms));
+}
+
+template <typename Real>
+void launch_fs_elem(const ElemArgs& ea, const Real* u, Real* fac, double* g, double* gabs,
+                    double* diag, double* part, int grid, cudaStream_t s) {
+  fullsp::fs_elem_kernel<Real><<<grid, fullsp::NT, 0, s>>>(ea, u, fac, g, gabs, diag, part);
+}
+
+template <typename Real>
+void launch_fs_hv(const int4* tets, const Real* dminv, int ne, const Real* fac, const double* p,
+                  double* y, const int* done, int grid, cudaStream_t s) {
+  fullsp::fs_hv_kernel<Real><<<grid, fullsp::HT, 0, s>>>(tets, dminv, ne, fac, p, y, done);
+}
+
+template <typename Real>
+void launch_fs_energy(const int4* tets, const Real* dminv, const Real* wv, int ne,
+                      const double* q, const double* X0, const double* d, double alpha,
+                      double mu, double lam, double* part, int grid, cudaStream_t s) {
+  fullsp::fs_energy_kernel<Real><<<grid, fullsp::HT, 0, s>>>(tets, dminv, wv, ne, q, X0, d,
+                                                             alpha, mu, lam, part);
+}
+
+template void launch_fs_elem<float>(const ElemArgs&, const float*, float*, double*, double*,
+                                    double*, double*, int, cudaStream_t);
+template void launch_fs_elem<double>(const ElemArgs&, const double*, double*, double*,
+                                     double*, double*, double*, int, cudaStream_t);
+template void launch_fs_hv<float>(const int4*, const float*, int, const float*, const double*,
+                                  double*, const int*, int, cudaStream_t);
+template void launch_fs_hv<double>(const int4*, const double*, int, const double*,
+                                   const double*, double*, const int*, int, cudaStream_t);
+template void launch_fs_energy<float>(const int4*, const float*, const float*, int,
+                                      const double*, const double*, const double*, double,
+                                      double, double, double*, int, cudaStream_t);
+template void launch_fs_energy<double>(const int4*, const double*, const double*, int,
+                                       const double*, const double*, const double*, double,
+                                       double, double, double*, int, cudaStream_t);
 
 int element_grad_grid(int S, int num_sms) {
   const int tiles = (S + gradel::ET - 1) / gradel::ET;

@@ -163,6 +163,26 @@ void launch_tet_forces(const int4* tets, const double* dminv, const double* vol,
 template <typename Real>
 void launch_element_grad(const ElemArgs& ea, const Real* u, const Real* J, const Real* ut,
                          double* part, int grid, cudaStream_t s);
+// Full-space projective Newton (the comparison solve, all tets at unit
+// weight).  fs_elem: at u = q - X0 the per-CTA energy sums (part[2 b],
+// part[2 b + 1] = sum |terms|), the gradient, its sum of |contributions| and
+// the diagonal of the projected Hessian added into g, gabs and diag (zeroed
+// by the caller), and the
+// per-tet factor data [FS_NF][ne] of Hproj_e = A_e^T A_e.  fs_hv: y +=
+// sum_e A_e^T A_e p_e unless *done.  fs_energy: per-CTA elastic energy sums
+// at q + alpha d.  ea.dminv / ea.wv hold Dm^-1 [9][ne] and V_e in Real.
+constexpr int FS_NF = 33;
+int fs_grid(int ne, int threads, int num_sms);
+template <typename Real>
+void launch_fs_elem(const ElemArgs& ea, const Real* u, Real* fac, double* g, double* gabs,
+                    double* diag, double* part, int grid, cudaStream_t s);
+template <typename Real>
+void launch_fs_hv(const int4* tets, const Real* dminv, int ne, const Real* fac, const double* p,
+                  double* y, const int* done, int grid, cudaStream_t s);
+template <typename Real>
+void launch_fs_energy(const int4* tets, const Real* dminv, const Real* wv, int ne,
+                      const double* q, const double* X0, const double* d, double alpha,
+                      double mu, double lam, double* part, int grid, cudaStream_t s);
 cudaError_t launch_element_tc(const ElemArgs& ea, const float* u, const float* J,
                               const float* ut, double* part, int grid, bool bf16, int* err,
                               cudaStream_t s);
@@ -177,6 +197,41 @@ cudaError_t cubature_normalise(double* A, int m, int ne, int r, std::vector<doub
 cudaError_t cubature_nnls(const double* A, int m, int ne, const std::vector<double>& b, int S,
                           std::vector<int>& P, std::vector<double>& xP, double& rel,
                           cudaStream_t s);
+
+// fullspace.cu: full-space projective Newton with preconditioned CG (the
+// comparison solve).  FsArgs carries the context's mesh, material, current
+// constraint targets and solver controls for one step; the solver owns its
+// full state q, v (n doubles each, device).
+struct FsArgs {
+  int nv, n, ne;
+  const double* X0;     // rest positions (n)
+  const int4* tets;     // (ne)
+  const double* dminv;  // Dm^-1 [9][ne]
+  const double* vol;    // (ne)
+  const double* mass;   // lumped, per vertex (nv)
+  const int* cslot;     // per vertex: constraint slot or -1
+  const double* cu;     // constrained displacement targets (3 per slot)
+  double mu, lam, grav[3];
+  double tol, armijo_c, cg_rtol;
+  int max_newton, max_ls, max_cg;
+};
+struct FsResult {
+  int status, newton_iters, ls_trials;
+  long long cg_iters;
+  double grad_inf, energy;
+};
+struct FullSpaceBase {
+  virtual ~FullSpaceBase() {}
+  virtual double* positions() = 0;   // q (device, n)
+  virtual double* velocities() = 0;  // v (device, n)
+  // One implicit-Euler step (dt > 0) or quasi-static solve (dt = 0) from the
+  // current q, v; res.status is an lsn_status (LSN_ERR_NONFINITE when E or g
+  // is not finite, q then left at the last finite iterate).
+  virtual cudaError_t step(const FsArgs& a, double dt, FsResult& res, cudaStream_t s) = 0;
+};
+// Allocates the solver (FP64 or FP32 element math) with q = X0, v = 0.
+cudaError_t make_fullspace(bool fp64, const FsArgs& a, int num_sms, cudaStream_t s,
+                           FullSpaceBase** out);
 
 // solve.cu
 // out[c] = sum over rows of A (all rows) and of B: rows [0, splitB) for

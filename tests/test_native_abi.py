@@ -19,7 +19,8 @@ def test_header_declares_the_solver_calls():
               "lsn_set_material", "lsn_set_constraints", "lsn_set_cubature",
               "lsn_set_ground", "lsn_set_decoder", "lsn_set_solver", "lsn_set_optimizer",
               "lsn_set_state",
-              "lsn_step", "lsn_get_positions", "lsn_eval"]:
+              "lsn_step", "lsn_get_positions", "lsn_eval", "lsn_fullspace_setup",
+              "lsn_fullspace_set_state", "lsn_fullspace_step"]:
         assert n in names
 
 
