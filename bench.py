@@ -59,6 +59,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train", action="store_true",
                     help="time decoder training steps (lsn_train_step) instead of the solve")
+    ap.add_argument("--fullspace", action="store_true",
+                    help="time the full-space GPU solve (the comparison) on the workload's "
+                         "mesh, constraints and frames, and the reduced solve's error against "
+                         "it; use a short run, e.g. --steps 20 --warmup 3")
+    ap.add_argument("--fs-precision", default="fp32", choices=["fp64", "fp32"],
+                    help="element math of the full-space solve")
+    ap.add_argument("--cg-rtol", type=float, default=1e-4,
+                    help="relative CG residual of the full-space Newton directions")
     ap.add_argument("--replay", type=int, default=10,
                     help="timed frames replayed with per-kernel CUDA events")
     return ap.parse_args()
@@ -534,11 +542,80 @@ def run_train(args, world, rank, local):
                           "last_losses": list(losses)}), flush=True)
 
 
+def run_fullspace(args, world, rank, local):
+    """The full-space GPU solve (projective Newton, Jacobi-PCG directions,
+    every tet) over frames 1..W+K of the workload, timed on frames W+1..W+K
+    (host clock around each call; every call ends with a stream
+    synchronisation), then the reduced solve (--precision, --optimizer) over
+    the same frames: its steps/s and its relative displacement error against
+    the full-space positions (the subspace error of the decoder)."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2409_03807_gb300.build import build
+    build()
+    import paper_2409_03807_gb300 as pkg
+    p = load_problem(args)
+    c = p.config
+    if c.ground_k > 0 or not (c.dt > 0):
+        raise SystemExit("--fullspace needs a dynamic workload without ground contact")
+    W, K = args.warmup, args.steps
+    X0 = p.X0.ravel()
+    ctx = pkg.Context()
+    ctx.set_mesh(p.X0, p.tets)
+    ctx.set_material(c.youngs, c.poisson, c.density, c.gravity)
+    ctx.set_solver(c.eps, c.max_newton, c.max_ls, c.armijo_c)
+    ctx.set_constraints(p.cnodes, p.targets(1))
+    ctx.fullspace_setup(args.fs_precision, args.cg_rtol, 4096)
+    Qf, t_full, its, cgs, exits = [], 0.0, 0, 0, {}
+    for k in range(1, W + K + 1):
+        ctx.set_constraints(None, p.targets(k))
+        t0 = time.perf_counter()
+        rc, st, q = ctx.fullspace_step(c.dt)
+        el = time.perf_counter() - t0
+        Qf.append(q.copy())
+        if k > W:
+            t_full += el
+            its += st["newton_iters"]
+            cgs += st["cg_iters"]
+            exits[str(rc)] = exits.get(str(rc), 0) + 1
+    ctx.close()
+    red = pkg.context_from_problem(p, precision=args.precision, optimizer=args.optimizer,
+                                   history=args.history)
+    t_red, err = 0.0, 0.0
+    for k in range(1, W + K + 1):
+        red.set_constraints(None, p.targets(k))
+        t0 = time.perf_counter()
+        red.step(dt=c.dt)
+        el = time.perf_counter() - t0
+        if k > W:
+            t_red += el
+        u, uf = red.get_positions() - X0, Qf[k - 1] - X0
+        err = max(err, float(np.linalg.norm(u - uf) / max(np.linalg.norm(uf), 1e-300)))
+    red.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "full-space GPU solve steps/s (comparison for the reduced solve)",
+            "value": K / t_full, "unit": "steps/s", "n_gpus": 1, "steps": K, "warmup": W,
+            "ms_per_step": 1000.0 * t_full / K, "higher_is_better": True,
+            "dtype": {"fp64": "f64", "fp32": "f32"}[args.fs_precision], "data": "synthetic",
+            "config": {"workload": args.workload, "n": p.n, "tets": p.ne, "dt": c.dt,
+                       "tol_inf": c.eps, "cg_rtol": args.cg_rtol,
+                       "frames": f"{W + 1}..{W + K}", "timing": "host clock per call"},
+            "newton_iters_per_step": its / K, "cg_iters_per_step": cgs / K, "exits": exits,
+            "reduced": {"precision": args.precision, "optimizer": args.optimizer,
+                        "steps_per_s": K / t_red,
+                        "max_rel_displacement_error_vs_fullspace": err,
+                        "frames_compared": f"1..{W + K}"}}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
     if args.train:
         run_train(args, world, rank, local)
+        return
+    if args.fullspace:
+        run_fullspace(args, world, rank, local)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)
