@@ -1,5 +1,6 @@
 """Pins of the oracle's full-space projective Newton solve (Eq. 1)."""
 import numpy as np
+import pytest
 
 from oracle.fullspace import FullModel, newton_solve
 from oracle.reduced import CONVERGED, model_from_problem, ReducedSimulator
@@ -48,3 +49,57 @@ def test_full_space_energy_bounds_subspace_energy():
     assert st.status == CONVERGED
     assert fm.energy(q) <= fm.energy(sim.q) + 1e-12
     assert abs(fm.energy(sim.q) - m.energy(sim.z)) < 1e-10
+
+
+@pytest.mark.parametrize("dt", [0.0, 1.0 / 60.0])
+def test_first_step_from_rest_is_the_linear_elastic_solution(dt):
+    """From rest under a small gravity load, the first full Newton step
+    (alpha = 1) solves (K0 + M / dt^2) u = M g on the free DOFs.  Here K0 is
+    the stiffness assembled from the closed-form rest Hessian of the density,
+    (3 mu / 4)(Id + T) + (lam - 5 mu / 8) v v^T.  Its vec(F) maps
+    (F_ij = sum_a (x_a - x_0)_i (Dm^-1)_{a j}) and the lumped mass are built
+    in this test, so the oracle's element Hessian, projection, assembly,
+    constraint elimination and load terms are all checked against them."""
+    mesh = make_bar(6, 3, 3, 0.05)
+    cn = face_nodes(mesh, 0)
+    E_, nu, rho = 1e5, 0.45, 1000.0
+    mu, lam = E_ / (2 * (1 + nu)), E_ * nu / ((1 + nu) * (1 - 2 * nu))
+    grav = np.array([0.0, 0.0, -1e-3])
+    X, T4 = mesh.X0, mesh.tets
+    nv = X.shape[0]
+    n = 3 * nv
+    v9 = np.eye(3).ravel()
+    Tm = np.zeros((9, 9))
+    for i in range(3):
+        for j in range(3):
+            Tm[3 * i + j, 3 * j + i] = 1.0
+    C0 = 0.75 * mu * (np.eye(9) + Tm) + (lam - 0.625 * mu) * np.outer(v9, v9)
+    K = np.zeros((n, n))
+    m = np.zeros(nv)
+    for t in T4:
+        Dm = np.stack([X[t[a]] - X[t[0]] for a in (1, 2, 3)], axis=1)
+        Dmi = np.linalg.inv(Dm)
+        V = np.linalg.det(Dm) / 6.0
+        coef = np.vstack([-Dmi.sum(axis=0), Dmi])     # coef[a, j] = dF_ij / dx_{a,i}
+        B = np.zeros((9, 12))
+        for i in range(3):
+            for j in range(3):
+                for a in range(4):
+                    B[3 * i + j, 3 * a + i] = coef[a, j]
+        dofs = (3 * np.asarray(t)[:, None] + np.arange(3)).ravel()
+        K[np.ix_(dofs, dofs)] += V * B.T @ C0 @ B
+        m[t] += rho * V / 4.0
+    mdof = np.repeat(m, 3)
+    if dt > 0:
+        K += np.diag(mdof / dt ** 2)
+    f = mdof * np.tile(grav, nv)
+    free = np.ones(n, bool)
+    free[(3 * cn[:, None] + np.arange(3)).ravel()] = False
+    u_lin = np.linalg.solve(K[np.ix_(free, free)], f[free])
+    fm = FullModel(X, T4, E_, nu, rho, grav, cn)
+    if dt > 0:
+        fm.set_dynamics(dt, X.ravel() + dt ** 2 * np.tile(grav, nv))
+    q1, st = newton_solve(fm, X.ravel(), X[cn], 1e-30, max_newton=1)
+    assert st.newton_iters == 1 and st.ls_trials == 1     # full step accepted
+    u1 = (q1 - X.ravel())[free]
+    assert np.linalg.norm(u1 - u_lin) < 1e-9 * np.linalg.norm(u_lin)
