@@ -276,8 +276,8 @@ int lsn_select_cubature(lsn_ctx* ctx, const double* z, int K, int S, int32_t* id
  * Requires lsn_set_mesh and lsn_set_material.  precision is LSN_PREC_FP64 or
  * LSN_PREC_FP32 (element math; vectors and sums are FP64); 0 <= cg_rtol < 1;
  * max_cg >= 1.  The solver keeps its own full state, independent of the
- * reduced solve's, starting at q = X0, v = 0.  Device memory: about
- * 13 n doubles plus 43 ne Real values.
+ * reduced solve's, starting at q = X0, v = 0.  Device memory: 13 n doubles,
+ * n + 43 ne values of the element precision and 16 ne bytes of tet indices.
  * lsn_fullspace_set_state: q, v (n each, host or device; NULL: X0 and 0).
  * lsn_fullspace_step: one implicit-Euler step (dt > 0: q_bar = q + dt v +
  * dt^2 g, then v = (q' - q) / dt) or quasi-static solve (dt == 0, gravity as
