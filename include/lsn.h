@@ -164,7 +164,9 @@ int lsn_set_affine_modes(lsn_ctx* ctx, int enable, const double* center);
 
 /* Newton controls: exit when ||g||_inf < tol_inf (Supplement, convergence
  * condition), at most max_newton iterations (Sec. 5: 1024) and max_ls line
- * search trials per iteration (Sec. 5: 128), Armijo constant armijo_c. */
+ * search trials per iteration (Sec. 5: 128), Armijo constant armijo_c.
+ * Defaults of a new context: tol_inf = 1e-5, max_newton = 1024,
+ * max_ls = 128, armijo_c = 1e-4. */
 int lsn_set_solver(lsn_ctx* ctx, double tol_inf, int max_newton, int max_ls,
                    double armijo_c);
 
