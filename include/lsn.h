@@ -339,6 +339,14 @@ int lsn_train_num_params(lsn_ctx* ctx, long long* count);
 /* Copy the flat parameter vector out of / into the trainer (host or device). */
 int lsn_train_get_params(lsn_ctx* ctx, double* theta);
 int lsn_train_set_params(lsn_ctx* ctx, const double* theta);
+/* Adam state, for checkpoint / resume of training: the first and second
+ * moment estimates m, v (num_params doubles each, host) and the number of
+ * Adam steps taken (the bias-correction exponent).  With the parameters
+ * (lsn_train_get_params) they resume training exactly where it stopped.
+ * set: m, v finite, v >= 0, step >= 0 (else LSN_ERR_ARG / LSN_ERR_NONFINITE,
+ * nothing changed). */
+int lsn_train_get_adam(lsn_ctx* ctx, double* m, double* v, long long* step);
+int lsn_train_set_adam(lsn_ctx* ctx, const double* m, const double* v, long long step);
 /* Losses (losses[0..2] = L_C, L_LS, L; host, may be NULL) and the gradient
  * of L w.r.t. the flat parameters (grad: host or device, may be NULL) for the
  * snapshot positions q (B x n doubles, host or device), B >= 1.  L_LS needs

@@ -82,6 +82,10 @@ _SIGS = {
     "lsn_train_num_params": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
     "lsn_train_get_params": [ctypes.c_void_p, ctypes.c_void_p],
     "lsn_train_set_params": [ctypes.c_void_p, ctypes.c_void_p],
+    "lsn_train_get_adam": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.POINTER(ctypes.c_longlong)],
+    "lsn_train_set_adam": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_longlong],
     "lsn_train_eval": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                        ctypes.c_void_p, ctypes.c_void_p],
     "lsn_train_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
@@ -401,6 +405,23 @@ class Context:
     def train_set_params(self, theta):
         theta = theta if hasattr(theta, "data_ptr") else np.ascontiguousarray(theta, np.float64)
         return self._check(self.lib.lsn_train_set_params(self.h, _ptr(theta)))
+
+    def train_checkpoint(self):
+        """Everything training needs to resume: parameters, Adam moments and
+        step count (a dict of numpy arrays; np.savez(path, **ckpt) stores it)."""
+        npar = self.train_num_params()
+        m, v = np.zeros(npar), np.zeros(npar)
+        step = ctypes.c_longlong()
+        self._check(self.lib.lsn_train_get_adam(self.h, _ptr(m), _ptr(v), ctypes.byref(step)))
+        return {"theta": self.train_get_params(), "adam_m": m, "adam_v": v,
+                "adam_step": np.array(step.value, np.int64)}
+
+    def train_restore(self, ckpt):
+        """Inverse of train_checkpoint (after train_init with the same shapes)."""
+        self.train_set_params(ckpt["theta"])
+        m, v = _f64(ckpt["adam_m"]), _f64(ckpt["adam_v"])
+        return self._check(self.lib.lsn_train_set_adam(self.h, _ptr(m), _ptr(v),
+                                                       int(ckpt["adam_step"])))
 
     def train_eval(self, q, lambda_ls, grad=None, want_grad=True):
         """(L_C, L_LS, L), gradient (numpy float64 unless `grad` is given)."""

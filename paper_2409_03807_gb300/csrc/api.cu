@@ -1568,6 +1568,44 @@ int lsn_train_get_params(lsn_ctx* c, double* theta) {
   LSN_GUARD_END
 }
 
+int lsn_train_get_adam(lsn_ctx* c, double* m, double* v, long long* step) {
+  int rc = train_ready(c);
+  if (rc != LSN_OK) return rc;
+  if (!m || !v || !step) return fail(c, LSN_ERR_ARG, "train_get_adam: null output");
+  if (is_device_ptr(m) || is_device_ptr(v))
+    return fail(c, LSN_ERR_ARG, "train_get_adam: m and v are host arrays");
+  LSN_GUARD_BEGIN
+  try {
+    c->trainer->get_adam(m, v, step);
+  } catch (...) {
+    return fail(c, LSN_ERR_CUDA, "train_get_adam: CUDA error");
+  }
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
+int lsn_train_set_adam(lsn_ctx* c, const double* m, const double* v, long long step) {
+  int rc = train_ready(c);
+  if (rc != LSN_OK) return rc;
+  if (!m || !v || step < 0) return fail(c, LSN_ERR_ARG, "train_set_adam: bad arguments");
+  if (is_device_ptr(m) || is_device_ptr(v))
+    return fail(c, LSN_ERR_ARG, "train_set_adam: m and v are host arrays");
+  const long long np = c->trainer->nparams;
+  for (long long i = 0; i < np; ++i) {
+    if (!std::isfinite(m[i]) || !std::isfinite(v[i]))
+      return fail(c, LSN_ERR_NONFINITE, "train_set_adam: non-finite moments");
+    if (v[i] < 0.0) return fail(c, LSN_ERR_ARG, "train_set_adam: negative second moment");
+  }
+  LSN_GUARD_BEGIN
+  try {
+    c->trainer->set_adam(m, v, step);
+  } catch (...) {
+    return fail(c, LSN_ERR_CUDA, "train_set_adam: CUDA error");
+  }
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
 int lsn_train_set_params(lsn_ctx* c, const double* theta) {
   int rc = train_ready(c);
   if (rc != LSN_OK) return rc;

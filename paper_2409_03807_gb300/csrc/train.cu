@@ -1035,6 +1035,22 @@ struct Trainer : TrainerBase {
     tck(cudaMemcpy(h.data(), grad, sizeof(Real) * nparams, cudaMemcpyDeviceToHost));
     for (long long i = 0; i < nparams; ++i) out[i] = (double)h[i];
   }
+  void get_adam(double* m, double* v, long long* st) override {
+    std::vector<Real> h(nparams);
+    tck(cudaMemcpy(h.data(), am, sizeof(Real) * nparams, cudaMemcpyDeviceToHost));
+    for (long long i = 0; i < nparams; ++i) m[i] = (double)h[i];
+    tck(cudaMemcpy(h.data(), av, sizeof(Real) * nparams, cudaMemcpyDeviceToHost));
+    for (long long i = 0; i < nparams; ++i) v[i] = (double)h[i];
+    *st = step;
+  }
+  void set_adam(const double* m, const double* v, long long st) override {
+    std::vector<Real> h(nparams);
+    for (long long i = 0; i < nparams; ++i) h[i] = (Real)m[i];
+    tck(cudaMemcpy(am, h.data(), sizeof(Real) * nparams, cudaMemcpyHostToDevice));
+    for (long long i = 0; i < nparams; ++i) h[i] = (Real)v[i];
+    tck(cudaMemcpy(av, h.data(), sizeof(Real) * nparams, cudaMemcpyHostToDevice));
+    step = st;
+  }
 
   void ensure_batch(int B) {
     if (B <= Bcap) return;

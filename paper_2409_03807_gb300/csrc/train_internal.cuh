@@ -54,6 +54,9 @@ struct TrainerBase {
   virtual void get_params(double* out) = 0;
   virtual void set_params(const double* in) = 0;
   virtual void get_grad(double* out) = 0;
+  // Adam moments (nparams each, host FP64) and step count
+  virtual void get_adam(double* m, double* v, long long* step) = 0;
+  virtual void set_adam(const double* m, const double* v, long long step) = 0;
 };
 
 }  // namespace lsn

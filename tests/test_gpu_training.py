@@ -170,3 +170,53 @@ def test_lower_order_lipschitz_losses_match_oracle(pkg, prec, order):
     assert L == pytest.approx(L0, rel=tl)
     assert rel(g, g0) < tg, rel(g, g0)
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_checkpoint_resumes_training(pkg, prec, tmp_path):
+    """Training checkpoint / resume (parameters, Adam moments and step count).
+    Take 4 Adam steps, checkpoint to an .npz file, take 4 more.  A fresh
+    context restored from the file takes the same 4 steps to the same
+    parameters.  A restore of the parameters alone, with fresh moments, does
+    not."""
+    from tests.gpu_util import rel
+    mesh, widths, cub, w, Ws, bs, Ew, eb, Q, tp, theta = make_case()
+    ctx = gpu_ctx(pkg, mesh, Ws, bs, Ew, eb, cub, w, prec)
+    for _ in range(4):
+        ctx.train_step(Q, 1e-3, 1e-3)
+    ck = ctx.train_checkpoint()
+    assert int(ck["adam_step"]) == 4
+    assert np.all(ck["adam_v"] >= 0) and np.any(ck["adam_m"] != 0)
+    np.savez(tmp_path / "ck.npz", **ck)
+    for _ in range(4):
+        ctx.train_step(Q, 1e-3, 1e-3)
+    th_a = ctx.train_get_params()
+    ctx.close()
+    ck2 = dict(np.load(tmp_path / "ck.npz"))
+    ctx2 = gpu_ctx(pkg, mesh, Ws, bs, Ew, eb, cub, w, prec)
+    ctx2.train_restore(ck2)
+    back = ctx2.train_checkpoint()
+    for k in ck:
+        assert np.array_equal(back[k], ck[k]), k
+    for _ in range(4):
+        ctx2.train_step(Q, 1e-3, 1e-3)
+    th_b = ctx2.train_get_params()
+    ctx2.close()
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert rel(th_b - ck["theta"], th_a - ck["theta"]) < tol
+    ctx3 = gpu_ctx(pkg, mesh, Ws, bs, Ew, eb, cub, w, prec)
+    ctx3.train_set_params(ck["theta"])
+    for _ in range(4):
+        ctx3.train_step(Q, 1e-3, 1e-3)
+    assert rel(ctx3.train_get_params() - ck["theta"], th_a - ck["theta"]) > 1e-3
+    bad = dict(ck)
+    bad["adam_v"] = -1.0 - np.abs(ck["adam_v"])
+    with pytest.raises(pkg.LsnError) as e:
+        ctx3.train_restore(bad)
+    assert e.value.code == -1
+    bad = dict(ck)
+    bad["adam_step"] = np.array(-1)
+    with pytest.raises(pkg.LsnError) as e:
+        ctx3.train_restore(bad)
+    assert e.value.code == -1
+    ctx3.close()
