@@ -110,6 +110,32 @@ def _fullspace_gravity_sign(old):
     return gradient
 
 
+def _elu_d2_zero(old):
+    return lambda a: np.zeros_like(np.asarray(a, dtype=np.float64))
+
+
+def _repulsion_halved(old):
+    def unsupervised_losses(tp, theta, Z, lam, sigma):
+        Lp, Lr, _ = old(tp, theta, Z, lam, sigma)
+        return Lp, 0.5 * Lr, Lp + lam * 0.5 * Lr
+    return unsupervised_losses
+
+
+def _forces_scaled(old):
+    return lambda model, Z: 1.0001 * old(model, Z)
+
+
+def _gradient_unweighted(old):
+    return lambda ge, tets, n, w=None: old(ge, tets, n, None)
+
+
+def _steepest_descent(old):
+    def cholesky_direction(K, g):   # -g instead of -K^-1 g
+        d, ok = old(K, g)
+        return (-np.asarray(g, dtype=np.float64), ok) if ok else (d, ok)
+    return cholesky_direction
+
+
 # name: (apply, the pin files that must catch it)
 MUTANTS = {
     "snh_psi_without_log_term": (lambda: _swap("oracle.snh", "psi", _psi_without_log),
@@ -142,6 +168,20 @@ MUTANTS = {
     "fullspace_gravity_sign": (lambda: _swap_method("oracle.fullspace", "FullModel", "gradient",
                                                     _fullspace_gravity_sign),
                                ["tests/test_oracle_fullspace.py"]),
+    "elu_second_derivative_zero": (lambda: _swap("oracle.decoder", "elu_d2", _elu_d2_zero),
+                                   ["tests/test_oracle_decoder.py"]),
+    "unsupervised_repulsion_halved": (lambda: _swap("oracle.training", "unsupervised_losses",
+                                                    _repulsion_halved),
+                                      ["tests/test_oracle_training.py"]),
+    "tet_forces_scaled": (lambda: _swap("oracle.cubature_fit", "tet_force_matrix",
+                                        _forces_scaled),
+                          ["tests/test_oracle_cubature.py"]),
+    "cubature_weights_ignored": (lambda: _swap("oracle.fem", "assemble_gradient",
+                                               _gradient_unweighted),
+                                 ["tests/test_oracle_fem.py"]),
+    "newton_direction_is_steepest_descent": (lambda: _swap("oracle.reduced", "cholesky_direction",
+                                                           _steepest_descent),
+                                             ["tests/test_oracle_reduced.py"]),
 }
 
 
