@@ -592,6 +592,29 @@ def run_fullspace(args, world, rank, local):
         u, uf = red.get_positions() - X0, Qf[k - 1] - X0
         err = max(err, float(np.linalg.norm(u - uf) / max(np.linalg.norm(uf), 1e-300)))
     red.close()
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # the FP64 full-space oracle (sparse direct Newton systems) on the host
+        # cores, on the same frames from rest within --cpu-seconds, and the
+        # GPU full-space positions against it (parity at full size)
+        from oracle.fullspace import FullModel, newton_solve
+        fm = FullModel(p.X0, p.tets, c.youngs, c.poisson, c.density, c.gravity, p.cnodes)
+        q, v = X0.copy(), np.zeros_like(X0)
+        gv = np.tile(np.asarray(c.gravity, np.float64), p.nv)
+        t0, done, gerr = time.perf_counter(), 0, 0.0
+        for k in range(1, W + K + 1):
+            fm.set_dynamics(c.dt, q + c.dt * v + c.dt ** 2 * gv)
+            q1, _ = newton_solve(fm, q, p.targets(k), c.eps, c.max_newton, c.max_ls, c.armijo_c)
+            v, q = (q1 - q) / c.dt, q1
+            done = k
+            uf, uo = Qf[k - 1] - X0, q - X0
+            gerr = max(gerr, float(np.linalg.norm(uf - uo) / max(np.linalg.norm(uo), 1e-300)))
+            if time.perf_counter() - t0 > args.cpu_seconds:
+                break
+        secs = time.perf_counter() - t0
+        cpu = {"value": done / secs, "unit": "steps/s", "cores": os.cpu_count(),
+               "kind": "oracle (full space, FP64, sparse direct)", "sample": f"frames 1..{done}",
+               "max_rel_displacement_error_gpu_vs_oracle": gerr}
     if rank == 0:
         print(json.dumps({
             "metric": "full-space GPU solve steps/s (comparison for the reduced solve)",
@@ -605,7 +628,8 @@ def run_fullspace(args, world, rank, local):
             "reduced": {"precision": args.precision, "optimizer": args.optimizer,
                         "steps_per_s": K / t_red,
                         "max_rel_displacement_error_vs_fullspace": err,
-                        "frames_compared": f"1..{W + K}"}}), flush=True)
+                        "frames_compared": f"1..{W + K}"},
+            "cpu_baseline": cpu}), flush=True)
 
 
 def main():
