@@ -222,3 +222,22 @@ def test_first_order_lipschitz_loss(setup):
         fd = (loss_and_grad(tp, tp_, Q, 0.7, Z_samples=Z, order=1)[0][2] -
               loss_and_grad(tp, tm_, Q, 0.7, Z_samples=Z, order=1)[0][2]) / (2 * h)
         assert fd == pytest.approx(g[k], rel=1e-5, abs=1e-8 * max(1.0, abs(L)))
+
+
+def test_lipschitz_measures_of_a_linear_hessian_field():
+    """For the Hessian field Ht(z) = z_0 A the Lipschitz constant of Eq. 7 is
+    ||A||_F: every pair's ratio is at most that, and a pair that differs only
+    in z_0 attains it (so its Eq. 9 term is ||A||_F^2)."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((4, 4))
+    A = A + A.T
+    nA = np.linalg.norm(A)
+    Z = rng.standard_normal((5, 3))
+    H = torch.tensor(Z[:, 0, None, None] * A)
+    assert lipschitz_estimate(H, torch.tensor(Z)) <= nA * (1 + 1e-12)
+    Z[1] = Z[0]
+    Z[1, 0] += 0.7
+    H = torch.tensor(Z[:, 0, None, None] * A)
+    assert lipschitz_estimate(H, torch.tensor(Z)) == pytest.approx(nA, rel=1e-12)
+    two = torch.tensor(Z[:2])
+    assert float(lipschitz_loss(H[:2], two)) == pytest.approx(nA ** 2, rel=1e-12)
