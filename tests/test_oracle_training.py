@@ -241,3 +241,25 @@ def test_lipschitz_measures_of_a_linear_hessian_field():
     assert lipschitz_estimate(H, torch.tensor(Z)) == pytest.approx(nA, rel=1e-12)
     two = torch.tensor(Z[:2])
     assert float(lipschitz_loss(H[:2], two)) == pytest.approx(nA ** 2, rel=1e-12)
+
+
+def test_repulsion_of_an_m_isometric_linear_decoder():
+    """Eq. 4's repulsion term in closed form.  For a linear decoder
+    x = X0 + s W z with W^T M W = c^2 I, every pair has
+    ||x_i - x_j||_M = s c ||z_i - z_j||, so L_R = log(s c / sigma)^2, and it
+    vanishes at sigma = s c."""
+    from oracle.training import unsupervised_losses
+    mesh = make_bar(5, 3, 3, 0.05)
+    n, r = 3 * mesh.nv, 3
+    cub = np.arange(6)
+    tp = TrainProblem(mesh.X0, mesh.tets, [r, n], 0.05, 1e5, 0.45, 1000.0, cub, np.ones(6))
+    m = np.repeat(tp.mass, 3)
+    Qm, _ = np.linalg.qr(np.sqrt(m)[:, None] * np.random.default_rng(1).standard_normal((n, r)))
+    c = 3.0
+    W = c * Qm / np.sqrt(m)[:, None]                    # W^T M W = c^2 I
+    assert np.allclose(W.T @ (m[:, None] * W), c * c * np.eye(r))
+    theta = torch.tensor(tp.pack(np.zeros((r, n)), np.zeros(r), [W], [np.zeros(n)]))
+    Z = torch.tensor(np.random.default_rng(2).standard_normal((5, r)))
+    for sigma in (0.02, 0.05 * c, 1.0):
+        _, Lr, _ = unsupervised_losses(tp, theta, Z, 0.1, sigma)
+        assert float(Lr) == pytest.approx(np.log(0.05 * c / sigma) ** 2, rel=1e-10, abs=1e-20)
