@@ -440,20 +440,27 @@ int lsn_reset_profile(lsn_ctx* ctx);
  * rejected with LSN_ERR_ARG; r is limited to 64 as elsewhere.
  *
  * All inputs are device pointers (FP32 apart from the indices): tets S x 4
- * vertex indices, dminv the per-tet inverse rest edge matrices stored
+ * vertex indices (16-byte aligned, every index < n / 3: the call cannot check
+ * device-resident indices, and an index out of range reads out of bounds),
+ * dminv the per-tet inverse rest edge matrices stored
  * structure-of-arrays (entry (a, b) of tet e at dminv[(3 a + b) S + e]),
  * wvol the weight times rest volume of each tet, u the n displacements
- * x - X0, J the n x r Jacobian (row-major).  mu, lam are the Lame
+ * x - X0 (n a multiple of 3), J the n x r Jacobian (row-major; 16-byte
+ * aligned when r is a multiple of 4).  A misaligned pointer or n not a
+ * multiple of 3 returns LSN_ERR_ARG.  mu, lam are the Lame
  * parameters.  out is device memory or pinned host memory.  Work is issued on
  * cuda_stream (a cudaStream_t, NULL = default stream) and is complete when
  * that stream has synchronised.
  *
  * The first call on a device (the current device when it is made) looks up
- * the device address of the scratch array for that device; make that first
- * call before any stream capture.  Every call on a device shares the one
- * scratch array, and the array keeps the last call's partial sums: calls that
- * may overlap on the GPU (different streams, or host threads without
- * ordering) race and must be serialised by the caller.  Nothing needs
+ * the device address of the scratch array for that device (under a mutex, so
+ * first calls from several host threads are safe); make that first call
+ * before any stream capture.  The address is cached for the life of the
+ * process: after cudaDeviceReset (or any teardown of the device's primary
+ * context) this call must not be used on that device again.  Every call on
+ * a device shares the one scratch array, and the array keeps the last call's
+ * partial sums: calls that may overlap on the GPU (different streams, or host
+ * threads without ordering) race and must be serialised by the caller.  Nothing needs
  * clearing between calls: each call writes every partial it reads. */
 #define LSN_NOALLOC_SCRATCH_DOUBLES 524288
 int lsn_element_system_noalloc(int S, int r, int n, const int32_t* tets,

@@ -417,7 +417,15 @@ class Context:
                 "adam_step": np.array(step.value, np.int64)}
 
     def train_restore(self, ckpt):
-        """Inverse of train_checkpoint (after train_init with the same shapes)."""
+        """Inverse of train_checkpoint (after train_init with the same shapes).
+        Raises ValueError when an array's length is not the network's
+        parameter count (a checkpoint of another network shape)."""
+        npar = self.train_num_params()
+        for key in ("theta", "adam_m", "adam_v"):
+            size = int(np.prod(np.shape(ckpt[key])))
+            if size != npar:
+                raise ValueError(f"checkpoint {key} has {size} values; this network has "
+                                 f"{npar} parameters")
         self.train_set_params(ckpt["theta"])
         m, v = _f64(ckpt["adam_m"]), _f64(ckpt["adam_v"])
         return self._check(self.lib.lsn_train_set_adam(self.h, _ptr(m), _ptr(v),

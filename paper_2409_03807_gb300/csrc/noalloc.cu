@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
+#include <mutex>
 
 #include "../../include/lsn.h"
 #include "lsn_internal.cuh"
@@ -27,12 +29,15 @@ static __device__ __align__(256) double g_noalloc_scratch[LSN_NOALLOC_SCRATCH_DO
 constexpr int kMaxDevices = 64;
 double* g_scratch_addr[kMaxDevices] = {nullptr};  // device address, per device
 int g_num_sms[kMaxDevices] = {0};
+std::mutex g_scratch_mutex;  // guards the two tables above
 
 // Host code must not use g_noalloc_scratch itself (on the host it names a
 // stand-in, not device memory): resolve its device address once per device,
-// with that device current.
+// with that device current.  Concurrent first calls from several host
+// threads serialise on the mutex.
 cudaError_t scratch_for_device(int dev, double** out, int* sms) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -55,8 +60,16 @@ extern "C" int lsn_element_system_noalloc(int S, int r, int n, const int32_t* te
                                           const float* dminv, const float* wvol,
                                           const float* u, const float* J, double mu,
                                           double lam, double* out, void* cuda_stream) {
-  if (S < 1 || r < 1 || r > RMAX || n < 12 || !tets || !dminv || !wvol || !u || !J || !out ||
-      !(mu > 0.0) || !(lam > 0.0))
+  if (S < 1 || r < 1 || r > RMAX || n < 12 || n % 3 != 0 || !tets || !dminv || !wvol || !u ||
+      !J || !out || !(mu > 0.0) || !(lam > 0.0))
+    return LSN_ERR_ARG;
+  // the kernel reads a tet's four indices as one 16-byte load and, when a J
+  // row is a whole number of 16-byte chunks, copies J rows 16 bytes at a time
+  auto misaligned = [](const void* p, uintptr_t a) {
+    return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0;
+  };
+  if (misaligned(tets, 16) || misaligned(J, (r * sizeof(float)) % 16 == 0 ? 16 : 4) ||
+      misaligned(dminv, 4) || misaligned(wvol, 4) || misaligned(u, 4) || misaligned(out, 8))
     return LSN_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {

@@ -1,5 +1,5 @@
-"""CPU checks of the seeded synthetic inputs: the sizes that the design doc's input
-table states, reproducibility (every array is a function of the config and
+"""CPU checks of the seeded synthetic inputs: the mesh and decoder sizes of
+each named workload, reproducibility (every array is a function of the config and
 its seeds), and the boundary motions (rigid face rotations and the
 twist-and-compress end face)."""
 import numpy as np

@@ -13,8 +13,9 @@ import numpy as np
 import pytest
 
 from oracle import fem
+from oracle.reduced import model_from_problem
 from workloads import build_problem
-from tests.gpu_util import rel
+from tests.gpu_util import rel, close_elementwise
 
 pytestmark = pytest.mark.gpu
 
@@ -58,6 +59,12 @@ def test_noalloc_element_system_matches_eval(pkg, name):
     dminv = torch.tensor(DmInv[idx].reshape(S, 9).T.copy(), dtype=torch.float32, device=dev)
     wvol = torch.tensor(p.cub_w * vol[idx], dtype=torch.float32, device=dev)
     ns = 2 + 2 * r + r * (r + 1) // 2
+    # the oracle's model with gravity off and no inertia: its E, g, K are the
+    # elastic cubature sums alone
+    om = model_from_problem(p)
+    om.gravity = np.zeros(3)
+    om.set_targets(p.targets(3))
+    om.set_dynamics(0.0, None)
     out = torch.zeros(ns, dtype=torch.float64, device=dev)
     rng = np.random.default_rng(17)
     first = None
@@ -80,21 +87,43 @@ def test_noalloc_element_system_matches_eval(pkg, name):
         assert abs(E - E_ref) <= TOL["E"] * max(1.0, abs(E_ref))
         assert rel(g, g_ref) < TOL["g"]
         assert rel(K, K_ref) < TOL["K"]
+        # and against the FP64 oracle's elastic system at the same z
+        Eo, go, Ko = om.eval(z)
+        assert abs(E - Eo) <= TOL["E"] * max(1.0, abs(Eo))
+        assert rel(g, go) < TOL["g"] and rel(K, Ko) < TOL["K"]
+        assert close_elementwise(g, go, TOL["g"]) and close_elementwise(K, Ko, TOL["K"])
         if first is not None:
             assert not np.array_equal(o, first)  # a new input really was evaluated
         first = o.copy()
     ctx.close()
 
 
+def _noalloc_rows(S, sms):
+    """CTAs of the solver's element launch shape for S tets (one per 64 tets
+    when S <= 128 * SMs, else one per 128, at most two per SM)."""
+    et = 64 if S <= 64 * 2 * sms else 128
+    return max(1, min((S + et - 1) // et, 2 * sms))
+
+
 def test_noalloc_rejects_oversize_and_bad_arguments(pkg):
     import torch
     dev = torch.device("cuda", 0)
-    buf = torch.zeros(16, dtype=torch.float32, device=dev)
-    out = torch.zeros(16, dtype=torch.float64, device=dev)
-    # r beyond the supported maximum
-    rc = pkg._native.element_system_noalloc(1, 65, 12, buf, buf, buf, buf, buf, 1.0, 1.0, out)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    r, S, n = 64, 960000, 12
+    nst = 2 + 2 * r + r * (r + 1) // 2 + 6
+    if (_noalloc_rows(S, sms) + 1) * nst <= 524288:
+        pytest.skip(f"{sms} SMs: 960,000 tets at r = 64 fit the scratch array here")
+    # buffers of the full size with every index 0 < n / 3, so that the call
+    # would stay in bounds even if it launched
+    tets = torch.zeros((S, 4), dtype=torch.int32, device=dev)
+    dminv = torch.zeros(9 * S, dtype=torch.float32, device=dev)
+    wvol = torch.zeros(S, dtype=torch.float32, device=dev)
+    u = torch.zeros(n, dtype=torch.float32, device=dev)
+    J = torch.zeros((n, r), dtype=torch.float32, device=dev)
+    out = torch.zeros(2 + 2 * r + r * (r + 1) // 2, dtype=torch.float64, device=dev)
+    # r beyond the supported maximum (rejected before anything is read)
+    rc = pkg._native.element_system_noalloc(1, 65, n, tets, dminv, wvol, u, J, 1.0, 1.0, out)
     assert rc == -1
     # partial sums beyond the fixed scratch size: 960,000 tets at r = 64
-    rc = pkg._native.element_system_noalloc(960000, 64, 12, buf, buf, buf, buf, buf, 1.0, 1.0,
-                                            out)
+    rc = pkg._native.element_system_noalloc(S, r, n, tets, dminv, wvol, u, J, 1.0, 1.0, out)
     assert rc == -1
