@@ -21,6 +21,9 @@ reduced   the reduced objective E(z) of Eq. 2, its gradient and Gauss-Newton
           Hessian, Cholesky + Armijo Newton, implicit Euler stepping.
 fullspace full-space projective Newton on Eq. 1 (the reference for the subspace error
           and snapshot generator).
+pool      worker processes (spawned, shared memory) that evaluate reduced's
+          chunked element sums in parallel; results are added in chunk
+          order, so they equal the serial loop's bit for bit.
 training  reconstruction loss (Eq. 3), cubature subspace Hessian (Sec. 4.3),
           Lipschitz loss (Eq. 9), combined loss (Eq. 10), Lip estimate
           (Eq. 7), with gradients by float64 autodiff (torch CPU), as the

@@ -64,6 +64,20 @@ from .decoder import Decoder
 CONVERGED, MAX_ITERS, LS_FAILED, NOT_SPD = 0, 1, 2, 3
 
 
+def chunk_terms(xv, J, tets, DmInv, vol, w, mu, lam):
+    """Elastic terms of one chunk of cubature tets (Eq. 11 with the projected
+    element Hessians): (sum_e w_e J_e^T g_e, sum_e w_e J_e^T Hproj_e J_e)."""
+    r = J.shape[1]
+    ge = fem.element_gradient(xv, tets, DmInv, vol, mu, lam)
+    He = fem.element_hessian(xv, tets, DmInv, vol, mu, lam, project=True)
+    Je = J[fem.element_dofs(tets)]                 # (c, 12, r)
+    g = np.einsum("e,eki,ek->i", w, Je, ge)
+    HJ = He @ Je                                   # H_e J_e
+    WJ = w[:, None, None] * Je
+    K = WJ.reshape(-1, r).T @ HJ.reshape(-1, r)    # sum_e w_e J_e^T H_e J_e
+    return g, K
+
+
 class ReducedModel:
     def __init__(self, X0, tets, decoder, youngs, poisson, rho, gravity,
                  cub_idx=None, cub_w=None, cnodes=None, chunk=65536, affine_center=None):
@@ -91,6 +105,7 @@ class ReducedModel:
         self.dt = 0.0
         self.qbar = None
         self.chunk = chunk
+        self.pool = None               # optional oracle.pool.ElementPool
         self.ground_h, self.ground_k = 0.0, 0.0
         self.r_nn = decoder.r
         self.Phi = None
@@ -191,19 +206,17 @@ class ReducedModel:
         g = np.zeros(r)
         K = np.zeros((r, r))
         xv = x.reshape(-1, 3)
-        for s in range(0, self.tets.shape[0], self.chunk):
-            sl = slice(s, s + self.chunk)
-            tets = self.tets[sl]
-            ge = fem.element_gradient(xv, tets, self.DmInv[sl], self.vol[sl],
-                                      self.mu, self.lam)
-            He = fem.element_hessian(xv, tets, self.DmInv[sl], self.vol[sl],
-                                     self.mu, self.lam, project=True)
-            Je = J[fem.element_dofs(tets)]                 # (c, 12, r)
-            w = self.w[sl]
-            g += np.einsum("e,eki,ek->i", w, Je, ge)
-            HJ = He @ Je                                   # H_e J_e
-            WJ = w[:, None, None] * Je
-            K += WJ.reshape(-1, r).T @ HJ.reshape(-1, r)   # sum_e w_e J_e^T H_e J_e
+        starts = range(0, self.tets.shape[0], self.chunk)
+        if self.pool is not None:      # the same chunks, evaluated in worker processes
+            parts = self.pool.chunk_terms(x, J, self.chunk)
+        else:
+            parts = (chunk_terms(xv, J, self.tets[s:s + self.chunk],
+                                 self.DmInv[s:s + self.chunk], self.vol[s:s + self.chunk],
+                                 self.w[s:s + self.chunk], self.mu, self.lam)
+                     for s in starts)
+        for gp, Kp in parts:           # summed in chunk order either way
+            g += gp
+            K += Kp
         m = self._mass_dof()
         if self.dt > 0.0:
             g += J.T @ (m * (x - self.qbar)) / self.dt ** 2

@@ -245,3 +245,26 @@ def test_affine_free_fall_is_exact_projectile_motion():
     assert np.allclose(sim.q, mesh.X0.ravel() + dt * v0 + dt * dt * np.tile(g, mesh.nv),
                        rtol=0, atol=1e-11)
     assert np.allclose(sim.v, v0 + dt * np.tile(g, mesh.nv), rtol=0, atol=1e-9)
+
+
+def test_worker_pool_gives_the_serial_sums_exactly():
+    """The chunked element sums evaluated in worker processes are the serial
+    loop's, bit for bit (same chunks, added in the same order)."""
+    from oracle.pool import ElementPool
+    from oracle.reduced import model_from_problem
+    from workloads import build_problem
+    p = build_problem("small_dyn_full")
+    m = model_from_problem(p, chunk=96)
+    m.set_targets(p.targets(2))
+    m.set_dynamics(p.config.dt, p.X0.ravel() + 1e-3)
+    z = np.random.default_rng(5).standard_normal(m.r) * 0.5
+    E0, g0, K0 = m.eval(z)
+    pool = ElementPool(m, workers=2)
+    try:
+        m.pool = pool
+        E1, g1, K1 = m.eval(z)
+    finally:
+        m.pool = None
+        pool.close()
+    assert E0 == E1
+    assert np.array_equal(g0, g1) and np.array_equal(K0, K1)
