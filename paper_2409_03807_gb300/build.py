@@ -13,7 +13,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "liblsn.so")
-SOURCES = ["mesh.cu", "decoder.cu", "element.cu", "solve.cu", "api.cu", "noalloc.cu",
+SOURCES = ["mesh.cu", "decoder.cu", "element.cu", "element_ws.cu", "solve.cu", "api.cu", "noalloc.cu",
            "train.cu", "tc_decoder.cu", "cubature.cu", "fullspace.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -323,7 +323,7 @@ struct Engine : EngineBase {
     }
     element_grids(S, r, c->num_sms, gfull, genergy);
     if (use_tc) {  // one complete partial row per CTA (trial energies included)
-      gfull = element_tc_grid(S, c->num_sms);
+      gfull = element_tc_grid(S, r, c->precision == LSN_PREC_BF16, c->num_sms);
       genergy = 0;
     }
     part_dec = dalloc<double>((size_t)grid_dec * nst);
@@ -476,7 +476,8 @@ struct Engine : EngineBase {
     if (use_tc)
       ck(launch_element_tc(ea, reinterpret_cast<const float*>(u),
                            reinterpret_cast<const float*>(J), reinterpret_cast<const float*>(ut),
-                           part_el, gfull, c->precision == LSN_PREC_BF16, tc_err, s));
+                           part_el, gfull, c->precision == LSN_PREC_BF16, tc_err, c->num_sms,
+                           s));
     else
       launch_element<Real>(ea, u, J, ut, part_el, gfull, genergy, s);
     if (prof) P.end(LSN_K_ELEMENT);

@@ -149,7 +149,15 @@ void element_grids(int S, int r, int num_sms, int& gfull, int& genergy);
 // Tensor-core element kernel (TF32 / BF16 forms, r <= 64): `grid` CTAs, each
 // writing one complete partial row (elastic slots and trial energies) of
 // nslots_total(r) doubles; err receives a nonzero code if a bounded wait ran out.
-int element_tc_grid(int S, int num_sms);
+int element_tc_grid(int S, int r, bool bf16, int num_sms);
+// Warp-specialised tensor-core element kernel (element_ws.cu) for large tet
+// sets: used by launch_element_tc when element_ws_applies (the BF16 form, r a
+// multiple of 4 and at most 64, at least 96 tets per SM); same partial-row
+// output.
+bool element_ws_applies(int S, int r, bool bf16, int num_sms);
+int element_ws_grid(int S, int num_sms);
+cudaError_t launch_element_ws(const ElemArgs& ea, const float* u, const float* J, const float* ut,
+                              double* part, int grid, int* err, cudaStream_t s);
 // Gradient-only element kernel of the L-BFGS passes (any precision form):
 // `grid` CTAs, each writing the E, g, gabs and trial-energy slots of one
 // partial row (stride nslots_total(r)); the K slots are not written.
@@ -185,7 +193,7 @@ void launch_fs_energy(const int4* tets, const Real* dminv, const Real* wv, int n
                       double mu, double lam, double* part, int grid, cudaStream_t s);
 cudaError_t launch_element_tc(const ElemArgs& ea, const float* u, const float* J,
                               const float* ut, double* part, int grid, bool bf16, int* err,
-                              cudaStream_t s);
+                              int num_sms, cudaStream_t s);
 
 // cubature.cu: optimised cubature fit on the per-tet force matrix A
 // ([m][ne] row-major, device, FP64; rows of r per snapshot).  normalise:

@@ -11,7 +11,7 @@ import pytest
 from oracle.cubature_fit import tet_force_matrix, select_cubature
 from oracle.reduced import model_from_problem
 from workloads import build_problem, CONFIGS, draw_cubature
-from tests.gpu_util import rel, round_bf16
+from tests.gpu_util import rel, round_bf16, assert_close, UNIT_ROUNDOFF
 
 pytestmark = pytest.mark.gpu
 
@@ -42,7 +42,7 @@ def test_tet_forces_match_oracle(pkg, name, prec):
     A = ctx.tet_forces(Z)
     A_ref = tet_force_matrix(m, Z)
     assert A.shape == A_ref.shape == (3 * m.r, p.ne)
-    assert rel(A, A_ref) < (1e-11 if prec == "fp64" else 2e-5), rel(A, A_ref)
+    assert_close(A, A_ref, (1e-11 if prec == "fp64" else 2e-5), u=UNIT_ROUNDOFF[prec])
     ctx.close()
 
 

@@ -5,7 +5,7 @@ import pytest
 from oracle.decoder import Decoder
 from oracle.reduced import ReducedModel
 from workloads import make_bar, face_nodes, xavier_decoder
-from tests.gpu_util import rel
+from tests.gpu_util import rel, assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -66,7 +66,8 @@ def test_ragged_tiles_single_cubature_tet_and_no_constraints(pkg, prec):
         E0, g0, K0 = m.eval(z)
         tol = 1e-10 if prec == "fp64" else 1e-4
         assert abs(E - E0) <= tol * max(1, abs(E0))
-        assert rel(g, g0) < tol * 10 and rel(K, K0) < tol
+        assert_close(g, g0, tol * 10)
+        assert_close(K, K0, tol)
         ctx.close()
 
 

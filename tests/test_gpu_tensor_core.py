@@ -19,7 +19,7 @@ import pytest
 
 from oracle.reduced import model_from_problem, ReducedSimulator
 from workloads import build_problem, CONFIGS
-from tests.gpu_util import rel, random_qbar, round_bf16
+from tests.gpu_util import rel, random_qbar, round_bf16, assert_close, UNIT_ROUNDOFF
 
 pytestmark = pytest.mark.gpu
 
@@ -74,15 +74,15 @@ def test_tc_positions_jacobian_and_system(pkg, name, prec):
         z = rng.standard_normal(p.config.r) * 0.5
         x, J = ctx.decode(z)
         x_ref, J_ref = m.positions_jac(z)
-        assert rel(x - p.X0.ravel(), x_ref - p.X0.ravel()) < t["x"]
-        assert rel(J, J_ref) < t["J"]
+        assert_close(x - p.X0.ravel(), x_ref - p.X0.ravel(), t["x"], u=UNIT_ROUNDOFF[prec])
+        assert_close(J, J_ref, t["J"], u=UNIT_ROUNDOFF[prec])
         cd = (3 * p.cnodes[:, None] + np.arange(3)).ravel()
         assert np.all(J[cd] == 0.0)
         E, g, K = ctx.eval(z)
         E_ref, g_ref, K_ref = m.eval(z)
         assert abs(E - E_ref) <= t["E"] * max(1.0, abs(E_ref)), (E, E_ref)
-        assert rel(g, g_ref) < t["g"], rel(g, g_ref)
-        assert rel(K, K_ref) < t["K"], rel(K, K_ref)
+        assert_close(g, g_ref, t["g"], u=UNIT_ROUNDOFF[prec])
+        assert_close(K, K_ref, t["K"], u=UNIT_ROUNDOFF["bf16_operands" if prec == "bf16" else prec])
         assert np.allclose(K, K.T)
     ctx.close()
 
@@ -156,7 +156,8 @@ def test_tc_single_tet_and_r1(pkg, prec):
         E, g, K = ctx.eval(z)
         E0, g0, K0 = m.eval(z)
         assert abs(E - E0) <= t["E"] * max(1.0, abs(E0))
-        assert rel(g, g0) < t["g"] and rel(K, K0) < t["K"], (rel(g, g0), rel(K, K0))
+        assert_close(g, g0, t["g"], u=UNIT_ROUNDOFF[prec])
+        assert_close(K, K0, t["K"], u=UNIT_ROUNDOFF["bf16_operands" if prec == "bf16" else prec])
     ctx.close()
 
 
@@ -176,9 +177,10 @@ def test_tc_ragged_tiles_and_fp32_output_layer_fallback(pkg, prec):
         z = np.random.default_rng(3).standard_normal(7)
         x, J = ctx.decode(z)
         x0, J0 = m.positions_jac(z)
-        assert rel(J, J0) < 1e-5  # FP32 output layer
+        assert_close(J, J0, 1e-5)  # FP32 output layer
         E, g, K = ctx.eval(z)
         E0, g0, K0 = m.eval(z)
         assert abs(E - E0) <= 1e-4 * max(1.0, abs(E0))
-        assert rel(g, g0) < 2e-3 and rel(K, K0) < TOL[prec]["K"], (rel(g, g0), rel(K, K0))
+        assert_close(g, g0, 2e-3, u=UNIT_ROUNDOFF[prec])
+        assert_close(K, K0, TOL[prec]["K"], u=UNIT_ROUNDOFF["bf16_operands" if prec == "bf16" else prec])
         ctx.close()

@@ -16,7 +16,7 @@ import pytest
 
 from oracle.training import TrainProblem, loss_and_grad
 from workloads import make_bar, xavier_decoder
-from tests.gpu_util import rel
+from tests.gpu_util import rel, assert_close, UNIT_ROUNDOFF
 
 pytestmark = pytest.mark.gpu
 
@@ -79,11 +79,12 @@ def test_losses_and_gradient_match_oracle(pkg, lam, prec):
         gb, g0b = g[o:o + sz], g0[o:o + sz]
         if np.linalg.norm(g0b) > 1e-8 * np.linalg.norm(g0):
             if prec == "fp64":
-                assert rel(gb, g0b) < 1e-8, (shp, rel(gb, g0b))
+                assert_close(gb, g0b, 1e-8, u=UNIT_ROUNDOFF[prec])
             elif lam == 0.0:
-                assert rel(gb, g0b) < (2e-3 if prec == "fp32" else 2e-2), (shp, rel(gb, g0b))
+                assert_close(gb, g0b, (2e-3 if prec == "fp32" else 2e-2), u=UNIT_ROUNDOFF[prec])
             else:
                 cos = gb @ g0b / (np.linalg.norm(gb) * np.linalg.norm(g0b))
+                print(f"{prec} lambda {lam} block {shp}: rel {rel(gb, g0b):.3e}, cos {cos:.6f}")
                 assert rel(gb, g0b) < 0.2 and cos > 0.98, (shp, rel(gb, g0b), cos)
         o += sz
     ctx.close()
@@ -99,7 +100,7 @@ def test_cubature_hessians_match_oracle(pkg, prec):
     P = tp.unpack(torch.tensor(theta))
     for b in range(Z.shape[0]):
         Hr = tp.hessian(P, torch.tensor(Z[b])).numpy()
-        assert rel(H[b], Hr) < (1e-10 if prec == "fp64" else 1e-4)
+        assert_close(H[b], Hr, (1e-10 if prec == "fp64" else 1e-4), u=UNIT_ROUNDOFF[prec])
     ctx.close()
 
 
@@ -168,7 +169,7 @@ def test_lower_order_lipschitz_losses_match_oracle(pkg, prec, order):
     assert lc == pytest.approx(lc0, rel=tl)
     assert l0 == pytest.approx(l00, rel=tl, abs=1e-12)
     assert L == pytest.approx(L0, rel=tl)
-    assert rel(g, g0) < tg, rel(g, g0)
+    assert_close(g, g0, tg, u=UNIT_ROUNDOFF[prec])
     ctx.close()
 
 
@@ -203,7 +204,7 @@ def test_checkpoint_resumes_training(pkg, prec, tmp_path):
     th_b = ctx2.train_get_params()
     ctx2.close()
     tol = 1e-12 if prec == "fp64" else 1e-5
-    assert rel(th_b - ck["theta"], th_a - ck["theta"]) < tol
+    assert_close(th_b - ck["theta"], th_a - ck["theta"], tol)
     ctx3 = gpu_ctx(pkg, mesh, Ws, bs, Ew, eb, cub, w, prec)
     ctx3.train_set_params(ck["theta"])
     for _ in range(4):

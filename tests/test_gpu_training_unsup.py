@@ -17,7 +17,7 @@ import pytest
 
 from oracle.training import unsupervised_loss_and_grad
 from workloads import build_problem, CONFIGS, draw_cubature, xavier_decoder
-from tests.gpu_util import rel
+from tests.gpu_util import rel, assert_close, UNIT_ROUNDOFF
 from tests.test_gpu_training import make_case, gpu_ctx
 
 pytestmark = pytest.mark.gpu
@@ -55,7 +55,7 @@ def test_unsupervised_losses_and_gradient_match_oracle(pkg, lam, lam_ls, prec):
         sz = int(np.prod(shp))
         gb, g0b = g[o:o + sz], g0[o:o + sz]
         if np.linalg.norm(g0b) > 1e-10 * np.linalg.norm(g0):
-            assert rel(gb, g0b) < tg, (shp, rel(gb, g0b))
+            assert_close(gb, g0b, tg, u=UNIT_ROUNDOFF[prec])
         else:
             assert np.linalg.norm(gb) <= 1e-6 * np.linalg.norm(g0) + 1e-30
         o += sz
