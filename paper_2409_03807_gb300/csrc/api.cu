@@ -255,6 +255,8 @@ struct Engine : EngineBase {
   TcLast tcl;          // tensor-core output layer (TF32 / BF16 forms)
   bool use_tc = false;       // TF32 / BF16 form: tensor-core element contraction
   bool use_tc_last = false;  // ... and tensor-core output layer (hidden width allows TMA)
+  bool use_tc_hidden = false;  // ... and tensor-core hidden layers
+  TcHidden tch;
   int* tc_err = nullptr;     // device flag: a bounded wait of a tensor-core kernel ran out
   DevHistory* hist = nullptr;  // L-BFGS curvature pairs
   double* Zd = nullptr;        // FP64 copy of the pass points (affine modes)
@@ -319,6 +321,19 @@ struct Engine : EngineBase {
         tcl.release();
       } else {
         ck(te);
+      }
+      if (L >= 2) {  // hidden layers on the tensor cores when every layer's plan fits
+        std::vector<const float*> wl;
+        for (int l = 0; l < L - 1; ++l) wl.push_back(reinterpret_cast<const float*>(dW[l]));
+        const cudaError_t he = tch.setup(wl, c->widths, C, nj, s);
+        if (he == cudaSuccess) {
+          use_tc_hidden = true;
+        } else if (he == cudaErrorInvalidValue) {
+          cudaGetLastError();
+          tch.release();
+        } else {
+          ck(he);
+        }
       }
     }
     element_grids(S, r, c->num_sms, gfull, genergy);
@@ -437,9 +452,17 @@ struct Engine : EngineBase {
       const int M = c->widths[l + 1], K = c->widths[l];
       // the last hidden layer also writes the tensor-core output layer's operand
       const bool pack = use_tc_last && l == L - 2;
-      launch_hidden_layer<Real>(dW[l], db[l], M, K, in, C, nj, Z[cur], s,
-                                pack ? tcl.Bh : nullptr, pack ? tcl.Bl : nullptr,
-                                pack ? tcl.bkind() : 0);
+      if (use_tc_hidden)  // tensor-core forms: tcgen05 layers; the unit-major columns
+                          // only when the CUDA-core output layer reads them
+        ck(tch.launch(l, reinterpret_cast<const float*>(db[l]),
+                      reinterpret_cast<const float*>(in),
+                      use_tc_last ? nullptr : reinterpret_cast<float*>(Z[cur]),
+                      pack ? tcl.Bh : nullptr, pack ? tcl.Bl : nullptr, pack ? tcl.bkind() : 0,
+                      tc_err, s));
+      else
+        launch_hidden_layer<Real>(dW[l], db[l], M, K, in, C, nj, Z[cur], s,
+                                  pack ? tcl.Bh : nullptr, pack ? tcl.Bl : nullptr,
+                                  pack ? tcl.bkind() : 0);
       in = Z[cur];
       cur ^= 1;
     }
@@ -583,8 +606,15 @@ void ensure_graph(lsn_ctx* c) {
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   ck(cudaStreamBeginCaptureToGraph(e->cap_stream, body, nullptr, nullptr, 0,
                                    cudaStreamCaptureModeThreadLocal));
-  e->pass(e->cap_stream, (unsigned long long)h, 1);
-  cudaError_t launch_err = cudaGetLastError();
+  // a launch that fails inside the capture must not leave the stream
+  // capturing: end the capture first, then report the error
+  cudaError_t launch_err = cudaSuccess;
+  try {
+    e->pass(e->cap_stream, (unsigned long long)h, 1);
+    launch_err = cudaGetLastError();
+  } catch (const CudaError& ce) {
+    launch_err = ce.e;
+  }
   cudaGraph_t captured = nullptr;
   cudaError_t err = cudaStreamEndCapture(e->cap_stream, &captured);
   if (err == cudaSuccess) err = launch_err;

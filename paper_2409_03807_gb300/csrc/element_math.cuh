@@ -71,7 +71,22 @@ __device__ __forceinline__ Real snh_psi(const Invariants<Real>& iv, Real mu, Rea
 
 // Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix A (in place:
 // A becomes diagonal), accumulating the rotations in Q (A_in = Q diag Q^T).
-template <typename Real>
+// FAST (FP32 only): the rotation's tangent from an approximate quotient and
+// reciprocal, and c = rsqrt(1 + t^2), s = t c.  The tangent only steers how
+// fast the sweep converges; c^2 + s^2 = 1 holds to the rsqrt rounding, so the
+// accumulated Q stays orthogonal and the stopping test is the same.
+template <bool FAST, typename Real>
+__device__ __forceinline__ Real quot(Real a, Real b) {
+  if (FAST && sizeof(Real) == 4) return (Real)__fdividef((float)a, (float)b);
+  return a / b;
+}
+template <bool FAST, typename Real>
+__device__ __forceinline__ Real inv_sqrt(Real x) {
+  if (FAST && sizeof(Real) == 4) return (Real)rsqrtf((float)x);
+  return Real(1) / sqrt_r<Real>(x);
+}
+
+template <typename Real, bool FAST = false>
 __device__ __forceinline__ void jacobi3(Real (&A)[3][3], Real (&Q)[3][3]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -90,12 +105,12 @@ __device__ __forceinline__ void jacobi3(Real (&A)[3][3], Real (&Q)[3][3]) {
       const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
       const Real apq = A[p][q];
       if (fabs(apq) > tiny) {
-        const Real theta = (A[q][q] - A[p][p]) / (Real(2) * apq);
+        const Real theta = quot<FAST>(A[q][q] - A[p][p], Real(2) * apq);
         const Real at = fabs(theta);
-        Real t = (at > Real(1e15)) ? Real(0.5) / at
-                                   : Real(1) / (at + sqrt_r<Real>(theta * theta + Real(1)));
+        Real t = (at > Real(1e15)) ? quot<FAST>(Real(0.5), at)
+                                   : quot<FAST>(Real(1), at + sqrt_r<Real>(theta * theta + Real(1)));
         if (theta < Real(0)) t = -t;
-        const Real c = Real(1) / sqrt_r<Real>(t * t + Real(1));
+        const Real c = inv_sqrt<FAST>(t * t + Real(1));
         const Real s = t * c;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -124,7 +139,7 @@ __device__ __forceinline__ void jacobi3(Real (&A)[3][3], Real (&Q)[3][3]) {
 
 // Rotation-signed SVD F = U diag(sig) V^T with det U = det V = +1 (sig[i]
 // may be negative for an inverted element).
-template <typename Real>
+template <typename Real, bool FAST = false>
 __device__ __forceinline__ void svd3(const Real (&F)[3][3], Real (&U)[3][3], Real (&sig)[3],
                                      Real (&V)[3][3]) {
   Real S[3][3];
@@ -132,7 +147,7 @@ __device__ __forceinline__ void svd3(const Real (&F)[3][3], Real (&U)[3][3], Rea
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) S[a][b] = F[0][a] * F[0][b] + F[1][a] * F[1][b] + F[2][a] * F[2][b];
-  jacobi3<Real>(S, V);
+  jacobi3<Real, FAST>(S, V);
   const Real detV = V[0][0] * (V[1][1] * V[2][2] - V[1][2] * V[2][1]) -
                     V[0][1] * (V[1][0] * V[2][2] - V[1][2] * V[2][0]) +
                     V[0][2] * (V[1][0] * V[2][1] - V[1][1] * V[2][0]);
@@ -160,7 +175,7 @@ __device__ __forceinline__ void svd3(const Real (&F)[3][3], Real (&U)[3][3], Rea
     n0 += u0[a] * u0[a];
   }
   if (n0 > tiny) {
-    n0 = Real(1) / sqrt_r<Real>(n0);
+    n0 = inv_sqrt<FAST>(n0);
 #pragma unroll
     for (int a = 0; a < 3; ++a) u0[a] *= n0;
   } else {
@@ -176,7 +191,7 @@ __device__ __forceinline__ void svd3(const Real (&F)[3][3], Real (&U)[3][3], Rea
     n1 += u1[a] * u1[a];
   }
   if (n1 > tiny * Real(1e6)) {
-    n1 = Real(1) / sqrt_r<Real>(n1);
+    n1 = inv_sqrt<FAST>(n1);
 #pragma unroll
     for (int a = 0; a < 3; ++a) u1[a] *= n1;
   } else {  // any unit vector orthogonal to u0
@@ -190,7 +205,7 @@ __device__ __forceinline__ void svd3(const Real (&F)[3][3], Real (&U)[3][3], Rea
       u1[a] = e[a] - ue * u0[a];
       nn += u1[a] * u1[a];
     }
-    nn = Real(1) / sqrt_r<Real>(nn);
+    nn = inv_sqrt<FAST>(nn);
 #pragma unroll
     for (int a = 0; a < 3; ++a) u1[a] *= nn;
   }

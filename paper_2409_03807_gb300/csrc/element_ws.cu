@@ -7,12 +7,15 @@
 // of J into g and K; the line-search trial energies), with the three kinds of
 // work running concurrently on different warps of a persistent CTA:
 //
-//   warps 0-2  (element math)  one tet per thread: energy, P, the signed SVD
+//   warps 0-6  (element math)  one tet per thread: energy, P, the signed SVD
 //              and the clamped eigensystem of d2Psi/dF2, and the KTRIAL
 //              trial energies; each tet's result is a 60-word record in
-//              shared memory (double-buffered units of 96 tets);
-//   warps 3-14 (column build)  for a tet and four adjacent subspace columns
-//              (one float4 per J row): dJ_a = J_a - J_0 (a = 1..3),
+//              shared memory (double-buffered units of 224 tets); the
+//              per-tet dependency chain (two 3x3 Jacobi decompositions) is
+//              long, so seven warps keep the column build supplied;
+//   warps 7-14 (column build)  for a tet and four adjacent subspace columns
+//              (one float4 per J row, staged in shared memory by
+//              asynchronous copies one tet ahead): dJ_a = J_a - J_0 (a = 1..3),
 //              w_a = U^T dJ_a, R = sum_a w_a y_a^T (= U^T G V with
 //              y_a = V^T Dm^-1 row a), the nine eigen-coordinates C_e (scaled
 //              by sqrt(w V lambda+)) and the gradient term sum_a ge_a . dJ_a;
@@ -41,8 +44,8 @@ namespace tcws {
 
 using namespace tc;
 
-constexpr int NPW = 3;                    // element-math warps
-constexpr int NBW = 12;                   // column-build warps
+constexpr int NPW = 7;                    // element-math warps
+constexpr int NBW = 8;                    // column-build warps
 constexpr int MMAW = NPW + NBW;           // the MMA-issuing warp
 constexpr int NT = 32 * (NPW + NBW + 1);  // 512 threads
 constexpr int UNIT = 32 * NPW;            // tets per record unit
@@ -59,15 +62,23 @@ constexpr int R_AS = 28;  // scaling modes: sqrt(w V lambda_m+) a_m[i]
 constexpr int R_TF = 40;  // sqrt(w V lambda+ / 2): 3 twist, then 3 flip modes
 constexpr int R_GE = 48;  // ge_a[i] = sum_j (w V P)[i][j] Dm^-1[a][j]
 
-constexpr int CH = 48;                    // tets per operand chunk
+constexpr int CH = NBT / 16;              // tets per operand chunk: one per column-build
+                                          // thread group of r / 4 <= 16 threads
 constexpr int NCH = UNIT / CH;            // chunks per unit
-constexpr int KR = 9 * CH;                // K rows per chunk
 constexpr int KSTEP = 16;                 // K rows (BF16 values) per MMA
+constexpr int KR = (9 * CH + KSTEP - 1) / KSTEP * KSTEP;  // K rows per chunk (zero-padded)
 constexpr int NSTEP = KR / KSTEP;         // MMAs per chunk
 constexpr uint32_t BUF = KR * 128u;       // operand bytes per chunk (128 bytes per K row)
-static_assert(UNIT % CH == 0 && KR % KSTEP == 0, "chunks tile a unit in whole MMA steps");
+constexpr uint32_t STG = 12 * 16;         // staged J rows per column-build thread
+constexpr int NOB = 3;                    // operand buffers (chunks in flight)
+static_assert(UNIT % CH == 0, "chunks tile a unit");
 
-constexpr size_t smem_bytes() { return 2 * (size_t)BUF + 2 * (size_t)UNIT * RW * 4 + 1024; }
+constexpr size_t smem_bytes() {
+  return NOB * (size_t)BUF + 2 * (size_t)UNIT * RW * 4 + (size_t)NBT * STG + 1024;
+}
+// the dynamic shared memory plus the kernel's static barriers and reduction
+// buffer (about 1.1 KB) must fit the 227 KB a block may use
+static_assert(smem_bytes() + 2048 <= 232448, "shared memory of the element kernel");
 
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
@@ -108,12 +119,28 @@ __device__ __forceinline__ uint32_t op_offset(uint32_t kr, uint32_t c) {
   return kr * 128u + (((c >> 3) ^ (kr & 7u)) << 4) + (c & 7u) * 2u;
 }
 
+// displacement gradient Hd = [x1 - x0, x2 - x0, x3 - x0] Dm^-1 from the four
+// vertex rows x[a][i] of a displacement field
+__device__ __forceinline__ void grad_of(const float (&x)[4][3], const float (&Dmi)[3][3],
+                                        float (&H)[3][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      H[i][j] = (x[1][i] - x[0][i]) * Dmi[0][j] + (x[2][i] - x[0][i]) * Dmi[1][j] +
+                (x[3][i] - x[0][i]) * Dmi[2][j];
+}
+
 // Element math of tet e into its record (zeros past the last tet) and the
-// energies at u and at the KTRIAL trial fields.
+// energies at u and at the KTRIAL trial fields.  tv: the tet's vertex
+// indices (loaded a unit ahead); every other load of the
+// tet (inverse rest edges, weight, the vertex rows of u and of the trial
+// fields) is issued together, and the trial energies come first so that
+// their registers are free before the eigen-decompositions
 __device__ __forceinline__ void tet_record(const ElemArgs& ea, const float* __restrict__ u,
-                                           const float* __restrict__ ut, int e, float* rec,
-                                           float mu, float lam, float oma, FAcc& eacc,
-                                           FAcc& eabs, FAcc (&etr)[KTRIAL],
+                                           const float* __restrict__ ut, int e, int4 tv,
+                                           float* rec, float mu, float lam, float oma,
+                                           FAcc& eacc, FAcc& eabs, FAcc (&etr)[KTRIAL],
                                            FAcc (&atr)[KTRIAL]) {
   float4* r4 = reinterpret_cast<float4*>(rec);
   if (e >= ea.S) {
@@ -121,10 +148,37 @@ __device__ __forceinline__ void tet_record(const ElemArgs& ea, const float* __re
     for (int k = 0; k < RW / 4; ++k) r4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
-  int4 tv;
+  const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
   float Dmi[3][3], wv, H[3][3];
-  load_tet<float>(ea, e, tv, Dmi, wv);
-  disp_grad<float>(u, tv, Dmi, H);
+  float xu[4][3], xt[KTRIAL][4][3];
+  {
+    const float* dm = static_cast<const float*>(ea.dminv);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Dmi[a][c] = dm[(3 * a + c) * ea.S + e];
+    wv = static_cast<const float*>(ea.wv)[e];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        xu[a][i] = u[3 * vv[a] + i];
+#pragma unroll
+        for (int j = 0; j < KTRIAL; ++j) xt[j][a][i] = ut[(size_t)j * ea.n + 3 * vv[a] + i];
+      }
+  }
+  // trial energies of the line search at this tet
+#pragma unroll
+  for (int j = 0; j < KTRIAL; ++j) {
+    float Ht[3][3];
+    grad_of(xt[j], Dmi, Ht);
+    Invariants<float> it;
+    invariants<float>(Ht, it);
+    const float pt = wv * snh_psi<float>(it, mu, lam, oma);
+    facc_add(etr[j], pt);
+    facc_add(atr[j], fabsf(pt));
+  }
+  grad_of(xu, Dmi, H);
   Invariants<float> iv;
   invariants<float>(H, iv);
   const float pe = wv * snh_psi<float>(iv, mu, lam, oma);
@@ -168,7 +222,7 @@ __device__ __forceinline__ void tet_record(const ElemArgs& ea, const float* __re
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) F[i][j] = H[i][j] + (i == j ? 1.f : 0.f);
-    svd3<float>(F, U, sg, V);
+    svd3<float, true>(F, U, sg, V);
     float As[3][3], Aq[3][3];
     const float pi3[3] = {sg[1] * sg[2], sg[0] * sg[2], sg[0] * sg[1]};
 #pragma unroll
@@ -176,7 +230,7 @@ __device__ __forceinline__ void tet_record(const ElemArgs& ea, const float* __re
 #pragma unroll
       for (int j = 0; j < 3; ++j)
         As[i][j] = c2 * sg[i] * sg[j] + lam * pi3[i] * pi3[j] + (i == j ? c1 : c3 * sg[3 - i - j]);
-    jacobi3<float>(As, Aq);
+    jacobi3<float, true>(As, Aq);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const float sc = sqrtf(wv * (As[m][m] > 0.f ? As[m][m] : 0.f));
@@ -201,50 +255,54 @@ __device__ __forceinline__ void tet_record(const ElemArgs& ea, const float* __re
   }
 #pragma unroll
   for (int k = 0; k < RW / 4; ++k) r4[k] = make_float4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
-  // trial energies of the line search at this tet
-#pragma unroll 1
-  for (int j = 0; j < KTRIAL; ++j) {
-    float Ht[3][3];
-    disp_grad<float>(ut + (size_t)j * ea.n, tv, Dmi, Ht);
-    Invariants<float> it;
-    invariants<float>(Ht, it);
-    const float pt = wv * snh_psi<float>(it, mu, lam, oma);
-    facc_add(etr[j], pt);
-    facc_add(atr[j], fabsf(pt));
-  }
 }
 
 // Column build of one tet (record rec) for the four columns c0 .. c0 + 3:
 // C_e rows into the operand (K rows 9 lt .. 9 lt + 8), gradient terms into gp.
-__device__ __forceinline__ void build_tet(const float* rec, const float* __restrict__ J, int r,
-                                          int c0, uint8_t* op, int lt, float (&gp)[4],
-                                          float (&ga)[4]) {
-  const int4 vv = *reinterpret_cast<const int4*>(rec + R_V);
-  const size_t rs = (size_t)r;
-  const float* j0 = J + 3 * (size_t)vv.x * rs + c0;
-  const float* j1 = J + 3 * (size_t)vv.y * rs + c0;
-  const float* j2 = J + 3 * (size_t)vv.z * rs + c0;
-  const float* j3 = J + 3 * (size_t)vv.w * rs + c0;
-  float d[3][3][4];  // dJ_a[i] for the four columns
-  {
-    float4 b0[3], x1[3], x2[3], x3[3];
+// The twelve J rows of a tet for a thread's four columns, staged in shared
+// memory by asynchronous copies issued one tet ahead.  Component-major: slot
+// k = 3 a + i (row 3 v_a + i) of thread tb is stg[k * NBT + tb], so the 16-byte
+// accesses of a warp fall on consecutive addresses (no bank conflicts).
+__device__ __forceinline__ void stage_rows(float4* stg, const float* __restrict__ J, int r, int c0,
+                                           int4 vv) {
+  const int v[4] = {vv.x, vv.y, vv.z, vv.w};
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      b0[i] = __ldg(reinterpret_cast<const float4*>(j0 + i * rs));
-      x1[i] = __ldg(reinterpret_cast<const float4*>(j1 + i * rs));
-      x2[i] = __ldg(reinterpret_cast<const float4*>(j2 + i * rs));
-      x3[i] = __ldg(reinterpret_cast<const float4*>(j3 + i * rs));
+      const uint32_t dst = smem_u32(stg + (3 * a + i) * NBT);
+      const float* src = J + (size_t)(3 * v[a] + i) * r + c0;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
     }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void staged_wait() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// dJ_a = J_{a+1} - J_0 (a = 0..2) for the four columns from the staged rows
+__device__ __forceinline__ void staged_diffs(const float4* stg, float (&d)[3][3][4]) {
+  float4 x[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) x[k] = stg[k * NBT];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      d[0][i][0] = x1[i].x - b0[i].x; d[0][i][1] = x1[i].y - b0[i].y;
-      d[0][i][2] = x1[i].z - b0[i].z; d[0][i][3] = x1[i].w - b0[i].w;
-      d[1][i][0] = x2[i].x - b0[i].x; d[1][i][1] = x2[i].y - b0[i].y;
-      d[1][i][2] = x2[i].z - b0[i].z; d[1][i][3] = x2[i].w - b0[i].w;
-      d[2][i][0] = x3[i].x - b0[i].x; d[2][i][1] = x3[i].y - b0[i].y;
-      d[2][i][2] = x3[i].z - b0[i].z; d[2][i][3] = x3[i].w - b0[i].w;
+      const float4 p = x[3 * (a + 1) + i], q = x[i];
+      d[a][i][0] = p.x - q.x;
+      d[a][i][1] = p.y - q.y;
+      d[a][i][2] = p.z - q.z;
+      d[a][i][3] = p.w - q.w;
     }
-  }
+}
+
+// Column build of one tet (record rec) from dJ (staged_diffs) for the four
+// columns c0 .. c0 + 3: C_e rows into the operand (K rows 9 lt .. 9 lt + 8),
+// gradient terms into gp.
+__device__ __forceinline__ void build_tet(const float* rec, const float (&d)[3][3][4], int c0,
+                                          uint8_t* op, int lt, float (&gp)[4], float (&ga)[4]) {
   const float4* r4 = reinterpret_cast<const float4*>(rec);
   // gradient: sum_a ge_a . dJ_a
   {
@@ -333,14 +391,14 @@ __global__ void __launch_bounds__(NT, 1)
                       const float* __restrict__ ut, double* __restrict__ part, int part_stride,
                       int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t cfull[2], cempty[2], ofull[2], oempty[2], fin;
+  __shared__ uint64_t cfull[2], cempty[2], ofull[NOB], oempty[NOB], fin;
   __shared__ uint32_t tbase_s;
   __shared__ FAcc red[NT / 32][2 + 2 * KTRIAL];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* sb = smem_raw + (base - raw);
-  float* recs = reinterpret_cast<float*>(sb + 2 * BUF);  // [2][UNIT][RW]
+  float* recs = reinterpret_cast<float*>(sb + NOB * BUF);  // [2][UNIT][RW]
   const int r = ea.r, S = ea.S;
   const int Ng = (r + 15) / 16 * 16;
   const uint32_t idesc = idesc_bf16(GROWS, Ng) | (1u << 15) | (1u << 16);  // both MN-major
@@ -348,7 +406,7 @@ __global__ void __launch_bounds__(NT, 1)
   const float oma = (float)(-0.75 * ea.mu / ea.lam);
   const int nunits = (S + UNIT - 1) / UNIT;
   // columns >= r of the operands are never written: zero both buffers once
-  for (int i = t; i < (int)(2 * BUF / 16); i += NT)
+  for (int i = t; i < (int)(NOB * BUF / 16); i += NT)
     reinterpret_cast<uint4*>(sb)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (warp == 0) {
     tmem_alloc(&tbase_s, 64);
@@ -359,10 +417,10 @@ __global__ void __launch_bounds__(NT, 1)
     mbar_init(&cfull[1], 32 * NPW);
     mbar_init(&cempty[0], NBT);
     mbar_init(&cempty[1], NBT);
-    mbar_init(&ofull[0], NBT);
-    mbar_init(&ofull[1], NBT);
-    mbar_init(&oempty[0], 1);
-    mbar_init(&oempty[1], 1);
+    for (int i = 0; i < NOB; ++i) {
+      mbar_init(&ofull[i], NBT);
+      mbar_init(&oempty[i], 1);
+    }
     mbar_init(&fin, 1);
     fence_barrier_init();
   }
@@ -379,14 +437,19 @@ __global__ void __launch_bounds__(NT, 1)
   bool alive = true;
   const int tb = t - 32 * NPW;  // column-build thread index
   const int Q = r >> 2;         // column quads (r is a multiple of 4)
-  const int slots = min(NBT / Q, CH);  // tets of a chunk in parallel
+  const int slots = min(NBT / Q, CH);  // tets of a chunk in parallel (== CH for r <= 64)
   const int slot = tb / Q, quad = tb - slot * Q;
 
   if (warp < NPW) {
     // ---------------- element math: one tet per thread per unit
     int li = 0;
+    const int4 z4 = make_int4(0, 0, 0, 0);
+    int4 tv = blockIdx.x * UNIT + t < S ? ea.tets[blockIdx.x * UNIT + t] : z4;
     for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x, ++li) {
       const int b = li & 1;
+      // the next unit's tet indices, a unit ahead
+      const int en = (unit + gridDim.x) * UNIT + t;
+      const int4 tv_next = (unit + (int)gridDim.x < nunits && en < S) ? ea.tets[en] : z4;
       if (li >= 2) {
         const bool ok = wait_bar(&cempty[b], ((li >> 1) - 1) & 1, err, 4);
         if (!__all_sync(0xffffffffu, ok)) {
@@ -394,13 +457,31 @@ __global__ void __launch_bounds__(NT, 1)
           break;
         }
       }
-      tet_record(ea, u, ut, unit * UNIT + t, recs + ((size_t)b * UNIT + t) * RW, mu, lam, oma,
-                 eacc, eabs, etr, atr);
+      tet_record(ea, u, ut, unit * UNIT + t, tv, recs + ((size_t)b * UNIT + t) * RW, mu, lam,
+                 oma, eacc, eabs, etr, atr);
       mbar_arrive(&cfull[b]);
+      tv = tv_next;
     }
   } else if (warp < MMAW) {
-    // ---------------- column build: chunks of CH tets, four columns per thread
+    // ---------------- column build: chunks of CH tets, four columns per thread;
+    // a thread takes tet `slot` of every chunk (slots == CH) and stages the J
+    // rows of its next tet while it builds the current one
     const int c0 = 4 * quad;
+    const bool act = slot < slots && c0 < r;
+    float4* stg = reinterpret_cast<float4*>(sb + NOB * BUF + 2 * UNIT * RW * 4) + tb;
+    const int my_units = (nunits - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int ntet = my_units * NCH;  // this thread's tets, one per chunk
+    const int4 z4 = make_int4(0, 0, 0, 0);
+    auto vids = [&](int idx) {  // vertex ids of the thread's idx-th tet (0 past the end)
+      if (idx >= ntet) return z4;
+      const int e = (blockIdx.x + (idx / NCH) * (int)gridDim.x) * UNIT + (idx % NCH) * CH + slot;
+      return e < S ? ea.tets[e] : z4;
+    };
+    int4 vnext = z4;
+    if (act) {
+      stage_rows(stg, J, r, c0, vids(0));
+      vnext = vids(1);
+    }
     int li = 0, q = 0;
     for (int unit = blockIdx.x; unit < nunits && alive; unit += gridDim.x, ++li) {
       const int b = li & 1;
@@ -411,19 +492,22 @@ __global__ void __launch_bounds__(NT, 1)
       }
       const float* urec = recs + (size_t)b * UNIT * RW;
       for (int h = 0; h < NCH; ++h, ++q) {
-        const int ob = q & 1;
-        if (q >= 2) {
-          const bool oko = wait_bar(&oempty[ob], ((q >> 1) - 1) & 1, err, 16);
+        const int ob = q % NOB;
+        if (q >= NOB) {  // the MMAs of chunk q - NOB have read the buffer
+          const bool oko = wait_bar(&oempty[ob], ((q / NOB) - 1) & 1, err, 16);
           if (!__all_sync(0xffffffffu, oko)) {
             alive = false;
             break;
           }
         }
-        uint8_t* op = sb + ob * BUF;
-        if (slot < slots && c0 < r) {
+        if (act) {
+          staged_wait();
+          float d[3][3][4];
+          staged_diffs(stg, d);  // consumes every staged row before it is refilled
+          if (q + 1 < ntet) stage_rows(stg, J, r, c0, vnext);
+          vnext = vids(q + 2);
           float gp[4] = {0.f, 0.f, 0.f, 0.f};
-          for (int lt = slot; lt < CH; lt += slots)
-            build_tet(urec + (size_t)(h * CH + lt) * RW, J, r, c0, op, lt, gp, gabs);
+          build_tet(urec + (size_t)(h * CH + slot) * RW, d, c0, sb + ob * BUF, slot, gp, gabs);
 #pragma unroll
           for (int k = 0; k < 4; ++k) facc_add(gacc[k], gp[k]);
         }
@@ -433,12 +517,13 @@ __global__ void __launch_bounds__(NT, 1)
       if (!alive) break;
       mbar_arrive(&cempty[b]);
     }
+    if (act) staged_wait();  // no copy is left in flight
   } else if (lane == 0) {
     // ---------------- MMA issue, one chain per operand chunk
     const int nchunks = ((nunits - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x) * NCH;
     for (int q = 0; q < nchunks; ++q) {
-      const int ob = q & 1;
-      if (!wait_bar(&ofull[ob], (q >> 1) & 1, err, 32)) {
+      const int ob = q % NOB;
+      if (!wait_bar(&ofull[ob], (q / NOB) & 1, err, 32)) {
         alive = false;
         break;
       }
@@ -481,8 +566,8 @@ __global__ void __launch_bounds__(NT, 1)
   }
   // gradient partials of the column-build threads, then a fixed-order sum
   // over the slots (the operand buffers are free once `fin` has completed)
-  FAcc* gred = reinterpret_cast<FAcc*>(sb);               // [slots <= 48][64]
-  float* ared = reinterpret_cast<float*>(sb + 48 * 64 * 8);  // [slots <= 48][64]
+  FAcc* gred = reinterpret_cast<FAcc*>(sb);                 // [slots <= CH][64]
+  float* ared = reinterpret_cast<float*>(sb + CH * 64 * 8);  // [slots <= CH][64]
   if (warp >= NPW && warp < MMAW && slot < slots && 4 * quad < r) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {

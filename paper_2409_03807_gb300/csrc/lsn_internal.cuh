@@ -124,6 +124,10 @@ template <typename Real>
 void launch_hidden_layer(const Real* W, const Real* b, int M, int K, const Real* Zin, int C,
                          int nj, Real* Zout, cudaStream_t s, void* Bh = nullptr,
                          void* Bl = nullptr, int bkind = 0);
+// tc_hidden.cu: hidden layers on the tensor cores (BF16 / TF32 forms; the
+// TcHidden handle is in tc_internal.cuh).  tc_hidden_applies: the layer's
+// shared-memory plan fits one CTA.
+bool tc_hidden_applies(int M, int K, int C);
 template <typename Real>
 void launch_last_layer(const Real* W, const Real* b, int M, int K, const Real* Zin, int C,
                        int nj, Real* u_out, Real* J_out, Real* u_trial, double* part,
@@ -152,7 +156,7 @@ void element_grids(int S, int r, int num_sms, int& gfull, int& genergy);
 int element_tc_grid(int S, int r, bool bf16, int num_sms);
 // Warp-specialised tensor-core element kernel (element_ws.cu) for large tet
 // sets: used by launch_element_tc when element_ws_applies (the BF16 form, r a
-// multiple of 4 and at most 64, at least 96 tets per SM); same partial-row
+// multiple of 4 and at most 64, at least 224 tets per SM); same partial-row
 // output.
 bool element_ws_applies(int S, int r, bool bf16, int num_sms);
 int element_ws_grid(int S, int num_sms);

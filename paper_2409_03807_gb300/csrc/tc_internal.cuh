@@ -4,6 +4,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "lsn_internal.cuh"
 
 namespace lsn {
@@ -32,6 +34,29 @@ struct TcLast {
               bool packed = false) const;
   int bkind() const { return bf16 ? 1 : 2; }
   ~TcLast() { release(); }
+};
+
+// The hidden layers in the BF16 / TF32 forms (tc_hidden.cu): every layer's
+// weights as per-CTA hi / lo TF32 images (built once), each layer writing the
+// next layer's input image.  setup: W[l] the FP32 weights of hidden layer l
+// (device), widths = r, H_1, ..., H_{L-1}, n; fails with cudaErrorInvalidValue
+// when a layer's plan does not fit one CTA.  launch(l): layer l from Zin (the
+// pass points, layer 0) or its input image; Zout (nullable) the unit-major
+// columns; Bh / Bl / bkind the output layer's packed operand (last layer).
+struct TcHidden {
+  struct Layer {
+    void* wimg = nullptr;
+    void* bimg = nullptr;  // input image (layers >= 1)
+    int M = 0, K = 0;
+  };
+  std::vector<Layer> layers;
+  int C = 0, nj = 0;
+  cudaError_t setup(const std::vector<const float*>& W, const std::vector<int>& widths, int C,
+                    int nj, cudaStream_t s);
+  cudaError_t launch(int l, const float* b, const float* Zin, float* Zout, void* Bh, void* Bl,
+                     int bkind, int* err, cudaStream_t s) const;
+  void release();
+  ~TcHidden() { release(); }
 };
 
 }  // namespace lsn
