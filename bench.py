@@ -318,7 +318,8 @@ def algorithmic_bytes(cls, p, precision):
         return S * (16 + 10 * b) + rows * (r + 4) * b
     if cls == "decoder_hidden":                  # weights once, activations in and out
         widths = p.widths[:-1]
-        return sum(o * i * b + (i + o) * C * 4 for i, o in zip(widths[:-1], widths[1:]))
+        wb = 8 if precision in ("bf16", "tf32") else b   # tensor-core forms: hi + lo TF32
+        return sum(o * i * wb + (i + o) * C * 4 for i, o in zip(widths[:-1], widths[1:]))
     return None
 
 
@@ -514,11 +515,18 @@ def run_ours(args, world, rank, local):
                                                                           args.precision)})
         elif cls == "decoder_hidden":
             fl = algorithmic_flops(cls, p)
-            peak, unit, src = peaks["fp64" if args.precision == "fp64" else "fp32"]
+            # tensor-core forms: tcgen05 TF32 layers (the products as three TF32
+            # MMAs; the flops counted are the layer's own); otherwise CUDA cores
+            peak, unit, src = peaks["tf32" if tc_form else
+                                    ("fp64" if args.precision == "fp64" else "fp32")]
             ach = fl / avg_s / 1e12
-            ent.update({"bound": "alu", "achieved": ach, "peak": peak, "peak_source": src,
-                        "unit": unit, "frac": ach / peak, "algorithmic_flops_per_launch": fl,
-                        "note": "all hidden layers of one pass (FP32 CUDA-core kernels)"})
+            ent.update({"bound": "tensor" if tc_form else "alu", "achieved": ach, "peak": peak,
+                        "peak_source": src, "unit": unit, "frac": ach / peak,
+                        "algorithmic_flops_per_launch": fl,
+                        "algorithmic_bytes_per_launch": algorithmic_bytes(cls, p, args.precision),
+                        "note": "all hidden layers of one pass" + (
+                            " (tcgen05, two-term TF32 split operands)" if tc_form else
+                            " (CUDA-core kernels)")})
         elif cls in ("decoder_last", "element"):
             ab = algorithmic_bytes(cls, p, args.precision)
             peak, unit, src = peaks["hbm"]

@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "liblsn.so")
 SOURCES = ["mesh.cu", "decoder.cu", "element.cu", "element_ws.cu", "solve.cu", "api.cu", "noalloc.cu",
-           "train.cu", "tc_decoder.cu", "tc_hidden.cu", "cubature.cu", "fullspace.cu"]
+           "train.cu", "tc_decoder.cu", "tc_hidden.cu", "tc_gemm.cu", "cubature.cu", "fullspace.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
@@ -56,7 +56,7 @@ def build(verbose=False, jobs=None):
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
         return LIB
-    cmd = [_nvcc(), *ARCH, "-shared", "--cudart=static", "-o", LIB, *objs, "-lcublas"]
+    cmd = [_nvcc(), *ARCH, "-shared", "--cudart=static", "-o", LIB, *objs]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

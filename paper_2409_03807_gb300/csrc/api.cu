@@ -1671,6 +1671,8 @@ int lsn_train_eval(lsn_ctx* c, const double* q, int B, double lambda_ls, double*
   const double* qd = train_upload_q(c, q, B);
   try {
     c->trainer->evaluate(qd, B, lambda_ls, l, c->stream);
+    if (c->trainer->device_error())
+      return fail(c, LSN_ERR_CUDA, "train_eval: a tensor-core GEMM wait ran out");
   } catch (...) {
     return fail(c, LSN_ERR_CUDA, "train_eval: CUDA error in the training kernels");
   }
@@ -1731,6 +1733,8 @@ int lsn_train_eval_unsup(lsn_ctx* c, const double* z, int B, double lambda, doub
   double l[5];
   try {
     c->trainer->evaluate_unsup(zh.data(), B, lambda, sigma, lambda_ls, l, c->stream);
+    if (c->trainer->device_error())
+      return fail(c, LSN_ERR_CUDA, "train_eval_unsup: a tensor-core GEMM wait ran out");
   } catch (...) {
     return fail(c, LSN_ERR_CUDA, "train_eval_unsup: CUDA error in the training kernels");
   }
@@ -1785,6 +1789,7 @@ int lsn_train_hessians(lsn_ctx* c, const double* z, int B, double* H) {
   std::vector<double> hs((size_t)B * P);
   try {
     tr.hessians_host(z, B, hs.data(), c->stream);
+    if (tr.device_error()) return fail(c, LSN_ERR_CUDA, "train_hessians: a tensor-core GEMM wait ran out");
   } catch (...) {
     return fail(c, LSN_ERR_CUDA, "train_hessians: CUDA error");
   }

@@ -124,6 +124,17 @@ template <typename Real>
 void launch_hidden_layer(const Real* W, const Real* b, int M, int K, const Real* Zin, int C,
                          int nj, Real* Zout, cudaStream_t s, void* Bh = nullptr,
                          void* Bl = nullptr, int bkind = 0);
+// tc_gemm.cu: C[m][n] = alpha sum_k A(m,k) B(k,n) + beta C[m][n] with
+// A(m,k) = A[m sam + k sak], B(k,n) = B[k sbk + n sbn] (any strides), FP32
+// operands read as TF32 on tcgen05; K split over the grid (deterministic
+// fixed-order sum) when the tiles leave SMs idle, using ws (ws_floats of
+// tc_gemm_workspace_floats; no split without it).  err: device flag, set
+// when a bounded wait ran out.
+size_t tc_gemm_workspace_floats(int M, int N, int K, int num_sms);
+cudaError_t tc_gemm_tf32(cudaStream_t s, int M, int N, int K, float alpha, const float* A,
+                         long long sam, long long sak, const float* B, long long sbk,
+                         long long sbn, float beta, float* C, long long ldc, float* ws,
+                         size_t ws_floats, int num_sms, int* err);
 // tc_hidden.cu: hidden layers on the tensor cores (BF16 / TF32 forms; the
 // TcHidden handle is in tc_internal.cuh).  tc_hidden_applies: the layer's
 // shared-memory plan fits one CTA.

@@ -25,7 +25,6 @@
 // of the element Hessian, evaluated with forward-mode dual numbers.
 //
 // Matrices are row-major; one sample's columns are contiguous.
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -917,10 +916,13 @@ __global__ void x0_rows_kernel(const double* __restrict__ X0, const int* __restr
 template <typename Real>
 struct Trainer : TrainerBase {
   TrainSetup ts;
-  // TF32 tensor-core GEMMs (cuBLAS) for the plain matrix products of the
+  // TF32 tensor-core GEMMs (tc_gemm.cu) for the plain matrix products of the
   // forward and backward passes; otherwise the CUDA-core kernel above
   bool tf32 = false;
-  cublasHandle_t blas = nullptr;
+  float* gws = nullptr;   // split-K workspace of the tensor-core GEMM (grown on demand)
+  size_t gws_cap = 0;
+  int* gerr = nullptr;    // device flag: a bounded wait of the GEMM ran out
+  int num_sms = 1;
 
   // C[m][n] = alpha sum_k A(m,k) B(k,n) + beta C[m][n] with the strides of
   // gemm(); as column-major, C^T (N x M, ld ldc) = op(B) op(A)
@@ -931,15 +933,23 @@ struct Trainer : TrainerBase {
       gemm<Real>(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, ldc);
       return;
     }
-    const cublasOperation_t opB = sbn == 1 ? CUBLAS_OP_N : CUBLAS_OP_T;
-    const cublasOperation_t opA = sak == 1 ? CUBLAS_OP_N : CUBLAS_OP_T;
-    const int ldb = (int)(sbn == 1 ? sbk : sbn), lda = (int)(sak == 1 ? sam : sak);
-    const float a = (float)alpha, b = (float)beta;
-    if (cublasSetStream(blas, s) != CUBLAS_STATUS_SUCCESS ||
-        cublasGemmEx(blas, opB, opA, N, M, K, &a, B, CUDA_R_32F, ldb, A, CUDA_R_32F, lda, &b, C,
-                     CUDA_R_32F, (int)ldc, CUBLAS_COMPUTE_32F_FAST_TF32,
-                     CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
-      throw CudaFail{cudaErrorUnknown};
+    const size_t need = tc_gemm_workspace_floats(M, N, K, num_sms);
+    if (need > gws_cap) {
+      if (gws) cudaFree(gws);
+      gws = nullptr;
+      gws_cap = 0;
+      tck(cudaMalloc(&gws, need * sizeof(float)));
+      gws_cap = need;
+    }
+    tck(tc_gemm_tf32(s, M, N, K, (float)alpha, reinterpret_cast<const float*>(A), sam, sak,
+                     reinterpret_cast<const float*>(B), sbk, sbn, (float)beta,
+                     reinterpret_cast<float*>(C), ldc, gws, gws_cap, num_sms, gerr));
+  }
+  int device_error() override {
+    if (!gerr) return 0;
+    int h = 0;
+    tck(cudaMemcpy(&h, gerr, sizeof(int), cudaMemcpyDeviceToHost));
+    return h;
   }
   std::vector<void*> sbufs, bbufs;   // static / per-batch allocations
   Real *theta = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr;
@@ -987,11 +997,18 @@ struct Trainer : TrainerBase {
   ~Trainer() override {
     for (void* p : bbufs) cudaFree(p);
     for (void* p : sbufs) cudaFree(p);
-    if (blas) cublasDestroy(blas);
+    if (gws) cudaFree(gws);
+    if (gerr) cudaFree(gerr);
   }
 
   void init_device(const double* theta_host) override {
-    if (tf32 && cublasCreate(&blas) != CUBLAS_STATUS_SUCCESS) throw CudaFail{cudaErrorUnknown};
+    if (tf32) {
+      int dev = 0;
+      tck(cudaGetDevice(&dev));
+      tck(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+      tck(cudaMalloc(&gerr, sizeof(int)));
+      tck(cudaMemset(gerr, 0, sizeof(int)));
+    }
     theta = alloc<Real>(sbufs, nparams);
     grad = alloc<Real>(sbufs, nparams);
     am = alloc<Real>(sbufs, nparams);

@@ -36,7 +36,7 @@ struct TrainerBase {
   int L = 0, P = 0, Cs = 0;
   int lip_order = 2;  // Lipschitz loss of the potential's Hessian (2) or of the potential (0)
   virtual ~TrainerBase() {}
-  // mode 0: FP32 (CUDA cores), 1: FP64, 2: FP32 with TF32 tensor-core GEMMs
+  // mode 0: FP32 (CUDA cores), 1: FP64, 2: FP32 with TF32 tensor-core GEMMs (tc_gemm.cu)
   static TrainerBase* create(int mode, const TrainSetup& ts);
   virtual void init_device(const double* theta_host) = 0;
   // losses[3] = L_C, L_LS, L; gradient kept on the device
@@ -57,6 +57,8 @@ struct TrainerBase {
   // Adam moments (nparams each, host FP64) and step count
   virtual void get_adam(double* m, double* v, long long* step) = 0;
   virtual void set_adam(const double* m, const double* v, long long step) = 0;
+  // nonzero when a bounded wait of a tensor-core GEMM ran out (reads a device flag)
+  virtual int device_error() { return 0; }
 };
 
 }  // namespace lsn

@@ -5,12 +5,13 @@ and that Adam steps lower the loss.
 
 Tolerances.  FP64 trainer: losses, Hessians and every gradient block to
 1e-8 relative.  FP32 trainer: losses and Hessians 1e-4 relative; the
-reconstruction gradient 2e-3; the Lipschitz-loss gradient sums adjoints
-several orders of magnitude above its own size, so FP32 gives it to a few
-percent: its blocks are checked to 0.2 relative and 0.98 cosine.  TF32
-trainer (the tensor-core forms: matrix products on TF32 tensor cores with
-FP32 accumulation): losses 2e-3, reconstruction gradient 2e-2, the
-Lipschitz-loss gradient as FP32."""
+reconstruction gradient 2e-3; with the Lipschitz loss every gradient block
+1e-4 (measured: about 2e-6), norm-wise and element-wise.  TF32 trainer (the
+tensor-core forms: matrix products on the project's TF32 tcgen05 GEMM with
+FP32 accumulation): losses 2e-3 (the Lipschitz loss 5e-3), reconstruction
+gradient 2e-2; the
+Lipschitz-loss gradient, whose adjoints are several orders of magnitude
+above its own size, to 0.2 relative and 0.98 cosine per block."""
 import numpy as np
 import pytest
 
@@ -69,9 +70,13 @@ def test_losses_and_gradient_match_oracle(pkg, lam, prec):
     (lc, lls, L), g = ctx.train_eval(Q, lam)
     (lc0, lls0, L0), g0, Z0, H0 = loss_and_grad(tp, th, Q, lam)
     tl = {"fp64": 1e-8, "fp32": 1e-4, "tf32": 2e-3}[prec]
+    # L_LS (Eq. 9) sums squared differences of subspace Hessians, which cancel:
+    # the TF32 rounding of every decoder product (11 significant bits) reaches
+    # it at a few 1e-3 (measured 2.8e-3), so the TF32 form gets 5e-3 there
+    tls = 5e-3 if prec == "tf32" else tl
     assert lc == pytest.approx(lc0, rel=tl)
-    assert lls == pytest.approx(lls0, rel=tl, abs=1e-12)
-    assert L == pytest.approx(L0, rel=tl)
+    assert lls == pytest.approx(lls0, rel=tls, abs=1e-12)
+    assert L == pytest.approx(L0, rel=tls)
     # gradient, block by block
     o = 0
     for shp in tp.shapes:
@@ -82,6 +87,9 @@ def test_losses_and_gradient_match_oracle(pkg, lam, prec):
                 assert_close(gb, g0b, 1e-8, u=UNIT_ROUNDOFF[prec])
             elif lam == 0.0:
                 assert_close(gb, g0b, (2e-3 if prec == "fp32" else 2e-2), u=UNIT_ROUNDOFF[prec])
+            elif prec == "fp32":
+                # FP32 rounding of the second-order terms: measured about 2e-6 per block
+                assert_close(gb, g0b, 1e-4, u=UNIT_ROUNDOFF[prec])
             else:
                 cos = gb @ g0b / (np.linalg.norm(gb) * np.linalg.norm(g0b))
                 print(f"{prec} lambda {lam} block {shp}: rel {rel(gb, g0b):.3e}, cos {cos:.6f}")
