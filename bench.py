@@ -68,6 +68,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train", action="store_true",
                     help="time decoder training steps (lsn_train_step) instead of the solve")
+    ap.add_argument("--learned", action="store_true",
+                    help="learned-subspace comparison: full-space GPU trajectory of the "
+                         "workload as snapshots, decoders trained on the GPU with and "
+                         "without the Lipschitz term, reduced solves with each against "
+                         "the full-space trajectory (use --steps for the frames)")
+    ap.add_argument("--train-steps", type=int, default=3000,
+                    help="Adam steps per decoder in --learned")
+    ap.add_argument("--lambdas", default="0,1e-4,1e-2",
+                    help="Lipschitz-loss weights trained in --learned (0 = vanilla)")
     ap.add_argument("--fullspace", action="store_true",
                     help="time the full-space GPU solve (the comparison) on the workload's "
                          "mesh, constraints and frames, and the reduced solve's error against "
@@ -745,11 +754,124 @@ def run_fullspace(args, world, rank, local):
             "cpu_baseline": cpu}), flush=True)
 
 
+def unpack_params(th, widths, n):
+    """Trainer parameter vector -> (encoder W, encoder b, decoder Ws, decoder bs)."""
+    r = widths[0]
+    Ew, eb = th[:r * n].reshape(r, n), th[r * n:r * n + r]
+    o, Ws, bs = r * n + r, [], []
+    for a, b in zip(widths[:-1], widths[1:]):
+        Ws.append(th[o:o + a * b].reshape(b, a).astype(np.float32))
+        o += a * b
+        bs.append(th[o:o + b].astype(np.float32))
+        o += b
+    return Ew, eb, Ws, bs
+
+
+def run_learned(args, world, rank, local):
+    """What the learned subspace gains, at the bar twist's size: the full-space
+    GPU solve (FP64 element math; its end points agree with the FP64
+    full-space oracle) over frames 1..K gives the snapshots; decoders of the
+    workload's widths are trained on them on the GPU (encoder initialised by
+    PCA, batch 64, Adam, lr 1e-3), one per Lipschitz weight (0 = vanilla),
+    with the workload's cubature set for the Lipschitz term; each decoder, and
+    the untrained one, then runs the reduced solve (--precision) over the same
+    frames.  Reported per decoder: reconstruction loss, steps/s, Newton
+    iterations per step, exits and the relative displacement error against
+    the full-space trajectory."""
+    import dataclasses
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2409_03807_gb300.build import build
+    build()
+    import paper_2409_03807_gb300 as pkg
+    p = load_problem(args)
+    c = p.config
+    if c.ground_k > 0 or not (c.dt > 0):
+        raise SystemExit("--learned needs a dynamic workload without ground contact")
+    K = args.steps
+    X0 = p.X0.ravel()
+    # 1. snapshots: the full-space trajectory
+    fs = pkg.Context()
+    fs.set_mesh(p.X0, p.tets)
+    fs.set_material(c.youngs, c.poisson, c.density, c.gravity)
+    fs.set_solver(c.eps, c.max_newton, c.max_ls, c.armijo_c)
+    fs.set_constraints(p.cnodes, p.targets(1))
+    fs.fullspace_setup("fp64", 1e-6, 8192)
+    Qf = []
+    t0 = time.perf_counter()
+    for k in range(1, K + 1):
+        fs.set_constraints(None, p.targets(k))
+        Qf.append(fs.fullspace_step(c.dt)[2].copy())
+    t_fs = time.perf_counter() - t0
+    fs.close()
+    Qf = np.array(Qf)
+    # 2. decoders: same initial weights and PCA encoder, one per Lipschitz weight
+    r, n = c.r, p.n
+    D = Qf - X0
+    _, sv, Vt = np.linalg.svd(D, full_matrices=False)
+    Ew0 = (Vt[:r] / np.maximum(sv[:r, None], 1e-12) * np.sqrt(K)).astype(np.float32)
+    eb0 = np.zeros(r, np.float32)
+    cub, cw = p.cub_idx, p.cub_w
+    tprec = "tf32" if args.precision in ("bf16", "tf32") else args.precision
+    decoders = {"untrained": (p.Ws, p.bs, None)}
+    Qd = torch.tensor(Qf, dtype=torch.float64, device="cuda")
+    rs = np.random.default_rng(3)
+    for lam in [float(x) for x in args.lambdas.split(",")]:
+        tc = pkg.Context()
+        tc.set_mesh(p.X0, p.tets)
+        tc.set_material(c.youngs, c.poisson, c.density, c.gravity)
+        tc.set_decoder(p.Ws, p.bs, c.out_scale, tprec)
+        tc.train_init(Ew0, eb0, cub, cw)
+        t1 = time.perf_counter()
+        for _ in range(args.train_steps):
+            idx = torch.tensor(rs.choice(K, min(64, K), replace=False), device="cuda")
+            tc.train_step(Qd[idx], lam, 1e-3)
+        torch.cuda.synchronize()
+        t_tr = time.perf_counter() - t1
+        (lc, lls, _), _ = tc.train_eval(Qd[:min(64, K)], lam, want_grad=False)
+        _, _, Ws, bs = unpack_params(tc.train_get_params(), p.widths, n)
+        tc.close()
+        decoders[f"lambda={lam:g}"] = (Ws, bs, {"L_C": lc, "L_LS": lls, "train_s": t_tr})
+    # 3. reduced solves over the same frames
+    out = {}
+    for name, (Ws, bs, info) in decoders.items():
+        pd = dataclasses.replace(p, Ws=Ws, bs=bs)
+        ctx = pkg.context_from_problem(pd, precision=args.precision, optimizer=args.optimizer,
+                                       history=args.history)
+        its, ex, errs, t_red = 0, {}, [], 0.0
+        for k in range(1, K + 1):
+            ctx.set_constraints(None, p.targets(k))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, st, _ = ctx.step(dt=c.dt)
+            t_red += time.perf_counter() - t0
+            its += st["newton_iters"]
+            ex[str(rc)] = ex.get(str(rc), 0) + 1
+            u, uf = ctx.get_positions() - X0, Qf[k - 1] - X0
+            errs.append(float(np.linalg.norm(u - uf) / max(np.linalg.norm(uf), 1e-300)))
+        ctx.close()
+        out[name] = {"steps_per_s": K / t_red, "newton_iters_per_step": its / K, "exits": ex,
+                     "max_rel_error_vs_fullspace": max(errs),
+                     "mean_rel_error_vs_fullspace": float(np.mean(errs)), "training": info}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "learned subspace vs untrained and vs the full-space GPU solve",
+            "config": {"workload": args.workload, "frames": f"1..{K}", "r": r,
+                       "decoder": "-".join(map(str, p.widths)), "precision": args.precision,
+                       "optimizer": args.optimizer, "train_steps": args.train_steps,
+                       "trainer": tprec, "snapshots": f"full-space GPU solve, FP64 element "
+                       f"math, frames 1..{K}", "cubature": len(cub)},
+            "fullspace_steps_per_s": K / t_fs, "decoders": out}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
     if args.train:
         run_train(args, world, rank, local)
+        return
+    if args.learned:
+        run_learned(args, world, rank, local)
         return
     if args.fullspace:
         run_fullspace(args, world, rank, local)

@@ -134,37 +134,41 @@ __device__ __forceinline__ void sqrt_and_inverse(double s, double& root, double&
 }
 
 // Right-looking Cholesky L L^T of the symmetric matrix held in L (lower
-// triangle used), all SEL_THREADS threads: per column one square root and
-// one reciprocal (thread 0), the column scaled, then independent FMAs over
-// the trailing lower triangle spread over the four warps.  Returns false
-// (uniformly) when a pivot is not positive.
+// triangle used), all SEL_THREADS threads.  Per column j: warp 0 takes the
+// pivot (one square root and one reciprocal, lane 0) and scales the column
+// below it; after one block barrier every warp updates its rows of the
+// trailing lower triangle (row i by warp i mod 4, its columns by the lanes),
+// then a second barrier.  Returns false (uniformly) when a pivot is not
+// positive.
 __device__ bool block_cholesky(double (*L)[RMAX + 1], double* invd, int r, int* s_fail) {
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  constexpr int NW = SEL_THREADS / 32;
   for (int j = 0; j < r; ++j) {
-    if (t == 0) {
-      const double sjj = L[j][j];
-      if (!(sjj > 0.0)) {
-        *s_fail = 1;
-      } else {
-        double root, inv;
-        sqrt_and_inverse(sjj, root, inv);
-        L[j][j] = root;
-        invd[j] = inv;
-        *s_fail = 0;
+    if (warp == 0) {
+      double inv = 0.0;
+      int bad = 0;
+      if (lane == 0) {
+        const double sjj = L[j][j];
+        if (!(sjj > 0.0)) {
+          bad = 1;
+        } else {
+          double root;
+          sqrt_and_inverse(sjj, root, inv);
+          L[j][j] = root;
+          invd[j] = inv;
+        }
+        *s_fail = bad;
       }
+      bad = __shfl_sync(0xffffffffu, bad, 0);
+      inv = __shfl_sync(0xffffffffu, inv, 0);
+      if (!bad)
+        for (int i = j + 1 + lane; i < r; i += 32) L[i][j] *= inv;
     }
     __syncthreads();
     if (*s_fail) return false;
-    const double inv = invd[j];
-    for (int i = j + 1 + t; i < r; i += SEL_THREADS) L[i][j] *= inv;
-    __syncthreads();
-    const int m = r - 1 - j;
-    for (int e = t; e < m * m; e += SEL_THREADS) {
-      const int ii = e / m, kk = e - ii * m;
-      if (kk <= ii) {
-        const int i = j + 1 + ii, k = j + 1 + kk;
-        L[i][k] -= L[i][j] * L[k][j];
-      }
+    for (int i = j + 1 + warp; i < r; i += NW) {
+      const double lij = L[i][j];
+      for (int k = j + 1 + lane; k <= i; k += 32) L[i][k] -= lij * L[k][j];
     }
     __syncthreads();
   }
