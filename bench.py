@@ -74,9 +74,14 @@ def parse():
                          "without the Lipschitz term, reduced solves with each against "
                          "the full-space trajectory (use --steps for the frames)")
     ap.add_argument("--train-steps", type=int, default=3000,
-                    help="Adam steps per decoder in --learned")
-    ap.add_argument("--lambdas", default="0,1e-4,1e-2",
-                    help="Lipschitz-loss weights trained in --learned (0 = vanilla)")
+                    help="Adam steps of the first training stage (L_C alone) in --learned")
+    ap.add_argument("--finetune-steps", type=int, default=3000,
+                    help="Adam steps of the second stage (L_C + lambda L_LS) per weight")
+    ap.add_argument("--lambdas", default="0,1e-7,1e-6,1e-5",
+                    help="Lipschitz-loss weights of the second stage in --learned "
+                         "(0 = vanilla)")
+    ap.add_argument("--learned-optimizers", default="newton,lbfgs",
+                    help="optimisers of the reduced solves in --learned")
     ap.add_argument("--fullspace", action="store_true",
                     help="time the full-space GPU solve (the comparison) on the workload's "
                          "mesh, constraints and frames, and the reduced solve's error against "
@@ -770,12 +775,18 @@ def unpack_params(th, widths, n):
 def run_learned(args, world, rank, local):
     """What the learned subspace gains, at the bar twist's size: the full-space
     GPU solve (FP64 element math; its end points agree with the FP64
-    full-space oracle) over frames 1..K gives the snapshots; decoders of the
-    workload's widths are trained on them on the GPU (encoder initialised by
-    PCA, batch 64, Adam, lr 1e-3), one per Lipschitz weight (0 = vanilla),
-    with the workload's cubature set for the Lipschitz term; each decoder, and
-    the untrained one, then runs the reduced solve (--precision) over the same
-    frames.  Reported per decoder: reconstruction loss, steps/s, Newton
+    full-space oracle) over frames 1..K gives the snapshots.  Decoders of the
+    workload's widths are trained on them on the GPU in the two stages of
+    Sec. 4.2: stage 1 minimises the reconstruction loss alone (Eq. 3) from the
+    Xavier weights and a PCA encoder; stage 2 continues from the stage-1
+    network once per Lipschitz weight, minimising L_C + lambda L_LS (Eq. 9 on
+    the workload's cubature set, codes pulled back through the encoder);
+    lambda = 0 is the vanilla decoder, trained for the same number of steps.
+    Each decoder, and the untrained one, then runs the reduced solve
+    (--precision) over the same frames, from the code of the rest shape, with
+    each optimiser of --learned-optimizers (projective Newton; L-BFGS, the
+    optimiser of the paper's main results, Sec. 5).  Reported per decoder:
+    L_C and L_LS on a fixed batch of 64 snapshots, and per optimiser steps/s,
     iterations per step, exits and the relative displacement error against
     the full-space trajectory."""
     import dataclasses
@@ -805,7 +816,7 @@ def run_learned(args, world, rank, local):
     t_fs = time.perf_counter() - t0
     fs.close()
     Qf = np.array(Qf)
-    # 2. decoders: same initial weights and PCA encoder, one per Lipschitz weight
+    # 2. decoders
     r, n = c.r, p.n
     D = Qf - X0
     _, sv, Vt = np.linalg.svd(D, full_matrices=False)
@@ -813,54 +824,81 @@ def run_learned(args, world, rank, local):
     eb0 = np.zeros(r, np.float32)
     cub, cw = p.cub_idx, p.cub_w
     tprec = "tf32" if args.precision in ("bf16", "tf32") else args.precision
-    decoders = {"untrained": (p.Ws, p.bs, None)}
     Qd = torch.tensor(Qf, dtype=torch.float64, device="cuda")
     rs = np.random.default_rng(3)
-    for lam in [float(x) for x in args.lambdas.split(",")]:
+    B = min(64, K)
+    ev = torch.tensor(np.sort(rs.choice(K, B, replace=False)), device="cuda")
+
+    def trainer(theta=None):
         tc = pkg.Context()
         tc.set_mesh(p.X0, p.tets)
         tc.set_material(c.youngs, c.poisson, c.density, c.gravity)
         tc.set_decoder(p.Ws, p.bs, c.out_scale, tprec)
         tc.train_init(Ew0, eb0, cub, cw)
+        if theta is not None:
+            tc.train_set_params(theta)
+        return tc
+
+    def train(tc, lam, steps):
         t1 = time.perf_counter()
-        for _ in range(args.train_steps):
-            idx = torch.tensor(rs.choice(K, min(64, K), replace=False), device="cuda")
+        for _ in range(steps):
+            idx = torch.tensor(rs.choice(K, B, replace=False), device="cuda")
             tc.train_step(Qd[idx], lam, 1e-3)
         torch.cuda.synchronize()
-        t_tr = time.perf_counter() - t1
-        (lc, lls, _), _ = tc.train_eval(Qd[:min(64, K)], lam, want_grad=False)
-        _, _, Ws, bs = unpack_params(tc.train_get_params(), p.widths, n)
+        return time.perf_counter() - t1
+
+    def measured(tc, t_tr, lam):
+        # L_LS is reported unweighted; any positive weight evaluates it
+        (lc, lls, _), _ = tc.train_eval(Qd[ev], 1e-30, want_grad=False)
+        Ew, eb, Ws, bs = unpack_params(tc.train_get_params(), p.widths, n)
+        return Ws, bs, eb, {"lambda": lam, "L_C": lc, "L_LS": lls, "train_s": t_tr}
+
+    decoders = {}
+    tc = trainer()
+    decoders["untrained"] = measured(tc, 0.0, None)
+    t_s1 = train(tc, 0.0, args.train_steps)
+    theta1 = tc.train_get_params()
+    decoders["stage 1"] = measured(tc, t_s1, 0.0)
+    tc.close()
+    for lam in [float(x) for x in args.lambdas.split(",")]:
+        tc = trainer(theta1)
+        t_tr = train(tc, lam, args.finetune_steps)
+        decoders[f"lambda={lam:g}"] = measured(tc, t_s1 + t_tr, lam)
         tc.close()
-        decoders[f"lambda={lam:g}"] = (Ws, bs, {"L_C": lc, "L_LS": lls, "train_s": t_tr})
-    # 3. reduced solves over the same frames
+    # 3. reduced solves over the same frames, from the rest code, with each optimiser
     out = {}
-    for name, (Ws, bs, info) in decoders.items():
+    for name, (Ws, bs, eb, info) in decoders.items():
         pd = dataclasses.replace(p, Ws=Ws, bs=bs)
-        ctx = pkg.context_from_problem(pd, precision=args.precision, optimizer=args.optimizer,
-                                       history=args.history)
-        its, ex, errs, t_red = 0, {}, [], 0.0
-        for k in range(1, K + 1):
-            ctx.set_constraints(None, p.targets(k))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            rc, st, _ = ctx.step(dt=c.dt)
-            t_red += time.perf_counter() - t0
-            its += st["newton_iters"]
-            ex[str(rc)] = ex.get(str(rc), 0) + 1
-            u, uf = ctx.get_positions() - X0, Qf[k - 1] - X0
-            errs.append(float(np.linalg.norm(u - uf) / max(np.linalg.norm(uf), 1e-300)))
-        ctx.close()
-        out[name] = {"steps_per_s": K / t_red, "newton_iters_per_step": its / K, "exits": ex,
-                     "max_rel_error_vs_fullspace": max(errs),
-                     "mean_rel_error_vs_fullspace": float(np.mean(errs)), "training": info}
+        out[name] = {"training": info}
+        for opt in args.learned_optimizers.split(","):
+            ctx = pkg.context_from_problem(pd, precision=args.precision, optimizer=opt,
+                                           history=args.history)
+            ctx.set_state(np.asarray(eb, np.float64), X0, None)
+            its, ex, errs, t_red = 0, {}, [], 0.0
+            for k in range(1, K + 1):
+                ctx.set_constraints(None, p.targets(k))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, st, _ = ctx.step(dt=c.dt)
+                t_red += time.perf_counter() - t0
+                its += st["newton_iters"]
+                ex[str(rc)] = ex.get(str(rc), 0) + 1
+                u, uf = ctx.get_positions() - X0, Qf[k - 1] - X0
+                errs.append(float(np.linalg.norm(u - uf) / max(np.linalg.norm(uf), 1e-300)))
+            ctx.close()
+            out[name][opt] = {"steps_per_s": K / t_red, "iters_per_step": its / K,
+                              "exits": ex, "max_rel_error_vs_fullspace": max(errs),
+                              "mean_rel_error_vs_fullspace": float(np.mean(errs))}
     if rank == 0:
         print(json.dumps({
             "metric": "learned subspace vs untrained and vs the full-space GPU solve",
             "config": {"workload": args.workload, "frames": f"1..{K}", "r": r,
                        "decoder": "-".join(map(str, p.widths)), "precision": args.precision,
-                       "optimizer": args.optimizer, "train_steps": args.train_steps,
+                       "optimizers": args.learned_optimizers, "stage1_steps": args.train_steps,
+                       "stage2_steps": args.finetune_steps, "batch": B, "lr": 1e-3,
                        "trainer": tprec, "snapshots": f"full-space GPU solve, FP64 element "
-                       f"math, frames 1..{K}", "cubature": len(cub)},
+                       f"math, frames 1..{K}", "cubature": len(cub),
+                       "start": "code of the rest shape (the trained encoder's bias)"},
             "fullspace_steps_per_s": K / t_fs, "decoders": out}), flush=True)
 
 
