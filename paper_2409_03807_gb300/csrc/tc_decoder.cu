@@ -20,7 +20,10 @@
 //   warp 1  MMA issuer: M = 128, N = Cp; TMEM accumulator double-buffered so
 //           the epilogue of tile i overlaps the main loop of tile i + 1; it
 //           also issues the inertia Gram MMA (M = 64) of the previous tile
-//   warps 2-5 epilogue: one thread per row (TMEM lane quadrant = warp % 4)
+//   warps 2-9 epilogue: one thread per row and column half, two warps per
+//           TMEM lane quadrant (= warp % 4): warps 2-5 take the column chunks
+//           below 32 (the value column and the first Jacobian columns),
+//           warps 6-9 the rest (further Jacobian columns, trial points)
 // Every mbarrier wait is bounded by wall time (globaltimer); a wait that
 // runs out records an error code and the CTA stops issuing work.
 #include <cuda_bf16.h>
@@ -41,7 +44,8 @@ using namespace tc;
 
 constexpr int TBM = 128;      // rows per tile
 constexpr int TST = 4;        // pipeline stages
-constexpr int TNT = 192;      // threads: producer, MMA, 4 epilogue warps
+constexpr int TNT = 320;      // threads: producer, MMA, 8 epilogue warps
+constexpr int NEW = 8;        // epilogue warps
 constexpr int GM = 64;        // Gram accumulator rows (M = 64 layout)
 constexpr uint32_t COL_ACC1 = 128, COL_GRAM = 256, TMEM_COLS = 512;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
@@ -64,14 +68,14 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* er
   }
 }
 
-__device__ __forceinline__ void epi_sync() {  // the 4 epilogue warps
-  asm volatile("bar.sync 1, 128;\n" ::: "memory");
+__device__ __forceinline__ void epi_sync() {  // the 8 epilogue warps
+  asm volatile("bar.sync 1, 256;\n" ::: "memory");
 }
-// barrier of the 4 epilogue warps that also returns the AND of `v` over them
+// barrier of the 8 epilogue warps that also returns the AND of `v` over them
 __device__ __forceinline__ bool epi_sync_and(bool v) {
   uint32_t out;
   asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.and.pred q, 1, 128, p;\n"
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.and.pred q, 1, 256, p;\n"
       " selp.u32 %0, 1, 0, q;\n}\n"
       : "=r"(out)
       : "r"((uint32_t)v)
@@ -175,8 +179,8 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, size_t count,
 }
 
 struct TcSmem {  // byte offsets from the 1024-aligned base
-  uint32_t stage_bytes, a_bytes, bh_off, bl_off, jt_off, jt_bytes, js_off, gv_off, red_off,
-      total;
+  uint32_t stage_bytes, a_bytes, bh_off, bl_off, jt_off, jt_bytes, js_off, gv_off, gp_off,
+      red_off, total;
 };
 
 // split: the Gram operand buffers hold a BF16 hi and lo part each
@@ -191,8 +195,9 @@ __host__ __device__ inline TcSmem tc_smem_layout(bool bf, int Cp, int r, bool sp
   L.js_off = L.jt_off + 2 * L.jt_bytes;
   const uint32_t js_bytes = TBM * (r + 4) * 4;
   L.gv_off = (L.js_off + js_bytes + 15) & ~15u;
-  L.red_off = L.gv_off + TBM * 8;  // (gv stored as float; 8 bytes kept)
-  L.total = L.red_off + 4 * (2 + 2 * KTRIAL) * 8;
+  L.gp_off = L.gv_off + TBM * 8;  // (gv stored as float; 8 bytes kept)
+  L.red_off = L.gp_off + 2 * 4 * 64 * 4;  // g partials of 4 row groups (value, |term|)
+  L.total = L.red_off + NEW * (2 + 2 * KTRIAL) * 8;
   return L;
 }
 
@@ -237,7 +242,7 @@ __global__ void __launch_bounds__(TNT, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], 4);
+      mbar_init(&tempty[i], NEW);
       mbar_init(&jfull[i], 1);
       mbar_init(&jempty[i], 1);
     }
@@ -366,11 +371,16 @@ __global__ void __launch_bounds__(TNT, 1)
   } else {
     // ------------------------------------------------ epilogue
     const int q = warp & 3;          // TMEM lane quadrant
-    const int et = t - 64;           // 0..127 within the epilogue warps
+    const int et = t - 64;           // 0..255 within the epilogue warps
+    const int ew = et >> 5;          // epilogue warp 0..7
+    const int h = ew >> 2;           // column half
     const int row = 32 * q + lane;   // row of the tile
     float* Js = reinterpret_cast<float*>(sb + SL.js_off);
     float* gvs = reinterpret_cast<float*>(sb + SL.gv_off);
-    const int JS = r + 4;
+    float* gp = reinterpret_cast<float*>(sb + SL.gp_off);
+    const int JS = r + 1 - (r & 1);  // odd row pitch: the per-row stores hit 32 banks
+    // column chunks of this warp: [0, 32) or [32, Cp)
+    const int cbeg = h ? 32 : 0, cend = h ? Cp : min(Cp, 32);
     const float inv_dt2 = (float)*la.inv_dt2;
     const float scale = (float)la.scale;
     const int ntr = C - nj;
@@ -395,7 +405,7 @@ __global__ void __launch_bounds__(TNT, 1)
           for (int k = 0; k < 3; ++k) dX[k] = la.X0[3 * v + k] - la.acen[k];
       }
       const int ab = i & 1;
-      // every decision to stop is taken by all 128 epilogue threads together
+      // every decision to stop is taken by all 256 epilogue threads together
       alive = epi_sync_and(wait_bar(&tfull[ab], (i >> 1) & 1, err, 16));
       if (!alive) break;
       tc_fence_after();
@@ -409,7 +419,35 @@ __global__ void __launch_bounds__(TNT, 1)
       const bool jok = (i < 2) || wait_bar(&jempty[jb], ((i >> 1) & 1) ^ 1, err, 32);
       uint8_t* jt = sb + SL.jt_off + jb * SL.jt_bytes;
       float gv = 0.f, wk = 0.f;
-      for (int c0 = 0; c0 < Cp; c0 += 16) {
+      // the value column: row terms, and u and the energies (owner); sqrt(kv)
+      // scales the Gram operand
+      auto value_col = [&](float a, bool owner) {
+        const bool aff = AFF && live && slot < 0;
+        const double u0d =
+            aff ? (double)(scale * (a + bm)) + la.scale * affine_disp_tc(la, comp, dX, 0)
+                : 0.0;
+        const float u0r = slot >= 0 ? cu : (aff ? (float)u0d : scale * (a + bm));
+        float e = 0.f, kv = 0.f;
+        if (live) {
+          if (aff)
+            row_terms_tc_aff(la, inv_dt2, comp, mv, la.ubar[m], la.X0[m], u0d, e, gv, kv);
+          else
+            row_terms_tc(la, inv_dt2, comp, mv, ub, x0, u0r, e, gv, kv);
+          if (owner) {
+            u_out[m] = u0r;
+            facc_add(eacc, e);
+            facc_add(eabs, fabsf(e));
+          }
+        }
+        wk = sqrtf(kv);
+      };
+      if (cbeg > 0 && cbeg < cend) {  // the second half needs sqrt(kv) too
+        uint32_t vv[16];
+        tmem_ld16(ta, vv);
+        tmem_ld_wait();
+        value_col(__uint_as_float(vv[0]), false);
+      }
+      for (int c0 = cbeg; c0 < cend; c0 += 16) {
         uint32_t vv[16];
         tmem_ld16(ta + c0, vv);
         tmem_ld_wait();
@@ -418,22 +456,7 @@ __global__ void __launch_bounds__(TNT, 1)
           const int c = c0 + j;
           const float a = __uint_as_float(vv[j]);
           if (c == 0) {
-            const bool aff = AFF && live && slot < 0;
-            const double u0d =
-                aff ? (double)(scale * (a + bm)) + la.scale * affine_disp_tc(la, comp, dX, 0)
-                    : 0.0;
-            const float u0r = slot >= 0 ? cu : (aff ? (float)u0d : scale * (a + bm));
-            float e = 0.f, kv = 0.f;
-            if (live) {
-              if (aff)
-                row_terms_tc_aff(la, inv_dt2, comp, mv, la.ubar[m], la.X0[m], u0d, e, gv, kv);
-              else
-                row_terms_tc(la, inv_dt2, comp, mv, ub, x0, u0r, e, gv, kv);
-              u_out[m] = u0r;
-              facc_add(eacc, e);
-              facc_add(eabs, fabsf(e));
-            }
-            wk = sqrtf(kv);
+            value_col(a, true);
           } else if (c <= r) {
             // Jacobian row into the staging tile; sqrt(kv) J row into the
             // Gram operand (K-major: operand row = column, K = tile row)
@@ -483,45 +506,54 @@ __global__ void __launch_bounds__(TNT, 1)
       }
       tc_fence_before();
       if (lane == 0) mbar_arrive(&tempty[ab]);
-      gvs[row] = live ? gv : 0.f;
+      if (h == 0) gvs[row] = live ? gv : 0.f;
       fence_proxy_async_smem();
       alive = epi_sync_and(jok);
       if (et == 0 && alive) mbar_arrive(&jfull[jb]);
       // g partial (double) and the coalesced copy of the J tile
       const int rows = min(TBM, M - m0);
-      if (et < r) {
-        // FP32 within the tile (four interleaved partial sums), FP64 across tiles
+      {
+        // FP32 within a group of 32 rows (four interleaved partial sums), the
+        // four groups in fixed order, FP64 (double-float) across tiles
+        const int c = et & 63, rg = et >> 6;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        int rr = 0;
-        for (; rr + 4 <= rows; rr += 4) {
-          const float t0 = gvs[rr] * Js[rr * JS + et];
-          const float t1 = gvs[rr + 1] * Js[(rr + 1) * JS + et];
-          const float t2 = gvs[rr + 2] * Js[(rr + 2) * JS + et];
-          const float t3 = gvs[rr + 3] * Js[(rr + 3) * JS + et];
-          s0 += t0;
-          s1 += t1;
-          s2 += t2;
-          s3 += t3;
-          a0 += fabsf(t0);
-          a1 += fabsf(t1);
-          a2 += fabsf(t2);
-          a3 += fabsf(t3);
+        if (c < r) {
+          const int rend = min(rows, 32 * rg + 32);
+          int rr = 32 * rg;
+          for (; rr + 4 <= rend; rr += 4) {
+            const float t0 = gvs[rr] * Js[rr * JS + c];
+            const float t1 = gvs[rr + 1] * Js[(rr + 1) * JS + c];
+            const float t2 = gvs[rr + 2] * Js[(rr + 2) * JS + c];
+            const float t3 = gvs[rr + 3] * Js[(rr + 3) * JS + c];
+            s0 += t0;
+            s1 += t1;
+            s2 += t2;
+            s3 += t3;
+            a0 += fabsf(t0);
+            a1 += fabsf(t1);
+            a2 += fabsf(t2);
+            a3 += fabsf(t3);
+          }
+          for (; rr < rend; ++rr) {
+            const float t0 = gvs[rr] * Js[rr * JS + c];
+            s0 += t0;
+            a0 += fabsf(t0);
+          }
         }
-        for (; rr < rows; ++rr) {
-          const float t0 = gvs[rr] * Js[rr * JS + et];
-          s0 += t0;
-          a0 += fabsf(t0);
-        }
-        facc_add(gacc, (s0 + s1) + (s2 + s3));
-        facc_add(gabs, (a0 + a1) + (a2 + a3));
+        gp[rg * 64 + c] = (s0 + s1) + (s2 + s3);
+        gp[256 + rg * 64 + c] = (a0 + a1) + (a2 + a3);
       }
       float* Jdst = J_out + (size_t)m0 * r;
-      for (int rr = et >> 5; rr < rows; rr += 4)
+      for (int rr = ew; rr < rows; rr += NEW)
         for (int c = lane; c < r; c += 32) Jdst[(size_t)rr * r + c] = Js[rr * JS + c];
       epi_sync();
+      if (et < r) {
+        facc_add(gacc, (gp[et] + gp[64 + et]) + (gp[128 + et] + gp[192 + et]));
+        facc_add(gabs, (gp[256 + et] + gp[320 + et]) + (gp[384 + et] + gp[448 + et]));
+      }
       if (!alive) break;
     }
-    // energy sums: warp shuffles, then the 4 warps in fixed order
+    // energy sums: warp shuffles, then the 8 warps in fixed order
     FAcc vals[2 + 2 * KTRIAL];
     vals[0] = eacc;
     vals[1] = eabs;
@@ -537,12 +569,12 @@ __global__ void __launch_bounds__(TNT, 1)
     FAcc* red = reinterpret_cast<FAcc*>(sb + SL.red_off);
     if (lane == 0)
 #pragma unroll
-      for (int j = 0; j < 2 + 2 * KTRIAL; ++j) red[q * (2 + 2 * KTRIAL) + j] = vals[j];
+      for (int j = 0; j < 2 + 2 * KTRIAL; ++j) red[ew * (2 + 2 * KTRIAL) + j] = vals[j];
     epi_sync();
     double* prow = part + (size_t)blockIdx.x * part_stride;
     if (et < 2 + 2 * KTRIAL) {
       FAcc sum;
-      for (int w = 0; w < 4; ++w) facc_merge(sum, red[w * (2 + 2 * KTRIAL) + et]);
+      for (int w = 0; w < NEW; ++w) facc_merge(sum, red[w * (2 + 2 * KTRIAL) + et]);
       const double v = facc_value(sum);
       const int tslot = nslots(r);
       if (et < 2) prow[et] = v;
@@ -552,9 +584,11 @@ __global__ void __launch_bounds__(TNT, 1)
       prow[slot_g(et)] = facc_value(gacc);
       prow[slot_gabs(r, et)] = facc_value(gabs);
     }
-    // inertia Gram: row c of the M = 64 accumulator is TMEM lane
-    // 32 (c / 16) + c % 16, i.e. lanes 0-15 of quadrant c / 16
-    const bool gok = __all_sync(0xffffffffu, alive && wait_bar(&gdone, 0, err, 64));
+    // inertia Gram (read by the first four epilogue warps): row c of the
+    // M = 64 accumulator is TMEM lane 32 (c / 16) + c % 16, i.e. lanes 0-15
+    // of quadrant c / 16
+    const bool gok =
+        h == 0 && __all_sync(0xffffffffu, alive && wait_bar(&gdone, 0, err, 64));
     tc_fence_after();
     if (gok) {
       const int c = 16 * q + lane;
