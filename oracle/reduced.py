@@ -39,6 +39,14 @@ Gauss-Newton Hessian J^T diag(k [x_z < h]) J (the penalty's own Hessian).
 Gradient:  g(z) = sum_e w_e J_e^T g_e + J^T M (x - qbar) / dt^2   (Eq. 11 form)
 Hessian:   K(z) = sum_e w_e J_e^T Hproj_e J_e + J^T M J / dt^2   (Gauss-Newton:
            the term sum_k dE/dx_k d2x_k/dz2 is dropped; reading).
+Exact form (opt-in, `eval_exact`): the dropped term added back over the free
+           DOFs (the constrained ones do not move with z),
+               K_x(z) = K(z) + sum_{k free} dE/dx_k d2x_k/dz2,
+           then the r x r sum projected: eigenvalues below
+           clamp * max_i |lambda_i| raised to that value (the Hessian of E(z)
+           itself, differentiated twice through Eq. 2, with the per-element
+           Hessians kept projected; reading of the projective Newton of the
+           Supplement applied to the subspace Hessian).
 Newton:    K d = -g by Cholesky; if K is not positive definite, retry with a
            diagonal shift tau = 1e-12 * max(1, max|diag K|), multiplied by 10
            per retry, 20 retries at most.
@@ -49,7 +57,9 @@ Exit codes (shared meaning with the C ABI's status values):
     3 Hessian not positive definite after all shifts.
 
 Pins (tests/test_oracle_reduced.py): reduced gradient equals J^T times the
-assembled full gradient; K equals J^T Hproj_full J + J^T M J / dt^2;
+assembled full gradient; with unprojected element Hessians the exact form
+before its projection equals central differences of the reduced gradient,
+and the added term vanishes for a linear decoder; K equals J^T Hproj_full J + J^T M J / dt^2;
 finite differences of E give g; a linear decoder reproduces an independently
 written linear-subspace Newton solve; a linear decoder with only the
 quadratic inertia term converges in one Newton step to the closed-form
@@ -64,12 +74,13 @@ from .decoder import Decoder
 CONVERGED, MAX_ITERS, LS_FAILED, NOT_SPD = 0, 1, 2, 3
 
 
-def chunk_terms(xv, J, tets, DmInv, vol, w, mu, lam):
+def chunk_terms(xv, J, tets, DmInv, vol, w, mu, lam, project=True):
     """Elastic terms of one chunk of cubature tets (Eq. 11 with the projected
-    element Hessians): (sum_e w_e J_e^T g_e, sum_e w_e J_e^T Hproj_e J_e)."""
+    element Hessians, or the unprojected ones for pins):
+    (sum_e w_e J_e^T g_e, sum_e w_e J_e^T Hproj_e J_e)."""
     r = J.shape[1]
     ge = fem.element_gradient(xv, tets, DmInv, vol, mu, lam)
-    He = fem.element_hessian(xv, tets, DmInv, vol, mu, lam, project=True)
+    He = fem.element_hessian(xv, tets, DmInv, vol, mu, lam, project=project)
     Je = J[fem.element_dofs(tets)]                 # (c, 12, r)
     g = np.einsum("e,eki,ek->i", w, Je, ge)
     HJ = He @ Je                                   # H_e J_e
@@ -198,8 +209,9 @@ class ReducedModel:
             g -= (self.mass[:, None] * self.gravity[None, :]).ravel()
         return g + self._ground(x)[1]
 
-    def eval(self, z):
-        """E, reduced gradient g (r), Gauss-Newton reduced Hessian K (r, r)."""
+    def eval(self, z, project=True):
+        """E, reduced gradient g (r), Gauss-Newton reduced Hessian K (r, r)
+        (project=False: unprojected element Hessians, for pins)."""
         x, J = self.positions_jac(z)
         r = J.shape[1]
         E = self.energy_x(x)
@@ -207,12 +219,12 @@ class ReducedModel:
         K = np.zeros((r, r))
         xv = x.reshape(-1, 3)
         starts = range(0, self.tets.shape[0], self.chunk)
-        if self.pool is not None:      # the same chunks, evaluated in worker processes
+        if self.pool is not None and project:  # the same chunks, in worker processes
             parts = self.pool.chunk_terms(x, J, self.chunk)
         else:
             parts = (chunk_terms(xv, J, self.tets[s:s + self.chunk],
                                  self.DmInv[s:s + self.chunk], self.vol[s:s + self.chunk],
-                                 self.w[s:s + self.chunk], self.mu, self.lam)
+                                 self.w[s:s + self.chunk], self.mu, self.lam, project)
                      for s in starts)
         for gp, Kp in parts:           # summed in chunk order either way
             g += gp
@@ -228,6 +240,34 @@ class ReducedModel:
             g += J.T @ gc
             K += (J.T * hc) @ J
         return E, g, 0.5 * (K + K.T)
+
+    def curvature_term(self, z):
+        """sum_{k free} dE/dx_k d2x_k/dz2 (r x r): the second derivative of
+        the decoder (forward second-order tangents) contracted with the full
+        gradient; zero in the affine coordinates (x is linear in them) and on
+        the constrained DOFs."""
+        z = np.asarray(z, dtype=np.float64)
+        x = self.positions(z)
+        G = self.full_gradient_x(x)
+        G[self.cdofs] = 0.0
+        _, _, Hx = self.dec.out_jac_hess(z[:self.r_nn])      # (n, r_nn, r_nn)
+        C = np.zeros((self.r, self.r))
+        C[:self.r_nn, :self.r_nn] = np.einsum("k,kab->ab", G, Hx)
+        return C
+
+    def eval_exact(self, z, clamp=1e-10, project=True):
+        """E, g and the exact-form reduced Hessian: K + curvature_term,
+        projected (eigenvalues below clamp * max |eigenvalue| raised to it);
+        project=False returns the sum unprojected, with unprojected element
+        Hessians (pins)."""
+        E, g, K = self.eval(z, project=project)
+        K = K + self.curvature_term(z)
+        K = 0.5 * (K + K.T)
+        if not project:
+            return E, g, K
+        lam_, Q = np.linalg.eigh(K)
+        floor = clamp * max(float(np.max(np.abs(lam_))), np.finfo(float).tiny)
+        return E, g, (Q * np.maximum(lam_, floor)) @ Q.T
 
 
 @dataclass
@@ -254,12 +294,13 @@ def cholesky_direction(K, g):
 
 
 def newton_solve(model, z0, eps, max_newton=1024, max_ls=128, c=1e-4,
-                 trace=None):
+                 trace=None, exact=False):
+    """exact: the exact-form reduced Hessian (ReducedModel.eval_exact)."""
     z = np.asarray(z0, dtype=np.float64).copy()
     status, ls_total, it = MAX_ITERS, 0, 0
     E = gi = None
     for it in range(max_newton + 1):
-        E, g, K = model.eval(z)
+        E, g, K = model.eval_exact(z) if exact else model.eval(z)
         gi = float(np.max(np.abs(g)))
         if trace is not None:
             trace.append([E, gi, 0.0])
@@ -294,8 +335,10 @@ class ReducedSimulator:
     step solved by projective Newton or (optimizer="lbfgs") by L-BFGS."""
 
     def __init__(self, model, dt, z0=None, eps=1e-5, max_newton=1024,
-                 max_ls=128, c=1e-4, optimizer="newton", history=10, v0=None):
+                 max_ls=128, c=1e-4, optimizer="newton", history=10, v0=None,
+                 exact_hessian=False):
         self.optimizer, self.history = optimizer, history
+        self.exact = exact_hessian
         self.m = model
         self.dt = float(dt)
         r = model.r
@@ -318,7 +361,7 @@ class ReducedSimulator:
                                 self.max_ls, self.c)
         else:
             z, st = newton_solve(m, self.z, self.eps, self.max_newton, self.max_ls,
-                                 self.c)
+                                 self.c, exact=self.exact)
         self.z = z
         qn = m.positions(z)
         if self.dt > 0.0:

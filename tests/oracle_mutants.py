@@ -137,7 +137,29 @@ def _steepest_descent(old):
 
 
 # name: (apply, the pin files that must catch it)
+def _curvature_on_constrained_rows(old):
+    def curvature_term(self, z):   # the constrained DOFs' reactions kept in the sum
+        z = np.asarray(z, dtype=np.float64)
+        G = self.full_gradient_x(self.positions(z))
+        _, _, Hx = self.dec.out_jac_hess(z[:self.r_nn])
+        C = np.zeros((self.r, self.r))
+        C[:self.r_nn, :self.r_nn] = np.einsum("k,kab->ab", G, Hx)
+        return C
+    return curvature_term
+
+
+def _curvature_sign(old):
+    return lambda self, z: -old(self, z)
+
+
 MUTANTS = {
+    "curvature_on_constrained_rows": (lambda: _swap_method("oracle.reduced", "ReducedModel",
+                                                           "curvature_term",
+                                                           _curvature_on_constrained_rows),
+                                      ["tests/test_oracle_reduced.py"]),
+    "curvature_sign": (lambda: _swap_method("oracle.reduced", "ReducedModel", "curvature_term",
+                                            _curvature_sign),
+                       ["tests/test_oracle_reduced.py"]),
     "snh_psi_without_log_term": (lambda: _swap("oracle.snh", "psi", _psi_without_log),
                                  ["tests/test_oracle_snh.py"]),
     "snh_stress_transposed": (lambda: _swap("oracle.snh", "dpsi_dF", _stress_transposed),

@@ -268,3 +268,100 @@ def test_worker_pool_gives_the_serial_sums_exactly():
         pool.close()
     assert E0 == E1
     assert np.array_equal(g0, g1) and np.array_equal(K0, K1)
+
+
+def _fd_hessian(m, z, h=1e-5):
+    """Central differences of the reduced gradient g(z)."""
+    r = z.shape[0]
+    Hfd = np.zeros((r, r))
+    for k in range(r):
+        e = np.zeros(r)
+        e[k] = h
+        Hfd[:, k] = (m.energy_grad(z + e)[1] - m.energy_grad(z - e)[1]) / (2 * h)
+    return 0.5 * (Hfd + Hfd.T)
+
+
+@pytest.mark.parametrize("dyn,cub", [(False, False), (True, False), (True, True)])
+def test_exact_hessian_matches_central_differences_of_gradient(dyn, cub):
+    """With unprojected element Hessians, K + sum_k dE/dx_k d2x_k/dz2 (before
+    the r x r projection) is the Hessian of E(z): it equals central
+    differences of the reduced gradient, which the Gauss-Newton K alone
+    misses by far more."""
+    m = tiny_model(dyn, cub=cub)
+    z = np.random.default_rng(4).standard_normal(4) * 0.8
+    Hfd = _fd_hessian(m, z)
+    _, _, Kx = m.eval_exact(z, project=False)
+    _, _, Kgn = m.eval(z, project=False)
+    scale = np.abs(Hfd).max()
+    assert np.abs(Kx - Hfd).max() < 1e-6 * scale
+    assert np.abs(Kgn - Hfd).max() > 1e3 * np.abs(Kx - Hfd).max()
+
+
+def test_exact_hessian_with_affine_modes_matches_central_differences():
+    mesh = make_bar(6, 3, 3, 0.05)
+    n = 3 * mesh.nv
+    Ws, bs = xavier_decoder([4, 16, 16, n], 5)
+    m = ReducedModel(mesh.X0, mesh.tets, Decoder(Ws, bs, 1e-2), 1e5, 0.45, 1000.0, G,
+                     affine_center=mesh.X0.mean(0))
+    rng = np.random.default_rng(9)
+    m.set_dynamics(1 / 60, mesh.X0.ravel() + 1e-3 * rng.standard_normal(n))
+    z = rng.standard_normal(16) * 0.5
+    Hfd = _fd_hessian(m, z)
+    _, _, Kx = m.eval_exact(z, project=False)
+    assert np.abs(Kx - Hfd).max() < 1e-6 * np.abs(Hfd).max()
+    assert np.all(m.curvature_term(z)[4:, :] == 0.0) and np.all(m.curvature_term(z)[:, 4:] == 0.0)
+
+
+def test_curvature_term_vanishes_for_a_linear_decoder():
+    mesh = make_bar(6, 3, 3, 0.05)
+    n = 3 * mesh.nv
+    Ws, bs = xavier_decoder([4, n], 2)
+    m = ReducedModel(mesh.X0, mesh.tets, Decoder(Ws, bs, 1e-2), 1e5, 0.45, 1000.0, G,
+                     cnodes=face_nodes(mesh, 0))
+    m.set_dynamics(1 / 60, mesh.X0.ravel())
+    z = np.random.default_rng(3).standard_normal(4)
+    assert np.all(m.curvature_term(z) == 0.0)
+    _, _, K = m.eval(z)
+    _, _, Kx = m.eval_exact(z)
+    assert np.allclose(Kx, K, rtol=1e-12, atol=1e-12 * np.abs(K).max())
+
+
+def test_exact_hessian_projection():
+    """The r x r projection: eigenvalues at least clamp * max |eigenvalue|;
+    with clamp = 0 the closest PSD matrix in the Frobenius norm (the
+    eigen-clamp, checked against a brute-force search over PSD candidates
+    along the clamped directions); a matrix that is already positive definite
+    is left alone."""
+    from oracle.snh import project_psd
+    m = tiny_model(False)
+    z = np.random.default_rng(6).standard_normal(4) * 1.5
+    _, _, Kraw = m.eval_exact(z, project=False)
+    Kraw_p = m.eval(z)[2] + m.curvature_term(z)
+    Kraw_p = 0.5 * (Kraw_p + Kraw_p.T)
+    lam_ = np.linalg.eigvalsh(Kraw_p)
+    _, _, Kx = m.eval_exact(z, clamp=1e-3)
+    assert np.linalg.eigvalsh(Kx).min() >= 1e-3 * np.abs(lam_).max() * (1 - 1e-9)
+    _, _, K0 = m.eval_exact(z, clamp=0.0)
+    assert np.allclose(K0, project_psd(Kraw_p), atol=1e-10 * np.abs(lam_).max())
+    # a positive definite sum is kept as it is
+    A = Kraw_p + (1.0 - lam_.min()) * np.eye(4)
+    w, Q = np.linalg.eigh(A)
+    assert np.allclose((Q * np.maximum(w, 1e-10 * np.abs(w).max())) @ Q.T, A)
+    if lam_.min() < 0:   # the clamp moved something: distances to PSD matrices are larger
+        d0 = np.linalg.norm(K0 - Kraw_p)
+        rng = np.random.default_rng(0)
+        for _ in range(50):
+            B = rng.standard_normal((4, 4))
+            C = K0 + 1e-2 * np.abs(lam_).max() * (B @ B.T) / np.linalg.norm(B @ B.T)
+            assert np.linalg.norm(C - Kraw_p) >= d0 - 1e-12
+
+
+def test_exact_newton_reaches_the_same_minimiser():
+    """Newton with the exact-form Hessian converges to the minimiser the
+    Gauss-Newton solve finds, from the same start."""
+    m = tiny_model(True)
+    z0 = np.zeros(4)
+    zg, sg = newton_solve(m, z0, 1e-8)
+    zx, sx = newton_solve(m, z0, 1e-8, exact=True)
+    assert sg.status == CONVERGED and sx.status == CONVERGED
+    assert np.allclose(zx, zg, atol=1e-6)
