@@ -80,8 +80,21 @@ def parse():
     ap.add_argument("--lambdas", default="0,1e-7,1e-6,1e-5",
                     help="Lipschitz-loss weights of the second stage in --learned "
                          "(0 = vanilla)")
+    ap.add_argument("--snapshots", type=int, default=1024,
+                    help="quasi-static snapshot loads in --learned (training bar)")
+    ap.add_argument("--snapshot-seconds", type=float, default=900.0,
+                    help="wall-clock budget of the quasi-static snapshot solves in --learned "
+                         "(training continues on the snapshots solved within it)")
+    ap.add_argument("--heldout", type=int, default=32,
+                    help="held-out loads solved by each decoder in --learned (training bar)")
+    ap.add_argument("--train-precision", default="tf32",
+                    choices=["fp64", "fp32", "tf32", "bf16"],
+                    help="trainer form in --learned")
     ap.add_argument("--learned-optimizers", default="newton,lbfgs",
                     help="optimisers of the reduced solves in --learned")
+    ap.add_argument("--exact-hessian", action="store_true",
+                    help="projective Newton with the exact-form reduced Hessian (the decoder's "
+                         "curvature added, the r x r sum projected)")
     ap.add_argument("--fullspace", action="store_true",
                     help="time the full-space GPU solve (the comparison) on the workload's "
                          "mesh, constraints and frames, and the reduced solve's error against "
@@ -188,7 +201,9 @@ def workload_config(args, p, world):
             "cubature": len(p.cub_idx), "dt": c.dt, "tol_inf": c.eps,
             "precision": args.precision + " (FP64 Cholesky + line search)",
             "optimizer": (f"L-BFGS (history {args.history})" if args.optimizer == "lbfgs"
-                          else "projective Newton"),
+                          else "projective Newton" + (
+                              ", exact-form reduced Hessian (decoder curvature added, "
+                              "r x r projection)" if args.exact_hessian else "")),
             "frames": f"1..{K} (timed from rest, after {W} warm-up steps of frames 1..{W})",
             "l2": "flushed between steps (256 MiB write, outside events)",
             "parallelism": "replicas" if world > 1 else "1 GPU"}
@@ -225,7 +240,7 @@ def oracle_sim(p, args, pool_workers=None):
         model.pool = pool
     sim = ReducedSimulator(model, c.dt, eps=c.eps, max_newton=c.max_newton, max_ls=c.max_ls,
                            c=c.armijo_c, optimizer=args.optimizer, history=args.history,
-                           v0=p.v0)
+                           v0=p.v0, exact_hessian=args.exact_hessian)
     return sim, pool, max(workers, 1)
 
 
@@ -396,6 +411,8 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream(dev)
     ctx = pkg.context_from_problem(p, precision=args.precision, device=local, stream=stream,
                                    optimizer=args.optimizer, history=args.history)
+    if args.exact_hessian:
+        ctx.set_exact_hessian(True)
     frames = max(W, K)
     targets = torch.tensor(np.stack([p.targets(k) for k in range(1, frames + 1)]),
                            dtype=torch.float64, device=dev)
@@ -614,7 +631,8 @@ def run_train(args, world, rank, local):
     """Decoder-training throughput: Adam steps of L = L_C + 1e-3 L_LS on a
     batch of 64 seeded smooth displacement fields (twist and bend along the
     bar), 512 cubature tets; the trainer follows --precision (FP64, FP32, or
-    FP32 with TF32 tensor-core matrix products for the tensor-core forms)."""
+    FP32 with tensor-core matrix products: TF32 operands in the TF32 form, BF16
+    operands with FP32 master weights in the BF16 form)."""
     import torch
     torch.cuda.set_device(local)
     from paper_2409_03807_gb300.build import build
@@ -642,7 +660,6 @@ def run_train(args, world, rank, local):
     ctx = pkg.Context()
     ctx.set_mesh(p.X0, p.tets)
     ctx.set_material(c.youngs, c.poisson, c.density, c.gravity)
-    # tensor-core forms train with TF32 tensor-core matrix products
     ctx.set_decoder(p.Ws, p.bs, c.out_scale, args.precision)
     r, n = c.r, p.n
     ctx.train_init((rng.standard_normal((r, n)) / np.sqrt(n)).astype(np.float32),
@@ -661,8 +678,8 @@ def run_train(args, world, rank, local):
                           "value": args.steps / el, "unit": "steps/s", "n_gpus": 1,
                           "steps": args.steps, "warmup": args.warmup,
                           "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True,
-                          "dtype": {"fp64": "f64", "fp32": "f32"}.get(args.precision,
-                                                                      "tf32"),
+                          "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32",
+                                    "bf16": "bf16 (FP32 master)"}[args.precision],
                           "data": "synthetic",
                           "config": {"workload": name, "n": p.n, "decoder": "-".join(
                               map(str, p.widths)), "cubature": S, "batch": 64},
@@ -772,62 +789,119 @@ def unpack_params(th, widths, n):
     return Ew, eb, Ws, bs
 
 
+def lipschitz_estimate(H, Z):
+    """Eq. 7 over the codes Z (B x r) with subspace Hessians H (B x r x r):
+    the largest ||H_i - H_j||_F / ||z_i - z_j|| over pairs."""
+    B, best = len(Z), 0.0
+    for i in range(B):
+        dH = np.linalg.norm((H[i] - H).reshape(B, -1), axis=1)
+        dz = np.linalg.norm(Z[i] - Z, axis=1)
+        m = dz > 0
+        if m.any():
+            best = max(best, float((dH[m] / dz[m]).max()))
+    return best
+
+
 def run_learned(args, world, rank, local):
-    """What the learned subspace gains, at the bar twist's size: the full-space
-    GPU solve (FP64 element math; its end points agree with the FP64
-    full-space oracle) over frames 1..K gives the snapshots.  Decoders of the
-    workload's widths are trained on them on the GPU in the two stages of
-    Sec. 4.2: stage 1 minimises the reconstruction loss alone (Eq. 3) from the
-    Xavier weights and a PCA encoder; stage 2 continues from the stage-1
-    network once per Lipschitz weight, minimising L_C + lambda L_LS (Eq. 9 on
-    the workload's cubature set, codes pulled back through the encoder);
-    lambda = 0 is the vanilla decoder, trained for the same number of steps.
-    Each decoder, and the untrained one, then runs the reduced solve
-    (--precision) over the same frames, from the code of the rest shape, with
-    each optimiser of --learned-optimizers (projective Newton; L-BFGS, the
-    optimiser of the paper's main results, Sec. 5).  Reported per decoder:
-    L_C and L_LS on a fixed batch of 64 snapshots, and per optimiser steps/s,
-    iterations per step, exits and the relative displacement error against
-    the full-space trajectory."""
+    """What the learned subspace gains.  Snapshots come from the full-space
+    GPU solve (FP64 element math; it agrees with the FP64 full-space oracle):
+    for a dynamic workload its trajectory over frames 1..K; for the quasi-static
+    training bar, --snapshots equilibria under seeded random loads (x = 0 face
+    fixed, x = L face twisted by U[0, 3] rad about the long axis and bent by
+    U[0, 0.5] rad, solved in a serpentine load order, each from the previous
+    one) and --heldout further loads (each from the nearest snapshot).
+    Decoders of the workload's widths are trained on them on the GPU in the
+    two stages of Sec. 4.2: stage 1 minimises the reconstruction loss alone
+    (Eq. 3) from the Xavier weights and a PCA encoder; stage 2 continues from
+    the stage-1 network once per Lipschitz weight, minimising L_C + lambda
+    L_LS (Eq. 9 on the workload's cubature set, codes pulled back through the
+    encoder); lambda = 0 is the vanilla decoder, trained for the same number
+    of steps.  Each decoder, and the untrained one, then runs the reduced
+    solve (--precision) from the code of the rest shape, with each optimiser
+    of --learned-optimizers (projective Newton; L-BFGS, the optimiser of the
+    paper's main results, Sec. 5): over the same frames (dynamic), or one
+    quasi-static solve per held-out load.  Reported per decoder: L_C, L_LS and
+    the Eq. 7 estimate on a fixed batch of 64 snapshots, and per optimiser
+    steps (or solves) per second, iterations, exits and the relative
+    displacement error against the full-space solution."""
     import dataclasses
     import torch
     torch.cuda.set_device(local)
     from paper_2409_03807_gb300.build import build
     build()
     import paper_2409_03807_gb300 as pkg
+    from workloads import twist_bend_loads, twist_bend_targets
     p = load_problem(args)
     c = p.config
-    if c.ground_k > 0 or not (c.dt > 0):
-        raise SystemExit("--learned needs a dynamic workload without ground contact")
-    K = args.steps
+    if c.ground_k > 0 or p.affine_center is not None:
+        raise SystemExit("--learned needs a workload without ground contact or affine modes")
+    static = not (c.dt > 0)
+    dt = c.dt if not static else 0.0
     X0 = p.X0.ravel()
-    # 1. snapshots: the full-space trajectory
+    if static:
+        xs = p.X0[:, 0]
+        f0 = np.flatnonzero(xs <= xs.min() + 1e-9).astype(np.int32)
+        f1 = np.flatnonzero(xs >= xs.max() - 1e-9).astype(np.int32)
+        cn = np.concatenate([f0, f1])
+
+        def targets(ld):
+            return twist_bend_targets(p.X0, f0, f1, ld[0], ld[1])
+        loads = twist_bend_loads(args.snapshots, 2)
+        held = twist_bend_loads(args.heldout, 7)
+    else:
+        cn = p.cnodes
+        targets = p.targets
+        loads = list(range(1, args.steps + 1))
+        held = loads
+    # 1. snapshots from the full-space solve
     fs = pkg.Context()
     fs.set_mesh(p.X0, p.tets)
     fs.set_material(c.youngs, c.poisson, c.density, c.gravity)
     fs.set_solver(c.eps, c.max_newton, c.max_ls, c.armijo_c)
-    fs.set_constraints(p.cnodes, p.targets(1))
-    fs.fullspace_setup("fp64", 1e-6, 8192)
-    Qf = []
+    fs.set_constraints(cn, targets(loads[0]))
+    fs.fullspace_setup("fp64", 1e-4 if static else 1e-6, 8192)
+    Qf, fex, fits = [], {}, 0
+    B0 = 64  # training batch
     t0 = time.perf_counter()
-    for k in range(1, K + 1):
-        fs.set_constraints(None, p.targets(k))
-        Qf.append(fs.fullspace_step(c.dt)[2].copy())
+    for i, ld in enumerate(loads):
+        if static and i >= 2 * B0 and time.perf_counter() - t0 > args.snapshot_seconds:
+            loads = loads[:i]  # the budget ran out: train on the snapshots solved so far
+            break
+        fs.set_constraints(None, targets(ld))
+        rc, st, q = fs.fullspace_step(dt)
+        Qf.append(q.copy())
+        fex[str(rc)] = fex.get(str(rc), 0) + 1
+        fits += st["newton_iters"]
+        if static and (i + 1) % 128 == 0:
+            print(f"snapshots {i + 1}/{len(loads)}: {time.perf_counter() - t0:.1f} s",
+                  file=sys.stderr, flush=True)
     t_fs = time.perf_counter() - t0
-    fs.close()
     Qf = np.array(Qf)
+    if static:
+        Qh = []
+        for ld in held:
+            j = int(np.argmin(np.linalg.norm(loads - ld, axis=1)))
+            fs.fullspace_set_state(Qf[j], None)
+            fs.set_constraints(None, targets(ld))
+            Qh.append(fs.fullspace_step(0.0)[2].copy())
+        Qh = np.array(Qh)
+    else:
+        Qh = Qf
+    fs.close()
     # 2. decoders
+    K = len(Qf)
     r, n = c.r, p.n
     D = Qf - X0
     _, sv, Vt = np.linalg.svd(D, full_matrices=False)
     Ew0 = (Vt[:r] / np.maximum(sv[:r, None], 1e-12) * np.sqrt(K)).astype(np.float32)
     eb0 = np.zeros(r, np.float32)
     cub, cw = p.cub_idx, p.cub_w
-    tprec = "tf32" if args.precision in ("bf16", "tf32") else args.precision
+    tprec = args.train_precision
     Qd = torch.tensor(Qf, dtype=torch.float64, device="cuda")
     rs = np.random.default_rng(3)
     B = min(64, K)
-    ev = torch.tensor(np.sort(rs.choice(K, B, replace=False)), device="cuda")
+    evi = np.sort(rs.choice(K, B, replace=False))
+    ev = torch.tensor(evi, device="cuda")
 
     def trainer(theta=None):
         tc = pkg.Context()
@@ -851,7 +925,10 @@ def run_learned(args, world, rank, local):
         # L_LS is reported unweighted; any positive weight evaluates it
         (lc, lls, _), _ = tc.train_eval(Qd[ev], 1e-30, want_grad=False)
         Ew, eb, Ws, bs = unpack_params(tc.train_get_params(), p.widths, n)
-        return Ws, bs, eb, {"lambda": lam, "L_C": lc, "L_LS": lls, "train_s": t_tr}
+        Z = (Qf[evi] - X0) @ Ew.T + eb
+        lip = lipschitz_estimate(tc.train_hessians(Z), Z)
+        return Ws, bs, eb, {"lambda": lam, "L_C": lc, "L_LS": lls, "lipschitz_eq7": lip,
+                            "train_s": t_tr}
 
     decoders = {}
     tc = trainer()
@@ -865,7 +942,7 @@ def run_learned(args, world, rank, local):
         t_tr = train(tc, lam, args.finetune_steps)
         decoders[f"lambda={lam:g}"] = measured(tc, t_s1 + t_tr, lam)
         tc.close()
-    # 3. reduced solves over the same frames, from the rest code, with each optimiser
+    # 3. reduced solves from the rest code, with each optimiser
     out = {}
     for name, (Ws, bs, eb, info) in decoders.items():
         pd = dataclasses.replace(p, Ws=Ws, bs=bs)
@@ -873,33 +950,45 @@ def run_learned(args, world, rank, local):
         for opt in args.learned_optimizers.split(","):
             ctx = pkg.context_from_problem(pd, precision=args.precision, optimizer=opt,
                                            history=args.history)
-            ctx.set_state(np.asarray(eb, np.float64), X0, None)
+            ctx.set_constraints(cn, targets(held[0]))
             its, ex, errs, t_red = 0, {}, [], 0.0
-            for k in range(1, K + 1):
-                ctx.set_constraints(None, p.targets(k))
+            if not static:
+                ctx.set_state(np.asarray(eb, np.float64), X0, None)
+            for k, ld in enumerate(held):
+                if static:  # every held-out load from the rest code
+                    ctx.set_state(np.asarray(eb, np.float64), X0, None)
+                ctx.set_constraints(None, targets(ld))
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                rc, st, _ = ctx.step(dt=c.dt)
+                rc, st, _ = ctx.step(dt=dt)
                 t_red += time.perf_counter() - t0
                 its += st["newton_iters"]
                 ex[str(rc)] = ex.get(str(rc), 0) + 1
-                u, uf = ctx.get_positions() - X0, Qf[k - 1] - X0
+                u, uf = ctx.get_positions() - X0, Qh[k] - X0
                 errs.append(float(np.linalg.norm(u - uf) / max(np.linalg.norm(uf), 1e-300)))
             ctx.close()
-            out[name][opt] = {"steps_per_s": K / t_red, "iters_per_step": its / K,
-                              "exits": ex, "max_rel_error_vs_fullspace": max(errs),
+            out[name][opt] = {"solves_per_s": len(held) / t_red,
+                              "iters_per_solve": its / len(held), "exits": ex,
+                              "max_rel_error_vs_fullspace": max(errs),
                               "mean_rel_error_vs_fullspace": float(np.mean(errs))}
     if rank == 0:
+        snap = (f"{K} quasi-static full-space GPU solves (FP64 element math) under seeded "
+                f"twist U[0, 3] rad and bend U[0, 0.5] rad of the x = L face; {len(held)} "
+                "held-out loads" if static else
+                f"full-space GPU solve, FP64 element math, frames 1..{K}")
         print(json.dumps({
             "metric": "learned subspace vs untrained and vs the full-space GPU solve",
-            "config": {"workload": args.workload, "frames": f"1..{K}", "r": r,
+            "config": {"workload": args.workload, "n": n, "tets": p.ne, "r": r,
                        "decoder": "-".join(map(str, p.widths)), "precision": args.precision,
                        "optimizers": args.learned_optimizers, "stage1_steps": args.train_steps,
                        "stage2_steps": args.finetune_steps, "batch": B, "lr": 1e-3,
-                       "trainer": tprec, "snapshots": f"full-space GPU solve, FP64 element "
-                       f"math, frames 1..{K}", "cubature": len(cub),
+                       "trainer": tprec, "snapshots": snap, "cubature": len(cub),
+                       "solves": "quasi-static, one per held-out load" if static
+                       else f"implicit Euler, frames 1..{K}",
                        "start": "code of the rest shape (the trained encoder's bias)"},
-            "fullspace_steps_per_s": K / t_fs, "decoders": out}), flush=True)
+            "fullspace": {"solves_per_s": K / t_fs, "newton_iters_per_solve": fits / K,
+                          "exits": fex},
+            "decoders": out}), flush=True)
 
 
 def main():

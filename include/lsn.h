@@ -190,6 +190,23 @@ int lsn_set_solver(lsn_ctx* ctx, double tol_inf, int max_newton, int max_ls,
 enum lsn_optimizer { LSN_OPT_NEWTON = 0, LSN_OPT_LBFGS = 1 };
 int lsn_set_optimizer(lsn_ctx* ctx, int kind, int history);
 
+/* Exact-form reduced Hessian for projective Newton (opt-in; off by default).
+ * The Gauss-Newton K of Eq. 2's reduced solve drops the decoder's curvature;
+ * with enable != 0 every evaluation pass adds it back over the free DOFs,
+ *   K_x = K + sum_{k free} dE/dx_k d2x_k/dz2
+ *       = K + s sum_j (W_L^T G)_j d2h_j/dz2   (G = dE/dx, 0 on constrained
+ *         DOFs; h the last hidden layer; x = X0 + s (W_L h + b_L)),
+ * with the second derivatives of h carried forward through the hidden layers
+ * (ELU' and ELU''), and then projects the r x r sum: its eigenvalues below
+ * clamp * max |eigenvalue| are raised to that value (cyclic Jacobi in FP64).
+ * The affine coordinates (lsn_set_affine_modes) add no curvature.  The
+ * element Hessians stay PSD-projected; lsn_eval's K is then K_x.  Used by
+ * LSN_OPT_NEWTON only.  0 <= clamp < 1 (else LSN_ERR_ARG).  Takes effect at
+ * the next call that evaluates (the device engine is rebuilt).  Device
+ * memory: 12 S + n values of the element precision and three
+ * (max hidden width) x (1 + r + r (r + 1) / 2) buffers. */
+int lsn_set_exact_hessian(lsn_ctx* ctx, int enable, double clamp);
+
 /* Execution of a solve: mode 0 (default) launches the whole Newton loop as
  * one CUDA graph whose conditional WHILE node repeats an evaluation pass
  * until the device-side solver stops it; mode 1 drives the same kernels from
@@ -326,8 +343,12 @@ int lsn_get_trace(lsn_ctx* ctx, int max, double* grad_inf, double* energy,
  * Parameters are one flat vector, exchanged as FP64 arrays: Ew (r x n
  * row-major), eb (r), then W_l (out x in row-major), b_l for each decoder
  * layer.  The trainer computes in FP64 when the decoder precision is
- * LSN_PREC_FP64 and in FP32 otherwise (FP64 loss sums in both); the Lipschitz
- * gradient sums large cancelling adjoints, so FP32 gives it to ~1e-2 relative.
+ * LSN_PREC_FP64 and in FP32 otherwise (FP64 loss sums in both).  Its plain
+ * matrix products run on the tensor cores in the tensor-core forms: with
+ * TF32 operands (LSN_PREC_TF32), or with BF16 operands, the weights and
+ * activations of every product rounded to BF16 with FP32 accumulation and the
+ * parameters, gradient and Adam moments kept in FP32 as the master copy
+ * (LSN_PREC_BF16).
  * --------------------------------------------------------------------------- */
 
 /* Start training: initial encoder (enc_W r x n, enc_b r; host), training

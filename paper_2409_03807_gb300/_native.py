@@ -52,6 +52,7 @@ _SIGS = {
     "lsn_set_solver": [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                        ctypes.c_double],
     "lsn_set_optimizer": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
+    "lsn_set_exact_hessian": [ctypes.c_void_p, ctypes.c_int, ctypes.c_double],
     "lsn_set_affine_modes": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "lsn_tet_forces": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "lsn_select_cubature": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -305,6 +306,12 @@ class Context:
     def set_optimizer(self, kind="newton", history=10):
         """kind: "newton" (projective Newton) or "lbfgs"; history: L-BFGS pairs."""
         return self._check(self.lib.lsn_set_optimizer(self.h, OPTIMIZERS[kind], history))
+
+    def set_exact_hessian(self, enable=True, clamp=1e-10):
+        """Projective Newton with the exact-form reduced Hessian (the decoder's
+        curvature added back, then the r x r sum projected)."""
+        return self._check(self.lib.lsn_set_exact_hessian(self.h, int(bool(enable)),
+                                                          float(clamp)))
 
     def set_state(self, z=None, q=None, v=None):
         z, q, v = _f64(z), _f64(q), _f64(v)

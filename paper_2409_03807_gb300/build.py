@@ -14,7 +14,8 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "liblsn.so")
 SOURCES = ["mesh.cu", "decoder.cu", "element.cu", "element_ws.cu", "solve.cu", "api.cu", "noalloc.cu",
-           "train.cu", "tc_decoder.cu", "tc_hidden.cu", "tc_gemm.cu", "cubature.cu", "fullspace.cu"]
+           "train.cu", "tc_decoder.cu", "tc_hidden.cu", "tc_gemm.cu", "cubature.cu", "fullspace.cu",
+           "curvature.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

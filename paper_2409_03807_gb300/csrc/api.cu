@@ -203,6 +203,8 @@ struct lsn_ctx {
   double tol = 1e-5, armijo_c = 1e-4;
   int max_newton = 1024, max_ls = 128;
   int opt_kind = LSN_OPT_NEWTON, hist_m = 10;  // optimiser and L-BFGS history size
+  bool exact_hessian = false;  // decoder-curvature term in K (curvature.cu)
+  double exact_clamp = 1e-10;
   // state
   double* q = nullptr;
   double* v = nullptr;
@@ -261,6 +263,8 @@ struct Engine : EngineBase {
   DevHistory* hist = nullptr;  // L-BFGS curvature pairs
   double* Zd = nullptr;        // FP64 copy of the pass points (affine modes)
   int ggrid = 0;               // CTAs of the gradient-only element kernel
+  Curvature<Real> curv;        // exact-form reduced Hessian (opt-in)
+  bool use_exact = false;
 
   explicit Engine(lsn_ctx* ctx) : c(ctx) {
     cudaStream_t s = c->stream;
@@ -408,6 +412,23 @@ struct Engine : EngineBase {
     ck(cudaMemcpyAsync(sv, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     ck(cudaStreamSynchronize(s));
     ck(cudaGetLastError());
+    if (c->exact_hessian && kind == LSN_OPT_NEWTON) {
+      CurvView cv;
+      cv.widths = c->widths;
+      cv.n = n;
+      cv.nv = c->nv;
+      cv.ne = c->ne;
+      cv.S = S;
+      cv.r = r;
+      cv.num_sms = c->num_sms;
+      cv.tets = c->tets;
+      cv.cub_idx = c->S > 0 ? c->cub_idx : nullptr;
+      cv.use_tc_gemm = use_tc;
+      cv.s = s;
+      curv.clamp = c->exact_clamp;
+      ck(curv.setup(cv));
+      use_exact = true;
+    }
   }
 
   ~Engine() override {
@@ -434,7 +455,9 @@ struct Engine : EngineBase {
     dfree(sv);
   }
 
-  int kernels_per_pass() const override { return (L - 1) + 4; }
+  int kernels_per_pass() const override {
+    return (L - 1) + 4 + (use_exact ? curv.launches() : 0);
+  }
 
   void begin(int eval_only) override {
     Profiler& P = c->prof;
@@ -504,9 +527,10 @@ struct Engine : EngineBase {
     else
       launch_element<Real>(ea, u, J, ut, part_el, gfull, genergy, s);
     if (prof) P.end(LSN_K_ELEMENT);
-    if (prof) P.begin(LSN_K_SOLVE, 2);
+    if (prof) P.begin(LSN_K_SOLVE, 2 + (use_exact ? curv.launches() : 0));
     launch_reduce_partials(part_dec, grid_dec, part_el, gfull + genergy, use_tc ? -1 : gfull,
                            nslots(r), nst, sys, s);
+    if (use_exact) ck(curv.launch(ea, la, u, Z0, zstride(C), dW, db, sys, s));
     launch_select_direction<Real>(sv, sys, Z0, cond, use_cond, s);
     if (prof) P.end(LSN_K_SOLVE);
   }
@@ -517,7 +541,7 @@ struct Engine : EngineBase {
     ck(cudaMemcpyAsync(&h[0], tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (use_tc_last) ck(cudaMemcpyAsync(&h[1], tcl.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     ck(cudaStreamSynchronize(s));
-    return h[0] | h[1];
+    return h[0] | h[1] | (use_exact ? curv.device_error() : 0);
   }
 
   void finish(double dt) override {
@@ -994,6 +1018,16 @@ int lsn_set_optimizer(lsn_ctx* c, int kind, int history) {
   if (kind != c->opt_kind || history != c->hist_m) c->dirty = true;
   c->opt_kind = kind;
   c->hist_m = history;
+  return LSN_OK;
+}
+
+int lsn_set_exact_hessian(lsn_ctx* c, int enable, double clamp) {
+  if (!c) return LSN_ERR_ARG;
+  if (!(clamp >= 0.0 && clamp < 1.0))
+    return fail(c, LSN_ERR_ARG, "set_exact_hessian: clamp must be in [0, 1)");
+  if ((enable != 0) != c->exact_hessian || clamp != c->exact_clamp) c->dirty = true;
+  c->exact_hessian = enable != 0;
+  c->exact_clamp = clamp;
   return LSN_OK;
 }
 
@@ -1544,10 +1578,12 @@ int lsn_train_init(lsn_ctx* c, const float* enc_W, const float* enc_b, const int
     ts.inc.insert(ts.inc.end(), lists[v].begin(), lists[v].end());
   }
   // initial parameters: encoder, then the context's decoder
-  // the tensor-core forms train with TF32 tensor-core matrix products
-  const int tmode = c->precision == LSN_PREC_FP64 ? 1
-                    : (c->precision == LSN_PREC_TF32 || c->precision == LSN_PREC_BF16) ? 2
-                                                                                      : 0;
+  // the tensor-core forms train with tensor-core matrix products: TF32
+  // operands, or BF16 operands (FP32 master weights) in the BF16 form
+  const int tmode = c->precision == LSN_PREC_FP64   ? 1
+                    : c->precision == LSN_PREC_TF32 ? 2
+                    : c->precision == LSN_PREC_BF16 ? 3
+                                                    : 0;
   std::unique_ptr<TrainerBase> tr(TrainerBase::create(tmode, ts));
   tr->lip_order = c->lip_order;
   std::vector<double> theta(tr->nparams);

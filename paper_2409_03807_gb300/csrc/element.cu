@@ -1034,31 +1034,8 @@ __global__ void __launch_bounds__(128) tet_force_kernel(const int4* __restrict__
     for (int b = 0; b < 3; ++b) Dmi[a][b] = (Real)dminv[(3 * a + b) * ne + e];
   const Real wv = (Real)vol[e];
   disp_grad<Real>(u, tv, Dmi, H);
-  Invariants<Real> iv;
-  invariants<Real>(H, iv);
-  const Real Ic = iv.Ic3 + Real(3);
-  const Real dl = iv.Ic3 / (Real(4) * (Ic + Real(1)));
-  const Real lJ = lam * iv.Jm1;
   Real ge[12];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    Real P[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const Real Fij = H[i][j] + (i == j ? Real(1) : Real(0));
-      P[j] = wv * (mu * dl * Fij + lJ * iv.cof[i][j] +
-                   Real(0.75) * mu *
-                       (H[i][j] + H[j][i] - (i == j ? iv.trH : Real(0)) - iv.cofH[i][j]));
-    }
-    Real s0 = Real(0);
-#pragma unroll
-    for (int a = 1; a < 4; ++a) {
-      const Real v = P[0] * Dmi[a - 1][0] + P[1] * Dmi[a - 1][1] + P[2] * Dmi[a - 1][2];
-      ge[3 * a + i] = v;
-      s0 += v;
-    }
-    ge[i] = -s0;
-  }
+  snh_tet_forces<Real>(H, Dmi, wv, mu, lam, ge);
   const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
   for (int c = 0; c < r; ++c) {
     Real acc = Real(0);

@@ -2,9 +2,9 @@
 // neo-Hookean energy; projective Newton's per-element eigensystem,
 // Supplement): invariants of the displacement gradient Hd = F - I, the
 // energy density, a cyclic Jacobi eigen-decomposition of symmetric 3x3
-// matrices and the rotation-signed SVD built on it, and the loads of a tet's
-// indices, inverse rest edges and weight.  Included by element.cu and
-// element_ws.cu.
+// matrices and the rotation-signed SVD built on it, the loads of a tet's
+// indices, inverse rest edges and weight, and a tet's elastic forces.
+// Included by element.cu, element_ws.cu and curvature.cu.
 #pragma once
 #include "lsn_internal.cuh"
 
@@ -254,6 +254,38 @@ __device__ __forceinline__ void disp_grad(const Real* __restrict__ u, const int4
 #pragma unroll
     for (int j = 0; j < 3; ++j)
       H[i][j] = Du[i][0] * Dmi[0][j] + Du[i][1] * Dmi[1][j] + Du[i][2] * Dmi[2][j];
+}
+
+// Elastic forces of one tet, d(wv Psi(F))/dx for its four vertices
+// (ge[3 a + i]: vertex a, component i), from the displacement gradient H =
+// F - I, the inverse rest edge matrix and the weighted volume wv.
+template <typename Real>
+__device__ __forceinline__ void snh_tet_forces(const Real (&H)[3][3], const Real (&Dmi)[3][3],
+                                               Real wv, Real mu, Real lam, Real (&ge)[12]) {
+  Invariants<Real> iv;
+  invariants<Real>(H, iv);
+  const Real Ic = iv.Ic3 + Real(3);
+  const Real dl = iv.Ic3 / (Real(4) * (Ic + Real(1)));
+  const Real lJ = lam * iv.Jm1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Real P[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const Real Fij = H[i][j] + (i == j ? Real(1) : Real(0));
+      P[j] = wv * (mu * dl * Fij + lJ * iv.cof[i][j] +
+                   Real(0.75) * mu *
+                       (H[i][j] + H[j][i] - (i == j ? iv.trH : Real(0)) - iv.cofH[i][j]));
+    }
+    Real s0 = Real(0);
+#pragma unroll
+    for (int a = 1; a < 4; ++a) {
+      const Real v = P[0] * Dmi[a - 1][0] + P[1] * Dmi[a - 1][1] + P[2] * Dmi[a - 1][2];
+      ge[3 * a + i] = v;
+      s0 += v;
+    }
+    ge[i] = -s0;
+  }
 }
 
 }  // namespace

@@ -134,7 +134,7 @@ size_t tc_gemm_workspace_floats(int M, int N, int K, int num_sms);
 cudaError_t tc_gemm_tf32(cudaStream_t s, int M, int N, int K, float alpha, const float* A,
                          long long sam, long long sak, const float* B, long long sbk,
                          long long sbn, float beta, float* C, long long ldc, float* ws,
-                         size_t ws_floats, int num_sms, int* err);
+                         size_t ws_floats, int num_sms, int* err, bool bf16_operands = false);
 // tc_hidden.cu: hidden layers on the tensor cores (BF16 / TF32 forms; the
 // TcHidden handle is in tc_internal.cuh).  tc_hidden_applies: the layer's
 // shared-memory plan fits one CTA.
@@ -284,5 +284,40 @@ void launch_finish_positions(const double* X0, const Real* u, int n, double dt, 
 void launch_begin_step(const double* X0, const double* q, const double* v, int n, double dt,
                        const double* g /* host, 3 */, double* ubar, DevSolver* sv,
                        cudaStream_t s);
+
+// Exact-form reduced Hessian (curvature.cu, lsn_set_exact_hessian): per
+// evaluation pass, the decoder-curvature term sum_{k free} dE/dx_k d2x_k/dz2
+// added to the K slots of the reduced system row, then the r x r projection.
+struct CurvView {
+  std::vector<int> widths;   // r_nn, hidden widths..., n
+  int n = 0, nv = 0, ne = 0, S = 0, r = 0, num_sms = 1;
+  const int4* tets = nullptr;     // every tet of the mesh (device)
+  const int* cub_idx = nullptr;   // cubature tets (device; null: every tet, S = ne)
+  bool use_tc_gemm = false;       // hidden-layer products on the TF32 tensor-core GEMM
+  cudaStream_t s = nullptr;
+};
+template <typename Real>
+struct Curvature {
+  CurvView v;
+  double clamp = 1e-10;
+  int rn = 0, NY = 0, Hl = 0, nb = 0;
+  size_t proj_smem = 0, ws_floats = 0;
+  Real *F = nullptr, *G = nullptr, *Y[2] = {nullptr, nullptr}, *A = nullptr, *vv = nullptr;
+  double* part = nullptr;
+  int *vptr = nullptr, *ventry = nullptr;
+  float* ws = nullptr;
+  int* gerr = nullptr;
+  cudaError_t setup(const CurvView& cv);
+  void release();
+  // u: displacements at the pass point y0; Z0: the pass points (column 0 =
+  // y0, column stride zcps); dW, db: the decoder (device, Real); sys: the
+  // reduced system row after the partial-row reduction
+  cudaError_t launch(const ElemArgs& ea, const LastArgs& la, const Real* u, const Real* Z0,
+                     int zcps, const std::vector<Real*>& dW, const std::vector<Real*>& db,
+                     double* sys, cudaStream_t s) const;
+  int launches() const { return 7 + 2 * ((int)v.widths.size() - 2); }
+  int device_error() const;
+  ~Curvature() { release(); }
+};
 
 }  // namespace lsn

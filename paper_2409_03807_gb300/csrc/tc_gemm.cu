@@ -6,8 +6,11 @@
 //   A(m, k) = A[m sam + k sak],  B(k, n) = B[k sbk + n sbn],  C row-major (ldc),
 //
 // with FP32 inputs rounded to TF32 (to nearest) and FP32 accumulation (the
-// products the trainer's TF32 form specifies).  Any strides: both transposes occur in the
-// backward pass.
+// products the trainer's TF32 form specifies), or rounded to BF16 (to nearest
+// even; the trainer's BF16 form: BF16 weights and activations in every
+// product, FP32 master weights).  A product of two BF16 values is exact in
+// FP32, so the TF32 MMA gives on BF16-valued operands the products of a BF16
+// MMA.  Any strides: both transposes occur in the backward pass.
 //
 // A CTA computes a 128 x BN tile of C (BN = 32, 64 or 128 from N) over a
 // range of K.  Operand tiles of one 128-byte K block (32 values) are copied
@@ -22,6 +25,7 @@
 // on scheduling) and applies alpha and beta.  Every mbarrier wait is bounded
 // by %globaltimer; a wait that runs out records an error flag the caller
 // reads.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -73,6 +77,9 @@ __device__ __forceinline__ float to_tf32(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
   return __uint_as_float(u);
 }
+__device__ __forceinline__ float to_bf16(float x) {
+  return __bfloat162float(__float2bfloat16_rn(x));
+}
 
 // (row, k) of one 128-byte K block of a K-major operand: chunk k / 4 of the
 // row, swizzled by the row, word k % 4
@@ -87,7 +94,7 @@ __global__ void __launch_bounds__(NT, 1)
     gemm_kernel(int M, int N, int K, int klen, const float* __restrict__ A, long long sam,
                 long long sak, const float* __restrict__ B, long long sbk, long long sbn,
                 float alpha, float beta, float* __restrict__ C, long long ldc,
-                float* __restrict__ ws, int* __restrict__ err) {
+                float* __restrict__ ws, int* __restrict__ err, int opbf16) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t done[STAGES], fin;
   __shared__ uint32_t tbase_s;
@@ -137,7 +144,8 @@ __global__ void __launch_bounds__(NT, 1)
     }
   };
   // the copies hand the MMA raw FP32 bits, which it would truncate to TF32:
-  // each thread rounds the values it copied (to nearest) once they have landed
+  // each thread rounds the values it copied (to nearest: TF32, or BF16 in
+  // the BF16 form) once they have landed
   auto round_stage = [&](int st) {
     uint8_t* sa = smem_raw + (base - raw) + st * stage_bytes;
     uint8_t* sbb = sa + BM * 128u;
@@ -147,14 +155,14 @@ __global__ void __launch_bounds__(NT, 1)
       if (sak == 1) { row = i >> 5; k = i & 31; }
       else { row = i & (BM - 1); k = i >> 7; }
       float* x = reinterpret_cast<float*>(sa + blk_offset(row, k));
-      *x = to_tf32(*x);
+      *x = opbf16 ? to_bf16(*x) : to_tf32(*x);
     }
     for (int i = t; i < BN * KB; i += NT) {
       int nn, k;
       if (sbk == 1) { nn = i >> 5; k = i & 31; }
       else { nn = i % BN; k = i / BN; }
       float* x = reinterpret_cast<float*>(sbb + blk_offset(nn, k));
-      *x = to_tf32(*x);
+      *x = opbf16 ? to_bf16(*x) : to_tf32(*x);
     }
   };
   bool ok = true;
@@ -259,7 +267,7 @@ size_t tc_gemm_workspace_floats(int M, int N, int K, int num_sms) {
 cudaError_t tc_gemm_tf32(cudaStream_t s, int M, int N, int K, float alpha, const float* A,
                          long long sam, long long sak, const float* B, long long sbk,
                          long long sbn, float beta, float* C, long long ldc, float* ws,
-                         size_t ws_floats, int num_sms, int* err) {
+                         size_t ws_floats, int num_sms, int* err, bool bf16_operands) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   const int BN = tcg::tile_n(N);
   const int tm = (M + tcg::BM - 1) / tcg::BM, tn = (N + BN - 1) / BN;
@@ -279,7 +287,8 @@ cudaError_t tc_gemm_tf32(cudaStream_t s, int M, int N, int K, float alpha, const
   }
   cudaError_t e = launch_pdl(tcg::gemm_kernel, dim3(tn, tm, splits), dim3(tcg::NT),
                              tcg::smem_bytes(BN), s, M, N, K, klen, A, sam, sak, B, sbk, sbn,
-                             alpha, beta, C, ldc, splits > 1 ? ws : nullptr, err);
+                             alpha, beta, C, ldc, splits > 1 ? ws : nullptr, err,
+                             bf16_operands ? 1 : 0);
   if (e != cudaSuccess || splits == 1) return e;
   const size_t MN = (size_t)M * N;
   const int grid = (int)std::min<size_t>((MN + 255) / 256, 4 * (size_t)num_sms);

@@ -919,6 +919,9 @@ struct Trainer : TrainerBase {
   // TF32 tensor-core GEMMs (tc_gemm.cu) for the plain matrix products of the
   // forward and backward passes; otherwise the CUDA-core kernel above
   bool tf32 = false;
+  // BF16 form: the GEMMs round both operands to BF16 (the weights and the
+  // activations of every product); theta, the gradient and Adam stay FP32
+  bool bf16ops = false;
   float* gws = nullptr;   // split-K workspace of the tensor-core GEMM (grown on demand)
   size_t gws_cap = 0;
   int* gerr = nullptr;    // device flag: a bounded wait of the GEMM ran out
@@ -943,7 +946,7 @@ struct Trainer : TrainerBase {
     }
     tck(tc_gemm_tf32(s, M, N, K, (float)alpha, reinterpret_cast<const float*>(A), sam, sak,
                      reinterpret_cast<const float*>(B), sbk, sbn, (float)beta,
-                     reinterpret_cast<float*>(C), ldc, gws, gws_cap, num_sms, gerr));
+                     reinterpret_cast<float*>(C), ldc, gws, gws_cap, num_sms, gerr, bf16ops));
   }
   int device_error() override {
     if (!gerr) return 0;
@@ -1497,7 +1500,8 @@ struct Trainer : TrainerBase {
 TrainerBase* TrainerBase::create(int mode, const TrainSetup& ts) {
   if (mode == 1) return new Trainer<double>(ts);
   Trainer<float>* t = new Trainer<float>(ts);
-  t->tf32 = mode == 2;
+  t->tf32 = mode == 2 || mode == 3;
+  t->bf16ops = mode == 3;
   return t;
 }
 

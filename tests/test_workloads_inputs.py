@@ -77,3 +77,35 @@ def test_twist_and_compress_end_face():
     D0 = np.linalg.norm(X1[:, None, 1:] - X1[None, :, 1:], axis=2)
     D1 = np.linalg.norm(T[nf:, None, 1:] - T[None, nf:, 1:], axis=2)
     assert np.allclose(D0, D1, atol=1e-12)                       # twisted rigidly in y-z
+
+
+def test_twist_bend_snapshot_loads():
+    """The snapshot loads of the training bar: reproducible by seed, inside
+    [0, 3] x [0, 0.5] rad, serpentine order (twist slices increasing, bends
+    alternating), and targets that hold the x = 0 face at rest and move the
+    x = L face rigidly by the two rotations about its centre."""
+    from workloads import twist_bend_loads, twist_bend_targets, make_bar, face_nodes
+    L = twist_bend_loads(1024, 2)
+    assert L.shape == (1024, 2)
+    assert np.array_equal(L, twist_bend_loads(1024, 2))
+    assert not np.array_equal(L, twist_bend_loads(1024, 3))
+    assert L[:, 0].min() >= 0 and L[:, 0].max() <= 3.0
+    assert L[:, 1].min() >= 0 and L[:, 1].max() <= 0.5
+    slot = np.minimum((L[:, 0] / 3.0 * 32).astype(int), 31)
+    assert np.all(np.diff(slot) >= 0)
+    for s in range(32):
+        b = L[slot == s, 1]
+        assert np.all(np.diff(b) >= 0) if s % 2 == 0 else np.all(np.diff(b) <= 0)
+    mesh = make_bar(6, 4, 4, 0.05)
+    f0, f1 = face_nodes(mesh, 0), face_nodes(mesh, 1)
+    T = twist_bend_targets(mesh.X0, f0, f1, 1.1, 0.3)
+    assert np.array_equal(T[:len(f0)], mesh.X0[f0])
+    P, Q = mesh.X0[f1], T[len(f0):]
+    assert np.allclose(Q.mean(0), P.mean(0))
+    dP = np.linalg.norm(P[:, None] - P[None], axis=-1)
+    dQ = np.linalg.norm(Q[:, None] - Q[None], axis=-1)
+    assert np.allclose(dP, dQ)
+    # the face normal (x) turns by the bend angle alone (a twist about x keeps it)
+    n = np.linalg.svd(Q - Q.mean(0))[2][-1]
+    assert np.isclose(abs(n[0]), np.cos(0.3))
+    assert np.allclose(twist_bend_targets(mesh.X0, f0, f1, 0.0, 0.0)[len(f0):], P)

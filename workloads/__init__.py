@@ -13,11 +13,13 @@ r 8-65) stand in for them.
 from .bar import BarMesh, make_bar, face_nodes
 from .decoder_init import xavier_decoder
 from .cubature import draw_cubature
-from .motion import rotate_face_targets, twist_compress_targets
+from .motion import (rotate_face_targets, twist_compress_targets, twist_bend_targets,
+                     twist_bend_loads)
 from .configs import CONFIGS, Config, build_problem, Problem
 
 __all__ = [
     "BarMesh", "make_bar", "face_nodes", "xavier_decoder", "draw_cubature",
-    "rotate_face_targets", "twist_compress_targets", "CONFIGS", "Config",
+    "rotate_face_targets", "twist_compress_targets", "twist_bend_targets",
+    "twist_bend_loads", "CONFIGS", "Config",
     "build_problem", "Problem",
 ]
