@@ -22,9 +22,10 @@
 //      T = e1 (W T), U_cd = e2 (W T)_c (W T)_d + e1 (W U)_cd
 //      (e1, e2 the ELU derivatives at a = W h + b); Y_0 = [z | I | 0]
 //   5. contract_kernel  C_cd = sum_j v_j U_j,cd, added to K in the system row
-//   6. project_kernel   one CTA: cyclic Jacobi (parallel round-robin pairs) on
-//      the r x r K in FP64, then K += sum_{lambda_i < f} (f - lambda_i) q_i q_i^T
-//      with f = clamp * max |lambda|
+//   6. project_kernel   one CTA, FP64: a Cholesky attempt first (a positive
+//      definite K is left as it is: the projection would move it by at most
+//      f = clamp * max |lambda|); otherwise cyclic Jacobi (parallel round-robin
+//      pairs) on the r x r K, then K += sum_{lambda_i < f} (f - lambda_i) q_i q_i^T
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -82,17 +83,18 @@ __global__ void full_gradient_kernel(int nv, const int* __restrict__ vptr,
 }
 
 constexpr int WTV_THREADS = 256;
-constexpr int WTV_ROWS = 512;  // rows of W_L per CTA
+constexpr int WTV_ROWS = 128;  // rows of W_L per CTA
 
-// part[b][j] = sum over rows m of chunk b of W[m][j] G[m]
+// part[b][j] = sum over rows m of chunk b of W[m][j] G[m] (in the element
+// precision within a chunk, FP64 across chunks)
 template <typename Real>
 __global__ void wtv_kernel(const Real* __restrict__ W, const Real* __restrict__ G, int n, int H,
                            double* __restrict__ part) {
   const int m0 = blockIdx.x * WTV_ROWS, m1 = min(n, m0 + WTV_ROWS);
   for (int j = threadIdx.x; j < H; j += WTV_THREADS) {
-    double acc = 0.0;
-    for (int m = m0; m < m1; ++m) acc += (double)W[(size_t)m * H + j] * (double)G[m];
-    part[(size_t)blockIdx.x * H + j] = acc;
+    Real acc = Real(0);
+    for (int m = m0; m < m1; ++m) acc += W[(size_t)m * H + j] * G[m];
+    part[(size_t)blockIdx.x * H + j] = (double)acc;
   }
 }
 
@@ -189,6 +191,9 @@ __global__ void contract_kernel(const Real* __restrict__ Y, const Real* __restri
 
 constexpr int PROJ_THREADS = 256;
 constexpr int PROJ_SWEEPS = 30;
+// Jacobi stops once the off-diagonal part is below (64 u)^2 of the squared
+// Frobenius norm, or stops shrinking (it stalls at the rounding level)
+constexpr double PROJ_OFF_REL = 1.9e-25;
 
 // The r x r K of the system row, eigen-decomposed by cyclic Jacobi (parallel
 // round-robin ordering, disjoint rotations per round) in FP64; eigenvalues
@@ -229,6 +234,53 @@ __global__ void __launch_bounds__(PROJ_THREADS) project_kernel(double* __restric
     __syncthreads();
     return s;  // valid in thread 0
   };
+  // Cholesky attempt of K - f' I with f' = clamp ||K||_F >= f (on a copy in
+  // V): when it succeeds every eigenvalue is above f and the projection is
+  // the identity, so K stays as it is
+  {
+    __shared__ int s_bad;
+    __shared__ double s_fp;
+    double sq = 0.0;
+    for (int e = t; e < m * m; e += PROJ_THREADS) {
+      const int i = e / m, j = e - i * m;
+      const double a = A[i * ld + j];
+      V[i * ld + j] = a;
+      sq += a * a;
+    }
+    sq = block_sum(sq);
+    if (t == 0) {
+      s_bad = 0;
+      s_fp = clamp * sqrt(sq);
+    }
+    __syncthreads();
+    for (int j = t; j < r; j += PROJ_THREADS) V[j * ld + j] -= s_fp;
+    __syncthreads();
+    for (int j = 0; j < r; ++j) {
+      if (t == 0) {
+        const double pv = V[j * ld + j];
+        if (!(pv > 0.0)) s_bad = 1;
+        else V[j * ld + j] = sqrt(pv);
+      }
+      __syncthreads();
+      if (s_bad) break;
+      const double inv = 1.0 / V[j * ld + j];
+      for (int i = j + 1 + t; i < r; i += PROJ_THREADS) V[i * ld + j] *= inv;
+      __syncthreads();
+      const int rem = r - j - 1;
+      for (int e = t; e < rem * rem; e += PROJ_THREADS) {
+        const int i = j + 1 + e / rem, k = j + 1 + e % rem;
+        if (k <= i) V[i * ld + k] -= V[i * ld + j] * V[k * ld + j];
+      }
+      __syncthreads();
+    }
+    if (!s_bad) return;
+    for (int e = t; e < m * m; e += PROJ_THREADS) {
+      const int i = e / m, j = e - i * m;
+      V[i * ld + j] = i == j ? 1.0 : 0.0;
+    }
+    __syncthreads();
+  }
+  double prev_off = -1.0;
   for (int sweep = 0; sweep < PROJ_SWEEPS; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int e = t; e < m * m; e += PROJ_THREADS) {
@@ -244,7 +296,10 @@ __global__ void __launch_bounds__(PROJ_THREADS) project_kernel(double* __restric
       s_tot = tot;
     }
     __syncthreads();
-    if (!(s_off > 1e-30 * s_tot)) break;
+    if (!(s_off > PROJ_OFF_REL * s_tot)) break;
+    // stalled at the rounding level
+    if (prev_off >= 0.0 && s_off < 1e-20 * s_tot && !(s_off < 0.5 * prev_off)) break;
+    prev_off = s_off;
     for (int round = 0; round < m - 1; ++round) {
       // round-robin pairs: index 0 fixed, the others rotate by `round`
       if (t < m / 2) {

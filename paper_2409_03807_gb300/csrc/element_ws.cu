@@ -281,8 +281,16 @@ __device__ __forceinline__ void staged_wait() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-// dJ_a = J_{a+1} - J_0 (a = 0..2) for the four columns from the staged rows
-__device__ __forceinline__ void staged_diffs(const float4* stg, float (&d)[3][3][4]) {
+// The column build works on column pairs: Blackwell's paired FP32
+// instructions (__ffma2_rn, __fmul2_rn, __fadd2_rn: two independent IEEE
+// operations per instruction) halve the instruction count of the
+// per-(tet, column) arithmetic, which together with the element math fills
+// the issue slots of the SM.
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+
+// dJ_a = J_{a+1} - J_0 (a = 0..2) for the four columns from the staged rows,
+// as two column pairs: d[a][i][0] = columns c0, c0 + 1; d[a][i][1] = c0 + 2, c0 + 3
+__device__ __forceinline__ void staged_diffs(const float4* stg, float2 (&d)[3][3][2]) {
   float4 x[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) x[k] = stg[k * NBT];
@@ -291,18 +299,17 @@ __device__ __forceinline__ void staged_diffs(const float4* stg, float (&d)[3][3]
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const float4 p = x[3 * (a + 1) + i], q = x[i];
-      d[a][i][0] = p.x - q.x;
-      d[a][i][1] = p.y - q.y;
-      d[a][i][2] = p.z - q.z;
-      d[a][i][3] = p.w - q.w;
+      d[a][i][0] = __fadd2_rn(make_float2(p.x, p.y), make_float2(-q.x, -q.y));
+      d[a][i][1] = __fadd2_rn(make_float2(p.z, p.w), make_float2(-q.z, -q.w));
     }
 }
 
 // Column build of one tet (record rec) from dJ (staged_diffs) for the four
 // columns c0 .. c0 + 3: C_e rows into the operand (K rows 9 lt .. 9 lt + 8),
-// gradient terms into gp.
-__device__ __forceinline__ void build_tet(const float* rec, const float (&d)[3][3][4], int c0,
-                                          uint8_t* op, int lt, float (&gp)[4], float (&ga)[4]) {
+// gradient terms into gp (two column pairs).
+__device__ __forceinline__ void build_tet(const float* rec, const float2 (&d)[3][3][2], int c0,
+                                          uint8_t* op, int lt, float2 (&gp)[2],
+                                          float2 (&ga)[2]) {
   const float4* r4 = reinterpret_cast<const float4*>(rec);
   // gradient: sum_a ge_a . dJ_a
   {
@@ -312,21 +319,20 @@ __device__ __forceinline__ void build_tet(const float* rec, const float (&d)[3][
       const float4 x = r4[R_GE / 4 + k];
       ge[4 * k] = x.x; ge[4 * k + 1] = x.y; ge[4 * k + 2] = x.z; ge[4 * k + 3] = x.w;
     }
-    float g4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int h = 0; h < 2; ++h) {
+      float2 g2 = __fmul2_rn(bc2(ge[0]), d[0][0][h]);
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
+      for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) g4[k] += ge[3 * a + i] * d[a][i][k];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      gp[k] += g4[k];
-      ga[k] += fabsf(g4[k]);
+        for (int i = 0; i < 3; ++i)
+          if (a > 0 || i > 0) g2 = __ffma2_rn(bc2(ge[3 * a + i]), d[a][i][h], g2);
+      gp[h] = __fadd2_rn(gp[h], g2);
+      ga[h] = __fadd2_rn(ga[h], make_float2(fabsf(g2.x), fabsf(g2.y)));
     }
   }
   // R = sum_a (U^T dJ_a) y_a^T
-  float R[3][3][4];
+  float2 R[3][3][2];
   {
     float ut[12], y[12];
 #pragma unroll
@@ -337,17 +343,23 @@ __device__ __forceinline__ void build_tet(const float* rec, const float (&d)[3][
     }
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
-      float wa[3][4];
+      float2 wa[3][2];
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          wa[a][k] = ut[3 * p] * d[a][0][k] + ut[3 * p + 1] * d[a][1][k] + ut[3 * p + 2] * d[a][2][k];
+        for (int h = 0; h < 2; ++h) {
+          float2 w = __fmul2_rn(bc2(ut[3 * p]), d[a][0][h]);
+          w = __ffma2_rn(bc2(ut[3 * p + 1]), d[a][1][h], w);
+          wa[a][h] = __ffma2_rn(bc2(ut[3 * p + 2]), d[a][2][h], w);
+        }
 #pragma unroll
       for (int q = 0; q < 3; ++q)
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          R[p][q][k] = wa[0][k] * y[q] + wa[1][k] * y[3 + q] + wa[2][k] * y[6 + q];
+        for (int h = 0; h < 2; ++h) {
+          float2 v = __fmul2_rn(wa[0][h], bc2(y[q]));
+          v = __ffma2_rn(wa[1][h], bc2(y[3 + q]), v);
+          R[p][q][h] = __ffma2_rn(wa[2][h], bc2(y[6 + q]), v);
+        }
     }
   }
   float as[12], tf[8];
@@ -365,20 +377,23 @@ __device__ __forceinline__ void build_tet(const float* rec, const float (&d)[3][
   const uint32_t kr0 = 9u * (uint32_t)lt;
 #pragma unroll
   for (int m = 0; m < 9; ++m) {
-    float cv[4];
-    if (m < 3) {
-      const float a0 = as[3 * m], a1 = as[3 * m + 1], a2 = as[3 * m + 2];
+    float2 cv[2];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) cv[k] = a0 * R[0][0][k] + a1 * R[1][1][k] + a2 * R[2][2][k];
-    } else {
-      const int i = (m - 3) % 3, j = (i + 1) % 3, l = (i + 2) % 3;
-      const float s = tf[m - 3];
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        cv[k] = m < 6 ? s * (R[j][l][k] - R[l][j][k]) : s * (R[j][l][k] + R[l][j][k]);
+    for (int h = 0; h < 2; ++h) {
+      if (m < 3) {
+        float2 v = __fmul2_rn(bc2(as[3 * m]), R[0][0][h]);
+        v = __ffma2_rn(bc2(as[3 * m + 1]), R[1][1][h], v);
+        cv[h] = __ffma2_rn(bc2(as[3 * m + 2]), R[2][2][h], v);
+      } else {
+        const int i = (m - 3) % 3, j = (i + 1) % 3, l = (i + 2) % 3;
+        const float2 o = R[l][j][h];
+        const float2 sum = m < 6 ? __fadd2_rn(R[j][l][h], make_float2(-o.x, -o.y))
+                                 : __fadd2_rn(R[j][l][h], o);
+        cv[h] = __fmul2_rn(bc2(tf[m - 3]), sum);
+      }
     }
-    const __nv_bfloat162 lo = __floats2bfloat162_rn(cv[0], cv[1]);
-    const __nv_bfloat162 hi = __floats2bfloat162_rn(cv[2], cv[3]);
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(cv[0].x, cv[0].y);
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(cv[1].x, cv[1].y);
     uint2 v;
     v.x = *reinterpret_cast<const uint32_t*>(&lo);
     v.y = *reinterpret_cast<const uint32_t*>(&hi);
@@ -433,7 +448,7 @@ __global__ void __launch_bounds__(NT, 1)
 
   FAcc eacc, eabs, etr[KTRIAL], atr[KTRIAL];
   FAcc gacc[4];
-  float gabs[4] = {0.f, 0.f, 0.f, 0.f};
+  float2 gabs[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   bool alive = true;
   const int tb = t - 32 * NPW;  // column-build thread index
   const int Q = r >> 2;         // column quads (r is a multiple of 4)
@@ -502,14 +517,16 @@ __global__ void __launch_bounds__(NT, 1)
         }
         if (act) {
           staged_wait();
-          float d[3][3][4];
+          float2 d[3][3][2];
           staged_diffs(stg, d);  // consumes every staged row before it is refilled
           if (q + 1 < ntet) stage_rows(stg, J, r, c0, vnext);
           vnext = vids(q + 2);
-          float gp[4] = {0.f, 0.f, 0.f, 0.f};
+          float2 gp[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
           build_tet(urec + (size_t)(h * CH + slot) * RW, d, c0, sb + ob * BUF, slot, gp, gabs);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) facc_add(gacc[k], gp[k]);
+          facc_add(gacc[0], gp[0].x);
+          facc_add(gacc[1], gp[0].y);
+          facc_add(gacc[2], gp[1].x);
+          facc_add(gacc[3], gp[1].y);
         }
         fence_proxy_async_smem();  // operand writes -> the MMAs (async proxy)
         mbar_arrive(&ofull[ob]);
@@ -572,7 +589,8 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       gred[slot * 64 + 4 * quad + k] = gacc[k];
-      ared[slot * 64 + 4 * quad + k] = gabs[k];
+      ared[slot * 64 + 4 * quad + k] = k < 2 ? (k == 0 ? gabs[0].x : gabs[0].y)
+                                             : (k == 2 ? gabs[1].x : gabs[1].y);
     }
   }
   __syncthreads();
