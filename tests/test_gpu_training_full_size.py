@@ -2,9 +2,14 @@
 n = 26,010; decoder 16-256x3-26010; 512 cubature tets; batch 64): the GPU
 gradient of L = L_C + lambda L_LS checked by central differences of the GPU
 loss itself on 8 random parameters (FP64 trainer, step 1e-6 max(1, |theta|)),
-and one FP32 Adam step that lowers the loss.  The snapshots are seeded
-smooth displacement fields (the oracle's 1,024 full-space solves at this size
-are far too slow for a test; the gradient check does not depend on them)."""
+and one FP32 Adam step that lowers the loss.  The BF16 trainer form (BF16
+operands in every product, FP32 master weights) against that central-
+difference-checked FP64 gradient at full size, every decoder block (the
+oracle's autodiff at this size is too slow for a test; the two forms agree
+with the oracle at the small size in test_gpu_training.py), and BF16 Adam steps
+that lower the loss.  The snapshots are seeded smooth displacement fields (the
+oracle's 1,024 full-space solves at this size are far too slow for a test; the
+gradient check does not depend on them)."""
 import numpy as np
 import pytest
 
@@ -85,3 +90,35 @@ def test_full_size_fp32_adam_steps_lower_the_loss(pkg):
     l1 = ctx.train_eval(Q, 1e-3, want_grad=False)[0][2]
     assert np.isfinite(l1) and l1 < l0
     ctx.close()
+
+
+def test_full_size_bf16_gradient_against_fp64(pkg):
+    """Losses and per-block gradient of the BF16 form against the FP64 form at
+    the same parameters: L_C 1e-3, L_LS 0.1 (BF16 rounding of every product,
+    as at the small size), gradient blocks 0.1 relative and 0.999 cosine."""
+    from tests.gpu_util import rel
+    lam = 1e-3
+    p, c64, Q = _setup(pkg, "fp64")
+    (lc0, lls0, _), g0 = c64.train_eval(Q, lam)
+    th = c64.train_get_params()
+    c64.close()
+    _, c16, _ = _setup(pkg, "bf16")
+    c16.train_set_params(th)
+    (lc, lls, _), g = c16.train_eval(Q, lam)
+    assert lc == pytest.approx(lc0, rel=1e-3)
+    assert lls == pytest.approx(lls0, rel=0.1)
+    r, n = p.config.r, p.n
+    sizes = [r * n, r] + [sz for a, b in zip(p.widths[:-1], p.widths[1:]) for sz in (a * b, b)]
+    o = 0
+    for sz in sizes:  # encoder W, b, then every decoder layer's W, b
+        gb, g0b = g[o:o + sz], g0[o:o + sz]
+        cos = gb @ g0b / (np.linalg.norm(gb) * np.linalg.norm(g0b))
+        assert rel(gb, g0b) < 0.1 and cos > 0.999, (o, sz, rel(gb, g0b), cos)
+        o += sz
+    assert o == g.shape[0]
+    l0 = c16.train_eval(Q, lam, want_grad=False)[0][2]
+    for _ in range(20):
+        c16.train_step(Q, lam, 1e-4)
+    l1 = c16.train_eval(Q, lam, want_grad=False)[0][2]
+    assert np.isfinite(l1) and l1 < l0
+    c16.close()
