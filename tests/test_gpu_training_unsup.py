@@ -35,7 +35,7 @@ def pkg():
     return pkg
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
 @pytest.mark.parametrize("lam,lam_ls", [(0.0, 0.0), (0.5, 0.0), (0.5, 1e-3)])
 def test_unsupervised_losses_and_gradient_match_oracle(pkg, lam, lam_ls, prec):
     mesh, widths, cub, w, Ws, bs, Ew, eb, Q, tp, theta = make_case(B=6)
@@ -45,9 +45,11 @@ def test_unsupervised_losses_and_gradient_match_oracle(pkg, lam, lam_ls, prec):
     sigma = 0.02
     losses, g = ctx.train_eval_unsup(Z, lam, sigma, lam_ls)
     losses0, g0 = unsupervised_loss_and_grad(tp, th, Z, lam, sigma, lam_ls)
-    tl, tg = {"fp64": (1e-8, 1e-8), "fp32": (1e-4, 2e-3), "tf32": (2e-3, 3e-2)}[prec]
+    # BF16 operands: eight times the TF32 bands (the ratio of the unit roundoffs)
+    tl, tg = {"fp64": (1e-8, 1e-8), "fp32": (1e-4, 2e-3), "tf32": (2e-3, 3e-2),
+              "bf16": (2e-2, 0.25)}[prec]
     if lam_ls > 0.0 and prec != "fp64":
-        tg = 0.2
+        tg = max(tg, 0.2)
     for a, b in zip(losses, losses0):
         assert a == pytest.approx(b, rel=tl, abs=1e-12)
     o = 0
@@ -55,7 +57,8 @@ def test_unsupervised_losses_and_gradient_match_oracle(pkg, lam, lam_ls, prec):
         sz = int(np.prod(shp))
         gb, g0b = g[o:o + sz], g0[o:o + sz]
         if np.linalg.norm(g0b) > 1e-10 * np.linalg.norm(g0):
-            assert_close(gb, g0b, tg, u=UNIT_ROUNDOFF[prec])
+            assert_close(gb, g0b, tg, u=UNIT_ROUNDOFF["bf16_operands" if prec == "bf16"
+                                                      else prec])
         else:
             assert np.linalg.norm(gb) <= 1e-6 * np.linalg.norm(g0) + 1e-30
         o += sz
