@@ -530,7 +530,9 @@ struct Engine : EngineBase {
     if (prof) P.begin(LSN_K_SOLVE, 2 + (use_exact ? curv.launches() : 0));
     launch_reduce_partials(part_dec, grid_dec, part_el, gfull + genergy, use_tc ? -1 : gfull,
                            nslots(r), nst, sys, s);
-    if (use_exact) ck(curv.launch(ea, la, u, Z0, zstride(C), dW, db, sys, s));
+    if (use_exact)
+      ck(curv.launch(ea, la, u, Z0, zstride(C), dW, db,
+                     (use_tc_last && tcl.bf16) ? tcl.Wlow : nullptr, sys, s));
     launch_select_direction<Real>(sv, sys, Z0, cond, use_cond, s);
     if (prof) P.end(LSN_K_SOLVE);
   }

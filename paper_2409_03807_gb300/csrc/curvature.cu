@@ -26,6 +26,7 @@
 //      definite K is left as it is: the projection would move it by at most
 //      f = clamp * max |lambda|); otherwise cyclic Jacobi (parallel round-robin
 //      pairs) on the r x r K, then K += sum_{lambda_i < f} (f - lambda_i) q_i q_i^T
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -85,15 +86,20 @@ __global__ void full_gradient_kernel(int nv, const int* __restrict__ vptr,
 constexpr int WTV_THREADS = 256;
 constexpr int WTV_ROWS = 128;  // rows of W_L per CTA
 
+__device__ __forceinline__ float wval(__nv_bfloat16 w) { return __bfloat162float(w); }
+__device__ __forceinline__ float wval(float w) { return w; }
+__device__ __forceinline__ double wval(double w) { return w; }
+
 // part[b][j] = sum over rows m of chunk b of W[m][j] G[m] (in the element
-// precision within a chunk, FP64 across chunks)
-template <typename Real>
-__global__ void wtv_kernel(const Real* __restrict__ W, const Real* __restrict__ G, int n, int H,
+// precision within a chunk, FP64 across chunks); W is the output layer's
+// weights as the output layer reads them (the BF16 copy in the BF16 form)
+template <typename Real, typename WT>
+__global__ void wtv_kernel(const WT* __restrict__ W, const Real* __restrict__ G, int n, int H,
                            double* __restrict__ part) {
   const int m0 = blockIdx.x * WTV_ROWS, m1 = min(n, m0 + WTV_ROWS);
   for (int j = threadIdx.x; j < H; j += WTV_THREADS) {
     Real acc = Real(0);
-    for (int m = m0; m < m1; ++m) acc += W[(size_t)m * H + j] * G[m];
+    for (int m = m0; m < m1; ++m) acc += (Real)wval(W[(size_t)m * H + j]) * G[m];
     part[(size_t)blockIdx.x * H + j] = (double)acc;
   }
 }
@@ -456,13 +462,17 @@ void Curvature<Real>::release() {
 template <typename Real>
 cudaError_t Curvature<Real>::launch(const ElemArgs& ea, const LastArgs& la, const Real* u,
                                     const Real* Z0, int zcps, const std::vector<Real*>& dW,
-                                    const std::vector<Real*>& db, double* sys,
-                                    cudaStream_t s) const {
+                                    const std::vector<Real*>& db, const void* wl_bf16,
+                                    double* sys, cudaStream_t s) const {
   const int L = (int)v.widths.size() - 1;
   tet_forces_kernel<Real><<<(ea.S + 127) / 128, 128, 0, s>>>(ea, u, F);
   full_gradient_kernel<Real><<<(v.nv + 127) / 128, 128, 0, s>>>(v.nv, vptr, ventry, F, u, la,
                                                                   G);
-  wtv_kernel<Real><<<nb, WTV_THREADS, 0, s>>>(dW[L - 1], G, v.n, Hl, part);
+  if (wl_bf16)
+    wtv_kernel<Real, __nv_bfloat16><<<nb, WTV_THREADS, 0, s>>>(
+        static_cast<const __nv_bfloat16*>(wl_bf16), G, v.n, Hl, part);
+  else
+    wtv_kernel<Real, Real><<<nb, WTV_THREADS, 0, s>>>(dW[L - 1], G, v.n, Hl, part);
   wtv_reduce_kernel<Real><<<(Hl + 127) / 128, 128, 0, s>>>(part, nb, Hl, la.scale, vv);
   y0_kernel<Real><<<(rn * NY + 255) / 256, 256, 0, s>>>(Z0, zcps, rn, NY, Y[0]);
   int cur = 0;

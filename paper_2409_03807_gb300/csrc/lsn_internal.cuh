@@ -310,11 +310,12 @@ struct Curvature {
   cudaError_t setup(const CurvView& cv);
   void release();
   // u: displacements at the pass point y0; Z0: the pass points (column 0 =
-  // y0, column stride zcps); dW, db: the decoder (device, Real); sys: the
-  // reduced system row after the partial-row reduction
+  // y0, column stride zcps); dW, db: the decoder (device, Real); wl_bf16: the
+  // BF16 copy of W_L the output layer reads in the BF16 form (else null);
+  // sys: the reduced system row after the partial-row reduction
   cudaError_t launch(const ElemArgs& ea, const LastArgs& la, const Real* u, const Real* Z0,
                      int zcps, const std::vector<Real*>& dW, const std::vector<Real*>& db,
-                     double* sys, cudaStream_t s) const;
+                     const void* wl_bf16, double* sys, cudaStream_t s) const;
   int launches() const { return 7 + 2 * ((int)v.widths.size() - 2); }
   int device_error() const;
   ~Curvature() { release(); }

@@ -7,7 +7,8 @@ operands in every product, FP32 master weights) against that central-
 difference-checked FP64 gradient at full size, every decoder block (the
 oracle's autodiff at this size is too slow for a test; the two forms agree
 with the oracle at the small size in test_gpu_training.py), and BF16 Adam steps
-that lower the loss.  The snapshots are seeded smooth displacement fields (the
+that lower the loss.  At this size the Lipschitz loss and its gradient cancel
+more than at the small size, so the BF16 form's bands are wider there.  The snapshots are seeded smooth displacement fields (the
 oracle's 1,024 full-space solves at this size are far too slow for a test; the
 gradient check does not depend on them)."""
 import numpy as np
@@ -96,9 +97,10 @@ def test_full_size_bf16_gradient_against_fp64(pkg):
     """Losses and per-block gradient of the BF16 form against the FP64 form at
     the same parameters.  L_C 1e-3.  L_LS sums squared differences of the
     subspace Hessians of 64 smooth, similar fields, which cancel: the BF16
-    rounding of every product reaches it at about 10 % here (3 % at the small
-    size), so 0.25.  Gradient blocks 0.3 relative and 0.99 cosine.  The
-    measured values are printed (pytest -s)."""
+    rounding of every product reaches it at 10.3 % here (3 % at the small
+    size), so 0.2.  Gradient blocks 0.2 relative and 0.99 cosine (measured:
+    the encoder 2.7e-3, the decoder blocks 0.04-0.12 with cosines above
+    0.993).  The measured values are printed (pytest -s)."""
     from tests.gpu_util import rel
     lam = 1e-3
     p, c64, Q = _setup(pkg, "fp64")
@@ -120,9 +122,9 @@ def test_full_size_bf16_gradient_against_fp64(pkg):
     for sz, rl, cs in blocks:
         print(f"  block of {sz}: rel {rl:.3e}, cos {cs:.6f}")
     assert lc == pytest.approx(lc0, rel=1e-3)
-    assert lls == pytest.approx(lls0, rel=0.25)
+    assert lls == pytest.approx(lls0, rel=0.2)
     for sz, rl, cs in blocks:
-        assert rl < 0.3 and cs > 0.99, (sz, rl, cs)
+        assert rl < 0.2 and cs > 0.99, (sz, rl, cs)
     l0 = c16.train_eval(Q, lam, want_grad=False)[0][2]
     for _ in range(20):
         c16.train_step(Q, lam, 1e-4)
