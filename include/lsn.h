@@ -207,6 +207,15 @@ int lsn_set_optimizer(lsn_ctx* ctx, int kind, int history);
  * (max hidden width) x (1 + r + r (r + 1) / 2) buffers. */
 int lsn_set_exact_hessian(lsn_ctx* ctx, int enable, double clamp);
 
+/* Failure detection without a GPU fault: every mbarrier wait of the tensor-
+ * core kernels gives up after a wall-clock limit (2 s), records an error code
+ * in a device flag and lets its CTA stop issuing work; the solve then returns
+ * LSN_ERR_CUDA.  This call runs that wait once on an mbarrier that nothing
+ * arrives on (no bulk copy or MMA is in flight), with a limit of `seconds`
+ * (0 < seconds <= 10, else LSN_ERR_ARG), and writes the recorded code (1) to
+ * *code (host).  The context stays usable. */
+int lsn_selftest_bounded_wait(lsn_ctx* ctx, double seconds, int* code);
+
 /* Execution of a solve: mode 0 (default) launches the whole Newton loop as
  * one CUDA graph whose conditional WHILE node repeats an evaluation pass
  * until the device-side solver stops it; mode 1 drives the same kernels from

@@ -53,6 +53,7 @@ _SIGS = {
                        ctypes.c_double],
     "lsn_set_optimizer": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
     "lsn_set_exact_hessian": [ctypes.c_void_p, ctypes.c_int, ctypes.c_double],
+    "lsn_selftest_bounded_wait": [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p],
     "lsn_set_affine_modes": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "lsn_tet_forces": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "lsn_select_cubature": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -306,6 +307,14 @@ class Context:
     def set_optimizer(self, kind="newton", history=10):
         """kind: "newton" (projective Newton) or "lbfgs"; history: L-BFGS pairs."""
         return self._check(self.lib.lsn_set_optimizer(self.h, OPTIMIZERS[kind], history))
+
+    def selftest_bounded_wait(self, seconds=0.05):
+        """Run one bounded mbarrier wait that nothing completes; returns the
+        error code the wait recorded (1 when it ran out)."""
+        code = ctypes.c_int(0)
+        self._check(self.lib.lsn_selftest_bounded_wait(self.h, float(seconds),
+                                                       ctypes.byref(code)))
+        return code.value
 
     def set_exact_hessian(self, enable=True, clamp=1e-10):
         """Projective Newton with the exact-form reduced Hessian (the decoder's

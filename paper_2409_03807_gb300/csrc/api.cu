@@ -1033,6 +1033,14 @@ int lsn_set_exact_hessian(lsn_ctx* c, int enable, double clamp) {
   return LSN_OK;
 }
 
+int lsn_selftest_bounded_wait(lsn_ctx* c, double seconds, int* code) {
+  if (!c || !code || !(seconds > 0.0 && seconds <= 10.0)) return LSN_ERR_ARG;
+  LSN_GUARD_BEGIN
+  ck(bounded_wait_selftest(seconds, code, c->stream));
+  return LSN_OK;
+  LSN_GUARD_END
+}
+
 int lsn_set_execution(lsn_ctx* c, int mode) {
   if (!c || mode < 0 || mode > 1) return LSN_ERR_ARG;
   c->use_graph = mode == 0;

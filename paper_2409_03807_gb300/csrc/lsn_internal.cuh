@@ -321,4 +321,8 @@ struct Curvature {
   ~Curvature() { release(); }
 };
 
+// tc_decoder.cu: one bounded mbarrier wait that runs out (nothing arrives):
+// *code (host) receives the error flag the wait records (1)
+cudaError_t bounded_wait_selftest(double seconds, int* code, cudaStream_t s);
+
 }  // namespace lsn

@@ -56,16 +56,29 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 // bounded wait; on time-out records `code` and returns false
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* err, int code) {
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* err, int code,
+                                         unsigned long long limit_ns = WAIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (gtimer() - t0 > WAIT_NS) {
+    if (gtimer() - t0 > limit_ns) {
       atomicOr(err, code);
       return false;
     }
   }
+}
+
+// The time-out path of wait_bar on an mbarrier that nothing arrives on (no
+// bulk copy or MMA is issued, so nothing is left in flight when it returns).
+__global__ void wait_selftest_kernel(unsigned long long limit_ns, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) wait_bar(&bar, 0, err, 1, limit_ns);
 }
 
 __device__ __forceinline__ void epi_sync() {  // the 8 epilogue warps
@@ -615,6 +628,25 @@ __global__ void __launch_bounds__(TNT, 1)
     tmem_dealloc(tbase, TMEM_COLS);
   }
 }
+
+}  // namespace
+
+cudaError_t bounded_wait_selftest(double seconds, int* code, cudaStream_t s) {
+  int* err = nullptr;
+  cudaError_t e = cudaMalloc(&err, sizeof(int));
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>((unsigned long long)(seconds * 1e9), err);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(code, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(err);
+  return e;
+}
+
+namespace {
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;

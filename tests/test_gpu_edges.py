@@ -151,3 +151,34 @@ def test_argument_errors_of_the_optimiser_cubature_and_training_calls(pkg):
         ctx.train_eval_unsup(Z, 0.1, 0.0)           # sigma must be positive
     assert e.value.code == -1
     ctx.close()
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(pkg):
+    """Failure detection without a GPU fault: one mbarrier wait of the
+    tensor-core kernels' kind on a barrier that nothing completes (no bulk
+    copy or MMA in flight) gives up after its limit (50 ms here) and records
+    its error code; the same context then evaluates as before (BF16 form,
+    against the FP64 oracle of its rounded weights)."""
+    import dataclasses
+    import time
+    from oracle.reduced import model_from_problem
+    from workloads import build_problem
+    from tests.gpu_util import round_bf16
+    p = build_problem("tiny_quasistatic")
+    ctx = pkg.context_from_problem(p, precision="bf16")
+    z = np.random.default_rng(3).standard_normal(p.config.r) * 0.4
+    E0, g0, K0 = ctx.eval(z)
+    t0 = time.perf_counter()
+    code = ctx.selftest_bounded_wait(0.05)
+    dt = time.perf_counter() - t0
+    assert code == 1
+    assert 0.05 <= dt < 5.0
+    with pytest.raises(Exception):
+        ctx.selftest_bounded_wait(0.0)   # argument check, nothing launched
+    E1, g1, K1 = ctx.eval(z)
+    assert E1 == E0 and np.array_equal(g1, g0) and np.array_equal(K1, K0)
+    m = model_from_problem(dataclasses.replace(p, Ws=[*p.Ws[:-1], round_bf16(p.Ws[-1])]))
+    m.set_targets(p.targets(0))
+    _, g_ref, _ = m.eval(z)
+    assert_close(g1, g_ref, 2e-4)
+    ctx.close()
