@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--train-precision", default="tf32",
                     choices=["fp64", "fp32", "tf32", "bf16"],
                     help="trainer form in --learned")
+    ap.add_argument("--train-seed", type=int, default=3,
+                    help="seed of the training batches and the evaluation batch in --learned")
     ap.add_argument("--learned-optimizers", default="newton,lbfgs",
                     help="optimisers of the reduced solves in --learned")
     ap.add_argument("--exact-hessian", action="store_true",
@@ -898,7 +900,7 @@ def run_learned(args, world, rank, local):
     cub, cw = p.cub_idx, p.cub_w
     tprec = args.train_precision
     Qd = torch.tensor(Qf, dtype=torch.float64, device="cuda")
-    rs = np.random.default_rng(3)
+    rs = np.random.default_rng(args.train_seed)
     B = min(64, K)
     evi = np.sort(rs.choice(K, B, replace=False))
     ev = torch.tensor(evi, device="cuda")
@@ -982,7 +984,8 @@ def run_learned(args, world, rank, local):
                        "decoder": "-".join(map(str, p.widths)), "precision": args.precision,
                        "optimizers": args.learned_optimizers, "stage1_steps": args.train_steps,
                        "stage2_steps": args.finetune_steps, "batch": B, "lr": 1e-3,
-                       "trainer": tprec, "snapshots": snap, "cubature": len(cub),
+                       "trainer": tprec, "train_seed": args.train_seed, "snapshots": snap,
+                       "cubature": len(cub),
                        "solves": "quasi-static, one per held-out load" if static
                        else f"implicit Euler, frames 1..{K}",
                        "start": "code of the rest shape (the trained encoder's bias)"},
