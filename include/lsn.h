@@ -175,7 +175,8 @@ int lsn_set_solver(lsn_ctx* ctx, double tol_inf, int max_newton, int max_ls,
  * search, the tolerance and the caps of lsn_set_solver (max_newton caps the
  * iterations of either).
  *   LSN_OPT_NEWTON (default): projective Newton, d = -K^-1 g with the
- *     Gauss-Newton reduced Hessian K (FP64 Cholesky).
+ *     Gauss-Newton reduced Hessian K (FP64 Cholesky, in its square-root-free
+ *     L D L^T form).
  *   LSN_OPT_LBFGS: L-BFGS, d = -H g by the two-loop recursion over the
  *     `history` (1..32) most recent curvature pairs s = alpha d,
  *     y = g(z + s) - g(z), initial matrix (s^T y / y^T y) I of the newest

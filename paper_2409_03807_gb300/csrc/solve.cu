@@ -1,8 +1,9 @@
 // Reduced-system kernels of the projective Newton solve (Supplement, "Tests
 // with Projective Newton's method"; exits of Sec. 5): fixed-order reduction
 // of the per-CTA partials, the Armijo test of the backtracking line search
-// (FP64 comparison), the FP64 r x r Cholesky with diagonal-shift retries and
-// the Newton direction.
+// (FP64 comparison), the FP64 r x r factorisation (L D L^T: the Cholesky
+// pivots without square roots) with diagonal-shift retries and the Newton
+// direction.
 //
 // Evaluation passes.  Every pass evaluates x, J, E, g, K at one point y0 and
 // the energies at KTRIAL more points.  While a line search is open the pass
@@ -113,34 +114,33 @@ __device__ __forceinline__ double warp_max(double v) {
 // decision logic of lane 0 does not wait on global-memory round trips.
 constexpr int SV_SCALAR_WORDS = (int)(offsetof(DevSolver, z) / sizeof(double));
 
-constexpr int SEL_THREADS = 128;  // warp 0: solver state logic; all four warps: Cholesky
+constexpr int SEL_THREADS = 128;  // warp 0: solver state logic; all four warps: L D L^T
 
-// FP64 square root and its reciprocal: an FP32 reciprocal-square-root
-// estimate refined by two Newton steps y <- y (3 - s y^2) / 2, which converge
-// quadratically (about 2^-22 -> 2^-44 -> FP64 rounding).  Few FP64
-// instructions on the serial path of the factorisation (GB300 issues a
-// warp-wide FP64 instruction in about 64 cycles per sub-partition).
-__device__ __forceinline__ void sqrt_and_inverse(double s, double& root, double& inv) {
-  if (s > 1e-30 && s < 1e30) {
-    double yv = (double)rsqrtf((float)s);
-    yv = yv * (1.5 - 0.5 * s * yv * yv);
-    yv = yv * (1.5 - 0.5 * s * yv * yv);
-    inv = yv;
-    root = s * yv;
-  } else {
-    root = sqrt(s);
-    inv = 1.0 / root;
-  }
+// FP64 reciprocal: an FP32 reciprocal estimate refined by two Newton steps
+// y <- y (2 - d y) (quadratic convergence: about 2^-23 -> 2^-46 -> FP64
+// rounding), a short chain of FP64 instructions on the factorisation's serial
+// path (GB300 issues a warp-wide FP64 instruction in about 64 cycles per
+// sub-partition).
+__device__ __forceinline__ double reciprocal(double d) {
+  if (!(fabs(d) > 1e-30 && fabs(d) < 1e30)) return 1.0 / d;
+  double y = (double)__frcp_rn((float)d);
+  y = y * fma(-d, y, 2.0);
+  y = y * fma(-d, y, 2.0);
+  return y;
 }
 
-// Right-looking Cholesky L L^T of the symmetric matrix held in L (lower
-// triangle used), all SEL_THREADS threads.  Per column j: warp 0 takes the
-// pivot (one square root and one reciprocal, lane 0) and scales the column
-// below it; after one block barrier every warp updates its rows of the
-// trailing lower triangle (row i by warp i mod 4, its columns by the lanes),
-// then a second barrier.  Returns false (uniformly) when a pivot is not
-// positive.
-__device__ bool block_cholesky(double (*L)[RMAX + 1], double* invd, int r, int* s_fail) {
+// Right-looking L D L^T factorisation (unit lower L, positive diagonal D) of
+// the symmetric matrix held in L (lower triangle used), all SEL_THREADS
+// threads; the same pivots as Cholesky without its square roots.  Per column
+// j: warp 0 takes the pivot d_j (lane 0: one reciprocal), keeps the column's
+// unscaled entries in u and scales the column by 1 / d_j; after one block
+// barrier every warp updates its rows of the trailing lower triangle
+// (a_ik -= l_ij a_kj; row i by warp i mod 4, its columns by the lanes), then
+// a second barrier.  On return L holds l_ij below the diagonal, d_j on it,
+// and invd[j] = 1 / d_j.  Returns false (uniformly) when a pivot is not
+// positive (the matrix is not positive definite).
+__device__ bool block_ldlt(double (*L)[RMAX + 1], double* invd, double* u, int r,
+                           int* s_fail) {
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   constexpr int NW = SEL_THREADS / 32;
   for (int j = 0; j < r; ++j) {
@@ -148,13 +148,11 @@ __device__ bool block_cholesky(double (*L)[RMAX + 1], double* invd, int r, int* 
       double inv = 0.0;
       int bad = 0;
       if (lane == 0) {
-        const double sjj = L[j][j];
-        if (!(sjj > 0.0)) {
+        const double djj = L[j][j];
+        if (!(djj > 0.0)) {
           bad = 1;
         } else {
-          double root;
-          sqrt_and_inverse(sjj, root, inv);
-          L[j][j] = root;
+          inv = reciprocal(djj);
           invd[j] = inv;
         }
         *s_fail = bad;
@@ -162,13 +160,17 @@ __device__ bool block_cholesky(double (*L)[RMAX + 1], double* invd, int r, int* 
       bad = __shfl_sync(0xffffffffu, bad, 0);
       inv = __shfl_sync(0xffffffffu, inv, 0);
       if (!bad)
-        for (int i = j + 1 + lane; i < r; i += 32) L[i][j] *= inv;
+        for (int i = j + 1 + lane; i < r; i += 32) {
+          const double a = L[i][j];
+          u[i] = a;
+          L[i][j] = a * inv;
+        }
     }
     __syncthreads();
     if (*s_fail) return false;
     for (int i = j + 1 + warp; i < r; i += NW) {
       const double lij = L[i][j];
-      for (int k = j + 1 + lane; k <= i; k += 32) L[i][k] -= lij * L[k][j];
+      for (int k = j + 1 + lane; k <= i; k += 32) L[i][k] -= lij * u[k];
     }
     __syncthreads();
   }
@@ -280,7 +282,7 @@ __device__ int gradient_exits(DevSolver* sv, DevSolver* gsv, const double* sE, c
   return -1;
 }
 
-// Warp-0 state logic around a block-wide FP64 Cholesky (SEL_THREADS threads,
+// Warp-0 state logic around a block-wide FP64 L D L^T (SEL_THREADS threads,
 // one CTA): the line-search decision on the trial energies of the pass, the
 // exit tests, and (when a new direction is due) d = -K^-1 g with diagonal
 // shifts on failure, then the points of the next pass.
@@ -290,7 +292,8 @@ __global__ void __launch_bounds__(SEL_THREADS) select_direction_kernel(
     int use_cond) {
   __shared__ double L[RMAX][RMAX + 1];
   __shared__ double y[RMAX];
-  __shared__ double invd[RMAX];  // reciprocals of the Cholesky diagonal
+  __shared__ double invd[RMAX];  // reciprocals of the L D L^T diagonal
+  __shared__ double ucol[RMAX];  // unscaled column of the factorisation step
   __shared__ double ssys[4 * RMAX + 2 * KTRIAL + 2];
   __shared__ __align__(16) DevSolver svs;
   __shared__ int s_need, s_fail;
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_direction_kernel(
   }
   __syncthreads();
   if (s_need) {
-    // Cholesky K + shift I = L L^T, shift = 0, then 1e-12 max(1, max|K_ii|) x 10^k
+    // K + shift I = L D L^T, shift = 0, then 1e-12 max(1, max|K_ii|) x 10^k
     double shift = 0.0;
     bool ok = false;
     for (int attempt = 0; attempt < 21 && !ok; ++attempt) {
@@ -381,7 +384,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_direction_kernel(
         }
         __syncthreads();
       }
-      ok = block_cholesky(L, invd, r, &s_fail);
+      ok = block_ldlt(L, invd, ucol, r, &s_fail);
       if (!ok) shift = shift == 0.0 ? s_base : shift * 10.0;
       __syncthreads();
     }
@@ -394,18 +397,17 @@ __global__ void __launch_bounds__(SEL_THREADS) select_direction_kernel(
         }
         cond_val = 0;
       } else {
-        // forward L y = -g, backward L^T d = y (column sweeps within warp 0)
+        // forward L y = -g (unit lower), y <- D^-1 y, backward L^T d = y (unit
+        // upper): column sweeps within warp 0
         for (int i = 0; i < r; ++i) {
-          const double yi = y[i] * invd[i];
-          __syncwarp();
-          if (t == 0) y[i] = yi;
+          const double yi = y[i];
           for (int k = i + 1 + t; k < r; k += 32) y[k] -= L[k][i] * yi;
           __syncwarp();
         }
+        for (int i = t; i < r; i += 32) y[i] *= invd[i];
+        __syncwarp();
         for (int i = r - 1; i >= 0; --i) {
-          const double yi = y[i] * invd[i];
-          __syncwarp();
-          if (t == 0) y[i] = yi;
+          const double yi = y[i];
           for (int k = t; k < i; k += 32) y[k] -= L[i][k] * yi;
           __syncwarp();
         }
