@@ -47,3 +47,25 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.aggregate_time(123.0, 1) == 123.0
     assert bench.job_value(1, 50, 1000.0) == pytest.approx(50.0)
+
+
+def test_bench_lipschitz_estimate_is_eq7():
+    """bench.py's Eq. 7 estimate (measurement code of the learned-subspace
+    comparison) against the oracle's pair loop, and against the closed form of
+    an affine Hessian field Ht(z) = z_0 A (the estimate is ||A||_F)."""
+    import numpy as np
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle.training import lipschitz_estimate
+    rng = np.random.default_rng(5)
+    Z = rng.standard_normal((12, 4))
+    H = rng.standard_normal((12, 4, 4))
+    H = H + np.swapaxes(H, 1, 2)
+    ref = lipschitz_estimate(torch.tensor(H), torch.tensor(Z))
+    assert bench.lipschitz_estimate(H, Z) == pytest.approx(ref, rel=1e-12)
+    A = rng.standard_normal((4, 4))
+    Z1 = np.zeros((6, 4))
+    Z1[:, 0] = rng.standard_normal(6)
+    H1 = Z1[:, 0, None, None] * A[None]
+    assert bench.lipschitz_estimate(H1, Z1) == pytest.approx(np.linalg.norm(A), rel=1e-12)
