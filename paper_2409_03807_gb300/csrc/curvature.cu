@@ -22,9 +22,9 @@
 //      T = e1 (W T), U_cd = e2 (W T)_c (W T)_d + e1 (W U)_cd
 //      (e1, e2 the ELU derivatives at a = W h + b); Y_0 = [z | I | 0]
 //   5. contract_kernel  C_cd = sum_j v_j U_j,cd, added to K in the system row
-//   6. project_kernel   one CTA, FP64: a Cholesky attempt first (a positive
-//      definite K is left as it is: the projection would move it by at most
-//      f = clamp * max |lambda|); otherwise cyclic Jacobi (parallel round-robin
+//   6. project_kernel   one CTA, FP64: an L D L^T attempt on K - clamp ||K||_F I
+//      first (when it succeeds every eigenvalue is above f = clamp max |lambda|
+//      and K is left as it is); otherwise cyclic Jacobi (parallel round-robin
 //      pairs) on the r x r K, then K += sum_{lambda_i < f} (f - lambda_i) q_i q_i^T
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -98,20 +98,32 @@ __global__ void wtv_kernel(const WT* __restrict__ W, const Real* __restrict__ G,
                            double* __restrict__ part) {
   const int m0 = blockIdx.x * WTV_ROWS, m1 = min(n, m0 + WTV_ROWS);
   for (int j = threadIdx.x; j < H; j += WTV_THREADS) {
-    Real acc = Real(0);
-    for (int m = m0; m < m1; ++m) acc += (Real)wval(W[(size_t)m * H + j]) * G[m];
-    part[(size_t)blockIdx.x * H + j] = (double)acc;
+    // four interleaved partial sums (independent FMA chains), added in order
+    Real a0 = Real(0), a1 = Real(0), a2 = Real(0), a3 = Real(0);
+    int m = m0;
+    for (; m + 4 <= m1; m += 4) {
+      a0 += (Real)wval(W[(size_t)m * H + j]) * G[m];
+      a1 += (Real)wval(W[(size_t)(m + 1) * H + j]) * G[m + 1];
+      a2 += (Real)wval(W[(size_t)(m + 2) * H + j]) * G[m + 2];
+      a3 += (Real)wval(W[(size_t)(m + 3) * H + j]) * G[m + 3];
+    }
+    for (; m < m1; ++m) a0 += (Real)wval(W[(size_t)m * H + j]) * G[m];
+    part[(size_t)blockIdx.x * H + j] = (double)((a0 + a1) + (a2 + a3));
   }
 }
 
+// v[j] = s sum_b part[b][j]: one warp per j, lanes over the chunks, then a
+// fixed shuffle tree (the order does not depend on scheduling)
 template <typename Real>
 __global__ void wtv_reduce_kernel(const double* __restrict__ part, int nb, int H, double s,
                                   Real* __restrict__ v) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (j >= H) return;
   double acc = 0.0;
-  for (int b = 0; b < nb; ++b) acc += part[(size_t)b * H + j];
-  v[j] = (Real)(s * acc);
+  for (int b = lane; b < nb; b += 32) acc += part[(size_t)b * H + j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) v[j] = (Real)(s * acc);
 }
 
 // pair index p (c <= d, row-major upper triangle of an rn x rn matrix) -> (c, d)
@@ -181,18 +193,38 @@ __global__ void act2_kernel(const Real* __restrict__ A, const Real* __restrict__
   Y[e] = v;
 }
 
-// sys K slots (c <= d < rn, in the r x r upper triangle) += sum_j v_j U_j,cd
+constexpr int CON_WARPS = 8;
+
+// sys K slots (c <= d < rn, in the r x r upper triangle) += sum_j v_j U_j,cd:
+// a CTA takes 32 pairs (one per lane); its warps split j into CON_WARPS
+// ranges (element precision within a range), summed in FP64 in warp order
 template <typename Real>
 __global__ void contract_kernel(const Real* __restrict__ Y, const Real* __restrict__ v, int H,
                                 int rn, int NY, int r, double* __restrict__ sys) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double red[CON_WARPS][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + lane;
   const int P = rn * (rn + 1) / 2;
-  if (p >= P) return;
-  double acc = 0.0;
-  for (int j = 0; j < H; ++j) acc += (double)v[j] * (double)Y[(size_t)j * NY + 1 + rn + p];
-  int c, d;
-  pair_of(p, rn, c, d);
-  sys[slot_K(r) + c * r - (c * (c - 1)) / 2 + (d - c)] += acc;
+  const int j0 = (H * w) / CON_WARPS, j1 = (H * (w + 1)) / CON_WARPS;
+  Real a0 = Real(0), a1 = Real(0);
+  if (p < P) {
+    const Real* y = Y + 1 + rn + p;
+    int j = j0;
+    for (; j + 2 <= j1; j += 2) {
+      a0 += v[j] * y[(size_t)j * NY];
+      a1 += v[j + 1] * y[(size_t)(j + 1) * NY];
+    }
+    for (; j < j1; ++j) a0 += v[j] * y[(size_t)j * NY];
+  }
+  red[w][lane] = (double)a0 + (double)a1;
+  __syncthreads();
+  if (w == 0 && p < P) {
+    double acc = 0.0;
+    for (int k = 0; k < CON_WARPS; ++k) acc += red[k][lane];
+    int c, d;
+    pair_of(p, rn, c, d);
+    sys[slot_K(r) + c * r - (c * (c - 1)) / 2 + (d - c)] += acc;
+  }
 }
 
 constexpr int PROJ_THREADS = 256;
@@ -240,7 +272,7 @@ __global__ void __launch_bounds__(PROJ_THREADS) project_kernel(double* __restric
     __syncthreads();
     return s;  // valid in thread 0
   };
-  // Cholesky attempt of K - f' I with f' = clamp ||K||_F >= f (on a copy in
+  // L D L^T attempt on K - f' I with f' = clamp ||K||_F >= f (on a copy in
   // V): when it succeeds every eigenvalue is above f and the projection is
   // the identity, so K stays as it is
   {
@@ -261,21 +293,28 @@ __global__ void __launch_bounds__(PROJ_THREADS) project_kernel(double* __restric
     __syncthreads();
     for (int j = t; j < r; j += PROJ_THREADS) V[j * ld + j] -= s_fp;
     __syncthreads();
+    // L D L^T pivots (positive definite iff every pivot is positive); the
+    // unscaled column j is kept in cs (free until the Jacobi rounds)
+    __shared__ double s_inv;
     for (int j = 0; j < r; ++j) {
       if (t == 0) {
         const double pv = V[j * ld + j];
         if (!(pv > 0.0)) s_bad = 1;
-        else V[j * ld + j] = sqrt(pv);
+        else s_inv = 1.0 / pv;
       }
       __syncthreads();
       if (s_bad) break;
-      const double inv = 1.0 / V[j * ld + j];
-      for (int i = j + 1 + t; i < r; i += PROJ_THREADS) V[i * ld + j] *= inv;
+      const double inv = s_inv;
+      for (int i = j + 1 + t; i < r; i += PROJ_THREADS) {
+        const double a = V[i * ld + j];
+        cs[i] = a;
+        V[i * ld + j] = a * inv;
+      }
       __syncthreads();
       const int rem = r - j - 1;
       for (int e = t; e < rem * rem; e += PROJ_THREADS) {
         const int i = j + 1 + e / rem, k = j + 1 + e % rem;
-        if (k <= i) V[i * ld + k] -= V[i * ld + j] * V[k * ld + j];
+        if (k <= i) V[i * ld + k] -= V[i * ld + j] * cs[k];
       }
       __syncthreads();
     }
@@ -473,7 +512,7 @@ cudaError_t Curvature<Real>::launch(const ElemArgs& ea, const LastArgs& la, cons
         static_cast<const __nv_bfloat16*>(wl_bf16), G, v.n, Hl, part);
   else
     wtv_kernel<Real, Real><<<nb, WTV_THREADS, 0, s>>>(dW[L - 1], G, v.n, Hl, part);
-  wtv_reduce_kernel<Real><<<(Hl + 127) / 128, 128, 0, s>>>(part, nb, Hl, la.scale, vv);
+  wtv_reduce_kernel<Real><<<(Hl + 3) / 4, 128, 0, s>>>(part, nb, Hl, la.scale, vv);
   y0_kernel<Real><<<(rn * NY + 255) / 256, 256, 0, s>>>(Z0, zcps, rn, NY, Y[0]);
   int cur = 0;
   for (int l = 0; l < L - 1; ++l) {
@@ -491,7 +530,8 @@ cudaError_t Curvature<Real>::launch(const ElemArgs& ea, const LastArgs& la, cons
     act2_kernel<Real><<<(M * NY + 255) / 256, 256, 0, s>>>(A, db[l], M, rn, NY, Y[cur ^ 1]);
     cur ^= 1;
   }
-  contract_kernel<Real><<<(NY + 127) / 128, 128, 0, s>>>(Y[cur], vv, Hl, rn, NY, v.r, sys);
+  contract_kernel<Real><<<(rn * (rn + 1) / 2 + 31) / 32, 32 * CON_WARPS, 0, s>>>(
+      Y[cur], vv, Hl, rn, NY, v.r, sys);
   project_kernel<<<1, PROJ_THREADS, proj_smem, s>>>(sys, v.r, clamp);
   return cudaGetLastError();
 }
