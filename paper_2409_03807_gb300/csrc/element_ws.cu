@@ -7,15 +7,15 @@
 // of J into g and K; the line-search trial energies), with the three kinds of
 // work running concurrently on different warps of a persistent CTA:
 //
-//   warps 0-6  (element math)  one tet per thread: energy, P, the signed SVD
+//   warps 0-4  (element math)  one tet per thread: energy, P, the signed SVD
 //              and the clamped eigensystem of d2Psi/dF2, and the KTRIAL
 //              trial energies; each tet's result is a 60-word record in
-//              shared memory (double-buffered units of 224 tets); the
-//              per-tet dependency chain (two 3x3 Jacobi decompositions) is
-//              long, so seven warps keep the column build supplied;
-//   warps 7-14 (column build)  for a tet and four adjacent subspace columns
+//              shared memory (double-buffered units of 160 tets); five
+//              warps of this long per-tet dependency chain (two 3x3 Jacobi
+//              decompositions) keep ten column-build warps supplied;
+//   warps 5-14 (column build)  for a tet and four adjacent subspace columns
 //              (one float4 per J row, staged in shared memory by
-//              asynchronous copies one tet ahead): dJ_a = J_a - J_0 (a = 1..3),
+//              asynchronous copies one tet ahead, bypassing L1): dJ_a = J_a - J_0 (a = 1..3),
 //              w_a = U^T dJ_a, R = sum_a w_a y_a^T (= U^T G V with
 //              y_a = V^T Dm^-1 row a), the nine eigen-coordinates C_e (scaled
 //              by sqrt(w V lambda+)) and the gradient term sum_a ge_a . dJ_a;
@@ -44,8 +44,8 @@ namespace tcws {
 
 using namespace tc;
 
-constexpr int NPW = 7;                    // element-math warps
-constexpr int NBW = 8;                    // column-build warps
+constexpr int NPW = 5;                    // element-math warps
+constexpr int NBW = 10;                   // column-build warps
 constexpr int MMAW = NPW + NBW;           // the MMA-issuing warp
 constexpr int NT = 32 * (NPW + NBW + 1);  // 512 threads
 constexpr int UNIT = 32 * NPW;            // tets per record unit
@@ -272,7 +272,7 @@ __device__ __forceinline__ void stage_rows(float4* stg, const float* __restrict_
     for (int i = 0; i < 3; ++i) {
       const uint32_t dst = smem_u32(stg + (3 * a + i) * NBT);
       const float* src = J + (size_t)(3 * v[a] + i) * r + c0;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
     }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }

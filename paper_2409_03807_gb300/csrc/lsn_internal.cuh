@@ -167,7 +167,7 @@ void element_grids(int S, int r, int num_sms, int& gfull, int& genergy);
 int element_tc_grid(int S, int r, bool bf16, int num_sms);
 // Warp-specialised tensor-core element kernel (element_ws.cu) for large tet
 // sets: used by launch_element_tc when element_ws_applies (the BF16 form, r a
-// multiple of 4 and at most 64, at least 224 tets per SM); same partial-row
+// multiple of 4 and at most 64, at least 160 tets per SM); same partial-row
 // output.
 bool element_ws_applies(int S, int r, bool bf16, int num_sms);
 int element_ws_grid(int S, int num_sms);
