@@ -6,7 +6,9 @@ tensor-core kernel and is checked alongside.
 Cases on the 30x17x17 bar (44,544 tets): every tet at r = 64 (ragged: 278.4
 units of 160 tets), a ragged cubature set of 40,003 tets with non-uniform weights at
 r = 32, and r = 44 (eleven column quads, so the column-build slots do not
-divide a chunk evenly).  E, g, K at random z are compared norm-wise and
+divide a chunk evenly), plus the cubature set in random order at r = 64 and
+r = 32 (neighbouring tets of a chunk then share no vertices, so the staged J
+rows are scattered gathers).  E, g, K at random z are compared norm-wise and
 element-wise (tolerances of the tensor-core forms: the BF16 form against the
 oracle of its BF16-rounded output weights, the TF32 form against the FP32
 weights), and two implicit-Euler frames of the r = 64 case are solved in the
@@ -42,7 +44,7 @@ def pkg():
     return pkg
 
 
-def bar(r, cubature):
+def bar(r, cubature, shuffle=False):
     c = dataclasses.replace(CONFIGS["block_twist_207k"], name=f"ws_bar_r{r}", dims=(30, 17, 17),
                             r=r, hidden=(128, 128), cubature=0, motion_frames=20)
     p = build_problem(c)
@@ -50,6 +52,9 @@ def bar(r, cubature):
         rng = np.random.default_rng(77)
         idx = np.sort(rng.choice(p.ne, cubature, replace=False)).astype(np.int32)
         w = rng.uniform(0.5, 4.0, cubature)
+        if shuffle:  # the same tets and weights in random order
+            perm = np.random.default_rng(78).permutation(cubature)
+            idx, w = idx[perm], w[perm]
         p = dataclasses.replace(p, cub_idx=idx, cub_w=w)
     return p
 
@@ -67,11 +72,17 @@ def make_ctx(pkg, p, prec):
     return ctx
 
 
-@pytest.mark.parametrize("r,cubature", [(64, 0), (32, 40003), (44, 0)])
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
-def test_ws_element_system_matches_oracle(pkg, r, cubature, prec):
+CASES = [(r, cub, False, prec) for r, cub in [(64, 0), (32, 40003), (44, 0)]
+         for prec in ("bf16", "tf32")]
+# the cubature set in random order: the tets of a chunk are scattered over the
+# mesh, so their J rows share nothing
+CASES += [(64, 40003, True, "bf16"), (32, 40003, True, "bf16")]
+
+
+@pytest.mark.parametrize("r,cubature,shuffle,prec", CASES)
+def test_ws_element_system_matches_oracle(pkg, r, cubature, shuffle, prec):
     import torch
-    p = bar(r, cubature)
+    p = bar(r, cubature, shuffle)
     S = len(p.cub_idx) if len(p.cub_idx) else p.ne
     assert S >= 160 * torch.cuda.get_device_properties(0).multi_processor_count
     m = oracle_for(p, prec)
