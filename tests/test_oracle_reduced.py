@@ -105,6 +105,69 @@ def test_linear_decoder_matches_independent_linear_subspace_newton():
     assert np.allclose(z_red, z, rtol=1e-8, atol=1e-10)
 
 
+def test_linear_decoder_minimiser_matches_torch_transcription():
+    """x = X0 + U z: the reduced solve's end point minimises an independent
+    torch transcription of the Eq. 2 objective at dt = 0 (stable neo-Hookean
+    density of the deformation gradient times rest volume, minus the work of
+    gravity on lumped masses), minimised here by autodiff Newton.  Shares no
+    code with the oracle's fem module, which the test above relies on."""
+    import torch
+    mesh = make_bar(6, 3, 3, 0.05)
+    n = 3 * mesh.nv
+    rng = np.random.default_rng(4)
+    U = 1e-2 * rng.standard_normal((n, 5))
+    cn = face_nodes(mesh, 0)
+    m = ReducedModel(mesh.X0, mesh.tets, Decoder([U], [np.zeros(n)], 1.0),
+                     1e5, 0.45, 1000.0, G, None, None, cn)
+    z_red, st = newton_solve(m, np.zeros(5), 1e-10)
+    assert st.status == CONVERGED
+
+    youngs, nu, rho = 1e5, 0.45, 1000.0
+    mu = youngs / (2.0 * (1.0 + nu))
+    lam = youngs * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    alpha = 1.0 + 0.75 * mu / lam
+    X = torch.tensor(mesh.X0, dtype=torch.float64)
+    T = torch.tensor(np.asarray(mesh.tets), dtype=torch.long)
+
+    def edge_matrix(P):  # columns P_a - P_0, a = 1..3, per tet
+        return torch.stack([P[T[:, a]] - P[T[:, 0]] for a in (1, 2, 3)], dim=2)
+
+    Dm = edge_matrix(X)
+    vol = torch.abs(torch.linalg.det(Dm)) / 6.0
+    Dm_inv = torch.linalg.inv(Dm)
+    mass = torch.zeros(mesh.nv, dtype=torch.float64)
+    for a in range(4):  # a quarter of each tet's mass on each of its vertices
+        mass.index_add_(0, T[:, a], rho * vol / 4.0)
+    keep = torch.ones(n, dtype=torch.float64)
+    keep[torch.tensor((3 * cn[:, None] + np.arange(3)).ravel())] = 0.0  # clamped face
+    Ut = torch.tensor(U) * keep[:, None]
+    grav = torch.tensor(G, dtype=torch.float64)
+
+    def energy(z):
+        x = X + (Ut @ z).reshape(-1, 3)
+        F = edge_matrix(x) @ Dm_inv
+        Ic = (F * F).sum(dim=(1, 2))
+        psi = (0.5 * mu * (Ic - 3.0) + 0.5 * lam * (torch.linalg.det(F) - alpha) ** 2
+               - 0.5 * mu * torch.log(Ic + 1.0))
+        return (vol * psi).sum() - (mass[:, None] * grav[None, :] * x).sum()
+
+    z = torch.zeros(5, dtype=torch.float64)
+    for _ in range(60):
+        gz = torch.autograd.functional.jacobian(energy, z)
+        if gz.abs().max() < 1e-10:
+            break
+        H = torch.autograd.functional.hessian(energy, z)
+        w, V = torch.linalg.eigh(H)
+        w = torch.clamp(w, min=1e-8 * w.abs().max())
+        d = -(V @ ((V.T @ gz) / w))
+        step, e0 = 1.0, energy(z)
+        while energy(z + step * d) > e0 + 1e-4 * step * (gz @ d):
+            step *= 0.5
+        z = z + step * d
+    assert gz.abs().max() < 1e-10
+    assert np.allclose(z_red, z.numpy(), rtol=1e-8, atol=1e-10), (z_red, z.numpy())
+
+
 def test_linear_decoder_with_quadratic_energy_converges_in_one_step():
     """Only the inertia term (all cubature weights zero): E is quadratic in z,
     Newton lands on the weighted least-squares solution in one step."""
